@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark of the encrypted logistic-regression worker step on GB300.
+
+Workload (one step): the encrypted gradient step of Eq. 7-8 with the Table 2
+binomial polynomial, over 4096 synthetic samples x 784 features (~80% zeros,
+values in (0,1], planted-model labels), packed 8 samples per ciphertext at
+N = 2^14 with eight ~40-bit limbs, one 60-bit special prime and scale 2^40:
+512 data ciphertexts, 2048 mul+relin+rescale and 5126 rotations per step.
+
+Our arm times K steps on the device with CUDA events on the context's stream
+(inputs resident in HBM, 1 GB of ciphertexts per step, well above L2); the
+e2e figure moves the step's input ciphertexts host->device from pinned memory
+and reads the result back, through the C ABI, every step.  The reference arm
+(--impl reference) times the CPU oracle on a bounded sample of the same step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "HE mul+relin+rescale/s and enc-LR grad steps/s, batched vs plain, 1 GB300"
+LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE = 14, 8, 40, 1, 60, 2.0 ** 40
+N_SAMPLES, N_FEATURES, G = 4096, 784, 8
+MASK_SCALE = 2.0 ** 40
+WORKLOAD = ("enc-LR gradient step (Eq. 7-8, Table 2 binomial): N=2^14, 8x40-bit limbs + 1x60-bit "
+            "special prime, scale 2^40; 4096 samples x 784 features, 8 samples per ciphertext "
+            "(512 data ciphertexts); one step = 2048 mul+relin+rescale + 5126 rotations")
+
+
+def rot_steps(n_slots: int, g: int) -> list[int]:
+    F = n_slots // g
+    return ([g << t for t in range(int(math.log2(F)))] + [1 << t for t in range(int(math.log2(g)))]
+            + [-(1 << t) for t in range(int(math.log2(g)))])
+
+
+def table2_binomial():
+    path = os.path.join(ROOT, "tests", "golden", "table2_gradient_polynomials.txt")
+    for line in open(path):
+        if line.startswith("binomial"):
+            return [float(v) for v in line.split()[1:]]
+    raise RuntimeError("Table 2 row missing")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# Integer-pipe roof: 152 SMs x 2070 MHz x 64 32-bit multiply-adds per clock per
+# SM; a 64-bit Shoup butterfly needs 10 32-bit multiplies (4 for the high
+# product of a*w', 3 each for the two low products).
+ALU_BFLY_PEAK = 152 * 2.070e9 * 64 / 10
+
+
+def roofline(prof: dict, hbm_peak: float, peak_kind: str):
+    """Dominant kernel class by device time -> achieved vs peak."""
+    if not prof:
+        return None
+    name = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[name]
+    per_launch_ms = p["ms"] / max(1, p["launches"])
+    gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else 0.0
+    if name in ("ntt", "intt"):
+        rate = p["work"] / (p["ms"] * 1e-3)
+        frac_alu = rate / ALU_BFLY_PEAK
+        frac_hbm = gbs / hbm_peak
+        if frac_alu >= frac_hbm:
+            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_BFLY_PEAK / 1e9,
+                    "unit": "Gbutterfly/s", "frac": frac_alu, "traffic": None,
+                    "per_launch_ms": per_launch_ms, "launches": p["launches"],
+                    "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
+                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 10 IMAD per 64-bit butterfly"}
+    return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": gbs / hbm_peak, "traffic": None, "per_launch_ms": per_launch_ms,
+            "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def build_inputs(he, ctx, data, level):
+    n_slots = ctx.n // 2
+    zs = __import__("paper_2006_10091_gb300.workloads", fromlist=["x"]).pack_samples(
+        data.X, data.y, n_slots, G)
+    Z = ctx.new_ct(level, len(zs))
+    for k, v in enumerate(zs):
+        he.he_encode_encrypt(ctx, v, SCALE, level, Z[k], cid=1000 + k)
+    from paper_2006_10091_gb300 import workloads
+    W = ctx.new_ct(level)
+    he.he_encode_encrypt(ctx, workloads.pack_weights(data.w0, n_slots, G), SCALE, level, W, cid=999)
+    return Z, W
+
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10091_gb300 as he
+    from paper_2006_10091_gb300 import workloads
+    from tests.lr_reference import lr_step_fp64
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n_slots = (1 << LOG_N) // 2
+    ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=rank,
+                     rot_steps=rot_steps(n_slots, G), stream=stream.cuda_stream)
+    data = workloads.LRData(seed=rank, n_samples=N_SAMPLES, n_features=N_FEATURES)
+    coeffs = table2_binomial()
+    lr = 1.0 / N_SAMPLES
+    cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
+    Z, W = build_inputs(he, ctx, data, L)
+    out = ctx.new_ct(L)
+    step = lambda: he.he_lr_gradient_step(ctx, Z, W, cfg, out)  # noqa: E731
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # accuracy of the step this bench times (decrypt vs FP64 Eq. 7-8)
+    got = he.he_decrypt_decode(ctx, out)
+    want = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, lr), n_slots, G)
+    rel_err = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+
+    # kernel-class timing over a profiled region of the same step
+    he.he_profile_enable(ctx, True)
+    prof_steps = max(1, min(3, args.steps))
+    for _ in range(prof_steps):
+        step()
+    prof = {k: he.he_profile_read(ctx, k) for k in he.he_profile_names(ctx)}
+    he.he_profile_enable(ctx, False)
+    hbm_peak, peak_kind = measured_peaks()
+    roof = roofline(prof, hbm_peak, peak_kind)
+    kernels = {k: {"launches_per_step": v["launches"] // prof_steps, "ms_per_step": v["ms"] / prof_steps}
+               for k, v in prof.items()}
+
+    # e2e: host->device copy of the step's inputs (pinned), the step, result read back
+    nZ = len(Z)
+    host_in = torch.empty((nZ, 2, L, ctx.n), dtype=torch.int64, pin_memory=True)
+    host_w = torch.empty((1, 2, L, ctx.n), dtype=torch.int64, pin_memory=True)
+    host_out = torch.empty((2, L - 5, ctx.n), dtype=torch.int64, pin_memory=True)
+    he.he_ct_export_batch(ctx, Z, host_in)
+    he.he_ct_export_batch(ctx, [W], host_w)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        he.he_ct_import_batch(ctx, host_in, L, SCALE, Z)
+        he.he_ct_import_batch(ctx, host_w, L, SCALE, [W])
+        step()
+        he.he_ct_export_batch(ctx, [out], host_out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = (nZ + 1) * 2 * L * ctx.n * 8
+    d2h = 2 * (L - 5) * ctx.n * 8
+
+    extra = {}
+    if not args.quick and rank == 0:
+        extra.update(hmult_rates(he, torch, stream))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(data, coeffs, lr)
+    value = world * 1000.0 / ms_per_step
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 1 << LOG_N, "limbs": L, "special_primes": ALPHA,
+                   "scale_log2": 40, "samples": N_SAMPLES, "features": N_FEATURES,
+                   "samples_per_ciphertext": G, "data_ciphertexts": nZ,
+                   "l2": "inputs larger than L2 (1.07 GB of ciphertexts per step)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "accuracy": {"max_rel_err_vs_fp64": rel_err, "gate": 2.0 ** -20, "ok": rel_err < 2.0 ** -20},
+        "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(v["launches"] for v in prof.values()) // prof_steps),
+        "roofline": roof, "kernels": kernels, "clocks": clk.summary(), "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def hmult_rates(he, torch, stream):
+    """mul+relin+rescale/s at the small (N=2^12, 3 limbs, 16 pairs) and large
+    (N=2^16, 24 limbs + 4 special primes, dnum 6, 64 ciphertexts)
+    configurations, batched (one call) and plain (one call per pair)."""
+    from paper_2006_10091_gb300 import workloads
+    out = {}
+    for name, (log_n, nl, bits, alpha, sbits, scale, count) in {
+            "hmult_small": (12, 3, 40, 1, 60, 2.0 ** 30, 16),
+            "hmult_large": (16, 24, 50, 4, 60, 2.0 ** 50, 64)}.items():
+        ctx = he.Context(log_n, nl, bits, alpha, sbits, scale, seed=0, stream=stream.cuda_stream)
+        n = 1 << log_n
+        A, B, O = ctx.new_ct(nl, count), ctx.new_ct(nl, count), ctx.new_ct(nl, count)
+        for i in range(count):
+            he.he_encode_encrypt(ctx, workloads.uniform_slots(2 * i, n // 2), scale, nl, A[i], cid=2 * i)
+            he.he_encode_encrypt(ctx, workloads.uniform_slots(2 * i + 1, n // 2), float(ctx.primes[nl - 1]),
+                                 nl, B[i], cid=2 * i + 1)
+        for _ in range(3):
+            he.he_mul_relin_rescale_batch(ctx, A, B, O)
+        torch.cuda.synchronize()
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            he.he_mul_relin_rescale_batch(ctx, A, B, O)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batched = count * reps * 1000.0 / e0.elapsed_time(e1)
+        e0.record(stream)
+        for _ in range(reps):
+            for i in range(count):
+                he.he_mul_relin_rescale(ctx, A[i], B[i], O[i])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain = count * reps * 1000.0 / e0.elapsed_time(e1)
+        got = he.he_decrypt_decode(ctx, O[0])
+        err = float(np.max(np.abs(got - workloads.uniform_slots(0, n // 2) * workloads.uniform_slots(1, n // 2))))
+        out[name] = {"per_s_batched": batched, "per_s_plain": plain, "count": count, "N": n, "limbs": nl,
+                     "max_abs_err": err}
+        ctx.close()
+        del A, B, O
+        torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline(data, coeffs, lr):
+    """The oracle as it stands on a bounded sample: the step over 1 and over 2
+    data ciphertexts, extrapolated linearly to the 512 ciphertexts of a step."""
+    import oracle
+    from paper_2006_10091_gb300 import workloads
+    n_slots = (1 << LOG_N) // 2
+    o = oracle.Oracle(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0,
+                      rot_steps=rot_steps(n_slots, G))
+    zs = workloads.pack_samples(data.X[:2 * G], data.y[:2 * G], n_slots, G)
+    Z = [o.encrypt(o.encode(v), L, cid=1000 + k) for k, v in enumerate(zs)]
+    W = o.encrypt(o.encode(workloads.pack_weights(data.w0, n_slots, G)), L, cid=999)
+    t = []
+    for k in (1, 2):
+        t0 = time.perf_counter()
+        o.lr_gradient_step(Z[:k], W, coeffs, lr, G, MASK_SCALE)
+        t.append(time.perf_counter() - t0)
+    per_ct = max(t[1] - t[0], 1e-9)
+    fixed = max(t[0] - per_ct, 0.0)
+    n_ct = N_SAMPLES // G
+    step_s = fixed + n_ct * per_ct
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"the step over 1 and 2 of the {n_ct} data ciphertexts ({t[0]:.1f} s, {t[1]:.1f} s), "
+                      f"extrapolated linearly; single-threaded C, exact __int128 residue arithmetic"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2006_10091_gb300 import workloads
+    data = workloads.LRData(seed=0, n_samples=N_SAMPLES, n_features=N_FEATURES)
+    coeffs = table2_binomial()
+    lr = 1.0 / N_SAMPLES
+    n_slots = (1 << LOG_N) // 2
+    o = oracle.Oracle(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0,
+                      rot_steps=rot_steps(n_slots, G))
+    zs = workloads.pack_samples(data.X[:2 * G], data.y[:2 * G], n_slots, G)
+    Z = [o.encrypt(o.encode(v), L, cid=1000 + k) for k, v in enumerate(zs)]
+    W = o.encrypt(o.encode(workloads.pack_weights(data.w0, n_slots, G)), L, cid=999)
+    n_ct = N_SAMPLES // G
+    # warm-up: the fixed (final-stage) cost from the 1- and 2-ciphertext samples
+    t = []
+    for k in (1, 2):
+        t0 = time.perf_counter()
+        o.lr_gradient_step(Z[:k], W, coeffs, lr, G, MASK_SCALE)
+        t.append(time.perf_counter() - t0)
+    fixed = max(t[0] - (t[1] - t[0]), 0.0)
+    for _ in range(max(0, args.warmup - 2)):
+        o.lr_gradient_step(Z[:1], W, coeffs, lr, G, MASK_SCALE)
+    step_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.lr_gradient_step(Z[:1], W, coeffs, lr, G, MASK_SCALE)
+        one = time.perf_counter() - t0
+        step_s.append(fixed + n_ct * (one - fixed))
+    mean = sum(step_s) / len(step_s)
+    value = 1.0 / mean
+    sample = (f"each step times the oracle's step over 1 of the {n_ct} data ciphertexts and "
+              f"extrapolates linearly (fixed final-stage cost {fixed:.2f} s from a 2-ciphertext run)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

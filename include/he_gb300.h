@@ -1,0 +1,241 @@
+/*
+ * he_gb300.h -- C ABI of the GB300 (sm_103a) library for the encrypted
+ * logistic-regression worker step of Li & Huang, "Faster Secure Data Mining
+ * via Distributed Homomorphic Encryption" (KDD'20).
+ *
+ * The paper's workers evaluate the linearised gradient update (Sec. 4,
+ * Eq. 7-8, Table 2) on CKKS ciphertexts (Sec. 3: encode/decode,
+ * encrypt/decrypt, addition, multiplication, rescaling) without
+ * bootstrapping, and hand the encrypted weights back to the key holder for
+ * a refresh every few iterations (Algorithm 1, Algorithm 2).  This library
+ * implements that arithmetic in its full-RNS form: residues modulo word-size
+ * primes q_0 > ... > q_{L-1} (the ciphertext modulus, "M" of Sec. 3) and
+ * alpha special primes (the key-switching modulus P), ring degree N
+ * ("N" of Sec. 3), N/2 complex slots.
+ *
+ * Conventions shared by every entry point
+ *  - Ciphertext residues live in device memory (HBM) and are owned by the
+ *    caller.  A ciphertext at level l (l limbs) in a buffer of `cap` limbs per
+ *    part keeps part p (0 or 1), limb t (prime q_t) at
+ *    data + (p*cap + t)*N, as N uint64 words in [0, q_t), in evaluation
+ *    (NTT) form: word j is the value at psi_t^(2*brv(j)+1), psi_t the least
+ *    primitive 2N-th root of unity mod q_t.  The buffer must hold 2*cap*N
+ *    words, cap >= level.
+ *  - Every call is asynchronous on the context's stream unless stated; host
+ *    buffers passed in are read before the call returns; host results are
+ *    complete when the call returns.
+ *  - Every call returns HE_OK (0) or an error code below; a description of
+ *    the last error on the calling thread is returned by he_last_error().
+ *    Calls never modify their input ciphertexts; an output may alias an
+ *    input only where stated.
+ */
+#ifndef HE_GB300_H
+#define HE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HE_OK = 0,
+  HE_EINVAL = 1,   /* null pointer, bad size, level or capacity */
+  HE_ELEVEL = 2,   /* too few limbs left: the key holder must refresh (Alg. 1) */
+  HE_ESCALE = 3,   /* operands' scales differ by more than 2^-40 relative */
+  HE_ENOKEY = 4,   /* no Galois key for the requested rotation */
+  HE_ENOMEM = 5,   /* device memory exhausted or budget exceeded */
+  HE_ECUDA = 6,    /* CUDA runtime error */
+  HE_ETIMEOUT = 7  /* a bounded device wait gave up */
+};
+
+/* Scheme parameters (Sec. 3 names two: the ring degree N and the modulus
+ * size M; the rest are the RNS form's).  limb_bits/special_bits must be in
+ * [20, 61]; scale is the default encoding scale Delta; sigma the standard
+ * deviation of the discrete Gaussian errors; seed keys every random stream. */
+typedef struct he_params {
+  uint32_t log_n;        /* N = 2^log_n, 4 <= log_n <= 16 */
+  uint32_t n_limbs;      /* L: limb primes q_0..q_{L-1} */
+  uint32_t limb_bits;
+  uint32_t n_special;    /* alpha: special primes (key-switching digit size) */
+  uint32_t special_bits;
+  uint32_t dnum;         /* 0, or must equal ceil(L / alpha) */
+  double scale;
+  double sigma;
+  uint64_t seed;
+} he_params;
+
+typedef struct he_ctx he_ctx;
+
+typedef struct he_ct {
+  uint64_t* data;  /* device, 2*cap*N words */
+  uint32_t level;  /* limbs in use */
+  uint32_t cap;    /* limbs per part the buffer holds */
+  double scale;    /* scale of the encoded message */
+} he_ct;
+
+/* Last error message of the calling thread ("" if none). */
+const char* he_last_error(void);
+
+/* Key generation from the seed (Algorithm 2, line 4: the parameter server
+ * generates pk and sk).  Finds the primes (q = 1 mod 2N, scanned downward
+ * from 2^bits), the secret s (ternary), the public key, the relinearisation
+ * key and one Galois key per distinct rotation step in rot_steps[0..n_rot)
+ * (steps are reduced mod N/2; 0 is ignored).  `stream` is a cudaStream_t (NULL
+ * = the legacy default stream) on which every later call runs.  Keys stay
+ * resident in device memory owned by the context.  Errors: HE_EINVAL,
+ * HE_ENOMEM, HE_ECUDA. */
+int he_ctx_create(const he_params* params, const int32_t* rot_steps, size_t n_rot, void* stream,
+                  he_ctx** out);
+int he_ctx_destroy(he_ctx* ctx);
+/* Switch the stream later calls run on (cudaStream_t). */
+int he_set_stream(he_ctx* ctx, void* stream);
+/* Synchronise the context's stream. */
+int he_sync(he_ctx* ctx);
+
+/* Context facts: N, L, alpha, beta (digits at the top level), and the
+ * L + alpha primes (limbs first) into primes_out (may be NULL). */
+int he_ctx_info(const he_ctx* ctx, uint32_t* n, uint32_t* n_limbs, uint32_t* n_special,
+                uint32_t* beta, uint64_t* primes_out);
+
+/* Encode (Sec. 3, canonical embedding): n_slots <= N/2 real values (host)
+ * at `scale` into N integer coefficients (host), coefficient
+ * i = round((2*scale/N) * sum_j Re(z_j * zeta_j^-i)), zeta_j = exp(i*pi*5^j/N),
+ * rounding half away from zero; computed on the device in double
+ * precision.  HE_EINVAL if a coefficient leaves int64. */
+int he_encode(he_ctx* ctx, const double* slots, size_t n_slots, double scale, int64_t* coeffs_out);
+
+/* Encrypt integer coefficients (host, N of them) at `level` (Sec. 3;
+ * Algorithm 1 line 4 uses pk, Algorithm 2 line 4 encrypts with sk).
+ * use_sk = 0: (v*b + e0 + m, v*a + e1); use_sk = 1: (-a*s + e + m, a).  The
+ * randomness is the stream of ciphertext id `cid`, so equal inputs give
+ * equal residues.  out->data must be allocated; sets level and scale. */
+int he_encrypt_poly(he_ctx* ctx, const int64_t* coeffs, double scale, uint32_t level, int use_sk,
+                    uint32_t cid, he_ct* out);
+
+/* he_encode followed by he_encrypt_poly. */
+int he_encode_encrypt(he_ctx* ctx, const double* slots, size_t n_slots, double scale,
+                      uint32_t level, int use_sk, uint32_t cid, he_ct* out);
+
+/* Decrypt to centered coefficients: m = c0 + c1*s mod Q_level, lifted to
+ * (-Q/2, Q/2] and written as doubles (host, N values).  Synchronous. */
+int he_decrypt_poly(he_ctx* ctx, const he_ct* ct, double* coeffs_out);
+
+/* Decrypt and decode (Sec. 3): real parts of the first n_slots slots, each
+ * divided by the ciphertext's scale (host).  Synchronous. */
+int he_decrypt_decode(he_ctx* ctx, const he_ct* ct, double* slots_out, size_t n_slots);
+
+/* Residues to and from host memory, packed [2][level][N] (uint64).  Export is
+ * synchronous; cap_words is the capacity of `host` in words. */
+int he_ct_export(he_ctx* ctx, const he_ct* ct, uint64_t* host, size_t cap_words);
+int he_ct_import(he_ctx* ctx, const uint64_t* host, uint32_t level, double scale, he_ct* out);
+
+/* Batched transfers of `count` ciphertexts packed [count][2][level][N] in
+ * host memory (pinned memory gives full copy bandwidth).  Import sets every
+ * out[i] to (level, scale); both are synchronous. */
+int he_ct_import_batch(he_ctx* ctx, const uint64_t* host, uint32_t level, double scale, he_ct* out,
+                       size_t count);
+int he_ct_export_batch(he_ctx* ctx, const he_ct* cts, size_t count, uint64_t* host, size_t cap_words);
+
+/* Homomorphic addition / subtraction (Sec. 3; Eq. 1-2).  Operands at
+ * different levels are taken at the lower one.  HE_ESCALE if the scales
+ * differ.  out may alias a or b. */
+int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+int he_sub(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+
+/* Keep the first `level` limbs (modulus reduction without division). */
+int he_drop_level(he_ctx* ctx, const he_ct* a, uint32_t level, he_ct* out);
+
+/* Multiply by the integer round(value * value_scale) (a constant plaintext
+ * at scale value_scale); out.scale = a.scale * value_scale.  No rescale. */
+int he_mul_const(he_ctx* ctx, const he_ct* a, double value, double value_scale, he_ct* out);
+
+/* Add the constant `value` (encoded as round(value * a.scale)). */
+int he_add_const(he_ctx* ctx, const he_ct* a, double value, he_ct* out);
+
+/* Multiply by a plaintext given as N integer coefficients (host) at scale
+ * pt_scale; out.scale = a.scale * pt_scale.  No rescale. */
+int he_mul_plain(he_ctx* ctx, const he_ct* a, const int64_t* coeffs, double pt_scale, he_ct* out);
+
+/* Rescale (Sec. 3 "scaling performs homomorphic rounding"): divide by the
+ * last limb prime q_{l-1} with rounding, out at level l-1, scale / q_{l-1}.
+ * HE_ELEVEL if l < 2. */
+int he_rescale(he_ctx* ctx, const he_ct* a, he_ct* out);
+
+/* Homomorphic multiplication (Sec. 3; the cost the paper names in Sec. 6):
+ * tensor product, relinearisation by hybrid key switching, rescale.  Both
+ * operands at the same level l >= 2 (else the lower is used); out at l-1
+ * with scale a.scale*b.scale/q_{l-1}. */
+int he_mul_relin_rescale(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+
+/* Same, without the rescale (out at level l, scale a.scale*b.scale). */
+int he_mul_relin(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+
+/* Rotate the slots left by `steps` (slot j <- slot j + steps), the packing
+ * primitive behind the sums of Sec. 3-4: Galois automorphism X -> X^(5^steps)
+ * and key switching.  HE_ENOKEY if the context has no key for the step. */
+int he_rotate(he_ctx* ctx, const he_ct* a, int32_t steps, he_ct* out);
+
+/* Batched forms: count independent operations in one launch sequence.  All
+ * inputs of one call share level and scale. */
+int he_mul_relin_rescale_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out,
+                               size_t count);
+int he_rotate_batch(he_ctx* ctx, const he_ct* a, int32_t steps, he_ct* out, size_t count);
+
+/* Encrypted logistic-regression gradient step (Sec. 4: Eq. 5-8 with a Table 2
+ * polynomial; Algorithm 1 line 7).  Z[k] hold g samples each, slot g*f + s =
+ * y_s*x_{s,f}; W holds w_f in slots g*f + s for every s.  Computes
+ * w' = w + lr * sum_k sum_s p(y_s w.x_s) y_s x_s with p(x) = c0 + c1 x +
+ * c2 x^2 + c3 x^3, replicated over the g slots of each feature.  Consumes 5
+ * levels: Z and W at the same level l >= 6; W_out at l - 5 with W's scale.
+ * Needs Galois keys for steps g*2^i (i < log2(N/(2g))), 2^i and -2^i (i < log2 g). */
+typedef struct he_lr_config {
+  double coeffs[4];     /* c0..c3 */
+  double lr;            /* learning rate, e.g. eta / n */
+  uint32_t g;           /* samples per ciphertext, a power of two */
+  uint32_t pad;
+  double mask_scale;    /* scale of the 0/1 slot mask plaintext */
+} he_lr_config;
+
+int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
+                        const he_lr_config* cfg, he_ct* W_out);
+
+/* The key holder's refresh (Algorithm 1 lines 8-10, Algorithm 2 lines 8-11),
+ * simulated in-process: decrypt, decode, re-encode at out_scale and encrypt
+ * at `level` with ciphertext id cid.  Synchronous. */
+int he_refresh(he_ctx* ctx, const he_ct* a, uint32_t level, double out_scale, uint32_t cid,
+               he_ct* out);
+
+/* Low-level entry points for kernel parity tests. */
+/* Forward (inverse = 0) or inverse negacyclic NTT of `nl` limbs (limb t with
+ * prime index prime0 + t) of `npolys` device polynomials at data +
+ * p*poly_stride words, in place. */
+int he_ntt(he_ctx* ctx, uint64_t* data, uint32_t npolys, uint64_t poly_stride, uint32_t nl,
+           uint32_t prime0, int inverse);
+/* Hybrid key switching of d (device, level limbs, evaluation form) with the
+ * relinearisation key (galois = 0) or the Galois key of element `galois`:
+ * out0 + out1*s ~ d*s'.  out0/out1: device, level limbs each. */
+int he_keyswitch(he_ctx* ctx, const uint64_t* d, uint32_t level, uint64_t galois, uint64_t* out0,
+                 uint64_t* out1);
+
+/* Kernel timing for measurement (not part of the paper's method).  While
+ * enabled, every launch of an instrumented kernel class ("ntt", "intt",
+ * "modup", "inner_product", "moddown_conv", "ks_combine", "rescale",
+ * "tensor", "automorph", "elementwise") is bracketed by CUDA events on the
+ * context's stream and its algorithmic work (butterflies for the
+ * transforms, modular products otherwise) and algorithmic DRAM bytes are
+ * added to the class.  Enabling or disabling resets the counters;
+ * he_profile_read synchronises and returns launches, total device time (ms),
+ * work and bytes of one class; he_profile_names lists the classes seen,
+ * comma-separated, into buf (HE_EINVAL if cap is too small). */
+int he_profile_enable(he_ctx* ctx, int enable);
+int he_profile_read(he_ctx* ctx, const char* kernel_class, uint64_t* launches, double* total_ms,
+                    double* work, double* bytes);
+int he_profile_names(he_ctx* ctx, char* buf, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HE_GB300_H */

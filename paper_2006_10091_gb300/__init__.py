@@ -1,0 +1,425 @@
+"""Python binding of libhegb300.so, the sm_103a library for the encrypted
+logistic-regression worker step of Li & Huang (KDD'20).
+
+Argument marshalling only: every residue operation runs in the library's
+CUDA kernels.  The functions keep the C ABI's names (include/he_gb300.h).
+PyTorch provides device memory (ciphertext buffers are int64 CUDA tensors
+holding uint64 residues) and the stream.  Importing the package does not
+touch the GPU; the first call that needs the library loads it and raises
+if it is missing -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhegb300.so")
+
+HE_OK, HE_EINVAL, HE_ELEVEL, HE_ESCALE, HE_ENOKEY, HE_ENOMEM, HE_ECUDA, HE_ETIMEOUT = range(8)
+
+
+class HeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class he_params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_limbs", ctypes.c_uint32),
+                ("limb_bits", ctypes.c_uint32), ("n_special", ctypes.c_uint32),
+                ("special_bits", ctypes.c_uint32), ("dnum", ctypes.c_uint32),
+                ("scale", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class he_ct(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("level", ctypes.c_uint32),
+                ("cap", ctypes.c_uint32), ("scale", ctypes.c_double)]
+
+
+class he_lr_config(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.c_double * 4), ("lr", ctypes.c_double),
+                ("g", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mask_scale", ctypes.c_double)]
+
+
+_lib = None
+VP = ctypes.c_void_p
+CTP = ctypes.POINTER(he_ct)
+
+
+def load():
+    """Load libhegb300.so (build it first with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2006_10091_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.he_last_error.restype = ctypes.c_char_p
+    sig = {
+        "he_ctx_create": [ctypes.POINTER(he_params), VP, ctypes.c_size_t, VP, ctypes.POINTER(VP)],
+        "he_ctx_destroy": [VP],
+        "he_set_stream": [VP, VP],
+        "he_sync": [VP],
+        "he_ctx_info": [VP, VP, VP, VP, VP, VP],
+        "he_encode": [VP, VP, ctypes.c_size_t, ctypes.c_double, VP],
+        "he_encrypt_poly": [VP, VP, ctypes.c_double, ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32, CTP],
+        "he_encode_encrypt": [VP, VP, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint32, ctypes.c_int,
+                              ctypes.c_uint32, CTP],
+        "he_decrypt_poly": [VP, CTP, VP],
+        "he_decrypt_decode": [VP, CTP, VP, ctypes.c_size_t],
+        "he_ct_export": [VP, CTP, VP, ctypes.c_size_t],
+        "he_ct_import": [VP, VP, ctypes.c_uint32, ctypes.c_double, CTP],
+        "he_add": [VP, CTP, CTP, CTP],
+        "he_sub": [VP, CTP, CTP, CTP],
+        "he_drop_level": [VP, CTP, ctypes.c_uint32, CTP],
+        "he_mul_const": [VP, CTP, ctypes.c_double, ctypes.c_double, CTP],
+        "he_add_const": [VP, CTP, ctypes.c_double, CTP],
+        "he_mul_plain": [VP, CTP, VP, ctypes.c_double, CTP],
+        "he_rescale": [VP, CTP, CTP],
+        "he_mul_relin_rescale": [VP, CTP, CTP, CTP],
+        "he_mul_relin": [VP, CTP, CTP, CTP],
+        "he_rotate": [VP, CTP, ctypes.c_int32, CTP],
+        "he_mul_relin_rescale_batch": [VP, CTP, CTP, CTP, ctypes.c_size_t],
+        "he_rotate_batch": [VP, CTP, ctypes.c_int32, CTP, ctypes.c_size_t],
+        "he_lr_gradient_step": [VP, CTP, ctypes.c_size_t, CTP, ctypes.POINTER(he_lr_config), CTP],
+        "he_refresh": [VP, CTP, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32, CTP],
+        "he_ntt": [VP, VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
+        "he_keyswitch": [VP, VP, ctypes.c_uint32, ctypes.c_uint64, VP, VP],
+        "he_ct_import_batch": [VP, VP, ctypes.c_uint32, ctypes.c_double, CTP, ctypes.c_size_t],
+        "he_ct_export_batch": [VP, CTP, ctypes.c_size_t, VP, ctypes.c_size_t],
+        "he_profile_enable": [VP, ctypes.c_int],
+        "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
+        "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != HE_OK:
+        raise HeError(rc, load().he_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def current_stream_handle():
+    torch = _torch()
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# Handles
+# ---------------------------------------------------------------------------
+
+class Context:
+    """An he_ctx*: parameters, primes and keys resident on the device."""
+
+    def __init__(self, log_n: int, n_limbs: int, limb_bits: int, n_special: int, special_bits: int,
+                 scale: float, sigma: float = 3.2, seed: int = 0, rot_steps=(), dnum: int = 0,
+                 stream=None):
+        lib = load()
+        p = he_params(log_n, n_limbs, limb_bits, n_special, special_bits, dnum, float(scale),
+                      float(sigma), seed)
+        rots = (ctypes.c_int32 * max(1, len(rot_steps)))(*rot_steps)
+        self.stream = current_stream_handle() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(lib.he_ctx_create(ctypes.byref(p), rots, len(rot_steps), ctypes.c_void_p(self.stream),
+                                 ctypes.byref(h)))
+        self.ptr = h
+        self.log_n, self.n, self.L, self.alpha = log_n, 1 << log_n, n_limbs, n_special
+        self.scale = float(scale)
+        n = ctypes.c_uint32()
+        beta = ctypes.c_uint32()
+        primes = np.zeros(n_limbs + n_special, dtype=np.uint64)
+        _check(lib.he_ctx_info(h, ctypes.byref(n), None, None, ctypes.byref(beta), _ptr(primes)))
+        self.beta = beta.value
+        self.primes = [int(x) for x in primes]
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().he_ctx_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_ct(self, cap: int, count: int | None = None):
+        """Ciphertext buffers of `cap` limbs: one, or `count` of them laid out
+        back to back in a single allocation (a uniform batch)."""
+        torch = _torch()
+        shape = (count if count is not None else 1, 2, cap, self.n)
+        buf = torch.empty(shape, dtype=torch.int64, device="cuda")
+        cts = [Ciphertext(buf[i], cap) for i in range(shape[0])]
+        return cts if count is not None else cts[0]
+
+
+class Ciphertext:
+    """A ciphertext buffer (int64 CUDA tensor [2][cap][N]) plus level and scale."""
+
+    def __init__(self, tensor, cap: int, level: int = 0, scale: float = 0.0):
+        self.tensor = tensor
+        self.cap = cap
+        self.level = level
+        self.scale = scale
+
+    def c(self) -> he_ct:
+        return he_ct(self.tensor.data_ptr(), self.level, self.cap, self.scale)
+
+    def update(self, s: he_ct):
+        self.level, self.scale = s.level, s.scale
+
+    def residues(self) -> np.ndarray:
+        """[2][level][N] uint64 on the host (synchronises)."""
+        return self.tensor[:, : self.level].cpu().numpy().view(np.uint64)
+
+
+def _run(fn, ctx, outs, *args):
+    """Call fn(ctx.ptr, *args) where args may contain Ciphertexts; outputs
+    listed in outs get their level/scale back."""
+    structs = {}
+    cargs = []
+    for a in args:
+        if isinstance(a, Ciphertext):
+            s = a.c()
+            structs[id(a)] = (a, s)
+            cargs.append(ctypes.byref(s))
+        else:
+            cargs.append(a)
+    _check(fn(ctx.ptr, *cargs))
+    for o in outs:
+        a, s = structs[id(o)]
+        a.update(s)
+
+
+def _batch(cts):
+    arr = (he_ct * len(cts))(*[c.c() for c in cts])
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# Entry points (names of the C ABI)
+# ---------------------------------------------------------------------------
+
+def he_set_stream(ctx: Context, stream):
+    ctx.stream = stream
+    _check(load().he_set_stream(ctx.ptr, ctypes.c_void_p(stream)))
+
+
+def he_sync(ctx: Context):
+    _check(load().he_sync(ctx.ptr))
+
+
+def he_encode(ctx: Context, slots, scale: float) -> np.ndarray:
+    z = np.ascontiguousarray(slots, dtype=np.float64)
+    out = np.zeros(ctx.n, dtype=np.int64)
+    _check(load().he_encode(ctx.ptr, _ptr(z), len(z), float(scale), _ptr(out)))
+    return out
+
+
+def he_encrypt_poly(ctx: Context, coeffs, scale: float, level: int, out: Ciphertext,
+                    use_sk: bool = False, cid: int = 0):
+    m = np.ascontiguousarray(coeffs, dtype=np.int64)
+    _run(load().he_encrypt_poly, ctx, [out], _ptr(m), float(scale), level, int(use_sk), cid, out)
+    return out
+
+
+def he_encode_encrypt(ctx: Context, slots, scale: float, level: int, out: Ciphertext,
+                      use_sk: bool = False, cid: int = 0):
+    z = np.ascontiguousarray(slots, dtype=np.float64)
+    _run(load().he_encode_encrypt, ctx, [out], _ptr(z), len(z), float(scale), level, int(use_sk), cid,
+         out)
+    return out
+
+
+def he_decrypt_poly(ctx: Context, ct: Ciphertext) -> np.ndarray:
+    out = np.zeros(ctx.n, dtype=np.float64)
+    _run(load().he_decrypt_poly, ctx, [], ct, _ptr(out))
+    return out
+
+
+def he_decrypt_decode(ctx: Context, ct: Ciphertext, n_slots: int | None = None) -> np.ndarray:
+    n_slots = ctx.n // 2 if n_slots is None else n_slots
+    out = np.zeros(n_slots, dtype=np.float64)
+    _run(load().he_decrypt_decode, ctx, [], ct, _ptr(out), n_slots)
+    return out
+
+
+def he_ct_export(ctx: Context, ct: Ciphertext) -> np.ndarray:
+    out = np.zeros((2, ct.level, ctx.n), dtype=np.uint64)
+    _run(load().he_ct_export, ctx, [], ct, _ptr(out), out.size)
+    return out
+
+
+def he_ct_import(ctx: Context, residues, level: int, scale: float, out: Ciphertext):
+    r = np.ascontiguousarray(residues, dtype=np.uint64)
+    _run(load().he_ct_import, ctx, [out], _ptr(r), level, float(scale), out)
+    return out
+
+
+def he_add(ctx, a, b, out):
+    _run(load().he_add, ctx, [out], a, b, out)
+    return out
+
+
+def he_sub(ctx, a, b, out):
+    _run(load().he_sub, ctx, [out], a, b, out)
+    return out
+
+
+def he_drop_level(ctx, a, level: int, out):
+    _run(load().he_drop_level, ctx, [out], a, level, out)
+    return out
+
+
+def he_mul_const(ctx, a, value: float, value_scale: float, out):
+    _run(load().he_mul_const, ctx, [out], a, float(value), float(value_scale), out)
+    return out
+
+
+def he_add_const(ctx, a, value: float, out):
+    _run(load().he_add_const, ctx, [out], a, float(value), out)
+    return out
+
+
+def he_mul_plain(ctx, a, coeffs, pt_scale: float, out):
+    m = np.ascontiguousarray(coeffs, dtype=np.int64)
+    _run(load().he_mul_plain, ctx, [out], a, _ptr(m), float(pt_scale), out)
+    return out
+
+
+def he_rescale(ctx, a, out):
+    _run(load().he_rescale, ctx, [out], a, out)
+    return out
+
+
+def he_mul_relin_rescale(ctx, a, b, out):
+    _run(load().he_mul_relin_rescale, ctx, [out], a, b, out)
+    return out
+
+
+def he_mul_relin(ctx, a, b, out):
+    _run(load().he_mul_relin, ctx, [out], a, b, out)
+    return out
+
+
+def he_rotate(ctx, a, steps: int, out):
+    _run(load().he_rotate, ctx, [out], a, steps, out)
+    return out
+
+
+def he_mul_relin_rescale_batch(ctx, a: list, b: list, out: list):
+    A, B, O = _batch(a), _batch(b), _batch(out)
+    _check(load().he_mul_relin_rescale_batch(ctx.ptr, A, B, O, len(a)))
+    for o, s in zip(out, O):
+        o.update(s)
+    return out
+
+
+def he_rotate_batch(ctx, a: list, steps: int, out: list):
+    A, O = _batch(a), _batch(out)
+    _check(load().he_rotate_batch(ctx.ptr, A, steps, O, len(a)))
+    for o, s in zip(out, O):
+        o.update(s)
+    return out
+
+
+def lr_config(coeffs, lr: float, g: int, mask_scale: float) -> he_lr_config:
+    return he_lr_config((ctypes.c_double * 4)(*coeffs), float(lr), g, 0, float(mask_scale))
+
+
+def he_lr_gradient_step(ctx, Z: list, W: Ciphertext, cfg: he_lr_config, W_out: Ciphertext):
+    Zs = _batch(Z)
+    Ws, Os = W.c(), W_out.c()
+    _check(load().he_lr_gradient_step(ctx.ptr, Zs, len(Z), ctypes.byref(Ws), ctypes.byref(cfg),
+                                      ctypes.byref(Os)))
+    W_out.update(Os)
+    return W_out
+
+
+def he_refresh(ctx, a, level: int, out_scale: float, cid: int, out):
+    _run(load().he_refresh, ctx, [out], a, level, float(out_scale), cid, out)
+    return out
+
+
+def he_ntt(ctx, tensor, npolys: int, poly_stride: int, nl: int, prime0: int, inverse: bool):
+    """In-place NTT of limbs of device polynomials held by an int64 tensor."""
+    _check(load().he_ntt(ctx.ptr, ctypes.c_void_p(tensor.data_ptr()), npolys, poly_stride, nl, prime0,
+                         int(inverse)))
+    return tensor
+
+
+def he_keyswitch(ctx, d, level: int, galois: int, out0, out1):
+    _check(load().he_keyswitch(ctx.ptr, ctypes.c_void_p(d.data_ptr()), level, galois,
+                               ctypes.c_void_p(out0.data_ptr()), ctypes.c_void_p(out1.data_ptr())))
+    return out0, out1
+
+
+def he_ct_import_batch(ctx, host, level: int, scale: float, out: list):
+    """host: uint64 array [count][2][level][N] (pinned memory copies fastest)."""
+    O = _batch(out)
+    _check(load().he_ct_import_batch(ctx.ptr, ctypes.c_void_p(_addr(host)), level, float(scale), O, len(out)))
+    for o, s in zip(out, O):
+        o.update(s)
+    return out
+
+
+def he_ct_export_batch(ctx, cts: list, host):
+    A = _batch(cts)
+    _check(load().he_ct_export_batch(ctx.ptr, A, len(cts), ctypes.c_void_p(_addr(host)), _nwords(host)))
+    return host
+
+
+def _addr(x) -> int:
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()  # a host torch tensor (e.g. pinned)
+
+
+def _nwords(x) -> int:
+    if isinstance(x, np.ndarray):
+        return x.size * x.itemsize // 8
+    return x.numel() * x.element_size() // 8
+
+
+def he_profile_enable(ctx, enable: bool):
+    _check(load().he_profile_enable(ctx.ptr, int(enable)))
+
+
+def he_profile_read(ctx, kernel_class: str) -> dict:
+    n = ctypes.c_uint64()
+    ms, work, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().he_profile_read(ctx.ptr, kernel_class.encode(), ctypes.byref(n), ctypes.byref(ms),
+                                  ctypes.byref(work), ctypes.byref(by)))
+    return {"launches": n.value, "ms": ms.value, "work": work.value, "bytes": by.value}
+
+
+def he_profile_names(ctx) -> list:
+    buf = ctypes.create_string_buffer(4096)
+    _check(load().he_profile_names(ctx.ptr, buf, 4096))
+    v = buf.value.decode()
+    return v.split(",") if v else []
+
+
+def galois_elt(log_n: int, r: int) -> int:
+    """5^(r mod N/2) mod 2N, the Galois element of a left rotation by r."""
+    slots = 1 << (log_n - 1)
+    return pow(5, r % slots, 2 << log_n)

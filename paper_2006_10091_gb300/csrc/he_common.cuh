@@ -1,0 +1,118 @@
+// he_common.cuh -- device arithmetic shared by the sm_103a kernels of the
+// RNS-CKKS worker library (residue arithmetic of Li & Huang, KDD'20, Sec. 3).
+//
+// All residues are uint64 words in [0, q) with q < 2^61 (so that the lazy
+// NTT range [0, 4q) fits a word).  Two reductions are used:
+//  * Shoup's precomputed-quotient product for a known operand w (twiddles,
+//    key-switch and rescale constants): w' = floor(w 2^64 / q),
+//    a*w - umulhi(a, w')*q lies in [0, 2q) for every 64-bit a.
+//  * Barrett (1986) for a product of two variable residues: k = bitlen(q),
+//    mu = floor(2^(2k) / q); for x < 2^(2k), t = x >> (k-1),
+//    qe = (t*mu) >> (k+1) undershoots floor(x/q) by at most 2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HE_MAX_PRIMES 64
+
+struct PrimeDev {
+  uint64_t q;
+  uint64_t mu;        // Barrett constant floor(2^(2k)/q)
+  uint32_t k;         // bit length of q
+  uint32_t pad;
+  uint64_t n_inv;     // N^-1 mod q
+  uint64_t n_inv_sh;  // its Shoup companion
+};
+
+__device__ __forceinline__ uint64_t shoup_companion_dev(uint64_t w, uint64_t q) {
+  return (uint64_t)(((unsigned __int128)w << 64) / q);
+}
+
+// a*w mod q in [0, 2q), any 64-bit a.
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t a, uint64_t w, uint64_t wsh, uint64_t q) {
+  uint64_t qh = __umul64hi(a, wsh);
+  return a * w - qh * q;
+}
+
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t a, uint64_t w, uint64_t wsh, uint64_t q) {
+  uint64_t r = mul_shoup_lazy(a, w, wsh, q);
+  return r >= q ? r - q : r;
+}
+
+// (hi:lo) mod q for hi:lo < 2^(2k).
+__device__ __forceinline__ uint64_t barrett_reduce128(uint64_t hi, uint64_t lo, const PrimeDev& p) {
+  const uint32_t k = p.k;
+  uint64_t t = (lo >> (k - 1)) | (hi << (65 - k));
+  uint64_t plo = t * p.mu, phi = __umul64hi(t, p.mu);
+  uint64_t qe = (plo >> (k + 1)) | (phi << (63 - k));
+  uint64_t r = lo - qe * p.q;
+  if (r >= p.q) r -= p.q;
+  if (r >= p.q) r -= p.q;
+  return r;
+}
+
+// a*b mod q for a, b < q.
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, const PrimeDev& p) {
+  return barrett_reduce128(__umul64hi(a, b), a * b, p);
+}
+
+// x mod q for any 64-bit x (x < 2^(2k) when k >= 32; hardware remainder otherwise).
+__device__ __forceinline__ uint64_t reduce64(uint64_t x, const PrimeDev& p) {
+  if (p.k >= 32) return barrett_reduce128(0, x, p);
+  return x % p.q;
+}
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+  uint64_t r = a + b;
+  return r >= q ? r - q : r;
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+  return a >= b ? a - b : a + q - b;
+}
+
+// Signed integer to residue.
+__device__ __forceinline__ uint64_t from_signed(int64_t x, const PrimeDev& p) {
+  if (x >= 0) return reduce64((uint64_t)x, p);
+  uint64_t r = reduce64((uint64_t)(-x), p);
+  return r ? p.q - r : 0;
+}
+
+// 128-bit word (w3:w2:w1:w0) mod q, by Horner on 64-bit halves:
+// x = hi*2^64 + lo; hi*2^64 mod q = (hi mod q) * (2^64 mod q).
+__device__ __forceinline__ uint64_t reduce_u128(uint64_t hi, uint64_t lo, const PrimeDev& p, uint64_t two64) {
+  uint64_t h = reduce64(hi, p);
+  uint64_t a = mul_mod(h, two64, p);
+  uint64_t b = reduce64(lo, p);
+  return add_mod(a, b, p.q);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter (c0..c3), key
+// (k0, k1); ten rounds of two multiply-xor boxes with a Weyl key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    uint4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+// Random stream domains (counter word 3).
+enum : uint32_t {
+  DOM_S = 1, DOM_PK_A = 2, DOM_PK_E = 3, DOM_EVK_A = 4, DOM_EVK_E = 5,
+  DOM_ENC_V = 6, DOM_ENC_E0 = 7, DOM_ENC_E1 = 8, DOM_ENC_A = 9
+};
+
+__device__ __forceinline__ uint32_t brev_bits(uint32_t x, int bits) {
+  return __brev(x) >> (32 - bits);
+}

@@ -1,0 +1,269 @@
+// ops.cu -- batched ciphertext operations: hybrid key switching, the
+// multiplication of Sec. 3 (tensor, relinearise, rescale), rotation, and the
+// circuit glue, each as a fixed sequence of kernel launches over a batch of
+// ciphertexts that share level and layout.
+//
+// Key switching at level l with digits D_j = [j*alpha, min((j+1)*alpha, l)):
+//   1. d to coefficient form (inverse NTT, l limbs);
+//   2. ModUp every digit to the l limbs and alpha special primes (approximate
+//      basis conversion, coefficient form), then forward NTT of the converted
+//      limbs (the digit's own limbs are taken from d as they are);
+//   3. inner product with the switching key, two accumulators over l + alpha limbs;
+//   4. ModDown: inverse NTT of the special limbs, conversion to each q_t,
+//      forward NTT, out_t = (acc_t - conv_t) * P^-1 (+ an optional addend).
+#include "he_ops.h"
+
+namespace he {
+
+unsigned grid_for(size_t work) {
+  size_t b = (work + 255) / 256;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)(b ? b : 1);
+}
+
+static PolyBatch pb(const uint64_t* src, uint64_t* dst, uint64_t src_stride, uint64_t dst_stride,
+                    uint32_t npolys, uint32_t nl, uint32_t limb0, uint32_t level) {
+  PolyBatch b;
+  b.src = src;
+  b.dst = dst;
+  b.src_stride = src_stride;
+  b.dst_stride = dst_stride;
+  b.npolys = npolys;
+  b.nl = nl;
+  b.limb0 = limb0;
+  b.level = level;
+  b.skip_alpha = 0;
+  b.skip_beta = 1;
+  return b;
+}
+
+size_t ks_words(const he_ctx* c, uint32_t level, uint32_t count) {
+  const size_t n = c->n, a = c->alpha, beta = (level + a - 1) / a, nt = level + a;
+  return count * n * (level + beta * nt + 2 * nt + 2 * level) + 4 * 32;
+}
+
+size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count) {
+  return (size_t)count * c->n * (2 + 2 * (level - 1)) + 2 * 32;
+}
+
+size_t mul_words(const he_ctx* c, uint32_t level, uint32_t count, bool rescale) {
+  size_t w = (size_t)count * c->n * (3 * level) + ks_words(c, level, count) + 2 * 32;
+  if (rescale) w += (size_t)count * c->n * 2 * level + rescale_words(c, level, count) + 32;
+  return w;
+}
+
+size_t rot_words(const he_ctx* c, uint32_t level, uint32_t count) {
+  return (size_t)count * c->n * 2 * level + ks_words(c, level, count) + 32;
+}
+
+const uint64_t* galois_key(const he_ctx* c, uint64_t gal) {
+  auto it = c->gal.find(gal);
+  return it == c->gal.end() ? nullptr : it->second;
+}
+
+int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar) {
+  const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
+  const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
+  uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
+  uint64_t* ext = ar.take<uint64_t>((size_t)count * beta * nt * n);
+  uint64_t* acc = ar.take<uint64_t>((size_t)count * 2 * nt * n);
+  uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
+  // 1. coefficient form
+  HE_TRY(ntt_inverse(c, pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level)));
+  // 2. ModUp, then NTT of the converted limbs
+  ModUpArgs m;
+  m.level = level;
+  m.alpha = alpha;
+  m.beta = beta;
+  m.L = L;
+  m.np = np;
+  for (uint32_t j = 0; j < beta; ++j) {
+    const ModUpConst& mc = c->modup[level][j];
+    m.lo[j] = mc.lo;
+    m.cnt[j] = mc.cnt;
+    m.off[j] = mc.off;
+  }
+  {
+    ProfScope prof(c, "modup", (double)count * beta * n * (double)(nt * alpha), (double)count * n * 8 * (level + (double)beta * nt));
+    k_modup<<<grid_for((size_t)count * beta * n), 256, 0, c->stream>>>(
+        d2c, (size_t)level * n, ext, (size_t)beta * nt * n, m, count, c->log_n, c->d_primes, c->d_modup);
+  }
+  HE_CUDA(cudaGetLastError());
+  PolyBatch e = pb(ext, ext, (size_t)nt * n, (size_t)nt * n, count * beta, nt, 0, level);
+  e.skip_alpha = alpha;
+  e.skip_beta = beta;
+  HE_TRY(ntt_forward(c, e));
+  // 3. inner product with the key
+  {
+    ProfScope prof(c, "inner_product", 2.0 * count * beta * nt * n, (double)n * 8 * ((double)count * beta * nt + 2.0 * beta * nt * count + 2.0 * count * nt));
+    k_inner_product<<<grid_for((size_t)count * nt * n / 2), 256, 0, c->stream>>>(
+        ext, (size_t)beta * nt * n, d, d_stride, evk, acc, (size_t)2 * nt * n, level, alpha, beta, L, np,
+        count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  // 4. ModDown
+  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
+                           (size_t)nt * n, count * 2, alpha, level, level)));
+  {
+    ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
+    k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, level, alpha, L, count, c->log_n,
+        c->d_primes, c->d_moddown);
+  }
+  HE_CUDA(cudaGetLastError());
+  HE_TRY(ntt_forward(c, pb(conv, conv, (size_t)level * n, (size_t)level * n, count * 2, level, 0, level)));
+  const uint64_t* pinv = c->d_moddown + 2 * alpha + (size_t)alpha * L;
+  {
+    ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
+    k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha,
+        count, c->log_n, c->d_primes, pinv);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch out, Arena& ar) {
+  const uint32_t n = c->n, lt = level - 1;
+  if (level < 2) return fail(HE_ELEVEL, "rescale needs two limbs");
+  uint64_t* last = ar.take<uint64_t>((size_t)count * 2 * n);
+  uint64_t* corr = ar.take<uint64_t>((size_t)count * 2 * lt * n);
+  if (!last || !corr) return fail(HE_ENOMEM, "rescale scratch too small");
+  for (uint32_t p = 0; p < 2; ++p)
+    HE_TRY(ntt_inverse(c, pb(in.base + ((size_t)p * in.cap + lt) * n, last + (size_t)p * n, in.stride,
+                             2ull * n, count, 1, lt, c->L)));
+  {
+    ProfScope prof(c, "rescale", (double)count * 2 * n * lt, (double)count * 2 * n * 8 * (1 + lt));
+    k_rescale_corr<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(last, corr, level, count,
+                                                                            c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  HE_TRY(ntt_forward(c, pb(corr, corr, (size_t)lt * n, (size_t)lt * n, count * 2, lt, 0, c->L)));
+  {
+    ProfScope prof(c, "rescale", (double)count * 2 * lt * n, (double)count * 2 * lt * n * 8 * 3);
+    k_rescale_final<<<grid_for((size_t)count * 2 * lt * n / 2), 256, 0, c->stream>>>(
+        in, corr, out, level, count, c->log_n, c->d_primes, c->d_rescale + (size_t)lt * c->L * 2);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t count, CtBatch out,
+                    bool rescale, Arena& ar) {
+  const uint32_t n = c->n;
+  uint64_t* d01 = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  uint64_t* d2 = ar.take<uint64_t>((size_t)count * level * n);
+  uint64_t* r = rescale ? ar.take<uint64_t>((size_t)count * 2 * level * n) : nullptr;
+  if (!d01 || !d2 || (rescale && !r)) return fail(HE_ENOMEM, "multiplication scratch too small");
+  CtBatch D{d01, (size_t)2 * level * n, level, 0};
+  {
+    ProfScope prof(c, "tensor", 4.0 * count * level * n, (double)count * level * n * 8 * 7);
+    k_tensor<<<grid_for((size_t)count * level * n / 2), 256, 0, c->stream>>>(
+        A, B, D, d2, (size_t)level * n, level, count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  CtBatch R = rescale ? CtBatch{r, (size_t)2 * level * n, level, 0} : out;
+  HE_TRY(keyswitch_batch(c, d2, (size_t)level * n, level, count, c->d_rlk, D, 2, R, ar));
+  if (rescale) HE_TRY(rescale_batch(c, R, level, count, out, ar));
+  return HE_OK;
+}
+
+int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out,
+                 Arena& ar) {
+  const uint32_t n = c->n;
+  const uint64_t* key = galois_key(c, gal);
+  if (!key) return fail(HE_ENOKEY, "no Galois key for this rotation");
+  uint64_t* t = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!t) return fail(HE_ENOMEM, "rotation scratch too small");
+  CtBatch T{t, (size_t)2 * level * n, level, 0};
+  {
+    ProfScope prof(c, "automorph", 0.0, (double)count * 2 * level * n * 16);
+    k_automorph<<<grid_for((size_t)count * 2 * level * n), 256, 0, c->stream>>>(A, T, 2, level, gal, count,
+                                                                                 c->log_n);
+  }
+  HE_CUDA(cudaGetLastError());
+  return keyswitch_batch(c, t + (size_t)level * n, (size_t)2 * level * n, level, count, key, T, 1, out, ar);
+}
+
+int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count) {
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * level * c->n * 24);
+    k_addsub<<<grid_for((size_t)count * 2 * level * c->n / 2), 256, 0, c->stream>>>(A, B, O, op, level, count,
+                                                                                    c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+static LimbConsts int_consts(const he_ctx* c, int64_t k, uint32_t level) {
+  LimbConsts kc;
+  for (uint32_t t = 0; t < level; ++t) {
+    const uint64_t q = c->q[t];
+    const __int128 r = (__int128)k % (__int128)q;
+    const uint64_t v = (uint64_t)(r < 0 ? r + q : r);
+    kc.w[t] = v;
+    kc.wsh[t] = h_shoup(v, q);
+  }
+  return kc;
+}
+
+int mul_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count) {
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * level * c->n * 16);
+    k_mul_const<<<grid_for((size_t)count * 2 * level * c->n / 2), 256, 0, c->stream>>>(
+        A, O, int_consts(c, k, level), level, count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+int add_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count) {
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * level * c->n * 16);
+    k_add_const<<<grid_for((size_t)count * 2 * level * c->n / 2), 256, 0, c->stream>>>(
+        A, O, int_consts(c, k, level), level, count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+int copy_batch(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, uint32_t count) {
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * level * c->n * 16);
+    k_copy_limbs<<<grid_for((size_t)count * 2 * level * c->n / 2), 256, 0, c->stream>>>(A, O, level, count,
+                                                                                        c->log_n);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+__global__ void k_accumulate(CtBatch in, uint32_t count, CtBatch acc, uint32_t level, int log_n,
+                             const PrimeDev* primes) {
+  const uint32_t n = 1u << log_n;
+  const size_t total = (size_t)2 * level * n;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(g % n);
+    const size_t r = g / n;
+    const uint32_t t = (uint32_t)(r % level), p = (uint32_t)(r / level);
+    const uint64_t q = primes[t].q;
+    uint64_t* a = acc.base + ((size_t)p * acc.cap + t) * n + k;
+    uint64_t s = *a;
+    for (uint32_t i = 0; i < count; ++i)
+      s = add_mod(s, in.base[(size_t)i * in.stride + ((size_t)p * in.cap + t) * n + k], q);
+    *a = s;
+  }
+}
+
+int accumulate_batch(he_ctx* c, CtBatch in, uint32_t count, CtBatch acc, uint32_t level) {
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)(count + 2) * 2 * level * c->n * 8);
+    k_accumulate<<<grid_for((size_t)2 * level * c->n), 256, 0, c->stream>>>(in, count, acc, level, c->log_n,
+                                                                            c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+}  // namespace he

@@ -1,0 +1,98 @@
+"""The encrypted logistic-regression step (Eq. 5-8, Table 2) on the GPU:
+residues bit-exact against the oracle's op-for-op evaluation, and the
+decrypted weights against the FP64 update."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_10091_gb300 import workloads
+from tests.gpu_util import Pair, assert_same_residues, gpu_lib
+from tests.lr_reference import lr_step_fp64, table2
+
+pytestmark = pytest.mark.gpu
+
+
+def rot_steps(n_slots, g):
+    F = n_slots // g
+    return [g << t for t in range(int(math.log2(F)))] + \
+        [1 << t for t in range(int(math.log2(g)))] + [-(1 << t) for t in range(int(math.log2(g)))]
+
+
+@pytest.fixture(scope="module")
+def lr_pair():
+    log_n, g = 10, 4
+    return Pair(log_n, 7, 40, 1, 60, 2.0 ** 40, seed=1, rots=rot_steps((1 << log_n) // 2, g)), g
+
+
+@pytest.mark.parametrize("loss", ["binomial", "hinge", "huber"])
+def test_lr_step_bit_exact(lr_pair, loss):
+    pair, g = lr_pair
+    he = pair.he
+    nZ, level = 5, 7  # ragged: not a power of two
+    coeffs = table2()[loss]
+    lr = 1.0 / (nZ * g)
+    ms = [workloads.int_poly(10 + k, pair.n, 1 << 28) for k in range(nZ)]
+    mw = workloads.int_poly(9, pair.n, 1 << 28)
+    Zg = pair.g.new_ct(level, nZ)
+    for k in range(nZ):
+        he.he_encrypt_poly(pair.g, ms[k], 2.0 ** 40, level, Zg[k], cid=100 + k)
+    Wg = pair.gpu_enc(mw, level, 99, scale=2.0 ** 40)
+    Zo = [pair.orc_enc(ms[k], level, 100 + k, scale=2.0 ** 40) for k in range(nZ)]
+    Wo = pair.orc_enc(mw, level, 99, scale=2.0 ** 40)
+    out = pair.g.new_ct(level)
+    he.he_lr_gradient_step(pair.g, Zg, Wg, he.lr_config(coeffs, lr, g, 2.0 ** 40), out)
+    want = pair.o.lr_gradient_step(Zo, Wo, coeffs, lr, g, 2.0 ** 40)
+    assert out.level == level - 5
+    assert_same_residues(out, want, he, pair.g)
+
+
+def test_lr_step_non_uniform_inputs(lr_pair):
+    pair, g = lr_pair
+    he = pair.he
+    coeffs = table2()["binomial"]
+    ms = [workloads.int_poly(30 + k, pair.n, 1 << 28) for k in range(3)]
+    Zg = [pair.gpu_enc(m, 6, 200 + k, scale=2.0 ** 40, cap=7) for k, m in enumerate(ms)]
+    mw = workloads.int_poly(31, pair.n, 1 << 28)
+    Wg = pair.gpu_enc(mw, 6, 199, scale=2.0 ** 40)
+    out = pair.g.new_ct(6)
+    he.he_lr_gradient_step(pair.g, Zg, Wg, he.lr_config(coeffs, 0.1, g, 2.0 ** 40), out)
+    Zo = [pair.orc_enc(m, 6, 200 + k, scale=2.0 ** 40) for k, m in enumerate(ms)]
+    want = pair.o.lr_gradient_step(Zo, pair.orc_enc(mw, 6, 199, scale=2.0 ** 40), coeffs, 0.1, g,
+                                   2.0 ** 40)
+    assert_same_residues(out, want, he, pair.g)
+
+
+@pytest.mark.parametrize("loss", ["binomial", "huber"])
+def test_lr_step_accuracy_vs_fp64(lr_pair, loss):
+    pair, g = lr_pair
+    he = pair.he
+    n_slots = pair.n // 2
+    data = workloads.LRData(seed=4, n_samples=24, n_features=100)
+    coeffs = table2()[loss]
+    lr = 1.0 / data.n
+    zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+    Z = pair.g.new_ct(7, len(zs))
+    for k, v in enumerate(zs):
+        he.he_encode_encrypt(pair.g, v, 2.0 ** 40, 7, Z[k], cid=300 + k)
+    W = pair.g.new_ct(7)
+    he.he_encode_encrypt(pair.g, workloads.pack_weights(data.w0, n_slots, g), 2.0 ** 40, 7, W, cid=299)
+    out = pair.g.new_ct(7)
+    he.he_lr_gradient_step(pair.g, Z, W, he.lr_config(coeffs, lr, g, 2.0 ** 40), out)
+    got = he.he_decrypt_decode(pair.g, out)
+    want = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, lr), n_slots, g)
+    rel = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    assert rel < 2.0 ** -20, rel
+
+
+def test_lr_step_refuses_low_level(lr_pair):
+    pair, g = lr_pair
+    he = pair.he
+    Z = pair.g.new_ct(5, 2)
+    for k in range(2):
+        he.he_encrypt_poly(pair.g, workloads.int_poly(k, pair.n, 100), 2.0 ** 40, 5, Z[k], cid=k)
+    W = pair.gpu_enc(workloads.int_poly(5, pair.n, 100), 5, 5, scale=2.0 ** 40)
+    out = pair.g.new_ct(5)
+    with pytest.raises(he.HeError) as e:
+        he.he_lr_gradient_step(pair.g, Z, W, he.lr_config(table2()["binomial"], 0.1, g, 2.0 ** 40), out)
+    assert e.value.code == he.HE_ELEVEL

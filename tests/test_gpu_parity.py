@@ -1,0 +1,342 @@
+"""Parity of the sm_103a library with the CPU oracle, through the C ABI.
+
+Residues must match bit for bit (integer work); encoding (floating point
+deciding an integer) must match except where the oracle's unrounded value
+lies within 1e-6 of a rounding tie; decryption to doubles within 1e-12
+relative.  Sizes span several NTT tiles and ragged batch counts."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_10091_gb300 import workloads
+from tests.gpu_util import Pair, assert_same_residues, gpu_lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def he():
+    return gpu_lib()
+
+
+@pytest.fixture(scope="module")
+def small():
+    # N = 2^10, five 40-bit limbs, one 60-bit special prime
+    return Pair(10, 5, 40, 1, 60, 2.0 ** 40, seed=3, rots=[1, 2, 5, -1, -7])
+
+
+@pytest.fixture(scope="module")
+def digits():
+    # N = 2^11, seven 45-bit limbs, two 50-bit special primes: digits of two limbs,
+    # a partial last digit at odd levels
+    return Pair(11, 7, 45, 2, 50, 2.0 ** 45, seed=5, rots=[3, -2])
+
+
+# ------------------------------------------------------------------ parameters / NTT
+
+
+def test_primes_match(small, digits):
+    assert small.g.primes == small.o.primes
+    assert digits.g.primes == digits.o.primes
+    assert small.g.beta == small.o.beta and digits.g.beta == digits.o.beta
+
+
+@pytest.mark.parametrize("log_n", [4, 7, 10, 12, 13, 14, 15, 16])
+def test_ntt_matches_oracle(he, log_n):
+    import torch
+    L = 3
+    ctx = he.Context(log_n, L, 50, 1, 60, 2.0 ** 40, seed=1)
+    n = 1 << log_n
+    npolys = 3  # ragged: three polynomials of L + 1 limbs
+    data = workloads.residues(log_n, ctx.primes, n, parts=npolys)  # [npolys][np][n]
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, False)
+    got = t.cpu().numpy().view(np.uint64)
+    for p in range(npolys):
+        for limb in range(L + 1):
+            q, psi = ctx.primes[limb], oracle.min_root(ctx.primes[limb], log_n)
+            want = oracle.ntt_r2(data[p, limb], log_n, q, psi)
+            assert np.array_equal(got[p, limb], want), (p, limb)
+    he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, True)
+    assert np.array_equal(t.cpu().numpy().view(np.uint64), data)
+
+
+def test_ntt_limb_subset_and_prime_offset(he):
+    import torch
+    log_n, L = 12, 4
+    ctx = he.Context(log_n, L, 45, 2, 55, 2.0 ** 40, seed=2)
+    n = 1 << log_n
+    data = workloads.residues(9, ctx.primes[2:5], n, parts=2)
+    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    he.he_ntt(ctx, t, 2, 3 * n, 3, 2, False)  # limbs use primes 2, 3, 4
+    got = t.cpu().numpy().view(np.uint64)
+    for p in range(2):
+        for k in range(3):
+            q = ctx.primes[2 + k]
+            assert np.array_equal(got[p, k], oracle.ntt_r2(data[p, k], log_n, q, oracle.min_root(q, log_n)))
+
+
+# ------------------------------------------------------------------ encryption / keys
+
+
+@pytest.mark.parametrize("use_sk", [False, True])
+@pytest.mark.parametrize("level", [1, 3, 5])
+def test_encryption_is_bit_exact(small, he, use_sk, level):
+    m = workloads.int_poly(level, small.n, 1 << 35)
+    g = small.gpu_enc(m, level, cid=17 + level, use_sk=use_sk)
+    o = small.orc_enc(m, level, cid=17 + level, use_sk=use_sk)
+    assert_same_residues(g, o, he, small.g)
+
+
+def test_encryption_into_larger_buffer(small, he):
+    m = workloads.int_poly(4, small.n, 1 << 30)
+    g = small.gpu_enc(m, 3, cid=4, cap=5)
+    assert_same_residues(g, small.orc_enc(m, 3, cid=4), he, small.g)
+
+
+@pytest.mark.parametrize("level", [7, 6, 3, 1])
+def test_keyswitch_relin_bit_exact(digits, he, level):
+    import torch
+    d = workloads.residues(40 + level, digits.o.primes[:level], digits.n)[0]
+    k0, k1 = digits.o.keyswitch(d, level, -1)
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    o0 = torch.empty_like(dt)
+    o1 = torch.empty_like(dt)
+    he.he_keyswitch(digits.g, dt, level, 0, o0, o1)
+    assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
+    assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
+
+
+def test_keyswitch_galois_bit_exact(digits, he):
+    import torch
+    level = 5
+    d = workloads.residues(77, digits.o.primes[:level], digits.n)[0]
+    gal = oracle.galois_elt(11, -2)
+    k0, k1 = digits.o.keyswitch(d, level, digits.o.gal_order.index(gal))
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+    he.he_keyswitch(digits.g, dt, level, gal, o0, o1)
+    assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
+    assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
+
+
+# ------------------------------------------------------------------ ciphertext operations
+
+
+def _ct_pair(pair, seed, level, scale=None):
+    m = workloads.int_poly(seed, pair.n, 1 << 30)
+    return (pair.gpu_enc(m, level, cid=seed, scale=scale),
+            pair.orc_enc(m, level, cid=seed, scale=scale))
+
+
+@pytest.mark.parametrize("pair_name,level", [("small", 5), ("small", 2), ("digits", 7), ("digits", 4)])
+def test_mul_relin_rescale_bit_exact(request, he, pair_name, level):
+    pair = request.getfixturevalue(pair_name)
+    ga, oa = _ct_pair(pair, 101, level)
+    gb, ob = _ct_pair(pair, 102, level)
+    out = pair.g.new_ct(level)
+    he.he_mul_relin_rescale(pair.g, ga, gb, out)
+    assert_same_residues(out, pair.o.mul_relin_rescale(oa, ob), he, pair.g)
+    out2 = pair.g.new_ct(level)
+    he.he_mul_relin(pair.g, ga, gb, out2)
+    assert_same_residues(out2, pair.o.mul_relin(oa, ob), he, pair.g)
+
+
+@pytest.mark.parametrize("count", [1, 3, 16])
+def test_batched_mul_matches_single(small, he, count):
+    level = 4
+    ms = [workloads.int_poly(200 + i, small.n, 1 << 30) for i in range(2 * count)]
+    A = small.g.new_ct(level, count)
+    B = small.g.new_ct(level, count)
+    for i in range(count):
+        he.he_encrypt_poly(small.g, ms[i], small.g.scale, level, A[i], cid=300 + i)
+        he.he_encrypt_poly(small.g, ms[count + i], small.g.scale, level, B[i], cid=400 + i)
+    O = small.g.new_ct(level, count)
+    he.he_mul_relin_rescale_batch(small.g, A, B, O)
+    for i in range(count):
+        oa = small.orc_enc(ms[i], level, cid=300 + i)
+        ob = small.orc_enc(ms[count + i], level, cid=400 + i)
+        assert_same_residues(O[i], small.o.mul_relin_rescale(oa, ob), he, small.g)
+
+
+def test_batched_mul_non_uniform_buffers(small, he):
+    level = 3
+    A = [small.gpu_enc(workloads.int_poly(i, small.n, 1 << 20), level, cid=i) for i in range(3)]
+    B = [small.gpu_enc(workloads.int_poly(9 + i, small.n, 1 << 20), level, cid=9 + i) for i in range(3)]
+    O = [small.g.new_ct(level + 1) for _ in range(3)]  # separate allocations, larger capacity
+    he.he_mul_relin_rescale_batch(small.g, A, B, O)
+    for i in range(3):
+        oa = small.orc_enc(workloads.int_poly(i, small.n, 1 << 20), level, cid=i)
+        ob = small.orc_enc(workloads.int_poly(9 + i, small.n, 1 << 20), level, cid=9 + i)
+        assert_same_residues(O[i], small.o.mul_relin_rescale(oa, ob), he, small.g)
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, -1, -7])
+def test_rotation_bit_exact(small, he, r):
+    ga, oa = _ct_pair(small, 500, 4)
+    out = small.g.new_ct(4)
+    he.he_rotate(small.g, ga, r, out)
+    assert_same_residues(out, small.o.rotate(oa, r), he, small.g)
+
+
+def test_rotation_batch_and_digits(digits, he):
+    count, level = 5, 5
+    ms = [workloads.int_poly(600 + i, digits.n, 1 << 30) for i in range(count)]
+    A = digits.g.new_ct(level, count)
+    for i in range(count):
+        he.he_encrypt_poly(digits.g, ms[i], digits.g.scale, level, A[i], cid=600 + i)
+    O = digits.g.new_ct(level, count)
+    he.he_rotate_batch(digits.g, A, 3, O)
+    for i in range(count):
+        want = digits.o.rotate(digits.orc_enc(ms[i], level, cid=600 + i), 3)
+        assert_same_residues(O[i], want, he, digits.g)
+
+
+def test_rescale_add_sub_drop_bit_exact(small, he):
+    ga, oa = _ct_pair(small, 700, 5)
+    gb, ob = _ct_pair(small, 701, 5)
+    out = small.g.new_ct(5)
+    he.he_rescale(small.g, ga, out)
+    assert_same_residues(out, small.o.rescale(oa), he, small.g)
+    he.he_add(small.g, ga, gb, out)
+    assert_same_residues(out, small.o.add(oa, ob), he, small.g)
+    he.he_sub(small.g, ga, gb, out)
+    assert_same_residues(out, small.o.sub(oa, ob), he, small.g)
+    he.he_drop_level(small.g, ga, 2, out)
+    assert_same_residues(out, small.o.drop(oa, 2), he, small.g)
+    # in place
+    c = small.gpu_ct(oa)
+    he.he_add(small.g, c, gb, c)
+    assert_same_residues(c, small.o.add(oa, ob), he, small.g)
+
+
+def test_constant_and_plaintext_ops_bit_exact(small, he):
+    ga, oa = _ct_pair(small, 800, 4)
+    out = small.g.new_ct(4)
+    he.he_mul_const(small.g, ga, -0.3125, 2.0 ** 38, out)
+    assert_same_residues(out, small.o.mul_int(oa, round(-0.3125 * 2 ** 38), 2.0 ** 38), he, small.g)
+    he.he_add_const(small.g, ga, 0.7, out)
+    want = small.o.add_int(oa, int(np.round(0.7 * oa.scale)))
+    assert_same_residues(out, want, he, small.g)
+    pt = workloads.int_poly(801, small.n, 1 << 38)
+    he.he_mul_plain(small.g, ga, pt, 2.0 ** 38, out)
+    assert_same_residues(out, small.o.mul_plain(oa, pt, 2.0 ** 38), he, small.g)
+
+
+# ------------------------------------------------------------------ encode / decrypt
+
+
+@pytest.mark.parametrize("log_n,logscale", [(10, 40), (12, 30), (14, 40), (16, 50)])
+def test_encode_matches_oracle_away_from_ties(he, log_n, logscale):
+    ctx = he.Context(log_n, 2, 50, 1, 60, 2.0 ** logscale)
+    o = oracle.Oracle(log_n, 2, 50, 1, 60, 2.0 ** logscale)
+    z = workloads.uniform_slots(log_n, ctx.n // 2)
+    got = he.he_encode(ctx, z, 2.0 ** logscale)
+    raw = o.encode_raw(z, scale=2.0 ** logscale)
+    want = o.encode(z, scale=2.0 ** logscale)
+    # the two sides sum in different orders; both round half away from zero
+    # unrounded values agree to a few units in the last place of Delta-sized doubles
+    tol = max(1e-6, 2.0 ** (logscale - 52) * log_n * 4)
+    frac = np.abs(np.abs(raw - np.trunc(raw)) - 0.5)
+    near_tie = frac < tol
+    assert np.array_equal(got[~near_tie], want[~near_tie])
+    assert np.all(np.abs(got - want) <= max(1, math.ceil(tol)))
+
+
+def test_decrypt_matches_oracle(small, he):
+    for level in (1, 3, 5):
+        ga, oa = _ct_pair(small, 900 + level, level)
+        got = he.he_decrypt_poly(small.g, ga)
+        want = small.o.decrypt_coeffs(oa)
+        assert np.allclose(got, want, rtol=1e-12, atol=0)
+        # decoding: compare with the oracle's decode of the same coefficients
+        re = he.he_decrypt_decode(small.g, ga)
+        ore, _ = small.o.decode(want, oa.scale)
+        assert np.max(np.abs(re - ore)) < 1e-9
+
+
+# ------------------------------------------------------------------ accuracy (decrypted vs FP64)
+
+
+def test_cfg1_mul_accuracy_and_parity(he):
+    """N = 2^12, three ~40-bit limbs + one special prime, 2^30 scale, 16 pairs
+    of 2048 uniform slots: each product within 1e-4 of FP64.  The second
+    operand is encoded at the prime the rescale divides by, so the product
+    lands back at scale 2^30."""
+    p = Pair(12, 3, 40, 1, 60, 2.0 ** 30, seed=0)
+    level, count = 3, 16
+    qlast = float(p.g.primes[level - 1])
+    A = p.g.new_ct(level, count)
+    B = p.g.new_ct(level, count)
+    zs = []
+    for i in range(count):
+        za = workloads.uniform_slots(2 * i, 2048)
+        zb = workloads.uniform_slots(2 * i + 1, 2048)
+        zs.append((za, zb))
+        he.he_encode_encrypt(p.g, za, 2.0 ** 30, level, A[i], cid=2 * i)
+        he.he_encode_encrypt(p.g, zb, qlast, level, B[i], cid=2 * i + 1)
+    O = p.g.new_ct(level, count)
+    he.he_mul_relin_rescale_batch(p.g, A, B, O)
+    worst = 0.0
+    for i in range(count):
+        assert O[i].scale == pytest.approx(2.0 ** 30, rel=1e-12)
+        got = he.he_decrypt_decode(p.g, O[i], 2048)
+        worst = max(worst, float(np.max(np.abs(got - zs[i][0] * zs[i][1]))))
+    assert worst < 1e-4, worst
+    # bit-exact against the oracle on the first pair, inputs from the oracle encoder
+    ma = p.o.encode(zs[0][0], scale=2.0 ** 30)
+    mb = p.o.encode(zs[0][1], scale=qlast)
+    oa = p.o.encrypt(ma, level, cid=50, scale=2.0 ** 30)
+    ob = p.o.encrypt(mb, level, cid=51, scale=qlast)
+    ga, gb = p.gpu_enc(ma, level, 50, scale=2.0 ** 30), p.gpu_enc(mb, level, 51, scale=qlast)
+    out = p.g.new_ct(level)
+    he.he_mul_relin_rescale(p.g, ga, gb, out)
+    assert_same_residues(out, p.o.mul_relin_rescale(oa, ob), he, p.g)
+
+
+def test_rotation_accuracy(small, he):
+    z = workloads.uniform_slots(11, small.n // 2)
+    a = small.g.new_ct(3)
+    he.he_encode_encrypt(small.g, z, 2.0 ** 40, 3, a, cid=11)
+    out = small.g.new_ct(3)
+    for r in (1, -7):
+        he.he_rotate(small.g, a, r, out)
+        got = he.he_decrypt_decode(small.g, out)
+        assert np.max(np.abs(got - np.roll(z, -r))) < 2.0 ** -20
+
+
+def test_refresh_round_trip(small, he):
+    z = workloads.uniform_slots(12, small.n // 2)
+    a = small.g.new_ct(5)
+    he.he_encode_encrypt(small.g, z, 2.0 ** 40, 2, a, cid=12)
+    out = small.g.new_ct(5)
+    he.he_refresh(small.g, a, 5, 2.0 ** 40, 99, out)
+    assert out.level == 5 and out.scale == 2.0 ** 40
+    got = he.he_decrypt_decode(small.g, out)
+    assert np.max(np.abs(got - z)) < 2.0 ** -20
+
+
+# ------------------------------------------------------------------ errors
+
+
+def test_errors_are_reported(small, he):
+    ga, _ = _ct_pair(small, 1000, 3)
+    out = small.g.new_ct(3)
+    with pytest.raises(he.HeError) as e:
+        he.he_rotate(small.g, ga, 3, out)  # no key for step 3
+    assert e.value.code == he.HE_ENOKEY
+    one = small.g.new_ct(1)
+    gb = small.gpu_enc(workloads.int_poly(1, small.n, 10), 1, cid=1)
+    with pytest.raises(he.HeError) as e:
+        he.he_mul_relin_rescale(small.g, gb, gb, one)
+    assert e.value.code == he.HE_ELEVEL
+    gc = small.gpu_enc(workloads.int_poly(2, small.n, 10), 3, cid=2, scale=2.0 ** 20)
+    with pytest.raises(he.HeError) as e:
+        he.he_add(small.g, ga, gc, out)
+    assert e.value.code == he.HE_ESCALE
+    small_out = small.g.new_ct(1)
+    with pytest.raises(he.HeError) as e:
+        he.he_add(small.g, ga, ga, small_out)
+    assert e.value.code == he.HE_EINVAL
