@@ -32,7 +32,10 @@ import numpy as np  # noqa: E402
 METRIC = "HE mul+relin+rescale/s and enc-LR grad steps/s, batched vs plain, 1 GB300"
 LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE = 14, 8, 40, 1, 60, 2.0 ** 40
 N_SAMPLES, N_FEATURES, G = 4096, 784, 8
-MASK_SCALE = 2.0 ** 40
+# The mask scale sets the scale of the polynomial's result (2^53 here) so that
+# the smallest constant, c3 * lr = 4.9e-8, is still encoded with ~2^28 of
+# relative precision; the mask itself keeps 2^24 (value (2^27/8) cos(...)).
+MASK_SCALE = 2.0 ** 27
 WORKLOAD = ("enc-LR gradient step (Eq. 7-8, Table 2 binomial): N=2^14, 8x40-bit limbs + 1x60-bit "
             "special prime, scale 2^40; 4096 samples x 784 features, 8 samples per ciphertext "
             "(512 data ciphertexts); one step = 2048 mul+relin+rescale + 5126 rotations")
@@ -122,9 +125,11 @@ def measured_peaks():
 
 
 # Integer-pipe roof: 152 SMs x 2070 MHz x 64 32-bit multiply-adds per clock per
-# SM; a 64-bit Shoup butterfly needs 10 32-bit multiplies (4 for the high
-# product of a*w', 3 each for the two low products).
-ALU_BFLY_PEAK = 152 * 2.070e9 * 64 / 10
+# SM (a register-resident IMAD chain reaches 60.4/clk/SM), divided by the 17.3
+# IMAD-pipe slots one 64-bit Shoup product takes (a register-resident chain of
+# Shoup products reaches 64/17.3 = 3.69 per clock per SM): one butterfly = one
+# Shoup product, so the transform roof is 1.16 T butterflies/s.
+ALU_BFLY_PEAK = 152 * 2.070e9 * 64 / 17.3
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
@@ -144,7 +149,7 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
                     "unit": "Gbutterfly/s", "frac": frac_alu, "traffic": None,
                     "per_launch_ms": per_launch_ms, "launches": p["launches"],
                     "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
-                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 10 IMAD per 64-bit butterfly"}
+                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots per 64-bit Shoup butterfly"}
     return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": gbs / hbm_peak, "traffic": None, "per_launch_ms": per_launch_ms,
             "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
@@ -209,7 +214,9 @@ def run_ours(args, rank: int, world: int):
     with ClockSampler(uuid) as clk:
         e0.record(stream)
         for _ in range(args.steps):
+            torch.cuda.nvtx.range_push("lr_step")  # lets ncu capture exactly the timed steps
             step()
+            torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -394,8 +401,45 @@ def run_reference(args, rank: int):
     print(json.dumps(line))
 
 
+def run_micro(args):
+    """One kernel class alone: forward/inverse NTT over `--polys` polynomials
+    of 8 limbs at N = 2^log_n (more than L2), timed with CUDA events."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10091_gb300 as he
+    from paper_2006_10091_gb300 import workloads
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    log_n, nl = args.log_n, 8
+    ctx = he.Context(log_n, nl, LIMB_BITS, 1, SPECIAL_BITS, SCALE, seed=0, stream=stream.cuda_stream)
+    n = 1 << log_n
+    host = workloads.residues(1, ctx.primes[:nl], n, parts=args.polys)
+    t = torch.from_numpy(host.view(np.int64)).cuda()
+    out = {}
+    for inverse in (False, True):
+        for _ in range(args.warmup):
+            he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        limbs = args.polys * nl
+        bfly = limbs * (n / 2) * log_n
+        out["intt" if inverse else "ntt"] = {
+            "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_BFLY_PEAK,
+            "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
+    print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--micro", choices=["ntt"], default=None, help="time one kernel class alone")
+    ap.add_argument("--log-n", type=int, default=14)
+    ap.add_argument("--polys", type=int, default=256)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
@@ -403,6 +447,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.micro:
+        run_micro(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

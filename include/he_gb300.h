@@ -94,6 +94,12 @@ int he_set_stream(he_ctx* ctx, void* stream);
 /* Synchronise the context's stream. */
 int he_sync(he_ctx* ctx);
 
+/* Tuning knobs (results never depend on them): "chunk_bytes" = scratch budget
+ * of one batched operation (default 2^31), "lr_chunk" = data ciphertexts per
+ * chunk of the logistic-regression step (0 = from the budget).  HE_EINVAL for
+ * an unknown key or a value out of range. */
+int he_set_tuning(he_ctx* ctx, const char* key, double value);
+
 /* Context facts: N, L, alpha, beta (digits at the top level), and the
  * L + alpha primes (limbs first) into primes_out (may be NULL). */
 int he_ctx_info(const he_ctx* ctx, uint32_t* n, uint32_t* n_limbs, uint32_t* n_special,
@@ -200,6 +206,31 @@ typedef struct he_lr_config {
 
 int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
                         const he_lr_config* cfg, he_ct* W_out);
+
+/* The paper's K workers (Sec. 4, Fig. 1; Algorithm 1) as independent
+ * instances on one GPU, all stepped in one batched launch sequence.  Shard k
+ * holds its own data ciphertexts Z[0..nZ) (one level, one scale), its weights
+ * W and an output buffer W_out.  A shard whose weights sit below level 6 (too
+ * few limbs for the step's five rescales) first goes through the in-process
+ * key-holder refresh (Algorithm 1 lines 8-10) to refresh_level (0 = refuse
+ * with HE_ELEVEL); the step then runs at the weights' level l with the data
+ * taken at l, and W_out receives level l - 5 and W's scale.  Shards with the
+ * same level and scales share every kernel launch; their data ciphertexts
+ * are processed together in chunks.  With HE_LR_GRAPH the whole launch
+ * sequence is captured once per distinct call (same buffers, sizes and
+ * configuration) as a CUDA graph and replayed; this needs a non-default
+ * stream, and a replay reuses the refresh encryptions' random streams. */
+typedef struct he_lr_shard {
+  const he_ct* Z;
+  size_t nZ;
+  const he_ct* W;
+  he_ct* W_out;
+} he_lr_shard;
+
+#define HE_LR_GRAPH 1
+
+int he_lr_gradient_step_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count,
+                                const he_lr_config* cfg, uint32_t refresh_level, int flags);
 
 /* The key holder's refresh (Algorithm 1 lines 8-10, Algorithm 2 lines 8-11),
  * simulated in-process: decrypt, decode, re-encode at out_scale and encrypt

@@ -40,6 +40,14 @@ class he_ct(ctypes.Structure):
                 ("cap", ctypes.c_uint32), ("scale", ctypes.c_double)]
 
 
+class he_lr_shard(ctypes.Structure):
+    _fields_ = [("Z", ctypes.c_void_p), ("nZ", ctypes.c_size_t), ("W", ctypes.c_void_p),
+                ("W_out", ctypes.c_void_p)]
+
+
+HE_LR_GRAPH = 1
+
+
 class he_lr_config(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_double * 4), ("lr", ctypes.c_double),
                 ("g", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mask_scale", ctypes.c_double)]
@@ -95,6 +103,9 @@ def load():
         "he_profile_enable": [VP, ctypes.c_int],
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
+        "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
+        "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
+                                        ctypes.c_uint32, ctypes.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -222,6 +233,10 @@ def _batch(cts):
 def he_set_stream(ctx: Context, stream):
     ctx.stream = stream
     _check(load().he_set_stream(ctx.ptr, ctypes.c_void_p(stream)))
+
+
+def he_set_tuning(ctx: Context, key: str, value: float):
+    _check(load().he_set_tuning(ctx.ptr, key.encode(), float(value)))
 
 
 def he_sync(ctx: Context):
@@ -353,6 +368,23 @@ def he_lr_gradient_step(ctx, Z: list, W: Ciphertext, cfg: he_lr_config, W_out: C
                                       ctypes.byref(Os)))
     W_out.update(Os)
     return W_out
+
+
+def he_lr_gradient_step_workers(ctx, shards: list, cfg: he_lr_config, refresh_level: int = 0,
+                                graph: bool = False):
+    """shards: list of (Z list, W, W_out) per worker."""
+    keep = []
+    arr = (he_lr_shard * len(shards))()
+    for k, (Z, W, W_out) in enumerate(shards):
+        zs, w, wo = _batch(Z), W.c(), W_out.c()
+        keep.append((zs, w, wo))
+        arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w),
+                             ctypes.addressof(wo))
+    _check(load().he_lr_gradient_step_workers(ctx.ptr, arr, len(shards), ctypes.byref(cfg), refresh_level,
+                                              HE_LR_GRAPH if graph else 0))
+    for (Z, W, W_out), (_, _, wo) in zip(shards, keep):
+        W_out.update(wo)
+    return [s[2] for s in shards]
 
 
 def he_refresh(ctx, a, level: int, out_scale: float, cid: int, out):

@@ -108,6 +108,7 @@ static void destroy(he_ctx* c) {
   cudaFree(c->d_rlk);
   for (auto& kv : c->gal) cudaFree(kv.second);
   for (auto& kv : c->lr_masks) cudaFree(kv.second);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   cudaFree(c->ws.ptr);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   prof_clear(c);
@@ -200,6 +201,21 @@ int he_set_stream(he_ctx* c, void* stream) {
 int he_sync(he_ctx* c) {
   if (!c) return fail(HE_EINVAL, "null context");
   HE_CUDA(cudaStreamSynchronize(c->stream));
+  return HE_OK;
+}
+
+int he_set_tuning(he_ctx* c, const char* key, double value) {
+  if (!c || !key) return fail(HE_EINVAL, "he_set_tuning: null argument");
+  const std::string k(key);
+  if (k == "chunk_bytes") {
+    if (!(value >= (1 << 20) && value <= 1e13)) return fail(HE_EINVAL, "chunk_bytes out of range");
+    c->chunk_bytes = (size_t)value;
+  } else if (k == "lr_chunk") {
+    if (!(value >= 0 && value <= 1 << 20)) return fail(HE_EINVAL, "lr_chunk out of range");
+    c->lr_chunk = (uint32_t)value;
+  } else {
+    return fail(HE_EINVAL, "unknown tuning key " + k);
+  }
   return HE_OK;
 }
 

@@ -25,10 +25,12 @@
 //   H  = G + rot(G, 1) + ... ;  R = rescale(H (x) mask) ;  R += rot(R, -1) + ...
 //   W' = drop(W) + R                        (scale sW, level l0-5)
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "he_ops.h"
@@ -121,11 +123,12 @@ static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_
   return HE_OK;
 }
 
-// Per-ciphertext words of the circuit's intermediates at input level l0.
+// Per-ciphertext words of the circuit's intermediates at input level l0:
+// U, T, A, C, B, Q, Gk, Tmp, and the gathered copies of Z and W.
 static size_t lr_ct_words(const he_ctx* c, uint32_t l0) {
   const size_t n = c->n;
-  // U, T, A, C, B, Q, Gk, tmp, Zc copy
-  return n * 2 * ((l0 - 1) + (l0 - 2) + (l0 - 2) + (l0 - 3) + (l0 - 2) + (l0 - 3) + (l0 - 4) + (l0 - 1) + l0);
+  return n * 2 * ((l0 - 1) + (l0 - 2) + (l0 - 2) + (l0 - 3) + (l0 - 2) + (l0 - 3) + (l0 - 4) + (l0 - 1) + 2 * l0) +
+         10 * 32;
 }
 
 static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk) {
@@ -135,139 +138,394 @@ static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk) {
   return w + 64;
 }
 
+struct LrGal {
+  std::vector<uint64_t> in, up, down;
+};
+
+static int lr_gal(he_ctx* c, const LrPlan& P, LrGal* gl) {
+  gl->in.clear();
+  gl->up.clear();
+  gl->down.clear();
+  for (uint32_t t = 0; t < P.logF; ++t) gl->in.push_back(h_galois_elt(c->log_n, (int32_t)(P.g << t)));
+  for (uint32_t t = 0; t < P.logg; ++t) {
+    gl->up.push_back(h_galois_elt(c->log_n, (int32_t)(1u << t)));
+    gl->down.push_back(h_galois_elt(c->log_n, -(int32_t)(1u << t)));
+  }
+  for (auto* v : {&gl->in, &gl->up, &gl->down})
+    for (uint64_t e : *v)
+      if (e != 1 && !galois_key(c, e)) return fail(HE_ENOKEY, "missing Galois key for the step's rotations");
+  return HE_OK;
+}
+
+struct LrBufs {
+  CtBatch U, T, A, Cc, B, Q, Gk, Tmp, Zcopy, Wrep;
+};
+
+static CtBatch carve(Arena& a, size_t count, uint32_t cap, uint32_t n) {
+  uint64_t* p = a.take<uint64_t>(count * 2 * cap * n);
+  return CtBatch{p, (uint64_t)2 * cap * n, cap, 0};
+}
+
+// The per-ciphertext part of the step for m data ciphertexts Zc with weights
+// Wc (stride 0: one W for all): G_k = p(M_k) * Z_k in b.Gk.
+static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtBatch Wc, uint32_t m, LrBufs& b,
+                    Arena& ops) {
+  const uint32_t l0 = P.l0;
+  auto fresh = [&]() -> Arena& {
+    ops.off = 0;
+    return ops;
+  };
+  // U = Z_k * W, then the rotate-and-sum over the F feature positions
+  HE_TRY(mul_relin_batch(c, Zc, Wc, l0, m, b.U, true, fresh()));
+  for (uint32_t t = 0; t < P.logF; ++t) {
+    HE_TRY(rotate_batch(c, b.U, l0 - 1, m, gl.in[t], b.Tmp, fresh()));
+    HE_TRY(addsub_batch(c, b.U, b.Tmp, b.U, 0, l0 - 1, m));
+  }
+  // T = M^2; A = c3 M; C = T A
+  HE_TRY(mul_relin_batch(c, b.U, b.U, l0 - 1, m, b.T, true, fresh()));
+  HE_TRY(mul_int_batch(c, b.U, b.Tmp, P.kA, l0 - 1, m));
+  HE_TRY(rescale_batch(c, b.Tmp, l0 - 1, m, b.A, fresh()));
+  HE_TRY(mul_relin_batch(c, b.T, b.A, l0 - 2, m, b.Cc, true, fresh()));
+  // B = c1 M (dropped to l0-3); Q = c2 M^2
+  HE_TRY(mul_int_batch(c, b.U, b.Tmp, P.kB, l0 - 1, m));
+  HE_TRY(rescale_batch(c, b.Tmp, l0 - 1, m, b.B, fresh()));
+  HE_TRY(addsub_batch(c, b.Cc, b.B, b.Cc, 0, l0 - 3, m));
+  if (P.has_c2) {
+    HE_TRY(mul_int_batch(c, b.T, b.Tmp, P.kQ, l0 - 2, m));
+    HE_TRY(rescale_batch(c, b.Tmp, l0 - 2, m, b.Q, fresh()));
+    HE_TRY(addsub_batch(c, b.Cc, b.Q, b.Cc, 0, l0 - 3, m));
+  }
+  HE_TRY(add_int_batch(c, b.Cc, b.Cc, P.k0, l0 - 3, m));
+  // G_k = S * Z_k
+  HE_TRY(mul_relin_batch(c, b.Cc, Zc, l0 - 3, m, b.Gk, true, fresh()));
+  return HE_OK;
+}
+
+// The per-feature sum over the g samples, the mask and the replication, for
+// `count` accumulated gradients G (uniform); result R (uniform, level l0-5).
+static int lr_finish(he_ctx* c, const LrPlan& P, const LrGal& gl, const int64_t* mask, CtBatch G, uint32_t count,
+                     CtBatch H1, CtBatch R, Arena& ops) {
+  const uint32_t l0 = P.l0;
+  auto fresh = [&]() -> Arena& {
+    ops.off = 0;
+    return ops;
+  };
+  for (uint32_t t = 0; t < P.logg; ++t) {
+    HE_TRY(rotate_batch(c, G, l0 - 4, count, gl.up[t], H1, fresh()));
+    HE_TRY(addsub_batch(c, G, H1, G, 0, l0 - 4, count));
+  }
+  HE_TRY(mul_plain_dev(c, G, mask, H1, l0 - 4, count, fresh()));
+  HE_TRY(rescale_batch(c, H1, l0 - 4, count, R, fresh()));
+  for (uint32_t t = 0; t < P.logg; ++t) {
+    HE_TRY(rotate_batch(c, R, l0 - 5, count, gl.down[t], H1, fresh()));
+    HE_TRY(addsub_batch(c, R, H1, R, 0, l0 - 5, count));
+  }
+  return HE_OK;
+}
+
+// One worker's inputs after validation.
+struct Shard {
+  const he_ct* Z;
+  size_t nZ;
+  he_ct W;       // weights at the level the step runs at (refreshed if needed)
+  he_ct* W_out;
+  uint32_t l0;
+  bool refresh;
+  const he_ct* W_in;
+};
+
+static int check_aligned(const void* p) { return ((uintptr_t)p & 15) == 0 ? HE_OK : HE_EINVAL; }
+
+// Runs the step for every shard.  Shards sharing (level, scales) are batched:
+// their data ciphertexts go through the same kernels in chunks, each chunk's
+// per-ciphertext results are summed into their shard's gradient, and the
+// final stage runs once over all shards of the group.
+static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, uint32_t refresh_level,
+                  Arena& pool) {
+  const uint32_t n = c->n;
+  // in-process refresh of weights below the circuit's depth (Algorithm 1 lines 8-10)
+  for (size_t k = 0; k < sh.size(); ++k) {
+    if (!sh[k].refresh) continue;
+    const size_t words = (size_t)sh[k].W_in->level * n + 2 * n + 2 * n * 2 + n + 4 * (size_t)refresh_level * n;
+    Arena a = pool;  // scratch after the refreshed buffers, reused per shard
+    uint64_t* m = a.take<uint64_t>((size_t)sh[k].W_in->level * n);
+    double* d = a.take<double>(n);
+    double* re = a.take<double>(n);
+    double2* fft = a.take<double2>(2 * n);
+    int64_t* coeffs = a.take<int64_t>(n);
+    int* ovf = a.take<int>(1);
+    uint64_t* scratch = a.take<uint64_t>((size_t)4 * refresh_level * n);
+    (void)words;
+    if (!scratch) return fail(HE_ENOMEM, "refresh scratch too small");
+    HE_TRY(decrypt_dev(c, sh[k].W_in, m, d));
+    HE_TRY(decode_dev(c, d, sh[k].W_in->scale, re, n / 2, fft));
+    HE_TRY(encode_dev(c, re, n / 2, sh[k].W.scale, coeffs, fft, ovf));
+    HE_TRY(encrypt_dev(c, coeffs, refresh_level, 0, 0x40000000u + (uint32_t)k, &sh[k].W, scratch));
+  }
+  // groups of shards that share the plan
+  std::vector<bool> done(sh.size(), false);
+  for (size_t k0 = 0; k0 < sh.size(); ++k0) {
+    if (done[k0]) continue;
+    std::vector<size_t> grp;
+    for (size_t k = k0; k < sh.size(); ++k)
+      if (!done[k] && sh[k].l0 == sh[k0].l0 && sh[k].Z[0].scale == sh[k0].Z[0].scale &&
+          sh[k].W.scale == sh[k0].W.scale) {
+        grp.push_back(k);
+        done[k] = true;
+      }
+    const uint32_t l0 = sh[k0].l0;
+    LrPlan P;
+    HE_TRY(lr_plan(c, l0, sh[k0].Z[0].scale, sh[k0].W.scale, cfg, &P));
+    LrGal gl;
+    HE_TRY(lr_gal(c, P, &gl));
+    const int64_t* mask = nullptr;
+    HE_TRY(lr_mask(c, P.g, cfg->mask_scale, &mask));
+    size_t total = 0;
+    for (size_t k : grp) total += sh[k].nZ;
+    const uint32_t ns = (uint32_t)grp.size();
+    Arena a = pool;
+    CtBatch G = carve(a, ns, l0 - 4, n), H1 = carve(a, ns, l0 - 4, n), R = carve(a, ns, l0 - 4, n);
+    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1)) * sizeof(uint64_t);
+    size_t chunk = std::max<size_t>(1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, total));
+    LrBufs b;
+    b.U = carve(a, chunk, l0 - 1, n);
+    b.T = carve(a, chunk, l0 - 2, n);
+    b.A = carve(a, chunk, l0 - 2, n);
+    b.Cc = carve(a, chunk, l0 - 3, n);
+    b.B = carve(a, chunk, l0 - 2, n);
+    b.Q = carve(a, chunk, l0 - 3, n);
+    b.Gk = carve(a, chunk, l0 - 4, n);
+    b.Tmp = carve(a, chunk, l0 - 1, n);
+    b.Zcopy = carve(a, chunk, l0, n);
+    b.Wrep = carve(a, chunk, l0, n);
+    Arena ops;
+    ops.base = a.base + a.off;
+    ops.size = a.size > a.off ? a.size - a.off : 0;
+    if (!b.Wrep.base || ops.size < lr_op_words(c, l0, (uint32_t)chunk) * sizeof(uint64_t))
+      return fail(HE_ENOMEM, "step scratch too small");
+    HE_CUDA(cudaMemsetAsync(G.base, 0, sizeof(uint64_t) * G.stride * ns, c->stream));
+    // walk the group's data ciphertexts chunk by chunk
+    size_t gi = 0, idx = 0;  // shard position in grp, ciphertext index in that shard
+    while (gi < grp.size()) {
+      // segments of this chunk: (group position, first ciphertext, count)
+      std::vector<std::pair<size_t, std::pair<size_t, size_t>>> seg;
+      size_t m = 0;
+      while (m < chunk && gi < grp.size()) {
+        const Shard& s = sh[grp[gi]];
+        const size_t take = std::min(chunk - m, s.nZ - idx);
+        seg.push_back({gi, {idx, take}});
+        m += take;
+        idx += take;
+        if (idx == s.nZ) {
+          ++gi;
+          idx = 0;
+        }
+      }
+      CtBatch Zc, Wc;
+      CtBatch zu;
+      const Shard& s0 = sh[grp[seg[0].first]];
+      if (seg.size() == 1 && uniform_view(s0.Z + seg[0].second.first, seg[0].second.second, &zu)) {
+        Zc = zu;
+        Wc = CtBatch{s0.W.data, 0, s0.W.cap, 0};
+      } else {
+        size_t off = 0;
+        for (auto& sg : seg) {
+          const Shard& s = sh[grp[sg.first]];
+          const size_t first = sg.second.first, cnt = sg.second.second;
+          CtBatch dz = b.Zcopy, dw = b.Wrep;
+          dz.base += off * b.Zcopy.stride;
+          dw.base += off * b.Wrep.stride;
+          if (uniform_view(s.Z + first, cnt, &zu)) {
+            HE_TRY(copy_batch(c, zu, dz, l0, (uint32_t)cnt));
+          } else {
+            for (size_t i = 0; i < cnt; ++i) {
+              CtBatch one{s.Z[first + i].data, 0, s.Z[first + i].cap, 0}, d1 = dz;
+              d1.base += i * b.Zcopy.stride;
+              HE_TRY(copy_batch(c, one, d1, l0, 1));
+            }
+          }
+          HE_TRY(copy_batch(c, CtBatch{s.W.data, 0, s.W.cap, 0}, dw, l0, (uint32_t)cnt));
+          off += cnt;
+        }
+        Zc = b.Zcopy;
+        Wc = b.Wrep;
+      }
+      HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops));
+      size_t off = 0;
+      for (auto& sg : seg) {
+        CtBatch gk = b.Gk, gs = G;
+        gk.base += off * b.Gk.stride;
+        gs.base += sg.first * G.stride;
+        HE_TRY(accumulate_batch(c, gk, (uint32_t)sg.second.second, gs, l0 - 4));
+        off += sg.second.second;
+      }
+    }
+    HE_TRY(lr_finish(c, P, gl, mask, G, ns, H1, R, ops));
+    for (uint32_t i = 0; i < ns; ++i) {
+      Shard& s = sh[grp[i]];
+      CtBatch r = R;
+      r.base += (size_t)i * R.stride;
+      HE_TRY(addsub_batch(c, CtBatch{s.W.data, 0, s.W.cap, 0}, r, CtBatch{s.W_out->data, 0, s.W_out->cap, 0}, 0,
+                          l0 - 5, 1));
+    }
+  }
+  return HE_OK;
+}
+
+// Workspace words lr_run needs for these shards.
+static size_t lr_words(he_ctx* c, const std::vector<Shard>& sh, uint32_t refresh_level) {
+  const size_t n = c->n;
+  size_t need = 0;
+  std::map<uint32_t, std::pair<size_t, size_t>> groups;  // l0 -> (shards, ciphertexts)
+  for (const Shard& s : sh) {
+    groups[s.l0].first += 1;
+    groups[s.l0].second += s.nZ;
+  }
+  for (auto& kv : groups) {
+    const uint32_t l0 = kv.first;
+    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1)) * sizeof(uint64_t);
+    const size_t chunk = std::max<size_t>(
+        1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, kv.second.second));
+    const size_t w = 3 * kv.second.first * 2 * (l0 - 4) * n + chunk * lr_ct_words(c, l0) +
+                     lr_op_words(c, l0, (uint32_t)chunk) + 4096;
+    need = std::max(need, w);
+  }
+  const size_t ref = (size_t)c->L * n + 2 * n + 4 * n + n + 4 * (size_t)refresh_level * n + 4096;
+  return std::max(need, ref);
+}
+
+static int validate_shard(he_ctx* c, const he_lr_shard& in, const he_lr_config* cfg, uint32_t refresh_level,
+                          Shard* out) {
+  if (!in.Z || in.nZ == 0 || !in.W || !in.W->data || !in.W_out || !in.W_out->data)
+    return fail(HE_EINVAL, "shard: null argument or no data ciphertexts");
+  const uint32_t zl = in.Z[0].level;
+  for (size_t k = 0; k < in.nZ; ++k) {
+    const he_ct& z = in.Z[k];
+    if (!z.data || z.level != zl || z.cap < z.level || z.level > (uint32_t)c->L)
+      return fail(HE_EINVAL, "shard: data ciphertexts must share one level");
+    if (check_aligned(z.data)) return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
+    if (!scales_eq(z.scale, in.Z[0].scale)) return fail(HE_ESCALE, "data ciphertexts at different scales");
+  }
+  if (check_aligned(in.W->data) || check_aligned(in.W_out->data))
+    return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
+  out->Z = in.Z;
+  out->nZ = in.nZ;
+  out->W_in = in.W;
+  out->W_out = in.W_out;
+  out->W = *in.W;
+  out->refresh = false;
+  uint32_t wl = in.W->level;
+  if (wl < 6) {
+    if (!refresh_level) return fail(HE_ELEVEL, "the step needs inputs at level >= 6: refresh the weights");
+    if (refresh_level < 6 || refresh_level > zl) return fail(HE_EINVAL, "refresh level must be in [6, data level]");
+    out->refresh = true;
+    wl = refresh_level;
+  }
+  if (wl > zl) return fail(HE_EINVAL, "weights above the data's level");
+  out->l0 = wl;
+  if (in.W_out->cap < wl - 5) return fail(HE_EINVAL, "output capacity too small");
+  const uint32_t g = cfg->g;
+  if (g < 1 || (g & (g - 1)) || g > (uint32_t)c->n / 2) return fail(HE_EINVAL, "g must be a power of two <= N/2");
+  if (!(cfg->mask_scale > 0.0)) return fail(HE_EINVAL, "mask_scale must be positive");
+  return HE_OK;
+}
+
 }  // namespace he
 
 using namespace he;
 
-extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const he_ct* W, const he_lr_config* cfg,
-                                   he_ct* W_out) {
-  if (!c || !Z || !W || !cfg || !W_out || !W_out->data || !W->data) return fail(HE_EINVAL, "he_lr_gradient_step: null argument");
-  if (nZ == 0) return fail(HE_EINVAL, "he_lr_gradient_step: no data ciphertexts");
-  const uint32_t n = c->n;
-  const uint32_t l0 = W->level;
-  if (l0 < 6 || l0 > (uint32_t)c->L || W->cap < l0) return fail(HE_ELEVEL, "the step needs inputs at level >= 6");
-  for (size_t k = 0; k < nZ; ++k) {
-    if (!Z[k].data || Z[k].level != l0 || Z[k].cap < l0) return fail(HE_EINVAL, "data and weights must share one level");
-    if ((uintptr_t)Z[k].data & 15) return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
-    if (!scales_eq(Z[k].scale, Z[0].scale)) return fail(HE_ESCALE, "data ciphertexts at different scales");
+static int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
+                    uint32_t refresh_level, int flags) {
+  if (!c || !shards || !cfg || count == 0) return fail(HE_EINVAL, "he_lr: null argument");
+  std::vector<Shard> sh(count);
+  for (size_t k = 0; k < count; ++k) HE_TRY(validate_shard(c, shards[k], cfg, refresh_level, &sh[k]));
+  // plans, keys and masks are checked (and masks encoded) before any capture
+  for (size_t k = 0; k < count; ++k) {
+    LrPlan P;
+    HE_TRY(lr_plan(c, sh[k].l0, sh[k].Z[0].scale, sh[k].refresh ? sh[k].W_in->scale : sh[k].W.scale, cfg, &P));
+    LrGal gl;
+    HE_TRY(lr_gal(c, P, &gl));
+    const int64_t* mask = nullptr;
+    HE_TRY(lr_mask(c, P.g, cfg->mask_scale, &mask));
   }
-  const uint32_t g = cfg->g;
-  if (g < 1 || (g & (g - 1)) || g > n / 2) return fail(HE_EINVAL, "g must be a power of two <= N/2");
-  if (!(cfg->mask_scale > 0.0)) return fail(HE_EINVAL, "mask_scale must be positive");
-  if (W_out->cap < l0 - 5) return fail(HE_EINVAL, "output capacity too small");
-  if (((uintptr_t)W->data & 15) || ((uintptr_t)W_out->data & 15)) return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
-  LrPlan P;
-  HE_TRY(lr_plan(c, l0, Z[0].scale, W->scale, cfg, &P));
-  std::vector<uint64_t> gal_in, gal_up, gal_down;
-  for (uint32_t t = 0; t < P.logF; ++t) gal_in.push_back(h_galois_elt(c->log_n, (int32_t)(g << t)));
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    gal_up.push_back(h_galois_elt(c->log_n, (int32_t)(1u << t)));
-    gal_down.push_back(h_galois_elt(c->log_n, -(int32_t)(1u << t)));
+  // refreshed weights live in a context-owned buffer per shard
+  size_t nref = 0;
+  for (auto& s : sh) nref += s.refresh;
+  const size_t ref_words = nref * 2 * (size_t)refresh_level * c->n;
+  const size_t need = lr_words(c, sh, refresh_level) + ref_words + 8192;
+  HE_TRY(ws_reserve(c, need * sizeof(uint64_t)));
+  Arena pool;
+  pool.base = (char*)c->ws.ptr;
+  pool.size = c->ws.size;
+  for (auto& s : sh) {
+    if (!s.refresh) continue;
+    uint64_t* p = pool.take<uint64_t>(2 * (size_t)refresh_level * c->n);
+    s.W = he_ct{p, refresh_level, refresh_level, s.W_in->scale};
   }
-  for (auto* v : {&gal_in, &gal_up, &gal_down})
-    for (uint64_t e : *v)
-      if (e != 1 && !galois_key(c, e)) return fail(HE_ENOKEY, "missing Galois key for the step's rotations");
-  const int64_t* mask = nullptr;
-  HE_TRY(lr_mask(c, g, cfg->mask_scale, &mask));
-
-  // chunk of data ciphertexts processed together
-  const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1)) * sizeof(uint64_t);
-  size_t chunk = std::max<size_t>(1, c->chunk_bytes / per);
-  chunk = std::min(chunk, nZ);
-  const size_t fixed = (size_t)n * 2 * ((l0 - 4) + 2 * (l0 - 4)) + lr_op_words(c, l0 - 4, 1) + 64;
-  const size_t total_words = fixed + chunk * lr_ct_words(c, l0) + lr_op_words(c, l0, (uint32_t)chunk) + 1024;
-  HE_TRY(ws_reserve(c, total_words * sizeof(uint64_t)));
-  Arena base;
-  base.base = (char*)c->ws.ptr;
-  base.size = c->ws.size;
-  const size_t C = chunk;
-  auto ctbuf = [&](size_t count, uint32_t cap) -> CtBatch {
-    uint64_t* p = base.take<uint64_t>(count * 2 * cap * n);
-    return CtBatch{p, (uint64_t)2 * cap * n, cap, 0};
-  };
-  CtBatch G = ctbuf(1, l0 - 4), H1 = ctbuf(1, l0 - 4), R = ctbuf(1, l0 - 4);
-  CtBatch U = ctbuf(C, l0 - 1), T = ctbuf(C, l0 - 2), A = ctbuf(C, l0 - 2), Cc = ctbuf(C, l0 - 3);
-  CtBatch B = ctbuf(C, l0 - 2), Q = ctbuf(C, l0 - 3), Gk = ctbuf(C, l0 - 4), Tmp = ctbuf(C, l0 - 1);
-  CtBatch Zcopy = ctbuf(C, l0);
-  if (!G.base || !Zcopy.base) return fail(HE_ENOMEM, "step scratch too small");
-  Arena ops;
-  ops.base = base.base + base.off;
-  ops.size = base.size - base.off;
-  auto fresh = [&]() {
-    ops.off = 0;
-    return ops;
-  };
-  HE_CUDA(cudaMemsetAsync(G.base, 0, sizeof(uint64_t) * 2 * (l0 - 4) * n, c->stream));
-  CtBatch Zall;
-  const bool zu = uniform_view(Z, nZ, &Zall);
-  const CtBatch Wb{W->data, 0, W->cap, 0};
-  for (size_t k0 = 0; k0 < nZ; k0 += C) {
-    const uint32_t m = (uint32_t)std::min(C, nZ - k0);
-    CtBatch Zc;
-    if (zu) {
-      Zc = Zall;
-      Zc.base += k0 * Zall.stride;
-    } else {
-      Zc = Zcopy;
-      for (uint32_t i = 0; i < m; ++i) {
-        CtBatch src{Z[k0 + i].data, 0, Z[k0 + i].cap, 0}, dst = Zcopy;
-        dst.base += (size_t)i * Zcopy.stride;
-        HE_TRY(copy_batch(c, src, dst, l0, 1));
+  Arena rest;
+  rest.base = pool.base + pool.off;
+  rest.size = pool.size - pool.off;
+  const bool graph = (flags & HE_LR_GRAPH) && c->stream != nullptr;
+  if (!graph) {
+    HE_TRY(lr_run(c, sh, cfg, refresh_level, rest));
+  } else {
+    // one CUDA graph per distinct call (pointers, sizes, configuration)
+    std::string key;
+    char buf[160];
+    snprintf(buf, sizeof buf, "%u|%a|%a|%a|%a|%a|%a|%u|", refresh_level, cfg->coeffs[0], cfg->coeffs[1],
+             cfg->coeffs[2], cfg->coeffs[3], cfg->lr, cfg->mask_scale, cfg->g);
+    key += buf;
+    for (auto& s : sh) {
+      snprintf(buf, sizeof buf, "%p,%zu,%p,%u,%a,%p,%u;", (const void*)s.Z, s.nZ, (const void*)s.W_in->data,
+               s.W_in->level, s.W_in->scale, (const void*)s.W_out->data, s.W_out->cap);
+      key += buf;
+      for (size_t i = 0; i < s.nZ; ++i) {
+        snprintf(buf, sizeof buf, "%p/%u/%u/%a,", (const void*)s.Z[i].data, s.Z[i].level, s.Z[i].cap, s.Z[i].scale);
+        key += buf;
       }
     }
-    Arena ar = fresh();
-    // U = Z_k * W, then the rotate-and-sum over the F feature positions
-    HE_TRY(mul_relin_batch(c, Zc, Wb, l0, m, U, true, ar));
-    for (uint32_t t = 0; t < P.logF; ++t) {
-      ar = fresh();
-      HE_TRY(rotate_batch(c, U, l0 - 1, m, gal_in[t], Tmp, ar));
-      HE_TRY(addsub_batch(c, U, Tmp, U, 0, l0 - 1, m));
+    snprintf(buf, sizeof buf, "ws=%p", c->ws.ptr);
+    key += buf;
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      const bool prof = c->prof_on;
+      c->prof_on = false;
+      cudaGraph_t g = nullptr;
+      HE_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = lr_run(c, sh, cfg, refresh_level, rest);
+      const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+      c->prof_on = prof;
+      if (rc != HE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce != cudaSuccess) return fail(HE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return fail(HE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      it = c->graphs.emplace(key, ex).first;
     }
-    // T = M^2; A = c3 M; C = T A
-    ar = fresh();
-    HE_TRY(mul_relin_batch(c, U, U, l0 - 1, m, T, true, ar));
-    HE_TRY(mul_int_batch(c, U, Tmp, P.kA, l0 - 1, m));
-    ar = fresh();
-    HE_TRY(rescale_batch(c, Tmp, l0 - 1, m, A, ar));
-    ar = fresh();
-    HE_TRY(mul_relin_batch(c, T, A, l0 - 2, m, Cc, true, ar));
-    // B = c1 M (dropped to l0-3) ; Q = c2 M^2
-    HE_TRY(mul_int_batch(c, U, Tmp, P.kB, l0 - 1, m));
-    ar = fresh();
-    HE_TRY(rescale_batch(c, Tmp, l0 - 1, m, B, ar));
-    HE_TRY(addsub_batch(c, Cc, B, Cc, 0, l0 - 3, m));
-    if (P.has_c2) {
-      HE_TRY(mul_int_batch(c, T, Tmp, P.kQ, l0 - 2, m));
-      ar = fresh();
-      HE_TRY(rescale_batch(c, Tmp, l0 - 2, m, Q, ar));
-      HE_TRY(addsub_batch(c, Cc, Q, Cc, 0, l0 - 3, m));
-    }
-    HE_TRY(add_int_batch(c, Cc, Cc, P.k0, l0 - 3, m));
-    // G_k = S * Z_k, accumulated into G
-    ar = fresh();
-    HE_TRY(mul_relin_batch(c, Cc, Zc, l0 - 3, m, Gk, true, ar));
-    HE_TRY(accumulate_batch(c, Gk, m, G, l0 - 4));
+    HE_CUDA(cudaGraphLaunch(it->second, c->stream));
   }
-  // per-feature sum over the g samples, mask, replicate
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    Arena ar = fresh();
-    HE_TRY(rotate_batch(c, G, l0 - 4, 1, gal_up[t], H1, ar));
-    HE_TRY(addsub_batch(c, G, H1, G, 0, l0 - 4, 1));
+  for (size_t k = 0; k < count; ++k) {
+    shards[k].W_out->level = sh[k].l0 - 5;
+    shards[k].W_out->scale = sh[k].W.scale;
   }
-  {
-    Arena ar = fresh();
-    HE_TRY(mul_plain_dev(c, G, mask, H1, l0 - 4, 1, ar));
-    ar = fresh();
-    HE_TRY(rescale_batch(c, H1, l0 - 4, 1, R, ar));
-  }
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    Arena ar = fresh();
-    HE_TRY(rotate_batch(c, R, l0 - 5, 1, gal_down[t], H1, ar));
-    HE_TRY(addsub_batch(c, R, H1, R, 0, l0 - 5, 1));
-  }
-  const CtBatch Wo{W_out->data, 0, W_out->cap, 0};
-  HE_TRY(addsub_batch(c, Wb, R, Wo, 0, l0 - 5, 1));
-  W_out->level = l0 - 5;
-  W_out->scale = W->scale;
   return HE_OK;
+}
+
+extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const he_ct* W, const he_lr_config* cfg,
+                                   he_ct* W_out) {
+  if (!c || !Z || !W || !cfg || !W_out) return fail(HE_EINVAL, "he_lr_gradient_step: null argument");
+  if (W->level < 6) return fail(HE_ELEVEL, "the step needs inputs at level >= 6");
+  for (size_t k = 0; k < nZ; ++k)
+    if (Z[k].level != W->level) return fail(HE_EINVAL, "data and weights must share one level");
+  he_lr_shard s{Z, nZ, W, W_out};
+  return lr_entry(c, &s, 1, cfg, 0, 0);
+}
+
+extern "C" int he_lr_gradient_step_workers(he_ctx* c, const he_lr_shard* shards, size_t count,
+                                           const he_lr_config* cfg, uint32_t refresh_level, int flags) {
+  return lr_entry(c, shards, count, cfg, refresh_level, flags);
 }

@@ -96,3 +96,81 @@ def test_lr_step_refuses_low_level(lr_pair):
     with pytest.raises(he.HeError) as e:
         he.he_lr_gradient_step(pair.g, Z, W, he.lr_config(table2()["binomial"], 0.1, g, 2.0 ** 40), out)
     assert e.value.code == he.HE_ELEVEL
+
+
+# ------------------------------------------------------------------ several workers in one call
+
+
+def _workers_inputs(pair, sizes, levels, seed0):
+    he = pair.he
+    out = []
+    for k, (nz, wl) in enumerate(zip(sizes, levels)):
+        Z = pair.g.new_ct(7, nz)
+        for i in range(nz):
+            he.he_encrypt_poly(pair.g, workloads.int_poly(seed0 + 100 * k + i, pair.n, 1 << 28), 2.0 ** 40, 7,
+                               Z[i], cid=seed0 + 100 * k + i)
+        W = pair.gpu_enc(workloads.int_poly(seed0 + 100 * k + 99, pair.n, 1 << 28), wl, seed0 + 100 * k + 99,
+                         scale=2.0 ** 40, cap=7)
+        out.append((Z, W, pair.g.new_ct(7)))
+    return out
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_workers_match_separate_calls(lr_pair, graph):
+    """Shards of uneven size at two levels in one call give the residues of
+    one call per shard (each of which is bit-exact against the oracle)."""
+    pair, g = lr_pair
+    he = pair.he
+    cfg = he.lr_config(table2()["hinge"], 0.05, g, 2.0 ** 40)
+    shards = _workers_inputs(pair, [3, 1, 5, 2], [7, 6, 7, 6], 5000)
+    import torch
+    side = torch.cuda.Stream()  # graph capture needs a non-default stream
+    torch.cuda.synchronize()
+    he.he_set_stream(pair.g, side.cuda_stream)
+    try:
+        for _ in range(2 if graph else 1):  # a graph call captures, the next one replays
+            he.he_lr_gradient_step_workers(pair.g, shards, cfg, graph=graph)
+        he.he_sync(pair.g)
+    finally:
+        he.he_set_stream(pair.g, torch.cuda.current_stream().cuda_stream)
+    for Z, W, W_out in shards:
+        Zv = [Z_i for Z_i in Z]
+        if W.level < 7:
+            Zd = pair.g.new_ct(7, len(Z))
+            for i, z in enumerate(Z):
+                he.he_drop_level(pair.g, z, W.level, Zd[i])
+            Zv = Zd
+        single = pair.g.new_ct(7)
+        he.he_lr_gradient_step(pair.g, Zv, W, cfg, single)
+        assert W_out.level == W.level - 5
+        assert np.array_equal(he.he_ct_export(pair.g, W_out), he.he_ct_export(pair.g, single))
+
+
+def test_workers_refresh_low_levels(lr_pair):
+    """A worker whose weights have too few limbs left is refreshed by the
+    in-process key holder first (Algorithm 1 lines 8-10); the decrypted
+    result still matches the FP64 update."""
+    pair, g = lr_pair
+    he = pair.he
+    n_slots = pair.n // 2
+    coeffs = table2()["binomial"]
+    shards, datas = [], []
+    for k, wl in enumerate([3, 7]):
+        data = workloads.LRData(seed=20 + k, n_samples=12, n_features=60)
+        datas.append(data)
+        zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+        Z = pair.g.new_ct(7, len(zs))
+        for i, v in enumerate(zs):
+            he.he_encode_encrypt(pair.g, v, 2.0 ** 40, 7, Z[i], cid=700 + 10 * k + i)
+        W = pair.g.new_ct(7)
+        he.he_encode_encrypt(pair.g, workloads.pack_weights(data.w0, n_slots, g), 2.0 ** 40, wl, W, cid=690 + k)
+        shards.append((Z, W, pair.g.new_ct(7)))
+    with pytest.raises(he.HeError) as e:
+        he.he_lr_gradient_step_workers(pair.g, shards, he.lr_config(coeffs, 1 / 12, g, 2.0 ** 40))
+    assert e.value.code == he.HE_ELEVEL
+    he.he_lr_gradient_step_workers(pair.g, shards, he.lr_config(coeffs, 1 / 12, g, 2.0 ** 40), refresh_level=7)
+    for (Z, W, W_out), data in zip(shards, datas):
+        assert W_out.level == 2
+        got = he.he_decrypt_decode(pair.g, W_out)
+        want = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, 1 / 12), n_slots, g)
+        assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20

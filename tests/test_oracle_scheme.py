@@ -94,8 +94,8 @@ def test_encode_decode_roundtrip():
     assert np.max(np.abs(im)) < 2.0 ** -(40 - 10 - 2)
 
 
-@pytest.mark.parametrize("g", [1, 2, 4, 8])
-def test_mask_encoding_closed_form(g):
+@pytest.mark.parametrize("g,logms", [(1, 40), (2, 40), (4, 40), (8, 40), (8, 27), (4, 27), (8, 30)])
+def test_mask_encoding_closed_form(g, logms):
     """The mask (1 on slots = 0 mod g) encodes to the polynomial with
     coefficient (Delta/g) cos(pi i / N) at i = 0 mod N/(2g) and 0 elsewhere:
     the slot positions = 0 mod g are the 2N-th roots exp(i pi t/N) with
@@ -104,7 +104,7 @@ def test_mask_encoding_closed_form(g):
     mpmath.mp.prec = 120
     log_n = 11
     o = oracle.Oracle(log_n, 2, 40, 1, 60, 2.0 ** 40)
-    ms = 2.0 ** 40
+    ms = 2.0 ** logms
     got = o.lr_mask(g, ms)
     step = o.n // (2 * g)
     for i in range(o.n):
