@@ -416,6 +416,14 @@ void orc_automorph(orc_ctx* c, const uint64_t* in, uint64_t* out, int nlimbs, ui
   for (int t = 0; t < nlimbs; t++) automorph_eval(c, POLY(in, t, c->n), POLY(out, t, c->n), k);
 }
 
+/* (P - 1)/2 mod m, with P = product of the special primes (odd): computed as
+ * (P mod m - 1) * 2^-1 mod m for odd m. */
+static uint64_t P_mod(orc_ctx* c, uint64_t m);
+static uint64_t half_P_mod(orc_ctx* c, uint64_t m) {
+  uint64_t pm1 = submod(P_mod(c, m), 1, m);
+  return mulmod(pm1, invmod(2, m), m);
+}
+
 /* P mod q_t, with P = product of the special primes. */
 static uint64_t P_mod(orc_ctx* c, uint64_t m) {
   uint64_t r = 1 % m;
@@ -931,8 +939,14 @@ static const uint64_t* find_key(orc_ctx* c, int key_id) {
 /* Hybrid key switching [ext], at `level`: input d (evaluation form [level][N]),
  * key for s' -> s; output (k0, k1) [level][N] each, with k0 + k1 s ~ d s'.
  * Steps in order: d to coefficients; per digit ModUp to Q_level + P and back
- * to evaluation form; inner product with the key; ModDown:
- *   out_t = (acc_t - NTT_t(BConv_{P->q_t}(INTT_P(acc_P)))) * P^-1  mod q_t. */
+ * to evaluation form; inner product with the key; ModDown with rounding
+ * (division by P rounds, as the rescale does -- Sec. 3's "homomorphic
+ * rounding"; flooring would leave a -1/2 bias on every coefficient of both
+ * parts, which concentrates in the lowest-frequency slot):
+ *   y = INTT_P(acc_P) + h (every coefficient),  h = (P-1)/2,
+ *   out_t = (acc_t - NTT_t(BConv_{P->q_t}(y) - h)) * P^-1  mod q_t,
+ * i.e. round(acc / P) minus the conversion's small multiple of P (for one
+ * special prime, BConv(y) - h is the centered residue of acc mod P). */
 static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key,
                       uint64_t* k0, uint64_t* k1) {
   uint32_t n = c->n;
@@ -971,13 +985,18 @@ static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* 
   for (int p = 0; p < 2; p++) {
     uint64_t* ap = acc + (size_t)p * nt * n;
     for (int k = 0; k < c->alpha; k++) {
+      uint64_t pk = c->q[c->L + k];
+      uint64_t hk = half_P_mod(c, pk);
       memcpy(POLY(yP, k, n), POLY(ap, level + k, n), sizeof(uint64_t) * n);
       intt_limb(c, c->L + k, POLY(yP, k, n));
+      for (uint32_t i = 0; i < n; i++) yP[(size_t)k * n + i] = addmod(yP[(size_t)k * n + i], hk, pk);
     }
     uint64_t* dst = p == 0 ? k0 : k1;
     for (int t = 0; t < level; t++) {
       uint64_t q = c->q[t];
+      uint64_t ht = half_P_mod(c, q);
       moddown_conv(c, yP, t, conv);
+      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
       ntt_limb(c, t, conv);
       uint64_t pinv = invmod(P_mod(c, q), q);
       const uint64_t* at = POLY(ap, t, n);

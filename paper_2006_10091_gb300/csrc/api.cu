@@ -210,6 +210,8 @@ int he_set_tuning(he_ctx* c, const char* key, double value) {
   if (k == "chunk_bytes") {
     if (!(value >= (1 << 20) && value <= 1e13)) return fail(HE_EINVAL, "chunk_bytes out of range");
     c->chunk_bytes = (size_t)value;
+  } else if (k == "ntt_generic") {
+    c->ntt_generic = value != 0.0;
   } else if (k == "lr_chunk") {
     if (!(value >= 0 && value <= 1 << 20)) return fail(HE_EINVAL, "lr_chunk out of range");
     c->lr_chunk = (uint32_t)value;

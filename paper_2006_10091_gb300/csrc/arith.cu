@@ -115,8 +115,10 @@ __global__ void k_inner_product(const uint64_t* ext, uint64_t ext_stride, const 
 }
 
 // ---- ModDown conversion: BConv from P to each limb q_t (coefficient form) ----
-// y (special limbs of the accumulator, coefficient form) -> conv[t] =
-// sum_k [y_k * (P/p_k)^-1]_{p_k} * ((P/p_k) mod q_t) mod q_t.
+// y (special limbs of the accumulator, coefficient form) plus h = (P-1)/2 ->
+// conv[t] = sum_k [(y_k + h) * (P/p_k)^-1]_{p_k} * ((P/p_k) mod q_t) - h mod q_t:
+// subtracting this from the accumulator divides by P with rounding (for one
+// special prime it is the centered residue of the accumulator mod P).
 __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_t* conv,
                                uint64_t conv_stride, uint32_t level, uint32_t alpha, uint32_t L,
                                uint32_t count, int log_n, const PrimeDev* primes,
@@ -130,9 +132,12 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
     const size_t r = g / n;
     const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
     uint64_t u[HE_MAX_DIGIT];
+    const uint64_t* hP = md + 2 * alpha + (size_t)alpha * L + 2 * L;
+    const uint64_t* hQ = hP + alpha;
     for (uint32_t a = 0; a < alpha; ++a) {
-      const uint64_t y = acc[(size_t)i * acc_stride + ((size_t)p * nt + level + a) * n + k];
-      u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], primes[L + a].q);
+      const uint64_t pa = primes[L + a].q;
+      const uint64_t y = add_mod(acc[(size_t)i * acc_stride + ((size_t)p * nt + level + a) * n + k], hP[a], pa);
+      u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], pa);
     }
     uint64_t* out = conv + (size_t)i * conv_stride + (size_t)p * level * n;
     for (uint32_t t = 0; t < level; ++t) {
@@ -140,7 +145,7 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
       uint64_t s = 0;
       for (uint32_t a = 0; a < alpha; ++a)
         s = add_mod(s, mul_mod(reduce64(u[a], pr), mat[(size_t)a * L + t], pr), pr.q);
-      out[(size_t)t * n + k] = s;
+      out[(size_t)t * n + k] = sub_mod(s, hQ[t], pr.q);
     }
   }
 }
@@ -150,7 +155,8 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
 __global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, const uint64_t* conv,
                              uint64_t conv_stride, CtBatch add, int has_add, CtBatch out,
                              uint32_t out_part0, uint32_t nparts, uint32_t level, uint32_t alpha,
-                             uint32_t count, int log_n, const PrimeDev* primes, const uint64_t* pinv) {
+                             uint32_t L_, uint32_t count, int log_n, const PrimeDev* primes,
+                             const uint64_t* pinv) {
   const uint32_t n = 1u << log_n, half = n >> 1;
   const uint32_t nt = level + alpha;
   const size_t total = (size_t)count * nparts * level * half;

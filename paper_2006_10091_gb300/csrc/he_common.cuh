@@ -22,6 +22,7 @@ struct PrimeDev {
   uint32_t pad;
   uint64_t n_inv;     // N^-1 mod q
   uint64_t n_inv_sh;  // its Shoup companion
+  uint64_t one_sh;    // Shoup companion of 1: floor(2^64 / q)
 };
 
 __device__ __forceinline__ uint64_t shoup_companion_dev(uint64_t w, uint64_t q) {

@@ -89,6 +89,7 @@ struct he_ctx {
   uint64_t* d_garner = nullptr;
   size_t chunk_bytes = (size_t)1 << 31;  // scratch budget of one batched operation
   uint32_t lr_chunk = 0;                 // data ciphertexts per chunk of the LR step (0: from the budget)
+  bool ntt_generic = false;              // force the runtime-shaped NTT kernel (tuning)
   std::map<std::string, cudaGraphExec_t> graphs;  // captured multi-worker steps
   std::vector<uint64_t> P_mod_q;  // [L] P mod q_t (host)
 

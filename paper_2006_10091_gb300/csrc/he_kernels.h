@@ -43,7 +43,8 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
 __global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, const uint64_t* conv,
                              uint64_t conv_stride, CtBatch add, int has_add, CtBatch out,
                              uint32_t out_part0, uint32_t nparts, uint32_t level, uint32_t alpha,
-                             uint32_t count, int log_n, const PrimeDev* primes, const uint64_t* pinv);
+                             uint32_t L_, uint32_t count, int log_n, const PrimeDev* primes,
+                             const uint64_t* pinv);
 __global__ void k_rescale_corr(const uint64_t* last, uint64_t* corr, uint32_t level, uint32_t count,
                                int log_n, const PrimeDev* primes);
 __global__ void k_rescale_final(CtBatch in, const uint64_t* corr, CtBatch out, uint32_t level,

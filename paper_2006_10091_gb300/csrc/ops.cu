@@ -9,7 +9,8 @@
 //      basis conversion, coefficient form), then forward NTT of the converted
 //      limbs (the digit's own limbs are taken from d as they are);
 //   3. inner product with the switching key, two accumulators over l + alpha limbs;
-//   4. ModDown: inverse NTT of the special limbs, conversion to each q_t,
+//   4. ModDown: inverse NTT of the special limbs, conversion of (y + h) to
+//      each q_t minus h (h = (P-1)/2, so that the division by P rounds),
 //      forward NTT, out_t = (acc_t - conv_t) * P^-1 (+ an optional addend).
 #include "he_ops.h"
 
@@ -118,7 +119,7 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   {
     ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
     k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha,
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha, L,
         count, c->log_n, c->d_primes, pinv);
   }
   HE_CUDA(cudaGetLastError());

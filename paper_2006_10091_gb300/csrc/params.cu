@@ -157,6 +157,7 @@ int build_tables(he_ctx* c) {
     p.mu = (uint64_t)(((u128)1 << (2 * p.k)) / q);
     p.n_inv = h_invmod((uint64_t)n % q, q);
     p.n_inv_sh = h_shoup(p.n_inv, q);
+    p.one_sh = h_shoup(1, q);
     two64[t] = (uint64_t)(((u128)1 << 64) % q);
   }
   HE_CUDA(cudaMalloc(&c->d_primes, sizeof(PrimeDev) * np));
@@ -238,7 +239,8 @@ int build_tables(he_ctx* c) {
   }
 
   // ModDown constants: [alpha] Shoup pairs of (P/p_k)^-1 mod p_k; [alpha][L] values
-  // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t.
+  // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2 reduced:
+  // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds).
   {
     std::vector<uint64_t> words;
     for (int k = 0; k < alpha; ++k) {
@@ -269,6 +271,13 @@ int build_tables(he_ctx* c) {
       words.push_back(inv);
       words.push_back(h_shoup(inv, qt));
     }
+    auto half_P = [&](uint64_t m) {  // (P - 1)/2 mod m = (P mod m - 1) * 2^-1 mod m
+      uint64_t P = 1 % m;
+      for (int k = 0; k < alpha; ++k) P = h_mulmod(P, c->q[L + k] % m, m);
+      return h_mulmod((P + m - 1) % m, h_invmod(2, m), m);
+    };
+    for (int k = 0; k < alpha; ++k) words.push_back(half_P(c->q[L + k]));
+    for (int t = 0; t < L; ++t) words.push_back(half_P(c->q[t]));
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }

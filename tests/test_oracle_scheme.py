@@ -371,3 +371,50 @@ def test_lr_step_matches_fp64_update(loss):
     want = workloads.pack_weights(w1, n_slots, g)
     rel = np.max(np.abs(re - want)) / np.max(np.abs(want))
     assert rel < 2.0 ** -20, rel
+
+
+def test_keyswitch_equals_big_integer_definition(tiny):
+    """Hybrid key switching recomputed with Python integers from its
+    definition: per digit the approximate ModUp y_j = sum_i [x_i (Q_j/q_i)^-1]_{q_i}
+    (Q_j/q_i) (an integer equal to [x]_{Q_j} + u Q_j), the products with the key
+    over the integers mod X^N + 1, then the division by P with rounding:
+    out = floor((acc + h - conv) / P) with h = (P-1)/2 and conv the same
+    approximate conversion of [acc + h]_P.  Must equal the oracle's residues."""
+    o = tiny
+    level, n, L, alpha = 5, o.n, o.L, o.alpha
+    q = o.primes
+    P = math.prod(q[L:L + alpha])
+    h = (P - 1) // 2
+    d = workloads.residues(91, q[:level], n)[0]
+    k0, k1 = o.keyswitch(d, level, -1)
+    dc = to_coef(o, d, level)
+    key = o.key(1)  # [beta][2][np][N], evaluation form
+    targets = list(range(level)) + list(range(L, L + alpha))
+    mod = math.prod(q[t] for t in targets)
+    acc = [[0] * n, [0] * n]
+    for j in range((level + alpha - 1) // alpha):
+        digit = list(range(j * alpha, min((j + 1) * alpha, level)))
+        Qj = math.prod(q[i] for i in digit)
+        y = [0] * n
+        for i in digit:
+            qhat = Qj // q[i]
+            inv = pow(qhat, -1, q[i])
+            for c in range(n):
+                y[c] += (int(dc[i][c]) * inv % q[i]) * qhat
+        for p in range(2):
+            kc = [oracle.intt_def(key[j, p, t], o.log_n, q[t], o.roots[t]) for t in targets]
+            kint = [crt([kc[ti][c] for ti in range(len(targets))], [q[t] for t in targets]) for c in range(n)]
+            prod = negacyclic(y, kint)
+            acc[p] = [(a + b) % mod for a, b in zip(acc[p], prod)]
+    for p, got in enumerate((k0, k1)):
+        gotc = to_coef(o, got, level)
+        for c in range(n):
+            v = acc[p][c] + h
+            conv = 0
+            for k in range(alpha):
+                pk = q[L + k]
+                phat = P // pk
+                conv += ((v % pk) * pow(phat, -1, pk) % pk) * phat
+            out = (v - conv) // P
+            for t in range(level):
+                assert int(gotc[t][c]) == out % q[t], (p, c, t)
