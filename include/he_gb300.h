@@ -169,6 +169,22 @@ int he_mul_plain(he_ctx* ctx, const he_ct* a, const int64_t* coeffs, double pt_s
  * HE_ELEVEL if l < 2. */
 int he_rescale(he_ctx* ctx, const he_ct* a, he_ct* out);
 
+/* he_rescale without any device allocation (the paper has no counterpart:
+ * this is a deployment variant).  he_rescale draws its scratch from the
+ * context's workspace, which may grow with cudaMalloc and synchronise the
+ * stream; callers that cannot allow that (a host that owns the device's
+ * memory through its own pool and a fixed HBM budget, or a latency-critical
+ * loop that must not stall on an allocation) use this entry point, whose
+ * scratch is a static 4 MiB device array present on every GPU that loads the
+ * library until exit.  Limit: 2*level*N + 64 words <= 2^19 (level <= 15 at
+ * N = 2^14), else HE_EINVAL with the sizes in the message.  The first call on
+ * a device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race, so serialise them; nothing in
+ * it needs clearing, each call writes every word it reads.  Same results,
+ * errors and aliasing rules as he_rescale; kernel timing is not recorded. */
+int he_rescale_noalloc(he_ctx* ctx, const he_ct* a, he_ct* out);
+
 /* Homomorphic multiplication (Sec. 3; the cost the paper names in Sec. 6):
  * tensor product, relinearisation by hybrid key switching, rescale.  Both
  * operands at the same level l >= 2 (else the lower is used); out at l-1

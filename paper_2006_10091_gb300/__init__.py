@@ -104,6 +104,7 @@ def load():
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
+        "he_rescale_noalloc": [VP, CTP, CTP],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
     }
@@ -323,6 +324,13 @@ def he_mul_plain(ctx, a, coeffs, pt_scale: float, out):
 
 def he_rescale(ctx, a, out):
     _run(load().he_rescale, ctx, [out], a, out)
+    return out
+
+
+def he_rescale_noalloc(ctx, a, out):
+    """he_rescale with its scratch in the library's static device array (no
+    allocation; for callers with a fixed device-memory budget)."""
+    _run(load().he_rescale_noalloc, ctx, [out], a, out)
     return out
 
 
