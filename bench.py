@@ -417,7 +417,8 @@ def run_micro(args):
     host = workloads.residues(1, ctx.primes[:nl], n, parts=args.polys)
     t = torch.from_numpy(host.view(np.int64)).cuda()
     out = {}
-    for inverse in (False, True):
+    for generic, inverse in ((False, False), (False, True), (True, False), (True, True)):
+        he.he_set_tuning(ctx, "ntt_generic", generic)
         for _ in range(args.warmup):
             he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -429,9 +430,10 @@ def run_micro(args):
         ms = e0.elapsed_time(e1) / args.steps
         limbs = args.polys * nl
         bfly = limbs * (n / 2) * log_n
-        out["intt" if inverse else "ntt"] = {
+        out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else "")] = {
             "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_BFLY_PEAK,
             "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
+    he.he_set_tuning(ctx, "ntt_generic", False)
     print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
 
 

@@ -96,7 +96,9 @@ int he_sync(he_ctx* ctx);
 
 /* Tuning knobs (results never depend on them): "chunk_bytes" = scratch budget
  * of one batched operation (default 2^31), "lr_chunk" = data ciphertexts per
- * chunk of the logistic-regression step (0 = from the budget).  HE_EINVAL for
+ * chunk of the logistic-regression step (0 = from the budget), "ntt_generic"
+ * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
+ * one for N = 2^12 .. 2^16.  HE_EINVAL for
  * an unknown key or a value out of range. */
 int he_set_tuning(he_ctx* ctx, const char* key, double value);
 

@@ -238,7 +238,14 @@ static int launch_pass(he_ctx* c, const PolyBatch& b, bool inv, bool col, int lo
   return HE_OK;
 }
 
+int ntt2(he_ctx* c, const PolyBatch& b, bool inv, bool* handled);
+
 int ntt_forward(he_ctx* c, const PolyBatch& b) {
+  if (!c->ntt_generic) {
+    bool handled = false;
+    const int rc = ntt2(c, b, false, &handled);
+    if (handled) return rc;
+  }
   const int n = c->log_n, n1 = split_bits(n);
   if (n1 == n) return launch_pass(c, b, false, true, n, 0, b.src, b.dst, b.src_stride, true);
   HE_TRY(launch_pass(c, b, false, true, n1, n - n1, b.src, b.dst, b.src_stride, false));
@@ -246,6 +253,11 @@ int ntt_forward(he_ctx* c, const PolyBatch& b) {
 }
 
 int ntt_inverse(he_ctx* c, const PolyBatch& b) {
+  if (!c->ntt_generic) {
+    bool handled = false;
+    const int rc = ntt2(c, b, true, &handled);
+    if (handled) return rc;
+  }
   const int n = c->log_n, n1 = split_bits(n);
   if (n1 == n) return launch_pass(c, b, true, true, n, 0, b.src, b.dst, b.src_stride, true);
   HE_TRY(launch_pass(c, b, true, false, n - n1, 0, b.src, b.dst, b.src_stride, false));

@@ -1,0 +1,144 @@
+// ntt2.cuh -- building blocks of the compile-time-shaped NTT passes, shared
+// by ntt2.cu (plain transforms) and ks_fused.cu (transforms fused into key
+// switching).  See ntt2.cu for the pass structure.
+#pragma once
+#include "he_common.cuh"
+
+namespace he {
+
+template <int LOG_N, int LOG_M, int LOG_K, bool COL>
+struct Shape {
+  static constexpr int M = 1 << LOG_M, K = 1 << LOG_K, TILE = M * K, T = TILE / 8;
+  static constexpr int BIT_LO = COL ? LOG_N - LOG_M : 0;  // lowest index bit this pass transforms
+  static constexpr int S0 = LOG_N - BIT_LO - LOG_M;      // global stage of local stage 0
+  static constexpr int TILES = 1 << (LOG_N - LOG_M - LOG_K);
+  static constexpr int NTW = COL ? M : K * M;             // staged twiddle pairs
+  // element (tile, k, x) -> global index
+  __device__ static __forceinline__ uint32_t gidx(uint32_t tile, uint32_t k, uint32_t x) {
+    const uint32_t f = (tile << LOG_K) | k;
+    return COL ? ((x << BIT_LO) | f) : ((f << LOG_M) | x);
+  }
+  __device__ static __forceinline__ uint32_t sidx(uint32_t k, uint32_t x) {
+    const uint32_t i = COL ? ((x << LOG_K) | k) : ((k << LOG_M) | x);
+    return i + (i >> 3);
+  }
+  // staged twiddle of local stage sigma for element (k, x)
+  __device__ static __forceinline__ uint32_t tidx(int sigma, uint32_t k, uint32_t x) {
+    return COL ? ((1u << sigma) | (x >> (LOG_M - sigma)))
+               : (uint32_t)(K * ((1 << sigma) - 1)) + (k << sigma) + (x >> (LOG_M - sigma));
+  }
+};
+
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R>
+__device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int sig0, uint64_t q) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+  constexpr int G = 1 << R, GPT = 8 >> R;
+  const uint64_t q2 = q + q;
+  const int lo_bits = LOG_M - sig0 - R;
+  const uint32_t lo_mask = (1u << lo_bits) - 1;
+#pragma unroll
+  for (int u = 0; u < GPT; ++u) {
+    const uint32_t g = threadIdx.x + u * S::T;
+    uint32_t k, xhi, xlo;
+    if (COL) {
+      k = g & (S::K - 1);
+      const uint32_t r = g >> LOG_K;
+      xlo = r & lo_mask;
+      xhi = r >> lo_bits;
+    } else {
+      xlo = g & lo_mask;
+      const uint32_t r = g >> lo_bits;
+      xhi = r & ((1u << sig0) - 1);
+      k = r >> sig0;
+    }
+    const uint32_t xbase = (xhi << (LOG_M - sig0)) | xlo;
+    uint64_t v[G];
+    uint32_t si[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+      si[j] = S::sidx(k, xbase | ((uint32_t)j << lo_bits));
+      v[j] = sm[si[j]];
+    }
+    if (!INV) {
+#pragma unroll
+      for (int st = 0; st < R; ++st) {
+        const int half = G >> (st + 1);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          if (j & half) continue;
+          const ulonglong2 w = stw[S::tidx(sig0 + st, k, xbase | ((uint32_t)j << lo_bits))];
+          uint64_t X = v[j];
+          if (!LAZY) X = X >= q2 ? X - q2 : X;
+          const uint64_t t = mul_shoup_lazy(v[j + half], w.x, w.y, q);
+          v[j] = X + t;
+          v[j + half] = X + q2 - t;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int st = R - 1; st >= 0; --st) {
+        const int half = G >> (st + 1);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          if (j & half) continue;
+          const ulonglong2 w = stw[S::tidx(sig0 + st, k, xbase | ((uint32_t)j << lo_bits))];
+          const uint64_t X = v[j], Y = v[j + half];
+          uint64_t sum = X + Y;
+          sum = sum >= q2 ? sum - q2 : sum;
+          v[j + half] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+          v[j] = sum;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) sm[si[j]] = v[j];
+  }
+}
+
+// Stage the twiddle pairs of one pass into shared memory: a column pass
+// needs tw[0 .. M), a row pass for rows f0 .. f0+K-1 needs, per local stage
+// sigma, the K*2^sigma entries from 2^(S0+sigma) + f0*2^sigma on.
+template <int LOG_N, int LOG_M, int LOG_K, bool COL>
+__device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+  if (COL) {
+    for (uint32_t e = threadIdx.x; e < (uint32_t)S::M; e += S::T) stw[e] = __ldg(tw + e);
+  } else {
+    const uint32_t f0 = tile << LOG_K;
+#pragma unroll
+    for (int sig = 0; sig < LOG_M; ++sig) {
+      const uint32_t cnt = (uint32_t)S::K << sig;
+      const uint32_t off = (uint32_t)(S::K * ((1 << sig) - 1));
+      const ulonglong2* g = tw + (1u << (S::S0 + sig)) + (f0 << sig);
+      for (uint32_t e = threadIdx.x; e < cnt; e += S::T) stw[off + e] = __ldg(g + e);
+    }
+  }
+}
+
+// All rounds of one pass on the tile in shared memory (ends with a barrier).
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL>
+__device__ __forceinline__ void run_rounds(uint64_t* sm, const ulonglong2* stw, uint64_t q) {
+  constexpr int NR = (LOG_M + 2) / 3;
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    const int r = INV ? NR - 1 - rr : rr;
+    const int sig0 = 3 * r;
+    const int R = LOG_M - sig0 < 3 ? LOG_M - sig0 : 3;
+    if (R == 3) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3>(sm, stw, sig0, q);
+    else if (R == 2) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2>(sm, stw, sig0, q);
+    else round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1>(sm, stw, sig0, q);
+    __syncthreads();
+  }
+}
+
+// Canonical residue of a forward-pass output: lazy values (< 33q) by one
+// Shoup product by 1, corrected ones ([0, 4q)) by subtractions.
+template <bool LAZY>
+__device__ __forceinline__ uint64_t fwd_final(uint64_t v, const PrimeDev& pr) {
+  const uint64_t q = pr.q, q2 = q + q;
+  if (LAZY) v = mul_shoup_lazy(v, 1, pr.one_sh, q);
+  else v = v >= q2 ? v - q2 : v;
+  return v >= q ? v - q : v;
+}
+
+}  // namespace he

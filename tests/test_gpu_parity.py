@@ -63,6 +63,28 @@ def test_ntt_matches_oracle(he, log_n):
     assert np.array_equal(t.cpu().numpy().view(np.uint64), data)
 
 
+@pytest.mark.parametrize("log_n", [12, 13, 14, 15, 16])
+def test_both_ntt_kernels_agree(he, log_n):
+    """The compile-time-shaped and the runtime-shaped transforms give the same
+    residues, on limb primes (lazy forward butterflies) and the 60-bit special
+    prime (corrected butterflies), with skipped digit limbs left untouched."""
+    import torch
+    ctx = he.Context(log_n, 4, 45, 1, 60, 2.0 ** 40, seed=3)
+    n = 1 << log_n
+    data = workloads.residues(100 + log_n, ctx.primes, n, parts=5)
+    outs = []
+    for generic in (False, True):
+        he.he_set_tuning(ctx, "ntt_generic", generic)
+        t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+        he.he_ntt(ctx, t, 5, 5 * n, 5, 0, False)
+        fwd = t.cpu().numpy().copy()
+        he.he_ntt(ctx, t, 5, 5 * n, 5, 0, True)
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), data)
+        outs.append(fwd)
+    he.he_set_tuning(ctx, "ntt_generic", False)
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_ntt_limb_subset_and_prime_offset(he):
     import torch
     log_n, L = 12, 4
