@@ -263,6 +263,7 @@ def run_ours(args, rank: int, world: int):
     extra = {}
     if not args.quick and rank == 0:
         extra.update(hmult_rates(he, torch, stream))
+        extra["batched_workers"] = batched_workers(he, torch, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(data, coeffs, lr)
@@ -296,7 +297,8 @@ def hmult_rates(he, torch, stream):
     for name, (log_n, nl, bits, alpha, sbits, scale, count) in {
             "hmult_small": (12, 3, 40, 1, 60, 2.0 ** 30, 16),
             "hmult_large": (16, 24, 50, 4, 60, 2.0 ** 50, 64)}.items():
-        ctx = he.Context(log_n, nl, bits, alpha, sbits, scale, seed=0, stream=stream.cuda_stream)
+        rots = [1 << t for t in range(10)] if name == "hmult_large" else []
+        ctx = he.Context(log_n, nl, bits, alpha, sbits, scale, seed=0, stream=stream.cuda_stream, rot_steps=rots)
         n = 1 << log_n
         A, B, O = ctx.new_ct(nl, count), ctx.new_ct(nl, count), ctx.new_ct(nl, count)
         for i in range(count):
@@ -325,9 +327,90 @@ def hmult_rates(he, torch, stream):
         err = float(np.max(np.abs(got - workloads.uniform_slots(0, n // 2) * workloads.uniform_slots(1, n // 2))))
         out[name] = {"per_s_batched": batched, "per_s_plain": plain, "count": count, "N": n, "limbs": nl,
                      "max_abs_err": err}
+        if name == "hmult_large":
+            # 1024-slot rotate-and-sum: ten rotations by 1, 2, ..., 512, each batched over the 64
+            T = ctx.new_ct(nl, count)
+            def rotsum():
+                for t in range(10):
+                    he.he_rotate_batch(ctx, O, 1 << t, T)
+                    for i in range(count):
+                        he.he_add(ctx, O[i], T[i], O[i])
+            rotsum()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            rotsum()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name]["rotate_and_sum_per_s"] = count * 1000.0 / e0.elapsed_time(e1)
+            out[name]["rotations_per_s"] = 10 * count * 1000.0 / e0.elapsed_time(e1)
         ctx.close()
         del A, B, O
         torch.cuda.empty_cache()
+    return out
+
+
+def batched_workers(he, torch, stream, reps=2):
+    """32 workers of log-uniform 512..8192 samples x 784 features, weights at
+    levels uniform in 2..8 (those below 6 are refreshed to 8 by the in-process
+    key holder first): all workers in one graph-replayed batched call vs one
+    call per worker (the per-instance path, no cross-worker batching)."""
+    from paper_2006_10091_gb300 import workloads
+    from tests.lr_reference import lr_step_fp64
+    n_slots = (1 << LOG_N) // 2
+    ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=rot_steps(n_slots, G),
+                     stream=stream.cuda_stream)
+    sizes = workloads.shard_sizes(0, 32)
+    levels = workloads.shard_levels(0, 32)
+    coeffs = table2_binomial()
+    lr = 1.0 / N_SAMPLES  # one learning rate for all workers
+    cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
+    shards, datas = [], []
+    t0 = time.perf_counter()
+    for k, (ns, lv) in enumerate(zip(sizes, levels)):
+        data = workloads.LRData(seed=100 + k, n_samples=ns, n_features=N_FEATURES)
+        datas.append(data)
+        zs = workloads.pack_samples(data.X, data.y, n_slots, G)
+        Z = ctx.new_ct(L, len(zs))
+        for i, v in enumerate(zs):
+            he.he_encode_encrypt(ctx, v, SCALE, L, Z[i], cid=(k << 16) + i)
+        W = ctx.new_ct(L)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(data.w0, n_slots, G), SCALE, lv, W, cid=(k << 16) + 0xFFFF)
+        shards.append((Z, W, ctx.new_ct(L)))
+    setup_s = time.perf_counter() - t0
+    n_ct = sum(len(z) for z, _, _ in shards)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    he.he_lr_gradient_step_workers(ctx, shards, cfg, refresh_level=L, graph=True)  # capture
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        he.he_lr_gradient_step_workers(ctx, shards, cfg, refresh_level=L, graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / reps
+    k_check = max(range(32), key=lambda k: sizes[k])
+    got = he.he_decrypt_decode(ctx, shards[k_check][2])
+    d = datas[k_check]
+    want = workloads.pack_weights(lr_step_fp64(d.X, d.y, d.w0, coeffs, lr), n_slots, G)
+    rel = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    for sh in shards:  # warm the per-worker path
+        he.he_lr_gradient_step_workers(ctx, [sh], cfg, refresh_level=L)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        for sh in shards:
+            he.he_lr_gradient_step_workers(ctx, [sh], cfg, refresh_level=L)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    out = {"workers": 32, "data_ciphertexts": n_ct, "samples": int(sum(sizes)),
+           "levels": levels, "refreshed": int(sum(1 for v in levels if v < 6)),
+           "batched_ms_per_round": batched_ms, "plain_ms_per_round": plain_ms,
+           "batched_worker_steps_per_s": 32 * 1000.0 / batched_ms,
+           "plain_worker_steps_per_s": 32 * 1000.0 / plain_ms, "speedup": plain_ms / batched_ms,
+           "max_rel_err_vs_fp64_largest_worker": rel, "setup_s": setup_s}
+    ctx.close()
+    del shards
+    torch.cuda.empty_cache()
     return out
 
 

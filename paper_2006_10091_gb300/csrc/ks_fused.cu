@@ -1,0 +1,227 @@
+// ks_fused.cu -- hybrid key switching with ModUp fused into the NTT's first
+// pass and the key inner product fused into its second pass (N = 2^12 ..
+// 2^16).  Same arithmetic and the same residues as the unfused sequence in
+// ops.cu (iNTT, k_modup, NTT, k_inner_product); what it saves is the round
+// trips of the converted digits through memory:
+//  * ks_modup_col: a CTA of digit j and target limb t builds its column tile
+//    straight from the coefficient-form input (the digit's limbs, converted
+//    to prime t as in k_modup) and runs the column pass; the ModUp output is
+//    never written;
+//  * ks_row_ip: a CTA of target limb t and one row tile keeps two
+//    accumulators per residue in registers, and for every digit finishes the
+//    row pass of that digit's tile (or, on the digit's own limb, reads the
+//    input as it is) and adds its products with the two key polynomials; the
+//    transformed digits are never written.
+#include "he_ops.h"
+#include "ntt2.cuh"
+
+namespace he {
+
+struct KsFusedArgs {
+  const uint64_t* d;     // input, evaluation form: count x [level][N] at d_stride
+  const uint64_t* d2c;   // input, coefficient form: count x [level][N]
+  uint64_t* ext;         // column-pass outputs: count x [beta][nt][N]
+  uint64_t* acc;         // accumulators: count x [2][nt][N]
+  const uint64_t* evk;   // [beta_top][2][np][N]
+  uint64_t d_stride;
+  uint32_t level, alpha, beta, L, np, nt;
+  const PrimeDev* primes;
+  const ulonglong2* tw;
+  const uint64_t* consts;  // ModUp constant tables
+  uint32_t lo[HE_MAX_PRIMES], cnt[HE_MAX_PRIMES];
+  uint64_t off[HE_MAX_PRIMES];
+};
+
+__device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level, uint32_t L) {
+  return t < level ? t : L + t - level;
+}
+
+// Column pass with the ModUp conversion in its load.  Grid: count * beta * nt * TILES.
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFusedArgs a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
+  constexpr uint32_t N = 1u << LOG_N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t t = b % a.nt;
+  b /= a.nt;
+  const uint32_t j = b % a.beta, i = b / a.beta;
+  const uint32_t lo = a.lo[j], cnt = a.cnt[j];
+  if (t >= lo && t < lo + cnt) return;  // the digit's own limbs are used as they are
+  const uint32_t prime = ks_prime(t, a.level, a.L);
+  const PrimeDev pr = a.primes[prime];
+  stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
+  const uint64_t* tab = a.consts + a.off[j];
+  const uint64_t* mat = tab + 2 * cnt;
+  const uint64_t* x = a.d2c + (size_t)i * a.level * N;
+#pragma unroll 2
+  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+    const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
+    const uint32_t e = S::gidx(tile, k, xx);
+    uint64_t y;
+    if (cnt == 1) {
+      y = reduce64(__ldg(x + (size_t)lo * N + e), pr);  // Q_j / q_lo = 1
+    } else {
+      y = 0;
+      for (uint32_t u = 0; u < cnt; ++u) {
+        const uint64_t qa = a.primes[lo + u].q;
+        const uint64_t v = mul_shoup(__ldg(x + (size_t)(lo + u) * N + e), tab[2 * u], tab[2 * u + 1], qa);
+        y = add_mod(y, mul_mod(reduce64(v, pr), mat[(size_t)u * a.np + prime], pr), pr.q);
+      }
+    }
+    sm[idx + (idx >> 3)] = y;
+  }
+  __syncthreads();
+  uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+  if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+  else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+#pragma unroll 4
+  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+    const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
+    out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
+  }
+}
+
+// Row pass of every digit's tile fused with the key inner product.
+// Grid: count * nt * TILES.  Each thread owns residues idx = tid + u*T.
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedArgs a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
+  constexpr uint32_t N = 1u << LOG_N;
+  constexpr int PER = S::TILE / S::T;  // 8
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t t = b % a.nt, i = b / a.nt;
+  const uint32_t prime = ks_prime(t, a.level, a.L);
+  const PrimeDev pr = a.primes[prime];
+  const bool lazy = pr.q < (1ull << 58);
+  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
+  uint64_t acc0[PER], acc1[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) acc0[u] = acc1[u] = 0;
+  for (uint32_t j = 0; j < a.beta; ++j) {
+    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
+    const uint64_t* kb = a.evk + (((size_t)j * 2 + 0) * a.np + prime) * N;
+    const uint64_t* ka = a.evk + (((size_t)j * 2 + 1) * a.np + prime) * N;
+    if (own) {
+      const uint64_t* dd = a.d + (size_t)i * a.d_stride + (size_t)t * N;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const uint32_t idx = threadIdx.x + u * S::T;
+        const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+        const uint64_t x = __ldg(dd + e);
+        acc0[u] = add_mod(acc0[u], mul_mod(x, __ldg(kb + e), pr), pr.q);
+        acc1[u] = add_mod(acc1[u], mul_mod(x, __ldg(ka + e), pr), pr.q);
+      }
+      continue;
+    }
+    const uint64_t* src = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+    }
+    __syncthreads();
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+      const uint64_t v = sm[idx + (idx >> 3)];
+      const uint64_t x = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
+      acc0[u] = add_mod(acc0[u], mul_mod(x, __ldg(kb + e), pr), pr.q);
+      acc1[u] = add_mod(acc1[u], mul_mod(x, __ldg(ka + e), pr), pr.q);
+    }
+    __syncthreads();  // the tile buffer is reused by the next digit
+  }
+  uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
+  uint64_t* o1 = a.acc + ((size_t)i * 2 * a.nt + a.nt + t) * N;
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const uint32_t idx = threadIdx.x + u * S::T;
+    const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+    o0[e] = acc0[u];
+    o1[e] = acc1[u];
+  }
+}
+
+template <int LOG_N, int M1, int K1, int M2, int K2>
+static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
+  using SC = Shape<LOG_N, M1, K1, true>;
+  using SR = Shape<LOG_N, M2, K2, false>;
+  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
+  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
+  static unsigned long long attr_set = 0;
+  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
+    HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    attr_set |= 1ull << c->device;
+  }
+  const double n = (double)(1u << LOG_N);
+  double own = 0;  // limbs each ciphertext takes as they are
+  for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
+  const double conv = (double)a.beta * a.nt - own;  // converted limbs per ciphertext
+  {
+    const size_t blocks = (size_t)count * a.beta * a.nt * SC::TILES;
+    ProfScope prof(c, "ks_modup_ntt", count * conv * n / 2 * M1, count * n * 8 * (a.level + conv));
+    ks_modup_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
+  }
+  HE_CUDA(cudaGetLastError());
+  {
+    const size_t blocks = (size_t)count * a.nt * SR::TILES;
+    ProfScope prof(c, "ks_ntt_inner_product", count * conv * n / 2 * M2,
+                   count * n * 8 * (conv + own + 2.0 * a.beta * a.nt + 2.0 * a.nt));
+    ks_row_ip<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+// ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
+// sets *handled when N has a compiled shape.
+int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
+             const uint64_t* evk, uint32_t level, uint32_t count, bool* handled) {
+  *handled = false;
+  if (c->ntt_generic || c->log_n < 12 || c->log_n > 16) return HE_OK;
+  KsFusedArgs a;
+  a.d = d;
+  a.d2c = d2c;
+  a.ext = ext;
+  a.acc = acc;
+  a.evk = evk;
+  a.d_stride = d_stride;
+  a.level = level;
+  a.alpha = (uint32_t)c->alpha;
+  a.beta = (level + a.alpha - 1) / a.alpha;
+  a.L = (uint32_t)c->L;
+  a.np = (uint32_t)c->np;
+  a.nt = level + a.alpha;
+  a.primes = c->d_primes;
+  a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.consts = c->d_modup;
+  for (uint32_t j = 0; j < a.beta; ++j) {
+    const ModUpConst& mc = c->modup[level][j];
+    a.lo[j] = mc.lo;
+    a.cnt[j] = mc.cnt;
+    a.off[j] = mc.off;
+  }
+  *handled = true;
+  switch (c->log_n) {
+    case 12: return ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
+    case 13: return ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
+    case 14: return ks_fused_run<14, 7, 4, 7, 4>(c, a, count);
+    case 15: return ks_fused_run<15, 8, 4, 7, 4>(c, a, count);
+    default: return ks_fused_run<16, 8, 4, 8, 3>(c, a, count);
+  }
+}
+
+}  // namespace he

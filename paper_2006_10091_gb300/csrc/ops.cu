@@ -15,6 +15,11 @@
 #include "he_ops.h"
 
 namespace he {
+int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
+             const uint64_t* evk, uint32_t level, uint32_t count, bool* handled);
+}
+
+namespace he {
 
 unsigned grid_for(size_t work) {
   size_t b = (work + 255) / 256;
@@ -62,18 +67,12 @@ const uint64_t* galois_key(const he_ctx* c, uint64_t gal) {
   return it == c->gal.end() ? nullptr : it->second;
 }
 
-int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
-                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar) {
+// ModUp, NTT of the converted limbs and the key inner product as separate
+// kernels (any N).
+static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext,
+                             uint64_t* acc, const uint64_t* evk, uint32_t level, uint32_t count) {
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
   const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
-  uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
-  uint64_t* ext = ar.take<uint64_t>((size_t)count * beta * nt * n);
-  uint64_t* acc = ar.take<uint64_t>((size_t)count * 2 * nt * n);
-  uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
-  if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
-  // 1. coefficient form
-  HE_TRY(ntt_inverse(c, pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level)));
-  // 2. ModUp, then NTT of the converted limbs
   ModUpArgs m;
   m.level = level;
   m.alpha = alpha;
@@ -104,6 +103,24 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
         count, c->log_n, c->d_primes);
   }
   HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar) {
+  const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
+  const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
+  uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
+  uint64_t* ext = ar.take<uint64_t>((size_t)count * beta * nt * n);
+  uint64_t* acc = ar.take<uint64_t>((size_t)count * 2 * nt * n);
+  uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
+  // 1. coefficient form
+  HE_TRY(ntt_inverse(c, pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level)));
+  // 2-3. fused ModUp + NTT + inner product where N has compiled shapes
+  bool fused = false;
+  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, &fused));
+  if (!fused) HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
   // 4. ModDown
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
                            (size_t)nt * n, count * 2, alpha, level, level)));

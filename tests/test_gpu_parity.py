@@ -362,3 +362,50 @@ def test_errors_are_reported(small, he):
     with pytest.raises(he.HeError) as e:
         he.he_add(small.g, ga, ga, small_out)
     assert e.value.code == he.HE_EINVAL
+
+
+# ------------------------------------------------------------------ fused key switching (N >= 2^12)
+
+
+@pytest.fixture(scope="module")
+def wide():
+    # N = 2^12, six 45-bit limbs, two 55-bit special primes (digits of two limbs)
+    return Pair(12, 6, 45, 2, 55, 2.0 ** 45, seed=8, rots=[5, -3])
+
+
+@pytest.mark.parametrize("level", [6, 5, 2])
+def test_fused_keyswitch_bit_exact(wide, he, level):
+    import torch
+    d = workloads.residues(500 + level, wide.o.primes[:level], wide.n)[0]
+    k0, k1 = wide.o.keyswitch(d, level, -1)
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    for generic in (False, True):  # fused kernels, then the unfused sequence
+        he.he_set_tuning(wide.g, "ntt_generic", generic)
+        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+        he.he_keyswitch(wide.g, dt, level, 0, o0, o1)
+        assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
+        assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
+    he.he_set_tuning(wide.g, "ntt_generic", False)
+
+
+def test_fused_rotation_and_mul_bit_exact(wide, he):
+    m1, m2 = workloads.int_poly(61, wide.n, 1 << 36), workloads.int_poly(62, wide.n, 1 << 36)
+    ga, oa = wide.gpu_enc(m1, 5, 61), wide.orc_enc(m1, 5, 61)
+    gb, ob = wide.gpu_enc(m2, 5, 62), wide.orc_enc(m2, 5, 62)
+    out = wide.g.new_ct(5)
+    he.he_rotate(wide.g, ga, -3, out)
+    assert_same_residues(out, wide.o.rotate(oa, -3), he, wide.g)
+    he.he_mul_relin_rescale(wide.g, ga, gb, out)
+    assert_same_residues(out, wide.o.mul_relin_rescale(oa, ob), he, wide.g)
+
+
+def test_fused_single_special_prime_n13(he):
+    p = Pair(13, 4, 40, 1, 60, 2.0 ** 40, seed=9, rots=[1])
+    m1, m2 = workloads.int_poly(71, p.n, 1 << 30), workloads.int_poly(72, p.n, 1 << 30)
+    ga, oa = p.gpu_enc(m1, 4, 71), p.orc_enc(m1, 4, 71)
+    gb, ob = p.gpu_enc(m2, 4, 72), p.orc_enc(m2, 4, 72)
+    out = p.g.new_ct(4)
+    he.he_mul_relin_rescale(p.g, ga, gb, out)
+    assert_same_residues(out, p.o.mul_relin_rescale(oa, ob), he, p.g)
+    he.he_rotate(p.g, ga, 1, out)
+    assert_same_residues(out, p.o.rotate(oa, 1), he, p.g)
