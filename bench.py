@@ -520,9 +520,47 @@ def run_micro(args):
     print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
 
 
+def run_micro_keyswitch(args):
+    """Rotation by 8 slots (automorphism + key switching) of `--polys`
+    ciphertexts at level 7 of the benchmark parameters, with the per-class
+    kernel times of the batch."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10091_gb300 as he
+    from paper_2006_10091_gb300 import workloads
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=[8],
+                     stream=stream.cuda_stream)
+    level, count = L - 1, args.polys
+    host = workloads.residues(2, ctx.primes[:level], ctx.n, parts=2 * count).reshape(count, 2, level, ctx.n)
+    A, O = ctx.new_ct(level, count), ctx.new_ct(level, count)
+    he.he_ct_import_batch(ctx, host, level, SCALE, A)
+    for _ in range(args.warmup):
+        he.he_rotate_batch(ctx, A, 8, O)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        he.he_rotate_batch(ctx, A, 8, O)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    he.he_profile_enable(ctx, True)
+    he.he_rotate_batch(ctx, A, 8, O)
+    prof = {k: he.he_profile_read(ctx, k) for k in he.he_profile_names(ctx)}
+    he.he_profile_enable(ctx, False)
+    print(json.dumps({"micro": "keyswitch", "N": ctx.n, "level": level, "ciphertexts": count,
+                      "ms_per_batch": ms, "rotations_per_s": count * 1000.0 / ms,
+                      "kernels": {k: {"ms": v["ms"], "GBs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
+                                      "work_per_s": v["work"] / max(v["ms"], 1e-9) * 1e3}
+                                  for k, v in prof.items()}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt"], default=None, help="time one kernel class alone")
+    ap.add_argument("--micro", choices=["ntt", "keyswitch"], default=None, help="time one kernel class alone")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--polys", type=int, default=256)
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,8 +570,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.micro:
+    if args.micro == "ntt":
         run_micro(args)
+        return
+    if args.micro == "keyswitch":
+        run_micro_keyswitch(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -239,16 +239,91 @@ int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
  * configuration) as a CUDA graph and replayed; this needs a non-default
  * stream, and a replay reuses the refresh encryptions' random streams. */
 typedef struct he_lr_shard {
-  const he_ct* Z;
+  const he_ct* Z;        /* nZ data ciphertexts */
   size_t nZ;
-  const he_ct* W;
-  he_ct* W_out;
+  const he_ct* W;        /* encrypted weights */
+  he_ct* W_out;          /* gradient step: the new weights */
+  he_ct* S_out;          /* inference: nZ outputs, S_k = p(M_k) (may be NULL for the step) */
+  uint32_t refresh_cid;  /* ciphertext id of the refresh encryption (if one is needed) */
+  uint32_t pad;
 } he_lr_shard;
 
 #define HE_LR_GRAPH 1
 
 int he_lr_gradient_step_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count,
                                 const he_lr_config* cfg, uint32_t refresh_level, int flags);
+
+/* Encrypted inference of the same model (the first half of the step): for
+ * every data ciphertext Z_k of every shard, S_k = p(M_k) with M_k = the
+ * per-sample inner products y_s w.x_s replicated over each sample's slots
+ * (packing as in he_lr_gradient_step) and p the configured cubic (c_i * lr).
+ * S_out[k] receives level l - 3 and W's scale (l = the weights' level after
+ * any refresh, which must be >= 5 so that the result keeps two limbs).
+ * Grouping, refresh and graph capture as in he_lr_gradient_step_workers. */
+int he_lr_inference_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count,
+                            const he_lr_config* cfg, uint32_t refresh_level, int flags);
+
+/* ---- Serving: a continuous-batching request loop ----------------------------
+ * The paper's workers answer gradient steps (Algorithm 1 line 7) and, with
+ * the same model, inference.  A server holds contexts of several ring sizes
+ * (keys resident in HBM) and a scheduler thread.  Requests carry host
+ * residues; the scheduler admits them oldest first while their device memory
+ * (inputs, outputs) plus the slots' workspaces stay within hbm_budget, groups
+ * pending requests with the same context, kind, data level, scales and
+ * configuration into a wave of at most max_wave, and runs each wave as one
+ * batched call on one of max_inflight streams per context: requests arriving
+ * while waves run join the next free slot without waiting for the others, and
+ * waves on different streams overlap on the device.  A request whose weights
+ * have too few limbs is refreshed in-process to the data's level first, with
+ * random stream refresh_cid, so its result does not depend on its wave. */
+enum { HE_REQ_GRADIENT = 0, HE_REQ_INFERENCE = 1 };
+
+typedef struct he_server he_server;
+
+typedef struct he_server_config {
+  he_ctx* const* ctxs;    /* contexts, one per ring size class; not owned */
+  size_t n_ctx;
+  size_t hbm_budget;      /* bytes of device memory for request buffers and workspaces */
+  uint32_t max_inflight;  /* concurrent waves per context (streams), 1..16 */
+  uint32_t max_wave;      /* requests per wave */
+} he_server_config;
+
+typedef struct he_request {
+  uint32_t ctx;          /* index into the server's contexts */
+  uint32_t kind;         /* HE_REQ_GRADIENT or HE_REQ_INFERENCE */
+  uint32_t nZ;           /* data ciphertexts */
+  uint32_t z_level;      /* level of the data (>= 6 for a step, >= 5 for inference) */
+  uint32_t w_level;      /* level of the weights (<= z_level) */
+  uint32_t refresh_cid;  /* ciphertext id of the refresh encryption, if one is needed */
+  double z_scale, w_scale;
+  const uint64_t* Z;     /* host, nZ x [2][z_level][N] residues (pinned memory keeps the loop asynchronous) */
+  const uint64_t* W;     /* host, [2][w_level][N] */
+  he_lr_config cfg;
+  uint64_t* out;         /* host result: step [2][l-5][N], inference nZ x [2][l-3][N], l = weights' level
+                            after any refresh; pinned */
+  size_t out_words;      /* capacity of out */
+} he_request;
+
+typedef struct he_result {
+  uint64_t id;
+  int32_t status;        /* HE_OK or the error of the request's wave */
+  uint32_t level;        /* level of the result ciphertext(s) */
+  double scale;          /* their scale */
+  double latency_ms;     /* submit to completion seen by the scheduler */
+} he_result;
+
+int he_server_create(const he_server_config* cfg, he_server** out);
+/* Queue a request (the descriptor is copied; host buffers must stay valid
+ * until its result is polled).  Returns its id. */
+int he_server_submit(he_server* s, const he_request* req, uint64_t* id);
+/* Results completed since the last poll (up to cap). */
+int he_server_poll(he_server* s, he_result* results, size_t cap, size_t* n);
+/* Wait until nothing is pending or running (HE_ETIMEOUT after timeout_s). */
+int he_server_drain(he_server* s, double timeout_s);
+/* Device bytes held now and at most so far (request buffers and slot
+ * workspaces), waves launched, and the most waves running at once. */
+int he_server_stats(he_server* s, size_t* used, size_t* peak_used, size_t* waves, size_t* peak_running);
+int he_server_destroy(he_server* s);
 
 /* The key holder's refresh (Algorithm 1 lines 8-10, Algorithm 2 lines 8-11),
  * simulated in-process: decrypt, decode, re-encode at out_scale and encrypt

@@ -100,6 +100,9 @@ def _load():
             lib.orc_get_beta.argtypes = [VP]
             lib.orc_get_key.argtypes = [VP, ctypes.c_int, VP]
             lib.orc_lr_mask.argtypes = [VP, ctypes.c_int, ctypes.c_double, VP]
+            lib.orc_lr_inference.argtypes = [
+                VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int, ctypes.c_double,
+                VP, ctypes.c_double, ctypes.c_int, VP, VP]
             lib.orc_lr_gradient_step.argtypes = [
                 VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int,
                 ctypes.c_double, VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, VP,
@@ -435,3 +438,18 @@ class Oracle:
         if rc:
             raise ValueError(f"lr_gradient_step failed ({rc})")
         return Ciphertext(out, lvl.value, sc.value)
+
+    def lr_inference(self, Z: list, W: Ciphertext, coeffs, lr: float, g: int) -> list:
+        """S_k = p(M_k) for each data ciphertext (level W.level - 3)."""
+        arrs = [_u64(z.data) for z in Z]
+        ptrs = np.array([a.ctypes.data for a in arrs], dtype=np.uint64)
+        co = np.ascontiguousarray(coeffs, dtype=np.float64)
+        lv = W.level - 3
+        out = np.zeros((len(Z), 2, lv, self.n), dtype=np.uint64)
+        sc = ctypes.c_double(0.0)
+        rc = self._lib.orc_lr_inference(self.ptr, _p(ptrs), len(Z), Z[0].level, float(Z[0].scale),
+                                         _p(_u64(W.data)), W.level, float(W.scale), _p(co), float(lr), g,
+                                         _p(out), ctypes.byref(sc))
+        if rc:
+            raise ValueError(f"lr_inference failed ({rc})")
+        return [Ciphertext(out[k], lv, sc.value) for k in range(len(Z))]

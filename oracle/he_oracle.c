@@ -1287,3 +1287,65 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
   free(Zd.d); free(Gk.d); free(R.d);
   return rc;
 }
+
+/* Encrypted inference of the same model (the first half of the step): for
+ * each data ciphertext, S = p(M) with M the replicated per-sample inner
+ * products, following the step's op sequence up to S, with the polynomial's
+ * result produced at W's scale: sS = sW (then sA, sigA, sigB, sigQ and the
+ * constants as in the step).  Output: nZ ciphertexts at level l0 - 3, each
+ * [2][l0-3][N] in `outs` back to back; *scale_out = the scale of S. */
+int orc_lr_inference(orc_ctx* c, const uint64_t* const* Z, int nZ, int levelZ, double sZ, const uint64_t* Wd,
+                     int levelW, double sW, const double coeffs[4], double lr, int g, uint64_t* outs,
+                     double* scale_out) {
+  uint32_t n = c->n;
+  int l0 = levelZ;
+  if (levelW != levelZ || l0 < 5 || nZ < 1) return -1;
+  if (g < 1 || (g & (g - 1)) || g > (int)n / 2) return -1;
+  int F = (int)(n / 2) / g;
+  int logF = ilog2i(F);
+  const uint64_t* q = c->q;
+  double sU = sZ * sW / (double)q[l0 - 1];
+  double sT = sU * sU / (double)q[l0 - 2];
+  double sS = sW;
+  double sA = (sS * (double)q[l0 - 3]) / sT;
+  double sigA = (sA * (double)q[l0 - 2]) / sU;
+  double sigB = (sS * (double)q[l0 - 2]) / sU;
+  double sigQ = (sS * (double)q[l0 - 3]) / sT;
+  int64_t kA = round_const(coeffs[3] * lr * sigA);
+  int64_t kB = round_const(coeffs[1] * lr * sigB);
+  int64_t kQ = round_const(coeffs[2] * lr * sigQ);
+  int rc = 0;
+  orc_ct U = ct_new(c, l0 - 1, sU), T = ct_new(c, l0 - 2, sT), A = ct_new(c, l0 - 2, 0.0);
+  orc_ct Cc = ct_new(c, l0 - 3, 0.0), B = ct_new(c, l0 - 2, 0.0), Qq = ct_new(c, l0 - 3, 0.0);
+  uint64_t* tmp = malloc(sizeof(uint64_t) * 2 * (size_t)l0 * n);
+  for (int k = 0; k < nZ && rc == 0; k++) {
+    orc_mul_relin_rescale(c, Z[k], Wd, l0, U.d);
+    rc = rotsum(c, &U, g, logF);
+    if (rc) break;
+    orc_mul_relin_rescale(c, U.d, U.d, l0 - 1, T.d);
+    orc_mul_int(c, U.d, l0 - 1, kA, tmp);
+    orc_rescale(c, tmp, l0 - 1, A.d);
+    A.scale = (sU * sigA) / (double)q[l0 - 2];
+    orc_mul_relin_rescale(c, T.d, A.d, l0 - 2, Cc.d);
+    Cc.scale = sT * A.scale / (double)q[l0 - 3];
+    orc_mul_int(c, U.d, l0 - 1, kB, tmp);
+    orc_rescale(c, tmp, l0 - 1, B.d);
+    B.scale = (sU * sigB) / (double)q[l0 - 2];
+    orc_drop(c, B.d, l0 - 2, l0 - 3, B.d);
+    if (!scales_match(Cc.scale, B.scale)) { rc = -3; break; }
+    orc_add(c, Cc.d, B.d, l0 - 3, Cc.d);
+    if (coeffs[2] != 0.0) {
+      orc_mul_int(c, T.d, l0 - 2, kQ, tmp);
+      orc_rescale(c, tmp, l0 - 2, Qq.d);
+      Qq.scale = (sT * sigQ) / (double)q[l0 - 3];
+      if (!scales_match(Cc.scale, Qq.scale)) { rc = -3; break; }
+      orc_add(c, Cc.d, Qq.d, l0 - 3, Cc.d);
+    }
+    orc_add_int(c, Cc.d, l0 - 3, round_const(coeffs[0] * lr * Cc.scale), Cc.d);
+    memcpy(outs + (size_t)k * 2 * (l0 - 3) * n, Cc.d, sizeof(uint64_t) * 2 * (size_t)(l0 - 3) * n);
+    *scale_out = Cc.scale;
+  }
+  free(tmp);
+  free(U.d); free(T.d); free(A.d); free(Cc.d); free(B.d); free(Qq.d);
+  return rc;
+}

@@ -42,15 +42,35 @@ class he_ct(ctypes.Structure):
 
 class he_lr_shard(ctypes.Structure):
     _fields_ = [("Z", ctypes.c_void_p), ("nZ", ctypes.c_size_t), ("W", ctypes.c_void_p),
-                ("W_out", ctypes.c_void_p)]
+                ("W_out", ctypes.c_void_p), ("S_out", ctypes.c_void_p), ("refresh_cid", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 HE_LR_GRAPH = 1
+HE_REQ_GRADIENT, HE_REQ_INFERENCE = 0, 1
 
 
 class he_lr_config(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_double * 4), ("lr", ctypes.c_double),
                 ("g", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mask_scale", ctypes.c_double)]
+
+
+class he_server_config(ctypes.Structure):
+    _fields_ = [("ctxs", ctypes.c_void_p), ("n_ctx", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_uint32), ("max_wave", ctypes.c_uint32)]
+
+
+class he_request(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("nZ", ctypes.c_uint32),
+                ("z_level", ctypes.c_uint32), ("w_level", ctypes.c_uint32), ("refresh_cid", ctypes.c_uint32),
+                ("z_scale", ctypes.c_double), ("w_scale", ctypes.c_double), ("Z", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("cfg", he_lr_config), ("out", ctypes.c_void_p),
+                ("out_words", ctypes.c_size_t)]
+
+
+class he_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("level", ctypes.c_uint32),
+                ("scale", ctypes.c_double), ("latency_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -107,6 +127,14 @@ def load():
         "he_rescale_noalloc": [VP, CTP, CTP],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
+        "he_lr_inference_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
+                                    ctypes.c_uint32, ctypes.c_int],
+        "he_server_create": [ctypes.POINTER(he_server_config), ctypes.POINTER(VP)],
+        "he_server_submit": [VP, ctypes.POINTER(he_request), ctypes.POINTER(ctypes.c_uint64)],
+        "he_server_poll": [VP, VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+        "he_server_drain": [VP, ctypes.c_double],
+        "he_server_stats": [VP, VP, VP, VP, VP],
+        "he_server_destroy": [VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -378,20 +406,45 @@ def he_lr_gradient_step(ctx, Z: list, W: Ciphertext, cfg: he_lr_config, W_out: C
     return W_out
 
 
+def _shards(shards, infer):
+    keep, arr = [], (he_lr_shard * len(shards))()
+    for k, sh in enumerate(shards):
+        Z, W, out = sh[0], sh[1], sh[2]
+        cid = sh[3] if len(sh) > 3 else 0x40000000 + k
+        zs, w = _batch(Z), W.c()
+        if infer:
+            so = _batch(out)
+            keep.append((zs, w, so))
+            arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w), None,
+                                 ctypes.cast(so, ctypes.c_void_p), cid, 0)
+        else:
+            wo = out.c()
+            keep.append((zs, w, wo))
+            arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w),
+                                 ctypes.addressof(wo), None, cid, 0)
+    return arr, keep
+
+
 def he_lr_gradient_step_workers(ctx, shards: list, cfg: he_lr_config, refresh_level: int = 0,
                                 graph: bool = False):
-    """shards: list of (Z list, W, W_out) per worker."""
-    keep = []
-    arr = (he_lr_shard * len(shards))()
-    for k, (Z, W, W_out) in enumerate(shards):
-        zs, w, wo = _batch(Z), W.c(), W_out.c()
-        keep.append((zs, w, wo))
-        arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w),
-                             ctypes.addressof(wo))
+    """shards: list of (Z list, W, W_out[, refresh_cid]) per worker."""
+    arr, keep = _shards(shards, False)
     _check(load().he_lr_gradient_step_workers(ctx.ptr, arr, len(shards), ctypes.byref(cfg), refresh_level,
                                               HE_LR_GRAPH if graph else 0))
-    for (Z, W, W_out), (_, _, wo) in zip(shards, keep):
-        W_out.update(wo)
+    for sh, (_, _, wo) in zip(shards, keep):
+        sh[2].update(wo)
+    return [s[2] for s in shards]
+
+
+def he_lr_inference_workers(ctx, shards: list, cfg: he_lr_config, refresh_level: int = 0,
+                            graph: bool = False):
+    """shards: list of (Z list, W, S_out list[, refresh_cid]) per worker."""
+    arr, keep = _shards(shards, True)
+    _check(load().he_lr_inference_workers(ctx.ptr, arr, len(shards), ctypes.byref(cfg), refresh_level,
+                                          HE_LR_GRAPH if graph else 0))
+    for sh, (_, _, so) in zip(shards, keep):
+        for o, s in zip(sh[2], so):
+            o.update(s)
     return [s[2] for s in shards]
 
 
@@ -463,3 +516,59 @@ def galois_elt(log_n: int, r: int) -> int:
     """5^(r mod N/2) mod 2N, the Galois element of a left rotation by r."""
     slots = 1 << (log_n - 1)
     return pow(5, r % slots, 2 << log_n)
+
+
+class Server:
+    """he_server: a continuous-batching request loop over several contexts."""
+
+    def __init__(self, ctxs: list, hbm_budget: int, max_inflight: int = 4, max_wave: int = 16):
+        self._ctxs = ctxs
+        self._arr = (ctypes.c_void_p * len(ctxs))(*[c.ptr.value for c in ctxs])
+        cfg = he_server_config(ctypes.cast(self._arr, ctypes.c_void_p), len(ctxs), int(hbm_budget),
+                               max_inflight, max_wave)
+        h = ctypes.c_void_p()
+        _check(load().he_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.ptr = h
+        self._keep = {}
+
+    def submit(self, ctx_index: int, kind: int, Z_host, z_level: int, z_scale: float, W_host, w_level: int,
+               w_scale: float, cfg: he_lr_config, out_host, refresh_cid: int = 0) -> int:
+        """Z_host, W_host, out_host: host arrays or (pinned) CPU torch tensors of uint64 residues."""
+        nZ = Z_host.shape[0]
+        r = he_request(ctx_index, kind, nZ, z_level, w_level, refresh_cid, float(z_scale), float(w_scale),
+                       _addr(Z_host), _addr(W_host), cfg, _addr(out_host), _nwords(out_host))
+        rid = ctypes.c_uint64()
+        _check(load().he_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (Z_host, W_host, out_host)
+        return rid.value
+
+    def poll(self, cap: int = 1024) -> list:
+        res = (he_result * cap)()
+        n = ctypes.c_size_t()
+        _check(load().he_server_poll(self.ptr, res, cap, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            r = res[i]
+            self._keep.pop(r.id, None)
+            out.append({"id": r.id, "status": r.status, "level": r.level, "scale": r.scale,
+                        "latency_ms": r.latency_ms})
+        return out
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(load().he_server_drain(self.ptr, float(timeout_s)))
+
+    def stats(self) -> dict:
+        v = [ctypes.c_size_t() for _ in range(4)]
+        _check(load().he_server_stats(self.ptr, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("used", "peak_used", "waves", "peak_running"), [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().he_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -21,13 +21,15 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+size_t ws_alloc_bytes(size_t bytes) { return bytes + bytes / 8 + (1 << 20); }
+
 int ws_reserve(he_ctx* c, size_t bytes) {
   if (c->ws.size >= bytes) return HE_OK;
   HE_CUDA(cudaStreamSynchronize(c->stream));
   if (c->ws.ptr) cudaFree(c->ws.ptr);
   c->ws.ptr = nullptr;
   c->ws.size = 0;
-  const size_t want = bytes + bytes / 8 + (1 << 20);
+  const size_t want = ws_alloc_bytes(bytes);
   if (cudaMalloc(&c->ws.ptr, want) != cudaSuccess) {
     cudaGetLastError();
     c->ws.ptr = nullptr;
@@ -91,9 +93,54 @@ bool uniform_view(const he_ct* a, size_t count, CtBatch* out) {
   return true;
 }
 
+he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
+  he_ctx* v = new he_ctx();
+  v->prm = base->prm;
+  v->view = true;
+  v->log_n = base->log_n;
+  v->n = base->n;
+  v->L = base->L;
+  v->alpha = base->alpha;
+  v->np = base->np;
+  v->beta = base->beta;
+  v->q = base->q;
+  v->psi = base->psi;
+  v->stream = stream;
+  v->device = base->device;
+  v->d_primes = base->d_primes;
+  v->d_tw = base->d_tw;
+  v->d_itw = base->d_itw;
+  v->d_two64 = base->d_two64;
+  v->d_gauss = base->d_gauss;
+  v->gK = base->gK;
+  v->modup = base->modup;
+  v->d_modup = base->d_modup;
+  v->d_moddown = base->d_moddown;
+  v->d_rescale = base->d_rescale;
+  v->d_garner = base->d_garner;
+  v->chunk_bytes = base->chunk_bytes;
+  v->lr_chunk = base->lr_chunk;
+  v->ntt_generic = base->ntt_generic;
+  v->P_mod_q = base->P_mod_q;
+  v->d_s = base->d_s;
+  v->d_pk = base->d_pk;
+  v->d_rlk = base->d_rlk;
+  v->gal = base->gal;
+  return v;
+}
+
 static void destroy(he_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->view) {  // only the view's own state
+    for (auto& kv : c->lr_masks) cudaFree(kv.second);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(c->ws.ptr);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    prof_clear(c);
+    delete c;
+    return;
+  }
   cudaFree(c->d_primes);
   cudaFree(c->d_tw);
   cudaFree(c->d_itw);
@@ -140,6 +187,8 @@ int mul_plain_dev(he_ctx* c, CtBatch A, const int64_t* d_coeffs, CtBatch O, uint
   HE_CUDA(cudaGetLastError());
   return HE_OK;
 }
+
+void ctx_destroy(he_ctx* c) { destroy(c); }
 
 }  // namespace he
 

@@ -63,6 +63,7 @@ struct ProfClass {
 
 struct he_ctx {
   he_params prm;
+  bool view = false;  // shares the tables and keys of another context (frees only its own state)
   int log_n = 0, n = 0, L = 0, alpha = 0, np = 0, beta = 0;
   std::vector<uint64_t> q;    // [np]: limbs then special primes
   std::vector<uint64_t> psi;  // [np]
@@ -128,6 +129,9 @@ void prof_clear(he_ctx* c);
 
 // ---- workspace ----------------------------------------------------------------
 int ws_reserve(he_ctx* c, size_t bytes);  // may reallocate (synchronises first)
+// A context sharing `base`'s tables and keys with its own stream and workspace.
+he_ctx* ctx_view(he_ctx* base, cudaStream_t stream);
+void ctx_destroy(he_ctx* c);
 int stage_reserve(he_ctx* c, size_t bytes);
 
 // ---- NTT (ntt.cu) -------------------------------------------------------------

@@ -59,6 +59,20 @@ int accumulate_batch(he_ctx* c, CtBatch in, uint32_t count, CtBatch acc, uint32_
 
 const uint64_t* galois_key(const he_ctx* c, uint64_t gal);
 bool uniform_view(const he_ct* a, size_t count, CtBatch* out);
+// The logistic-regression step (infer = false) or inference (true) for
+// several workers; see he_lr_gradient_step_workers.
+int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg, uint32_t refresh_level,
+             int flags, bool infer);
+// Workspace bytes lr_entry reserves for shards of these shapes (circuit input
+// level l0, data ciphertexts nZ, weights refreshed first or not).
+struct LrShape {
+  uint32_t l0;
+  size_t nZ;
+  bool refresh;
+};
+size_t lr_ws_bytes(he_ctx* c, const LrShape* sh, size_t count, uint32_t refresh_level);
+// Bytes ws_reserve allocates for a request of `bytes` (headroom included).
+size_t ws_alloc_bytes(size_t bytes);
 int mul_plain_dev(he_ctx* c, CtBatch A, const int64_t* d_coeffs, CtBatch O, uint32_t level, uint32_t count,
                   Arena& ar);
 

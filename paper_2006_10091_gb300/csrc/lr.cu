@@ -90,7 +90,11 @@ struct LrPlan {
   bool has_c2;
 };
 
-static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_lr_config* cfg, LrPlan* p) {
+// Scale plan; for inference the polynomial's output S is produced at W's scale
+// (it is the result, two levels above the lowest), otherwise at the scale
+// that brings the step's output back to W's scale (see the header comment).
+static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_lr_config* cfg, bool infer,
+                   LrPlan* p) {
   const std::vector<uint64_t>& q = c->q;
   p->l0 = l0;
   p->g = cfg->g;
@@ -101,7 +105,7 @@ static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_
   const double lr = cfg->lr, ms = cfg->mask_scale;
   p->sU = sZ * sW / (double)q[l0 - 1];
   p->sT = p->sU * p->sU / (double)q[l0 - 2];
-  p->sS = ((sW * (double)q[l0 - 5]) * (double)q[l0 - 4]) / (ms * sZ);
+  p->sS = infer ? sW : ((sW * (double)q[l0 - 5]) * (double)q[l0 - 4]) / (ms * sZ);
   const double sA = (p->sS * (double)q[l0 - 3]) / p->sT;
   p->sigA = (sA * (double)q[l0 - 2]) / p->sU;
   p->sigB = (p->sS * (double)q[l0 - 2]) / p->sU;
@@ -117,6 +121,7 @@ static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_
   p->sQ = (p->sT * p->sigQ) / (double)q[l0 - 3];
   if (p->has_c2 && !scales_eq(p->sC, p->sQ)) return fail(HE_ESCALE, "quadratic term scale mismatch");
   if (!to_int(cfg->coeffs[0] * lr * p->sC, &p->k0)) return fail(HE_EINVAL, "constant beyond int64");
+  if (infer) return HE_OK;
   p->sG = p->sC * sZ / (double)q[l0 - 4];
   p->sR = (p->sG * ms) / (double)q[l0 - 5];
   if (!scales_eq(p->sR, sW)) return fail(HE_ESCALE, "output scale mismatch");
@@ -169,7 +174,7 @@ static CtBatch carve(Arena& a, size_t count, uint32_t cap, uint32_t n) {
 // The per-ciphertext part of the step for m data ciphertexts Zc with weights
 // Wc (stride 0: one W for all): G_k = p(M_k) * Z_k in b.Gk.
 static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtBatch Wc, uint32_t m, LrBufs& b,
-                    Arena& ops) {
+                    Arena& ops, bool infer) {
   const uint32_t l0 = P.l0;
   auto fresh = [&]() -> Arena& {
     ops.off = 0;
@@ -196,6 +201,7 @@ static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtB
     HE_TRY(addsub_batch(c, b.Cc, b.Q, b.Cc, 0, l0 - 3, m));
   }
   HE_TRY(add_int_batch(c, b.Cc, b.Cc, P.k0, l0 - 3, m));
+  if (infer) return HE_OK;  // S_k = p(M_k) is in b.Cc
   // G_k = S * Z_k
   HE_TRY(mul_relin_batch(c, b.Cc, Zc, l0 - 3, m, b.Gk, true, fresh()));
   return HE_OK;
@@ -229,7 +235,9 @@ struct Shard {
   size_t nZ;
   he_ct W;       // weights at the level the step runs at (refreshed if needed)
   he_ct* W_out;
+  he_ct* S_out;  // inference outputs
   uint32_t l0;
+  uint32_t cid;  // refresh encryption id
   bool refresh;
   const he_ct* W_in;
 };
@@ -241,7 +249,7 @@ static int check_aligned(const void* p) { return ((uintptr_t)p & 15) == 0 ? HE_O
 // per-ciphertext results are summed into their shard's gradient, and the
 // final stage runs once over all shards of the group.
 static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, uint32_t refresh_level,
-                  Arena& pool) {
+                  Arena& pool, bool infer) {
   const uint32_t n = c->n;
   // in-process refresh of weights below the circuit's depth (Algorithm 1 lines 8-10)
   for (size_t k = 0; k < sh.size(); ++k) {
@@ -260,7 +268,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     HE_TRY(decrypt_dev(c, sh[k].W_in, m, d));
     HE_TRY(decode_dev(c, d, sh[k].W_in->scale, re, n / 2, fft));
     HE_TRY(encode_dev(c, re, n / 2, sh[k].W.scale, coeffs, fft, ovf));
-    HE_TRY(encrypt_dev(c, coeffs, refresh_level, 0, 0x40000000u + (uint32_t)k, &sh[k].W, scratch));
+    HE_TRY(encrypt_dev(c, coeffs, refresh_level, 0, sh[k].cid, &sh[k].W, scratch));
   }
   // groups of shards that share the plan
   std::vector<bool> done(sh.size(), false);
@@ -275,7 +283,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
       }
     const uint32_t l0 = sh[k0].l0;
     LrPlan P;
-    HE_TRY(lr_plan(c, l0, sh[k0].Z[0].scale, sh[k0].W.scale, cfg, &P));
+    HE_TRY(lr_plan(c, l0, sh[k0].Z[0].scale, sh[k0].W.scale, cfg, infer, &P));
     LrGal gl;
     HE_TRY(lr_gal(c, P, &gl));
     const int64_t* mask = nullptr;
@@ -350,8 +358,21 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
         Zc = b.Zcopy;
         Wc = b.Wrep;
       }
-      HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops));
+      HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops, infer));
       size_t off = 0;
+      if (infer) {  // copy S_k of each segment's ciphertexts to their outputs
+        for (auto& sg : seg) {
+          const Shard& s = sh[grp[sg.first]];
+          for (size_t i = 0; i < sg.second.second; ++i) {
+            CtBatch src = b.Cc;
+            src.base += (off + i) * b.Cc.stride;
+            he_ct& o = s.S_out[sg.second.first + i];
+            HE_TRY(copy_batch(c, src, CtBatch{o.data, 0, o.cap, 0}, l0 - 3, 1));
+          }
+          off += sg.second.second;
+        }
+        continue;
+      }
       for (auto& sg : seg) {
         CtBatch gk = b.Gk, gs = G;
         gk.base += off * b.Gk.stride;
@@ -360,6 +381,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
         off += sg.second.second;
       }
     }
+    if (infer) continue;
     HE_TRY(lr_finish(c, P, gl, mask, G, ns, H1, R, ops));
     for (uint32_t i = 0; i < ns; ++i) {
       Shard& s = sh[grp[i]];
@@ -373,13 +395,13 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
 }
 
 // Workspace words lr_run needs for these shards.
-static size_t lr_words(he_ctx* c, const std::vector<Shard>& sh, uint32_t refresh_level) {
+static size_t lr_words(he_ctx* c, const LrShape* sh, size_t count, uint32_t refresh_level) {
   const size_t n = c->n;
   size_t need = 0;
   std::map<uint32_t, std::pair<size_t, size_t>> groups;  // l0 -> (shards, ciphertexts)
-  for (const Shard& s : sh) {
-    groups[s.l0].first += 1;
-    groups[s.l0].second += s.nZ;
+  for (size_t k = 0; k < count; ++k) {
+    groups[sh[k].l0].first += 1;
+    groups[sh[k].l0].second += sh[k].nZ;
   }
   for (auto& kv : groups) {
     const uint32_t l0 = kv.first;
@@ -394,10 +416,23 @@ static size_t lr_words(he_ctx* c, const std::vector<Shard>& sh, uint32_t refresh
   return std::max(need, ref);
 }
 
+size_t lr_ws_bytes(he_ctx* c, const LrShape* sh, size_t count, uint32_t refresh_level) {
+  size_t nref = 0;
+  for (size_t k = 0; k < count; ++k) nref += sh[k].refresh;
+  const size_t ref_words = nref * 2 * (size_t)refresh_level * c->n;
+  return (lr_words(c, sh, count, refresh_level) + ref_words + 8192) * sizeof(uint64_t);
+}
+
 static int validate_shard(he_ctx* c, const he_lr_shard& in, const he_lr_config* cfg, uint32_t refresh_level,
-                          Shard* out) {
-  if (!in.Z || in.nZ == 0 || !in.W || !in.W->data || !in.W_out || !in.W_out->data)
-    return fail(HE_EINVAL, "shard: null argument or no data ciphertexts");
+                          bool infer, Shard* out) {
+  if (!in.Z || in.nZ == 0 || !in.W || !in.W->data) return fail(HE_EINVAL, "shard: null argument or no data ciphertexts");
+  if (!infer && (!in.W_out || !in.W_out->data)) return fail(HE_EINVAL, "shard: null output");
+  if (infer) {
+    if (!in.S_out) return fail(HE_EINVAL, "shard: null inference outputs");
+    for (size_t k = 0; k < in.nZ; ++k)
+      if (!in.S_out[k].data || ((uintptr_t)in.S_out[k].data & 15)) return fail(HE_EINVAL, "shard: bad inference output");
+  }
+  const uint32_t need = infer ? 5 : 6;
   const uint32_t zl = in.Z[0].level;
   for (size_t k = 0; k < in.nZ; ++k) {
     const he_ct& z = in.Z[k];
@@ -406,54 +441,53 @@ static int validate_shard(he_ctx* c, const he_lr_shard& in, const he_lr_config* 
     if (check_aligned(z.data)) return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
     if (!scales_eq(z.scale, in.Z[0].scale)) return fail(HE_ESCALE, "data ciphertexts at different scales");
   }
-  if (check_aligned(in.W->data) || check_aligned(in.W_out->data))
+  if (check_aligned(in.W->data) || (!infer && check_aligned(in.W_out->data)))
     return fail(HE_EINVAL, "ciphertext data must be 16-byte aligned");
   out->Z = in.Z;
   out->nZ = in.nZ;
   out->W_in = in.W;
   out->W_out = in.W_out;
+  out->S_out = in.S_out;
+  out->cid = in.refresh_cid;
   out->W = *in.W;
   out->refresh = false;
   uint32_t wl = in.W->level;
-  if (wl < 6) {
-    if (!refresh_level) return fail(HE_ELEVEL, "the step needs inputs at level >= 6: refresh the weights");
-    if (refresh_level < 6 || refresh_level > zl) return fail(HE_EINVAL, "refresh level must be in [6, data level]");
+  if (wl < need) {
+    if (!refresh_level) return fail(HE_ELEVEL, "too few levels left: refresh the weights");
+    if (refresh_level < need || refresh_level > zl) return fail(HE_EINVAL, "refresh level out of range");
     out->refresh = true;
     wl = refresh_level;
   }
   if (wl > zl) return fail(HE_EINVAL, "weights above the data's level");
   out->l0 = wl;
-  if (in.W_out->cap < wl - 5) return fail(HE_EINVAL, "output capacity too small");
+  if (!infer && in.W_out->cap < wl - 5) return fail(HE_EINVAL, "output capacity too small");
+  if (infer)
+    for (size_t k = 0; k < in.nZ; ++k)
+      if (in.S_out[k].cap < wl - 3) return fail(HE_EINVAL, "inference output capacity too small");
   const uint32_t g = cfg->g;
   if (g < 1 || (g & (g - 1)) || g > (uint32_t)c->n / 2) return fail(HE_EINVAL, "g must be a power of two <= N/2");
   if (!(cfg->mask_scale > 0.0)) return fail(HE_EINVAL, "mask_scale must be positive");
   return HE_OK;
 }
 
-}  // namespace he
-
-using namespace he;
-
-static int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
-                    uint32_t refresh_level, int flags) {
+int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
+             uint32_t refresh_level, int flags, bool infer) {
   if (!c || !shards || !cfg || count == 0) return fail(HE_EINVAL, "he_lr: null argument");
   std::vector<Shard> sh(count);
-  for (size_t k = 0; k < count; ++k) HE_TRY(validate_shard(c, shards[k], cfg, refresh_level, &sh[k]));
+  for (size_t k = 0; k < count; ++k) HE_TRY(validate_shard(c, shards[k], cfg, refresh_level, infer, &sh[k]));
   // plans, keys and masks are checked (and masks encoded) before any capture
   for (size_t k = 0; k < count; ++k) {
     LrPlan P;
-    HE_TRY(lr_plan(c, sh[k].l0, sh[k].Z[0].scale, sh[k].refresh ? sh[k].W_in->scale : sh[k].W.scale, cfg, &P));
+    HE_TRY(lr_plan(c, sh[k].l0, sh[k].Z[0].scale, sh[k].refresh ? sh[k].W_in->scale : sh[k].W.scale, cfg, infer, &P));
     LrGal gl;
     HE_TRY(lr_gal(c, P, &gl));
     const int64_t* mask = nullptr;
     HE_TRY(lr_mask(c, P.g, cfg->mask_scale, &mask));
   }
   // refreshed weights live in a context-owned buffer per shard
-  size_t nref = 0;
-  for (auto& s : sh) nref += s.refresh;
-  const size_t ref_words = nref * 2 * (size_t)refresh_level * c->n;
-  const size_t need = lr_words(c, sh, refresh_level) + ref_words + 8192;
-  HE_TRY(ws_reserve(c, need * sizeof(uint64_t)));
+  std::vector<LrShape> shapes(count);
+  for (size_t k = 0; k < count; ++k) shapes[k] = LrShape{sh[k].l0, sh[k].nZ, sh[k].refresh};
+  HE_TRY(ws_reserve(c, lr_ws_bytes(c, shapes.data(), count, refresh_level)));
   Arena pool;
   pool.base = (char*)c->ws.ptr;
   pool.size = c->ws.size;
@@ -467,17 +501,18 @@ static int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he
   rest.size = pool.size - pool.off;
   const bool graph = (flags & HE_LR_GRAPH) && c->stream != nullptr;
   if (!graph) {
-    HE_TRY(lr_run(c, sh, cfg, refresh_level, rest));
+    HE_TRY(lr_run(c, sh, cfg, refresh_level, rest, infer));
   } else {
     // one CUDA graph per distinct call (pointers, sizes, configuration)
     std::string key;
     char buf[160];
-    snprintf(buf, sizeof buf, "%u|%a|%a|%a|%a|%a|%a|%u|", refresh_level, cfg->coeffs[0], cfg->coeffs[1],
-             cfg->coeffs[2], cfg->coeffs[3], cfg->lr, cfg->mask_scale, cfg->g);
+    snprintf(buf, sizeof buf, "%d|%u|%a|%a|%a|%a|%a|%a|%u|", (int)infer, refresh_level, cfg->coeffs[0],
+             cfg->coeffs[1], cfg->coeffs[2], cfg->coeffs[3], cfg->lr, cfg->mask_scale, cfg->g);
     key += buf;
     for (auto& s : sh) {
-      snprintf(buf, sizeof buf, "%p,%zu,%p,%u,%a,%p,%u;", (const void*)s.Z, s.nZ, (const void*)s.W_in->data,
-               s.W_in->level, s.W_in->scale, (const void*)s.W_out->data, s.W_out->cap);
+      snprintf(buf, sizeof buf, "%p,%zu,%p,%u,%a,%p,%p,%u;", (const void*)s.Z, s.nZ, (const void*)s.W_in->data,
+               s.W_in->level, s.W_in->scale, (const void*)(s.W_out ? s.W_out->data : nullptr),
+               (const void*)s.S_out, s.cid);
       key += buf;
       for (size_t i = 0; i < s.nZ; ++i) {
         snprintf(buf, sizeof buf, "%p/%u/%u/%a,", (const void*)s.Z[i].data, s.Z[i].level, s.Z[i].cap, s.Z[i].scale);
@@ -492,7 +527,7 @@ static int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he
       c->prof_on = false;
       cudaGraph_t g = nullptr;
       HE_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      const int rc = lr_run(c, sh, cfg, refresh_level, rest);
+      const int rc = lr_run(c, sh, cfg, refresh_level, rest, infer);
       const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
       c->prof_on = prof;
       if (rc != HE_OK) {
@@ -509,11 +544,24 @@ static int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he
     HE_CUDA(cudaGraphLaunch(it->second, c->stream));
   }
   for (size_t k = 0; k < count; ++k) {
-    shards[k].W_out->level = sh[k].l0 - 5;
-    shards[k].W_out->scale = sh[k].W.scale;
+    if (infer) {
+      LrPlan P;
+      HE_TRY(lr_plan(c, sh[k].l0, sh[k].Z[0].scale, sh[k].W.scale, cfg, true, &P));
+      for (size_t i = 0; i < sh[k].nZ; ++i) {
+        shards[k].S_out[i].level = sh[k].l0 - 3;
+        shards[k].S_out[i].scale = P.sC;
+      }
+    } else {
+      shards[k].W_out->level = sh[k].l0 - 5;
+      shards[k].W_out->scale = sh[k].W.scale;
+    }
   }
   return HE_OK;
 }
+
+}  // namespace he
+
+using namespace he;
 
 extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const he_ct* W, const he_lr_config* cfg,
                                    he_ct* W_out) {
@@ -521,11 +569,16 @@ extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const h
   if (W->level < 6) return fail(HE_ELEVEL, "the step needs inputs at level >= 6");
   for (size_t k = 0; k < nZ; ++k)
     if (Z[k].level != W->level) return fail(HE_EINVAL, "data and weights must share one level");
-  he_lr_shard s{Z, nZ, W, W_out};
-  return lr_entry(c, &s, 1, cfg, 0, 0);
+  he_lr_shard s{Z, nZ, W, W_out, nullptr, 0, 0};
+  return lr_entry(c, &s, 1, cfg, 0, 0, false);
 }
 
 extern "C" int he_lr_gradient_step_workers(he_ctx* c, const he_lr_shard* shards, size_t count,
                                            const he_lr_config* cfg, uint32_t refresh_level, int flags) {
-  return lr_entry(c, shards, count, cfg, refresh_level, flags);
+  return lr_entry(c, shards, count, cfg, refresh_level, flags, false);
+}
+
+extern "C" int he_lr_inference_workers(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
+                                       uint32_t refresh_level, int flags) {
+  return lr_entry(c, shards, count, cfg, refresh_level, flags, true);
 }

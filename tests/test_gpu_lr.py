@@ -174,3 +174,42 @@ def test_workers_refresh_low_levels(lr_pair):
         got = he.he_decrypt_decode(pair.g, W_out)
         want = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, 1 / 12), n_slots, g)
         assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20
+
+
+# ------------------------------------------------------------------ inference
+
+
+def test_inference_bit_exact_and_accurate(lr_pair):
+    pair, g = lr_pair
+    he = pair.he
+    n_slots = pair.n // 2
+    coeffs = table2()["hinge"]
+    ms = [workloads.int_poly(80 + k, pair.n, 1 << 28) for k in range(3)]
+    mw = workloads.int_poly(89, pair.n, 1 << 28)
+    Z = pair.g.new_ct(7, 3)
+    for k, m in enumerate(ms):
+        he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 6, Z[k], cid=80 + k)
+    W = pair.gpu_enc(mw, 6, 89, scale=2.0 ** 40)
+    S = pair.g.new_ct(7, 3)
+    he.he_lr_inference_workers(pair.g, [(Z, W, S)], he.lr_config(coeffs, 1.0, g, 2.0 ** 40))
+    Zo = [pair.orc_enc(m, 6, 80 + k, scale=2.0 ** 40) for k, m in enumerate(ms)]
+    want = pair.o.lr_inference(Zo, pair.orc_enc(mw, 6, 89, scale=2.0 ** 40), coeffs, 1.0, g)
+    for k in range(3):
+        assert_same_residues(S[k], want[k], he, pair.g)
+    # accuracy on real data
+    data = workloads.LRData(seed=9, n_samples=2 * g, n_features=90)
+    zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+    Z2 = pair.g.new_ct(7, len(zs))
+    for k, v in enumerate(zs):
+        he.he_encode_encrypt(pair.g, v, 2.0 ** 40, 7, Z2[k], cid=900 + k)
+    W2 = pair.g.new_ct(7)
+    he.he_encode_encrypt(pair.g, workloads.pack_weights(data.w0, n_slots, g), 2.0 ** 40, 7, W2, cid=899)
+    S2 = pair.g.new_ct(7, len(zs))
+    he.he_lr_inference_workers(pair.g, [(Z2, W2, S2)], he.lr_config(coeffs, 1.0, g, 2.0 ** 40))
+    m = data.y * (data.X @ data.w0)
+    p = coeffs[0] + coeffs[1] * m + coeffs[2] * m * m + coeffs[3] * m ** 3
+    for k in range(len(zs)):
+        assert S2[k].level == 4
+        got = he.he_decrypt_decode(pair.g, S2[k])
+        for s in range(g):
+            assert np.max(np.abs(got[s::g] - p[k * g + s])) < 2.0 ** -20

@@ -1,0 +1,121 @@
+"""The continuous-batching request loop: requests of two ring sizes and both
+kinds (gradient step, inference), some with weights too low for the circuit
+(refreshed in-process first), submitted together to a server with several
+concurrent waves, give exactly the residues they give when served one at a
+time; the decrypted results match FP64; the device memory held stays within
+the budget."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2006_10091_gb300 import workloads
+from tests.gpu_util import gpu_lib
+from tests.lr_reference import lr_step_fp64, table2
+
+pytestmark = pytest.mark.gpu
+
+
+def rots(n_slots):
+    k = int(math.log2(n_slots))
+    return [1 << t for t in range(k)] + [-(1 << t) for t in range(k)]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    he = gpu_lib()
+    ctxs = [he.Context(11, 7, 40, 1, 60, 2.0 ** 40, seed=31, rot_steps=rots(1 << 10)),
+            he.Context(12, 7, 40, 2, 50, 2.0 ** 40, seed=32, rot_steps=rots(1 << 11))]
+    coeffs = table2()["binomial"]
+    reqs = []
+    for r in range(10):
+        ci = r % 2
+        ctx = ctxs[ci]
+        n_slots = ctx.n // 2
+        feats = 64 if ci == 0 else 128  # 16 samples per ciphertext in both rings
+        g = n_slots // feats
+        kind = he.HE_REQ_GRADIENT if r % 3 else he.HE_REQ_INFERENCE
+        nz = 1 + r % 3
+        w_level = [7, 3, 6, 2, 7][r % 5]
+        data = workloads.LRData(seed=200 + r, n_samples=nz * g, n_features=feats - 3)
+        zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+        Z = ctx.new_ct(7, nz)
+        for k, v in enumerate(zs):
+            he.he_encode_encrypt(ctx, v, 2.0 ** 40, 7, Z[k], cid=1000 * r + k)
+        W = ctx.new_ct(7)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(data.w0, n_slots, g), 2.0 ** 40, w_level, W, cid=1000 * r + 99)
+        Zh = np.stack([he.he_ct_export(ctx, z) for z in Z])
+        Wh = he.he_ct_export(ctx, W)
+        lr = 1.0 / 64 if kind == he.HE_REQ_GRADIENT else 1.0
+        cfg = he.lr_config(coeffs, lr, g, 2.0 ** 27 if kind == he.HE_REQ_GRADIENT else 2.0 ** 40)
+        l0 = w_level if w_level >= (6 if kind == he.HE_REQ_GRADIENT else 5) else 7
+        l_out = l0 - (5 if kind == he.HE_REQ_GRADIENT else 3)
+        shape = (2, l_out, ctx.n) if kind == he.HE_REQ_GRADIENT else (nz, 2, l_out, ctx.n)
+        reqs.append(dict(ci=ci, kind=kind, Zh=Zh, Wh=Wh, w_level=w_level, cfg=cfg, shape=shape, data=data,
+                         g=g, lr=lr, nz=nz, l_out=l_out, cid=77000 + r))
+    return he, ctxs, reqs, coeffs
+
+
+def serve(he, ctxs, reqs, budget, inflight, wave, one_at_a_time):
+    srv = he.Server(ctxs, budget, max_inflight=inflight, max_wave=wave)
+    outs, ids = {}, {}
+    try:
+        for i, r in enumerate(reqs):
+            out = np.zeros(r["shape"], dtype=np.uint64)
+            rid = srv.submit(r["ci"], r["kind"], r["Zh"], 7, 2.0 ** 40, r["Wh"], r["w_level"], 2.0 ** 40,
+                             r["cfg"], out, refresh_cid=r["cid"])
+            outs[rid] = out
+            ids[rid] = i
+            if one_at_a_time:
+                srv.drain()
+        srv.drain()
+        res = srv.poll()
+        stats = srv.stats()
+    finally:
+        srv.close()
+    assert len(res) == len(reqs)
+    by_index = {}
+    for x in res:
+        assert x["status"] == 0, x
+        by_index[ids[x["id"]]] = (outs[x["id"]], x)
+    return by_index, stats
+
+
+def test_results_are_the_same_alone_and_in_the_mix(setup):
+    he, ctxs, reqs, coeffs = setup
+    alone, _ = serve(he, ctxs, reqs, 1 << 34, 1, 1, True)
+    mixed, stats = serve(he, ctxs, reqs, 1 << 34, 3, 4, False)
+    for i in range(len(reqs)):
+        assert np.array_equal(alone[i][0], mixed[i][0]), i
+        assert alone[i][1]["level"] == mixed[i][1]["level"] == reqs[i]["l_out"]
+    assert stats["waves"] < len(reqs)  # requests that arrived together shared a wave
+    # decrypted results against FP64
+    for i, r in enumerate(reqs):
+        ctx = ctxs[r["ci"]]
+        n_slots = ctx.n // 2
+        out, info = mixed[i]
+        if r["kind"] == he.HE_REQ_GRADIENT:
+            ct = ctx.new_ct(r["l_out"])
+            he.he_ct_import(ctx, out, r["l_out"], info["scale"], ct)
+            got = he.he_decrypt_decode(ctx, ct)
+            d = r["data"]
+            want = workloads.pack_weights(lr_step_fp64(d.X, d.y, d.w0, coeffs, r["lr"]), n_slots, r["g"])
+            assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20
+        else:
+            d = r["data"]
+            m = d.y * (d.X @ d.w0)
+            p = coeffs[0] + coeffs[1] * m + coeffs[2] * m * m + coeffs[3] * m ** 3
+            for k in range(r["nz"]):
+                ct = ctx.new_ct(r["l_out"])
+                he.he_ct_import(ctx, out[k], r["l_out"], info["scale"], ct)
+                got = he.he_decrypt_decode(ctx, ct)
+                for s in range(r["g"]):
+                    assert np.max(np.abs(got[s::r["g"]] - p[k * r["g"] + s])) < 2.0 ** -20
+
+
+def test_budget_bounds_device_memory(setup):
+    he, ctxs, reqs, _ = setup
+    budget = 256 << 20
+    _, stats = serve(he, ctxs, reqs[:6], budget, 3, 4, False)
+    assert stats["used"] == 0 or stats["used"] <= stats["peak_used"]
+    assert stats["peak_used"] <= budget

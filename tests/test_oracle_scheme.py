@@ -418,3 +418,24 @@ def test_keyswitch_equals_big_integer_definition(tiny):
             out = (v - conv) // P
             for t in range(level):
                 assert int(gotc[t][c]) == out % q[t], (p, c, t)
+
+
+def test_lr_inference_matches_fp64_polynomial():
+    log_n, g = 10, 4
+    n_slots = (1 << log_n) // 2
+    F = n_slots // g
+    data = workloads.LRData(seed=2, n_samples=8, n_features=90)
+    rots = [g << t for t in range(int(math.log2(F)))]
+    o = oracle.Oracle(log_n, 6, 40, 1, 60, 2.0 ** 40, seed=4, rot_steps=rots)
+    coeffs = table2()["binomial"]
+    Z = [_enc(o, v, 5, 300 + k) for k, v in enumerate(workloads.pack_samples(data.X, data.y, n_slots, g))]
+    W = _enc(o, workloads.pack_weights(data.w0, n_slots, g), 5, 299)
+    S = o.lr_inference(Z, W, coeffs, 1.0, g)
+    assert S[0].level == 2 and abs(S[0].scale / W.scale - 1) < 1e-12
+    m = data.y * (data.X @ data.w0)
+    p = coeffs[0] + coeffs[1] * m + coeffs[3] * m ** 3
+    for k, ct in enumerate(S):
+        re, _ = o.decrypt(ct)
+        for s in range(g):
+            i = k * g + s
+            assert np.max(np.abs(re[s::g] - p[i])) < 2.0 ** -20
