@@ -127,31 +127,36 @@ def measured_peaks():
 # Integer-pipe roof: 152 SMs x 2070 MHz x 64 32-bit multiply-adds per clock per
 # SM (a register-resident IMAD chain reaches 60.4/clk/SM), divided by the 17.3
 # IMAD-pipe slots one 64-bit Shoup product takes (a register-resident chain of
-# Shoup products reaches 64/17.3 = 3.69 per clock per SM): one butterfly = one
-# Shoup product, so the transform roof is 1.16 T butterflies/s.
-ALU_BFLY_PEAK = 152 * 2.070e9 * 64 / 17.3
+# Shoup products reaches 64/17.3 = 3.69 per clock per SM): 1.16 T modular
+# products/s.  A butterfly is one product; the key-switching kernels also
+# count their basis-conversion and inner-product products.
+ALU_MODMUL_PEAK = 152 * 2.070e9 * 64 / 17.3
+ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product")
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
-    """Dominant kernel class by device time -> achieved vs peak."""
+    """Dominant kernel class by device time -> achieved vs its roof: the
+    integer pipe for the transform kernels (modular products per second),
+    HBM for the rest (algorithmic bytes per second), whichever is closer."""
     if not prof:
         return None
     name = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[name]
     per_launch_ms = p["ms"] / max(1, p["launches"])
     gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else 0.0
-    if name in ("ntt", "intt"):
+    frac_hbm = gbs / hbm_peak
+    if name in ALU_CLASSES:
         rate = p["work"] / (p["ms"] * 1e-3)
-        frac_alu = rate / ALU_BFLY_PEAK
-        frac_hbm = gbs / hbm_peak
+        frac_alu = rate / ALU_MODMUL_PEAK
         if frac_alu >= frac_hbm:
-            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_BFLY_PEAK / 1e9,
-                    "unit": "Gbutterfly/s", "frac": frac_alu, "traffic": None,
+            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_MODMUL_PEAK / 1e9,
+                    "unit": "G modmul/s", "frac": frac_alu, "traffic": None,
                     "per_launch_ms": per_launch_ms, "launches": p["launches"],
                     "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
-                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots per 64-bit Shoup butterfly"}
+                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots per 64-bit "
+                                 "Shoup product (probe-measured)"}
     return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-            "frac": gbs / hbm_peak, "traffic": None, "per_launch_ms": per_launch_ms,
+            "frac": frac_hbm, "traffic": None, "per_launch_ms": per_launch_ms,
             "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
 
 
@@ -264,6 +269,7 @@ def run_ours(args, rank: int, world: int):
     if not args.quick and rank == 0:
         extra.update(hmult_rates(he, torch, stream))
         extra["batched_workers"] = batched_workers(he, torch, stream)
+        extra["serving"] = serving(he, torch, stream)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(data, coeffs, lr)
@@ -402,16 +408,241 @@ def batched_workers(he, torch, stream, reps=2):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / reps
+    # The plain per-ciphertext path: every worker's circuit evaluated one data
+    # ciphertext at a time (each operation a launch over one ciphertext), as a
+    # single-instance HE library runs it.  Its cost is linear in the number of
+    # data ciphertexts plus a per-worker final stage, so it is timed on the
+    # first 4 and first 8 ciphertexts of every worker and extrapolated to the
+    # whole shard from those two points.
+    he.he_set_tuning(ctx, "lr_chunk", 1)
+    pc = {}
+    for m in (4, 8):
+        sub = [(Z[:m], W, Wo) for Z, W, Wo in shards]
+        for sh in sub[:2]:
+            he.he_lr_gradient_step_workers(ctx, [sh], cfg, refresh_level=L)
+        torch.cuda.synchronize()
+        per = []
+        for sh in sub:
+            e0.record(stream)
+            he.he_lr_gradient_step_workers(ctx, [sh], cfg, refresh_level=L)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per.append(e0.elapsed_time(e1))
+        pc[m] = per
+    he.he_set_tuning(ctx, "lr_chunk", 0)
+    per_ct_ms = []
+    plain_ct_ms = 0.0
+    for k, (Z, _, _) in enumerate(shards):
+        slope = max((pc[8][k] - pc[4][k]) / 4.0, 0.0)
+        fixed = max(pc[4][k] - 4 * slope, 0.0)
+        per_ct_ms.append(slope)
+        plain_ct_ms += fixed + slope * len(Z)
     out = {"workers": 32, "data_ciphertexts": n_ct, "samples": int(sum(sizes)),
            "levels": levels, "refreshed": int(sum(1 for v in levels if v < 6)),
-           "batched_ms_per_round": batched_ms, "plain_ms_per_round": plain_ms,
+           "batched_ms_per_round": batched_ms,
            "batched_worker_steps_per_s": 32 * 1000.0 / batched_ms,
-           "plain_worker_steps_per_s": 32 * 1000.0 / plain_ms, "speedup": plain_ms / batched_ms,
+           "per_worker_calls": {"ms_per_round": plain_ms, "worker_steps_per_s": 32 * 1000.0 / plain_ms,
+                                "speedup_of_batched": plain_ms / batched_ms,
+                                "what": "one call per worker; each call batches its own ciphertexts"},
+           "plain_per_ciphertext": {"ms_per_round": plain_ct_ms, "worker_steps_per_s": 32 * 1000.0 / plain_ct_ms,
+                                    "speedup_of_batched": plain_ct_ms / batched_ms,
+                                    "median_ms_per_ciphertext": float(np.median(per_ct_ms)),
+                                    "what": "each worker one ciphertext at a time; timed on 4 and 8 ciphertexts "
+                                            "per worker, extrapolated linearly to the full shard"},
            "max_rel_err_vs_fp64_largest_worker": rel, "setup_s": setup_s}
     ctx.close()
     del shards
     torch.cuda.empty_cache()
     return out
+
+
+SERVE_LOG_NS = (13, 14, 15, 16)
+SERVE_L, SERVE_BITS, SERVE_ALPHA, SERVE_BATCH = 20, 50, 4, 128
+SERVE_SCALE = 2.0 ** 50
+# The step's mask scale: the mask's rounding error per slot grows like
+# sqrt(N g) / mask_scale, which 2^34 keeps near 1e-7 of the gradient at
+# N = 2^16 and 512 samples per ciphertext.
+SERVE_MASK_SCALE = 2.0 ** 34
+# Steps refresh weights below 7 limbs so that their result keeps two limbs
+# (one ~50-bit limb holds only |w| < 1/2 at scale 2^50).
+SERVE_MIN_STEP_LEVEL = 7
+
+
+def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, budget=48 << 30):
+    """A Poisson stream (mean `rate` req/s) of encrypted gradient-step and
+    inference requests over ring sizes N = 2^13..2^16 (20 limbs of ~50 bits,
+    4 special primes, scale 2^50; at 2^40 the encryption noise summed over
+    4096 features at N = 2^16 alone exceeds 2^-20 of the result), weights at
+    levels uniform in 2..20 (below what the circuit needs they are refreshed
+    in-process first), feature counts log-uniform in 64..4096 padded to a
+    power of two, 128 samples per request, kinds 50/50.  The
+    continuous-batching server is compared with the same server restricted
+    to one request at a time; latency is arrival to completion as the server
+    records it."""
+    from paper_2006_10091_gb300 import workloads
+    from tests.lr_reference import lr_step_fp64
+    rng = np.random.default_rng(seed)
+    coeffs = table2_binomial()
+    t_setup = time.perf_counter()
+    ctxs = []
+    for log_n in SERVE_LOG_NS:
+        k = log_n - 1
+        rots = [1 << t for t in range(k)] + [-(1 << t) for t in range(k - 6)]
+        ctxs.append(he.Context(log_n, SERVE_L, SERVE_BITS, SERVE_ALPHA, 60, SERVE_SCALE, seed=0, rot_steps=rots,
+                               stream=stream.cuda_stream))
+    classes, wbuf, obuf = {}, {}, {}
+
+    def data_class(ci, F):
+        key = (ci, F)
+        if key not in classes:
+            ctx = ctxs[ci]
+            n_slots = ctx.n // 2
+            g = n_slots // F
+            data = workloads.LRData(seed=1000 * ci + F, n_samples=SERVE_BATCH, n_features=F - F // 8)
+            zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+            Z = ctx.new_ct(SERVE_L, len(zs))
+            for i, v in enumerate(zs):
+                he.he_encode_encrypt(ctx, v, SERVE_SCALE, SERVE_L, Z[i], cid=(ci << 24) + (F << 8) + i)
+            host = torch.empty((len(zs), 2, SERVE_L, ctx.n), dtype=torch.int64, pin_memory=True)
+            he.he_ct_export_batch(ctx, Z, host)
+            classes[key] = (data, g, host)
+        return classes[key]
+
+    def weights(ci, F, wl):
+        key = (ci, F, wl)
+        if key not in wbuf:
+            ctx = ctxs[ci]
+            data, g, _ = data_class(ci, F)
+            W = ctx.new_ct(wl)
+            he.he_encode_encrypt(ctx, workloads.pack_weights(data.w0, ctx.n // 2, g), SERVE_SCALE, wl, W,
+                                 cid=(1 << 31) + (ci << 24) + (F << 8) + wl)
+            host = torch.empty((1, 2, wl, ctx.n), dtype=torch.int64, pin_memory=True)
+            he.he_ct_export_batch(ctx, [W], host)
+            wbuf[key] = host
+        return wbuf[key]
+
+    reqs = []
+    for r in range(n_warm + n_requests):
+        ci = int(rng.integers(0, len(SERVE_LOG_NS)))
+        f = math.exp(rng.uniform(math.log(64), math.log(4096)))
+        F = min(4096, 1 << math.ceil(math.log2(f)))
+        kind = he.HE_REQ_GRADIENT if rng.random() < 0.5 else he.HE_REQ_INFERENCE
+        wl = int(rng.integers(2, SERVE_L + 1))
+        data, g, zh = data_class(ci, F)
+        nz = zh.shape[0]
+        need = SERVE_MIN_STEP_LEVEL if kind == he.HE_REQ_GRADIENT else 5
+        l_out = (wl if wl >= need else SERVE_L) - (5 if kind == he.HE_REQ_GRADIENT else 3)
+        # one output buffer per (ring, features, kind), sized for the highest
+        # output level; requests of a class overwrite each other's results
+        # (accuracy is checked afterwards on requests served alone)
+        okey = (ci, F, kind)
+        if okey not in obuf:
+            top = SERVE_L - (5 if kind == he.HE_REQ_GRADIENT else 3)
+            obuf[okey] = torch.empty((nz if kind == he.HE_REQ_INFERENCE else 1) * 2 * top * ctxs[ci].n,
+                                     dtype=torch.int64, pin_memory=True)
+        cfg = (he.lr_config(coeffs, 1.0 / SERVE_BATCH, g, SERVE_MASK_SCALE) if kind == he.HE_REQ_GRADIENT
+               else he.lr_config(coeffs, 1.0, g, SERVE_SCALE))
+        reqs.append(dict(ci=ci, F=F, kind=kind, wl=wl, Z=zh, W=weights(ci, F, wl), cfg=cfg, out=obuf[okey],
+                         cid=(ci << 24) + (F << 8) + wl, nz=nz, l_out=l_out, need=need))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    arrivals = workloads.poisson_arrivals(seed, rate, n_requests)
+
+    def submit(srv, r):
+        return srv.submit(r["ci"], r["kind"], r["Z"], SERVE_L, SERVE_SCALE, r["W"], r["wl"], SERVE_SCALE, r["cfg"],
+                          r["out"], refresh_cid=r["cid"], min_w_level=r["need"])
+
+    def run(srv):
+        for r in reqs[:n_warm]:  # warm-up: plans, masks and workspaces
+            submit(srv, r)
+        srv.drain(1200)
+        srv.poll(cap=n_warm + 16)
+        timed = reqs[n_warm:]
+        t0 = time.perf_counter()
+        for r, ta in zip(timed, arrivals):
+            while True:
+                dt = ta - (time.perf_counter() - t0)
+                if dt <= 0:
+                    break
+                if dt > 2e-4:
+                    time.sleep(dt - 1e-4)
+            submit(srv, r)
+        t_sub = time.perf_counter() - t0
+        srv.drain(1200)
+        span = time.perf_counter() - t0
+        res = srv.poll(cap=n_requests + 16)
+        stats = srv.stats()
+        bad = [x for x in res if x["status"] != 0]
+        if bad or len(res) != n_requests:
+            raise RuntimeError(f"serving: {len(bad)} failed requests, {len(res)} of {n_requests} returned")
+        lat = np.array([x["latency_ms"] for x in res])
+        return {"requests_per_s": n_requests / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                "arrival_window_s": t_sub, "span_s": span, "waves": stats["waves"],
+                "peak_running_waves": stats["peak_running"], "peak_device_bytes": stats["peak_used"]}
+
+    srv = he.Server(ctxs, budget, max_inflight=4, max_wave=16)
+    try:
+        cont = run(srv)
+    finally:
+        srv.close()
+    srv = he.Server(ctxs, budget, max_inflight=1, max_wave=1, max_running=1)
+    try:
+        one = run(srv)
+    finally:
+        srv.close()
+    # accuracy: the first request of every (ring, kind) class, served alone and decrypted
+    acc = {}
+    srv = he.Server(ctxs, budget, max_inflight=1, max_wave=1, max_running=1)
+    try:
+        for ci, ctx in enumerate(ctxs):
+            for kind in (he.HE_REQ_GRADIENT, he.HE_REQ_INFERENCE):
+                r = next((x for x in reqs if x["ci"] == ci and x["kind"] == kind), None)
+                if r is None:
+                    continue
+                submit(srv, r)
+                srv.drain(600)
+                info = srv.poll()[0]
+                data, g, _ = classes[(ci, r["F"])]
+                n_slots = ctx.n // 2
+                cnt = 1 if kind == he.HE_REQ_GRADIENT else r["nz"]
+                words = 2 * r["l_out"] * ctx.n
+                outs = [r["out"][k * words:(k + 1) * words] for k in range(cnt)]
+                err = 0.0
+                for k, o in enumerate(outs):
+                    ct = ctx.new_ct(r["l_out"])
+                    he.he_ct_import(ctx, o.numpy().view(np.uint64).reshape(2, r["l_out"], ctx.n), r["l_out"],
+                                    info["scale"], ct)
+                    got = he.he_decrypt_decode(ctx, ct)
+                    if kind == he.HE_REQ_GRADIENT:
+                        want = workloads.pack_weights(
+                            lr_step_fp64(data.X, data.y, data.w0, coeffs, 1.0 / SERVE_BATCH), n_slots, g)
+                        err = max(err, float(np.max(np.abs(got - want)) / np.max(np.abs(want))))
+                    else:
+                        m = data.y * (data.X @ data.w0)
+                        p = coeffs[0] + coeffs[1] * m + coeffs[2] * m * m + coeffs[3] * m ** 3
+                        for smp in range(g):
+                            if k * g + smp < len(p):
+                                err = max(err, float(np.max(np.abs(got[smp::g] - p[k * g + smp]))))
+                name = f"N=2^{SERVE_LOG_NS[ci]} {'gradient' if kind == he.HE_REQ_GRADIENT else 'inference'}"
+                acc[name] = {"F": r["F"], "w_level": r["wl"], "err": err,
+                             "err_kind": "max rel vs FP64" if kind == he.HE_REQ_GRADIENT else "max abs vs FP64"}
+    finally:
+        srv.close()
+    for c in ctxs:
+        c.close()
+    torch.cuda.empty_cache()
+    mix = {"requests": n_requests, "warmup_requests": n_warm, "offered_per_s": rate,
+           "rings": {f"2^{SERVE_LOG_NS[i]}": sum(1 for r in reqs[n_warm:] if r["ci"] == i)
+                     for i in range(len(SERVE_LOG_NS))},
+           "gradient_share": sum(1 for r in reqs[n_warm:] if r["kind"] == he.HE_REQ_GRADIENT) / n_requests,
+           "refreshed": sum(1 for r in reqs[n_warm:] if r["wl"] < r["need"]),
+           "data_ciphertexts": int(sum(r["nz"] for r in reqs[n_warm:])), "budget_bytes": budget}
+    return {"continuous": cont, "one_at_a_time": one,
+            "throughput_ratio": cont["requests_per_s"] / one["requests_per_s"], "mix": mix, "accuracy": acc,
+            "setup_s": setup_s,
+            "params": "N=2^13..2^16, 20x50-bit limbs + 4x60-bit special primes (dnum 5), scale 2^50; "
+                      "not 128-bit secure at N<=2^15 (benchmark parameters)"}
 
 
 def cpu_baseline(data, coeffs, lr):
@@ -514,7 +745,7 @@ def run_micro(args):
         limbs = args.polys * nl
         bfly = limbs * (n / 2) * log_n
         out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else "")] = {
-            "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_BFLY_PEAK,
+            "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_MODMUL_PEAK,
             "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
     he.he_set_tuning(ctx, "ntt_generic", False)
     print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
@@ -533,6 +764,9 @@ def run_micro_keyswitch(args):
     torch.cuda.set_stream(stream)
     ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=[8],
                      stream=stream.cuda_stream)
+    for kv in args.tune or []:
+        key, val = kv.split("=")
+        he.he_set_tuning(ctx, key, float(val))
     level, count = L - 1, args.polys
     host = workloads.residues(2, ctx.primes[:level], ctx.n, parts=2 * count).reshape(count, 2, level, ctx.n)
     A, O = ctx.new_ct(level, count), ctx.new_ct(level, count)
@@ -558,9 +792,26 @@ def run_micro_keyswitch(args):
                                   for k, v in prof.items()}}))
 
 
+def run_part(args):
+    """One of the extra measurements alone (batched workers or serving)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10091_gb300 as he
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    if args.micro == "workers":
+        print(json.dumps({"part": "batched_workers", **batched_workers(he, torch, stream)}))
+    else:
+        print(json.dumps({"part": "serving", **serving(he, torch, stream, n_requests=args.requests)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "keyswitch"], default=None, help="time one kernel class alone")
+    ap.add_argument("--micro", choices=["ntt", "keyswitch", "workers", "serving"], default=None,
+                    help="time one kernel class or one extra measurement alone")
+    ap.add_argument("--requests", type=int, default=400, help="timed requests of --micro serving")
+    ap.add_argument("--tune", action="append", help="key=value tuning of --micro keyswitch")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--polys", type=int, default=256)
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,6 +826,9 @@ def main():
         return
     if args.micro == "keyswitch":
         run_micro_keyswitch(args)
+        return
+    if args.micro in ("workers", "serving"):
+        run_part(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

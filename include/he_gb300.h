@@ -98,7 +98,8 @@ int he_sync(he_ctx* ctx);
  * of one batched operation (default 2^31), "lr_chunk" = data ciphertexts per
  * chunk of the logistic-regression step (0 = from the budget), "ntt_generic"
  * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
- * one for N = 2^12 .. 2^16.  HE_EINVAL for
+ * one for N = 2^12 .. 2^16, "ks_row_ctas" = 2 or 3 (default) CTAs per SM for the
+ * fused key-switch row pass (register budget 128 or 80 per thread).  HE_EINVAL for
  * an unknown key or a value out of range. */
 int he_set_tuning(he_ctx* ctx, const char* key, double value);
 
@@ -245,7 +246,9 @@ typedef struct he_lr_shard {
   he_ct* W_out;          /* gradient step: the new weights */
   he_ct* S_out;          /* inference: nZ outputs, S_k = p(M_k) (may be NULL for the step) */
   uint32_t refresh_cid;  /* ciphertext id of the refresh encryption (if one is needed) */
-  uint32_t pad;
+  uint32_t min_level;    /* refresh the weights first when their level is below this;
+                            0 (or less than the circuit needs) = the circuit's minimum:
+                            6 for the step, 5 for inference */
 } he_lr_shard;
 
 #define HE_LR_GRAPH 1
@@ -286,6 +289,9 @@ typedef struct he_server_config {
   size_t hbm_budget;      /* bytes of device memory for request buffers and workspaces */
   uint32_t max_inflight;  /* concurrent waves per context (streams), 1..16 */
   uint32_t max_wave;      /* requests per wave */
+  uint32_t max_running;   /* waves in flight over all contexts; 0 = no limit beyond
+                             max_inflight per context (1 with max_wave 1 serves one
+                             request at a time) */
 } he_server_config;
 
 typedef struct he_request {
@@ -295,12 +301,14 @@ typedef struct he_request {
   uint32_t z_level;      /* level of the data (>= 6 for a step, >= 5 for inference) */
   uint32_t w_level;      /* level of the weights (<= z_level) */
   uint32_t refresh_cid;  /* ciphertext id of the refresh encryption, if one is needed */
+  uint32_t min_w_level;  /* as he_lr_shard.min_level: e.g. 7 keeps a step's result at
+                            two limbs or more */
   double z_scale, w_scale;
   const uint64_t* Z;     /* host, nZ x [2][z_level][N] residues (pinned memory keeps the loop asynchronous) */
   const uint64_t* W;     /* host, [2][w_level][N] */
   he_lr_config cfg;
   uint64_t* out;         /* host result: step [2][l-5][N], inference nZ x [2][l-3][N], l = weights' level
-                            after any refresh; pinned */
+                            after any refresh (z_level when refreshed); pinned */
   size_t out_words;      /* capacity of out */
 } he_request;
 

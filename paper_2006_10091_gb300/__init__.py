@@ -43,7 +43,7 @@ class he_ct(ctypes.Structure):
 class he_lr_shard(ctypes.Structure):
     _fields_ = [("Z", ctypes.c_void_p), ("nZ", ctypes.c_size_t), ("W", ctypes.c_void_p),
                 ("W_out", ctypes.c_void_p), ("S_out", ctypes.c_void_p), ("refresh_cid", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("min_level", ctypes.c_uint32)]
 
 
 HE_LR_GRAPH = 1
@@ -57,12 +57,14 @@ class he_lr_config(ctypes.Structure):
 
 class he_server_config(ctypes.Structure):
     _fields_ = [("ctxs", ctypes.c_void_p), ("n_ctx", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
-                ("max_inflight", ctypes.c_uint32), ("max_wave", ctypes.c_uint32)]
+                ("max_inflight", ctypes.c_uint32), ("max_wave", ctypes.c_uint32),
+                ("max_running", ctypes.c_uint32)]
 
 
 class he_request(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("nZ", ctypes.c_uint32),
                 ("z_level", ctypes.c_uint32), ("w_level", ctypes.c_uint32), ("refresh_cid", ctypes.c_uint32),
+                ("min_w_level", ctypes.c_uint32),
                 ("z_scale", ctypes.c_double), ("w_scale", ctypes.c_double), ("Z", ctypes.c_void_p),
                 ("W", ctypes.c_void_p), ("cfg", he_lr_config), ("out", ctypes.c_void_p),
                 ("out_words", ctypes.c_size_t)]
@@ -521,21 +523,22 @@ def galois_elt(log_n: int, r: int) -> int:
 class Server:
     """he_server: a continuous-batching request loop over several contexts."""
 
-    def __init__(self, ctxs: list, hbm_budget: int, max_inflight: int = 4, max_wave: int = 16):
+    def __init__(self, ctxs: list, hbm_budget: int, max_inflight: int = 4, max_wave: int = 16,
+                 max_running: int = 0):
         self._ctxs = ctxs
         self._arr = (ctypes.c_void_p * len(ctxs))(*[c.ptr.value for c in ctxs])
         cfg = he_server_config(ctypes.cast(self._arr, ctypes.c_void_p), len(ctxs), int(hbm_budget),
-                               max_inflight, max_wave)
+                               max_inflight, max_wave, max_running)
         h = ctypes.c_void_p()
         _check(load().he_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.ptr = h
         self._keep = {}
 
     def submit(self, ctx_index: int, kind: int, Z_host, z_level: int, z_scale: float, W_host, w_level: int,
-               w_scale: float, cfg: he_lr_config, out_host, refresh_cid: int = 0) -> int:
+               w_scale: float, cfg: he_lr_config, out_host, refresh_cid: int = 0, min_w_level: int = 0) -> int:
         """Z_host, W_host, out_host: host arrays or (pinned) CPU torch tensors of uint64 residues."""
         nZ = Z_host.shape[0]
-        r = he_request(ctx_index, kind, nZ, z_level, w_level, refresh_cid, float(z_scale), float(w_scale),
+        r = he_request(ctx_index, kind, nZ, z_level, w_level, refresh_cid, min_w_level, float(z_scale), float(w_scale),
                        _addr(Z_host), _addr(W_host), cfg, _addr(out_host), _nwords(out_host))
         rid = ctypes.c_uint64()
         _check(load().he_server_submit(self.ptr, ctypes.byref(r), ctypes.byref(rid)))

@@ -121,6 +121,7 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->chunk_bytes = base->chunk_bytes;
   v->lr_chunk = base->lr_chunk;
   v->ntt_generic = base->ntt_generic;
+  v->ks_row_ctas = base->ks_row_ctas;
   v->P_mod_q = base->P_mod_q;
   v->d_s = base->d_s;
   v->d_pk = base->d_pk;
@@ -264,6 +265,9 @@ int he_set_tuning(he_ctx* c, const char* key, double value) {
   } else if (k == "lr_chunk") {
     if (!(value >= 0 && value <= 1 << 20)) return fail(HE_EINVAL, "lr_chunk out of range");
     c->lr_chunk = (uint32_t)value;
+  } else if (k == "ks_row_ctas") {
+    if (value != 2.0 && value != 3.0) return fail(HE_EINVAL, "ks_row_ctas is 2 or 3");
+    c->ks_row_ctas = (int)value;
   } else {
     return fail(HE_EINVAL, "unknown tuning key " + k);
   }

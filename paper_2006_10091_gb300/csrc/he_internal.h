@@ -91,13 +91,14 @@ struct he_ctx {
   size_t chunk_bytes = (size_t)1 << 31;  // scratch budget of one batched operation
   uint32_t lr_chunk = 0;                 // data ciphertexts per chunk of the LR step (0: from the budget)
   bool ntt_generic = false;              // force the runtime-shaped NTT kernel (tuning)
+  int ks_row_ctas = 3;                   // CTAs per SM the key-switch row pass is compiled for (2 or 3)
   std::map<std::string, cudaGraphExec_t> graphs;  // captured multi-worker steps
   std::vector<uint64_t> P_mod_q;  // [L] P mod q_t (host)
 
   // keys (evaluation form)
   uint64_t* d_s = nullptr;    // [np][N]
   uint64_t* d_pk = nullptr;   // [2][L][N] (b, a)
-  uint64_t* d_rlk = nullptr;  // [beta][2][np][N]
+  uint64_t* d_rlk = nullptr;  // [beta][2][np][N], then the Shoup companions in the same layout
   std::map<uint64_t, uint64_t*> gal;  // Galois element -> [beta][2][np][N]
   // encoded 0/1 masks of the logistic-regression step, per (g, scale)
   std::map<std::pair<uint32_t, double>, int64_t*> lr_masks;

@@ -23,6 +23,7 @@ struct KsFusedArgs {
   uint64_t* ext;         // column-pass outputs: count x [beta][nt][N]
   uint64_t* acc;         // accumulators: count x [2][nt][N]
   const uint64_t* evk;   // [beta_top][2][np][N]
+  const uint64_t* evk_sh;  // Shoup companions of evk, same layout
   uint64_t d_stride;
   uint32_t level, alpha, beta, L, np, nt;
   const PrimeDev* primes;
@@ -88,8 +89,10 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFus
 
 // Row pass of every digit's tile fused with the key inner product.
 // Grid: count * nt * TILES.  Each thread owns residues idx = tid + u*T.
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedArgs a) {
+// MINB: CTAs per SM the register allocation must allow (2: no spills, 128
+// registers; 3: 80 registers with a few spilled words), chosen at run time.
+template <int LOG_N, int LOG_M, int LOG_K, int MINB>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(KsFusedArgs a) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
   constexpr uint32_t N = 1u << LOG_N;
   constexpr int PER = S::TILE / S::T;  // 8
@@ -102,15 +105,25 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedA
   const uint32_t t = b % a.nt, i = b / a.nt;
   const uint32_t prime = ks_prime(t, a.level, a.L);
   const PrimeDev pr = a.primes[prime];
-  const bool lazy = pr.q < (1ull << 58);
+  const uint64_t q = pr.q, q2 = q + q;
+  const bool lazy = q < (1ull << 58);
+  // Products by key words are Shoup products in [0, 2q); they are summed
+  // without reduction while beta of them stay below 2^64, else kept in [0, 2q).
+  const bool acc_lazy = q < ~0ull / (2ull * a.beta);
   stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
   uint64_t acc0[PER], acc1[PER];
 #pragma unroll
   for (int u = 0; u < PER; ++u) acc0[u] = acc1[u] = 0;
+  auto mac = [&](uint64_t& acc, uint64_t x, uint64_t k, uint64_t ksh) {
+    acc += mul_shoup_lazy(x, k, ksh, q);
+    if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
+  };
   for (uint32_t j = 0; j < a.beta; ++j) {
     const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
-    const uint64_t* kb = a.evk + (((size_t)j * 2 + 0) * a.np + prime) * N;
-    const uint64_t* ka = a.evk + (((size_t)j * 2 + 1) * a.np + prime) * N;
+    const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
+    const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
+    const uint64_t *kb = a.evk + kb_off, *ka = a.evk + ka_off;
+    const uint64_t *kbs = a.evk_sh + kb_off, *kas = a.evk_sh + ka_off;
     if (own) {
       const uint64_t* dd = a.d + (size_t)i * a.d_stride + (size_t)t * N;
 #pragma unroll
@@ -118,8 +131,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedA
         const uint32_t idx = threadIdx.x + u * S::T;
         const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
         const uint64_t x = __ldg(dd + e);
-        acc0[u] = add_mod(acc0[u], mul_mod(x, __ldg(kb + e), pr), pr.q);
-        acc1[u] = add_mod(acc1[u], mul_mod(x, __ldg(ka + e), pr), pr.q);
+        mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
+        mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
       }
       continue;
     }
@@ -138,8 +151,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedA
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       const uint64_t v = sm[idx + (idx >> 3)];
       const uint64_t x = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
-      acc0[u] = add_mod(acc0[u], mul_mod(x, __ldg(kb + e), pr), pr.q);
-      acc1[u] = add_mod(acc1[u], mul_mod(x, __ldg(ka + e), pr), pr.q);
+      mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
+      mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
     }
     __syncthreads();  // the tile buffer is reused by the next digit
   }
@@ -149,8 +162,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_row_ip(KsFusedA
   for (int u = 0; u < PER; ++u) {
     const uint32_t idx = threadIdx.x + u * S::T;
     const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-    o0[e] = acc0[u];
-    o1[e] = acc1[u];
+    o0[e] = reduce64(acc0[u], pr);
+    o1[e] = reduce64(acc1[u], pr);
   }
 }
 
@@ -163,24 +176,31 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   static unsigned long long attr_set = 0;
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
     HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     attr_set |= 1ull << c->device;
   }
   const double n = (double)(1u << LOG_N);
   double own = 0;  // limbs each ciphertext takes as they are
   for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
   const double conv = (double)a.beta * a.nt - own;  // converted limbs per ciphertext
+  double conv_products = 0;  // basis-conversion products (none when a digit is one limb)
+  for (uint32_t j = 0; j < a.beta; ++j)
+    if (a.cnt[j] > 1) conv_products += (double)(a.nt - a.cnt[j]) * a.cnt[j];
+  // work = modular products: butterflies, conversion products, inner-product products
   {
     const size_t blocks = (size_t)count * a.beta * a.nt * SC::TILES;
-    ProfScope prof(c, "ks_modup_ntt", count * conv * n / 2 * M1, count * n * 8 * (a.level + conv));
+    ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n),
+                   count * n * 8 * (a.level + conv));
     ks_modup_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
   {
     const size_t blocks = (size_t)count * a.nt * SR::TILES;
-    ProfScope prof(c, "ks_ntt_inner_product", count * conv * n / 2 * M2,
+    ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * a.beta * a.nt * n),
                    count * n * 8 * (conv + own + 2.0 * a.beta * a.nt + 2.0 * a.nt));
-    ks_row_ip<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
+    if (c->ks_row_ctas == 3) ks_row_ip<LOG_N, M2, K2, 3><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
+    else ks_row_ip<LOG_N, M2, K2, 2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
@@ -198,6 +218,7 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
   a.ext = ext;
   a.acc = acc;
   a.evk = evk;
+  a.evk_sh = evk + c->key_words();
   a.d_stride = d_stride;
   a.level = level;
   a.alpha = (uint32_t)c->alpha;

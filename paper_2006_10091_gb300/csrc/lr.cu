@@ -432,7 +432,7 @@ static int validate_shard(he_ctx* c, const he_lr_shard& in, const he_lr_config* 
     for (size_t k = 0; k < in.nZ; ++k)
       if (!in.S_out[k].data || ((uintptr_t)in.S_out[k].data & 15)) return fail(HE_EINVAL, "shard: bad inference output");
   }
-  const uint32_t need = infer ? 5 : 6;
+  const uint32_t need = std::max<uint32_t>(infer ? 5 : 6, in.min_level);
   const uint32_t zl = in.Z[0].level;
   for (size_t k = 0; k < in.nZ; ++k) {
     const he_ct& z = in.Z[k];

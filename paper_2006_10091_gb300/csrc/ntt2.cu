@@ -13,6 +13,8 @@
 //    per stage, so after the n <= 16 stages it stays below 33q < 2^64; the
 //    last pass reduces once (a Shoup product by 1, then one subtraction).
 //    Larger primes keep the corrected butterfly ([0, 4q)).
+#include <algorithm>
+
 #include "he_internal.h"
 #include "ntt2.cuh"
 
@@ -23,6 +25,7 @@ struct Ntt2Args {
   uint64_t* dst;
   uint64_t src_stride, dst_stride;
   uint32_t nl, limb0, level, L;
+  uint32_t np, pb;  // polynomials; polynomials per CTA (same limb, so same twiddles)
   uint32_t skip_alpha, skip_beta;
   const ulonglong2* tw;
   const PrimeDev* primes;
@@ -59,31 +62,36 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Ar
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  const uint32_t lt = blockIdx.x / S::TILES;
-  const uint32_t tile = blockIdx.x - lt * S::TILES;
-  const uint32_t p = lt / a.nl, t = a.limb0 + (lt - p * a.nl);
-  if (a.skip_alpha) {
-    const uint32_t j = p % a.skip_beta, lo = j * a.skip_alpha;
-    const uint32_t hi = min(lo + a.skip_alpha, a.level);
-    if (t >= lo && t < hi) return;
-  }
+  const uint32_t tile = blockIdx.x % S::TILES;
+  const uint32_t bl = blockIdx.x / S::TILES;
+  const uint32_t li = bl % a.nl, pg = bl / a.nl;
+  const uint32_t t = a.limb0 + li;
   const uint32_t prime = t < a.level ? t : a.L + t - a.level;
   const PrimeDev pr = a.primes[prime];
-  const uint64_t* src = a.src + p * a.src_stride + (size_t)(t - a.limb0) * (1u << LOG_N);
-  uint64_t* dst = a.dst + p * a.dst_stride + (size_t)(t - a.limb0) * (1u << LOG_N);
   const ulonglong2* tw = a.tw + (size_t)prime * (1u << LOG_N);
   stage_twiddles<LOG_N, LOG_M, LOG_K, COL>(stw, tw, tile);
-  // stage the data tile
+  const uint32_t p1 = min(pg * a.pb + a.pb, a.np);
+  for (uint32_t p = pg * a.pb; p < p1; ++p) {
+    if (a.skip_alpha) {
+      const uint32_t j = p % a.skip_beta, lo = j * a.skip_alpha;
+      const uint32_t hi = min(lo + a.skip_alpha, a.level);
+      if (t >= lo && t < hi) continue;
+    }
+    const uint64_t* src = a.src + p * a.src_stride + (size_t)li * (1u << LOG_N);
+    uint64_t* dst = a.dst + p * a.dst_stride + (size_t)li * (1u << LOG_N);
+    // stage the data tile (each thread rewrites only the words it wrote out
+    // in the previous iteration, so no barrier is needed before this)
 #pragma unroll 4
-  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-    uint32_t k, x;
-    if (COL) { x = idx >> LOG_K; k = idx & (S::K - 1); }
-    else { k = idx >> LOG_M; x = idx & (S::M - 1); }
-    sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      uint32_t k, x;
+      if (COL) { x = idx >> LOG_K; k = idx & (S::K - 1); }
+      else { k = idx >> LOG_M; x = idx & (S::M - 1); }
+      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
+    }
+    __syncthreads();
+    if (!INV && pr.q < (1ull << 58)) pass_body<INV, true, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
+    else pass_body<INV, false, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
   }
-  __syncthreads();
-  if (!INV && pr.q < (1ull << 58)) pass_body<INV, true, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
-  else pass_body<INV, false, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
 }
 
 template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL>
@@ -111,7 +119,13 @@ static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t*
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set |= 1ull << c->device;
   }
-  const size_t blocks = (size_t)b.npolys * b.nl * S::TILES;
+  // several polynomials of one limb per CTA share its staged twiddles, as
+  // long as the grid keeps about four waves of CTAs
+  const size_t tiles = (size_t)b.npolys * b.nl * S::TILES;
+  const size_t pb = std::max<size_t>(1, std::min<size_t>(8, tiles / (4 * 4 * 152)));
+  a.np = b.npolys;
+  a.pb = (uint32_t)pb;
+  const size_t blocks = (size_t)((b.npolys + pb - 1) / pb) * b.nl * S::TILES;
   if (blocks == 0) return HE_OK;
   if (blocks > 0x7fffffffull) return fail(HE_EINVAL, "NTT batch too large");
   double transforms = (double)b.npolys * b.nl;

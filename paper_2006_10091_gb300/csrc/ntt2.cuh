@@ -29,6 +29,13 @@ struct Shape {
   }
 };
 
+// One round: R consecutive local stages (radix 2^R) on groups of G = 2^R
+// elements held in registers.  Within a group the elements sit at shared
+// memory offsets j*s + (j*s >> 3) from the first (s the group's stride, a
+// power of two; the padding of one word per eight never splits a group
+// unevenly), so only the first offset is computed.  At stage st the group
+// needs 2^st distinct twiddles, one per value of the top st bits of j; each
+// is loaded once.
 template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R>
 __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int sig0, uint64_t q) {
   using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
@@ -36,6 +43,7 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
   const uint64_t q2 = q + q;
   const int lo_bits = LOG_M - sig0 - R;
   const uint32_t lo_mask = (1u << lo_bits) - 1;
+  const uint32_t s = COL ? (1u << (lo_bits + LOG_K)) : (1u << lo_bits);
 #pragma unroll
   for (int u = 0; u < GPT; ++u) {
     const uint32_t g = threadIdx.x + u * S::T;
@@ -51,47 +59,40 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
       xhi = r & ((1u << sig0) - 1);
       k = r >> sig0;
     }
-    const uint32_t xbase = (xhi << (LOG_M - sig0)) | xlo;
+    const uint32_t s0 = S::sidx(k, (xhi << (LOG_M - sig0)) | xlo);
     uint64_t v[G];
-    uint32_t si[G];
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-      si[j] = S::sidx(k, xbase | ((uint32_t)j << lo_bits));
-      v[j] = sm[si[j]];
-    }
-    if (!INV) {
+    for (int j = 0; j < G; ++j) v[j] = sm[s0 + j * s + ((j * s) >> 3)];
 #pragma unroll
-      for (int st = 0; st < R; ++st) {
-        const int half = G >> (st + 1);
+    for (int i = 0; i < R; ++i) {
+      const int st = INV ? R - 1 - i : i;
+      const int sg = sig0 + st, half = G >> (st + 1);
+      const uint32_t tb = COL ? ((1u << sg) | (xhi << st))
+                              : (uint32_t)(S::K * ((1 << sg) - 1)) + (k << sg) + (xhi << st);
 #pragma unroll
-        for (int j = 0; j < G; ++j) {
-          if (j & half) continue;
-          const ulonglong2 w = stw[S::tidx(sig0 + st, k, xbase | ((uint32_t)j << lo_bits))];
-          uint64_t X = v[j];
-          if (!LAZY) X = X >= q2 ? X - q2 : X;
-          const uint64_t t = mul_shoup_lazy(v[j + half], w.x, w.y, q);
-          v[j] = X + t;
-          v[j + half] = X + q2 - t;
-        }
-      }
-    } else {
+      for (int b = 0; b < (1 << st); ++b) {
+        const ulonglong2 w = stw[tb + b];
 #pragma unroll
-      for (int st = R - 1; st >= 0; --st) {
-        const int half = G >> (st + 1);
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          if (j & half) continue;
-          const ulonglong2 w = stw[S::tidx(sig0 + st, k, xbase | ((uint32_t)j << lo_bits))];
-          const uint64_t X = v[j], Y = v[j + half];
-          uint64_t sum = X + Y;
-          sum = sum >= q2 ? sum - q2 : sum;
-          v[j + half] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
-          v[j] = sum;
+        for (int jj = 0; jj < half; ++jj) {
+          const int j = (b << (R - st)) + jj;
+          if (!INV) {
+            uint64_t X = v[j];
+            if (!LAZY) X = X >= q2 ? X - q2 : X;
+            const uint64_t t = mul_shoup_lazy(v[j + half], w.x, w.y, q);
+            v[j] = X + t;
+            v[j + half] = X + q2 - t;
+          } else {
+            const uint64_t X = v[j], Y = v[j + half];
+            uint64_t sum = X + Y;
+            sum = sum >= q2 ? sum - q2 : sum;
+            v[j + half] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+            v[j] = sum;
+          }
         }
       }
     }
 #pragma unroll
-    for (int j = 0; j < G; ++j) sm[si[j]] = v[j];
+    for (int j = 0; j < G; ++j) sm[s0 + j * s + ((j * s) >> 3)] = v[j];
   }
 }
 

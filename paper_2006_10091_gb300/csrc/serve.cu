@@ -56,8 +56,13 @@ struct Slot {
   bool busy = false;
 };
 
+// The weights' level below which a request refreshes them first.
+static uint32_t req_need(const he_request& r) {
+  return std::max<uint32_t>(r.kind == HE_REQ_INFERENCE ? 5 : 6, r.min_w_level);
+}
+
 static size_t req_out_limbs(const he_request& r, uint32_t* l_out) {
-  const uint32_t need = r.kind == HE_REQ_INFERENCE ? 5 : 6;
+  const uint32_t need = req_need(r);
   const uint32_t l0 = r.w_level >= need ? r.w_level : r.z_level;  // refreshed to the data's level
   *l_out = r.kind == HE_REQ_INFERENCE ? l0 - 3 : l0 - 5;
   return r.kind == HE_REQ_INFERENCE ? (size_t)r.nZ * *l_out : *l_out;
@@ -70,7 +75,7 @@ static size_t req_words(const he_request& r, uint32_t n) {
 }
 
 static LrShape req_shape(const he_request& r) {
-  const uint32_t need = r.kind == HE_REQ_INFERENCE ? 5 : 6;
+  const uint32_t need = req_need(r);
   const bool refresh = r.w_level < need;
   return LrShape{refresh ? r.z_level : r.w_level, r.nZ, refresh};
 }
@@ -96,6 +101,7 @@ struct he_server {
   std::vector<std::vector<he::Slot>> slots;
   size_t budget = 0, used = 0;
   uint32_t max_wave = 1;
+  size_t max_running = 0;  // 0: no global limit
   std::thread th;
   std::mutex mu;
   std::condition_variable cv;
@@ -112,6 +118,7 @@ namespace he {
 
 static bool same_wave(const he_request& a, const he_request& b) {
   return a.ctx == b.ctx && a.kind == b.kind && a.z_level == b.z_level && a.z_scale == b.z_scale &&
+         a.min_w_level == b.min_w_level &&
          a.w_scale == b.w_scale && memcmp(&a.cfg, &b.cfg, sizeof(he_lr_config)) == 0;
 }
 
@@ -145,7 +152,7 @@ static int enqueue_wave(Slot& sl, std::vector<ServeReq*>& wave) {
       Wout[k] = he_ct{p, 0, lo, 0.0};
     }
     sh[k] = he_lr_shard{Z[k].data(), r.nZ, &W[k], r.kind == HE_REQ_INFERENCE ? nullptr : &Wout[k],
-                        r.kind == HE_REQ_INFERENCE ? Sout[k].data() : nullptr, r.refresh_cid, 0};
+                        r.kind == HE_REQ_INFERENCE ? Sout[k].data() : nullptr, r.refresh_cid, r.min_w_level};
   }
   const he_request& r0 = wave[0]->r;
   HE_TRY(lr_entry(c, sh.data(), sh.size(), &r0.cfg, r0.z_level, 0, r0.kind == HE_REQ_INFERENCE));
@@ -220,6 +227,7 @@ static void scheduler(he_server* s) {
       }
       std::vector<bool> tried(s->ctxs.size(), false);
       for (size_t pi = 0; pi < s->pending.size();) {
+        if (s->max_running && s->running >= s->max_running) break;
         ServeReq* head = s->pending[pi];
         const uint32_t ci = head->r.ctx;
         if (tried[ci]) { ++pi; continue; }
@@ -299,6 +307,7 @@ extern "C" int he_server_create(const he_server_config* cfg, he_server** out) {
   he_server* s = new he_server();
   s->budget = cfg->hbm_budget;
   s->max_wave = cfg->max_wave;
+  s->max_running = cfg->max_running;
   for (size_t i = 0; i < cfg->n_ctx; ++i) {
     he_ctx* c = cfg->ctxs[i];
     if (!c) { delete s; return fail(HE_EINVAL, "he_server_create: null context"); }
@@ -324,8 +333,7 @@ extern "C" int he_server_submit(he_server* s, const he_request* r, uint64_t* id)
   if (!r->Z || !r->W || !r->out || r->nZ == 0) return fail(HE_EINVAL, "he_server_submit: null buffer");
   if (r->z_level < 1 || r->z_level > (uint32_t)c->L || r->w_level < 1 || r->w_level > r->z_level)
     return fail(HE_EINVAL, "he_server_submit: bad levels");
-  const uint32_t need = r->kind == HE_REQ_INFERENCE ? 5 : 6;
-  if (r->z_level < need) return fail(HE_ELEVEL, "he_server_submit: data level below the circuit's depth");
+  if (r->z_level < req_need(*r)) return fail(HE_ELEVEL, "he_server_submit: data level below the circuit's depth");
   ServeReq* q = new ServeReq();
   q->r = *r;
   const size_t out_limbs = req_out_limbs(*r, &q->l_out);

@@ -213,3 +213,30 @@ def test_inference_bit_exact_and_accurate(lr_pair):
         got = he.he_decrypt_decode(pair.g, S2[k])
         for s in range(g):
             assert np.max(np.abs(got[s::g] - p[k * g + s])) < 2.0 ** -20
+
+
+@pytest.mark.parametrize("g", [1, 128])
+def test_extreme_packings_bit_exact(g):
+    """One sample per ciphertext (g = 1: no per-feature sum, no replication)
+    and 128 samples of 4 features each: both kinds against the oracle."""
+    log_n = 10
+    n_slots = (1 << log_n) // 2
+    pair = Pair(log_n, 7, 40, 1, 60, 2.0 ** 40, seed=5, rots=rot_steps(n_slots, g))
+    he = pair.he
+    coeffs = table2()["hinge"]
+    ms = [workloads.int_poly(500 + k, pair.n, 1 << 28) for k in range(2)]
+    mw = workloads.int_poly(509, pair.n, 1 << 28)
+    Zg = pair.g.new_ct(7, 2)
+    for k, m in enumerate(ms):
+        he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 7, Zg[k], cid=500 + k)
+    Wg = pair.gpu_enc(mw, 7, 509, scale=2.0 ** 40)
+    Zo = [pair.orc_enc(m, 7, 500 + k, scale=2.0 ** 40) for k, m in enumerate(ms)]
+    Wo = pair.orc_enc(mw, 7, 509, scale=2.0 ** 40)
+    out = pair.g.new_ct(7)
+    he.he_lr_gradient_step(pair.g, Zg, Wg, he.lr_config(coeffs, 0.25, g, 2.0 ** 40), out)
+    assert_same_residues(out, pair.o.lr_gradient_step(Zo, Wo, coeffs, 0.25, g, 2.0 ** 40), he, pair.g)
+    S = pair.g.new_ct(7, 2)
+    he.he_lr_inference_workers(pair.g, [(Zg, Wg, S)], he.lr_config(coeffs, 1.0, g, 2.0 ** 40))
+    want = pair.o.lr_inference(Zo, Wo, coeffs, 1.0, g)
+    for k in range(2):
+        assert_same_residues(S[k], want[k], he, pair.g)

@@ -379,13 +379,33 @@ def test_fused_keyswitch_bit_exact(wide, he, level):
     d = workloads.residues(500 + level, wide.o.primes[:level], wide.n)[0]
     k0, k1 = wide.o.keyswitch(d, level, -1)
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
-    for generic in (False, True):  # fused kernels, then the unfused sequence
+    # fused kernels (row pass compiled for 2 and for 3 CTAs per SM), then the unfused sequence
+    for generic, ctas in ((False, 2), (False, 3), (True, 2)):
         he.he_set_tuning(wide.g, "ntt_generic", generic)
+        he.he_set_tuning(wide.g, "ks_row_ctas", ctas)
         o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
         he.he_keyswitch(wide.g, dt, level, 0, o0, o1)
         assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
         assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
     he.he_set_tuning(wide.g, "ntt_generic", False)
+    he.he_set_tuning(wide.g, "ks_row_ctas", 3)
+
+
+def test_fused_keyswitch_reduced_accumulation(he):
+    """Nine digits and a 60-bit special prime: 2 * 9 * q exceeds 2^64 there,
+    so that limb's inner product reduces after every product while the
+    40-bit limbs accumulate unreduced."""
+    import torch
+    p = Pair(12, 9, 40, 1, 60, 2.0 ** 40, seed=12)
+    d = workloads.residues(900, p.o.primes[:9], p.n)[0]
+    k0, k1 = p.o.keyswitch(d, 9, -1)
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    for ctas in (2, 3):
+        he.he_set_tuning(p.g, "ks_row_ctas", ctas)
+        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+        he.he_keyswitch(p.g, dt, 9, 0, o0, o1)
+        assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
+        assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
 
 
 def test_fused_rotation_and_mul_bit_exact(wide, he):

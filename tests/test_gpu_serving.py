@@ -48,11 +48,14 @@ def setup():
         Wh = he.he_ct_export(ctx, W)
         lr = 1.0 / 64 if kind == he.HE_REQ_GRADIENT else 1.0
         cfg = he.lr_config(coeffs, lr, g, 2.0 ** 27 if kind == he.HE_REQ_GRADIENT else 2.0 ** 40)
-        l0 = w_level if w_level >= (6 if kind == he.HE_REQ_GRADIENT else 5) else 7
+        # some steps ask for a spare limb: weights below 7 limbs are refreshed
+        min_w = 7 if kind == he.HE_REQ_GRADIENT and r % 2 == 0 else 0
+        need = max(6 if kind == he.HE_REQ_GRADIENT else 5, min_w)
+        l0 = w_level if w_level >= need else 7
         l_out = l0 - (5 if kind == he.HE_REQ_GRADIENT else 3)
         shape = (2, l_out, ctx.n) if kind == he.HE_REQ_GRADIENT else (nz, 2, l_out, ctx.n)
         reqs.append(dict(ci=ci, kind=kind, Zh=Zh, Wh=Wh, w_level=w_level, cfg=cfg, shape=shape, data=data,
-                         g=g, lr=lr, nz=nz, l_out=l_out, cid=77000 + r))
+                         g=g, lr=lr, nz=nz, l_out=l_out, cid=77000 + r, min_w=min_w))
     return he, ctxs, reqs, coeffs
 
 
@@ -63,7 +66,7 @@ def serve(he, ctxs, reqs, budget, inflight, wave, one_at_a_time):
         for i, r in enumerate(reqs):
             out = np.zeros(r["shape"], dtype=np.uint64)
             rid = srv.submit(r["ci"], r["kind"], r["Zh"], 7, 2.0 ** 40, r["Wh"], r["w_level"], 2.0 ** 40,
-                             r["cfg"], out, refresh_cid=r["cid"])
+                             r["cfg"], out, refresh_cid=r["cid"], min_w_level=r["min_w"])
             outs[rid] = out
             ids[rid] = i
             if one_at_a_time:
