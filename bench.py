@@ -131,7 +131,7 @@ def measured_peaks():
 # products/s.  A butterfly is one product; the key-switching kernels also
 # count their basis-conversion and inner-product products.
 ALU_MODMUL_PEAK = 152 * 2.070e9 * 64 / 17.3
-ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product")
+ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "moddown_ntt", "moddown_ntt_combine")
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
@@ -194,6 +194,7 @@ def run_ours(args, rank: int, world: int):
     coeffs = table2_binomial()
     lr = 1.0 / N_SAMPLES
     cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
+    tuned = he.he_autotune(ctx, L - 1, 64)  # kernel knobs by timing, before any timed step
     Z, W = build_inputs(he, ctx, data, L)
     out = ctx.new_ct(L)
     step = lambda: he.he_lr_gradient_step(ctx, Z, W, cfg, out)  # noqa: E731
@@ -287,6 +288,7 @@ def run_ours(args, rank: int, world: int):
         "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(v["launches"] for v in prof.values()) // prof_steps),
+        "autotune": tuned,
         "roofline": roof, "kernels": kernels, "clocks": clk.summary(), "cpu_baseline": cpu,
     }
     line.update(extra)
@@ -370,6 +372,7 @@ def batched_workers(he, torch, stream, reps=2):
     coeffs = table2_binomial()
     lr = 1.0 / N_SAMPLES  # one learning rate for all workers
     cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
+    tuned = he.he_autotune(ctx, L, 64)
     shards, datas = [], []
     t0 = time.perf_counter()
     for k, (ns, lv) in enumerate(zip(sizes, levels)):
@@ -449,7 +452,7 @@ def batched_workers(he, torch, stream, reps=2):
                                     "median_ms_per_ciphertext": float(np.median(per_ct_ms)),
                                     "what": "each worker one ciphertext at a time; timed on 4 and 8 ciphertexts "
                                             "per worker, extrapolated linearly to the full shard"},
-           "max_rel_err_vs_fp64_largest_worker": rel, "setup_s": setup_s}
+           "max_rel_err_vs_fp64_largest_worker": rel, "setup_s": setup_s, "autotune": tuned}
     ctx.close()
     del shards
     torch.cuda.empty_cache()
@@ -731,8 +734,10 @@ def run_micro(args):
     host = workloads.residues(1, ctx.primes[:nl], n, parts=args.polys)
     t = torch.from_numpy(host.view(np.int64)).cuda()
     out = {}
-    for generic, inverse in ((False, False), (False, True), (True, False), (True, True)):
+    for shape, generic, inverse in ((0, False, False), (0, False, True), (1, False, False), (1, False, True),
+                                    (2, False, False), (2, False, True), (0, True, False), (0, True, True)):
         he.he_set_tuning(ctx, "ntt_generic", generic)
+        he.he_set_tuning(ctx, "ntt_shape", shape)
         for _ in range(args.warmup):
             he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -744,7 +749,7 @@ def run_micro(args):
         ms = e0.elapsed_time(e1) / args.steps
         limbs = args.polys * nl
         bfly = limbs * (n / 2) * log_n
-        out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else "")] = {
+        out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else f"_shape{shape}" if shape else "")] = {
             "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_MODMUL_PEAK,
             "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
     he.he_set_tuning(ctx, "ntt_generic", False)

@@ -99,9 +99,24 @@ int he_sync(he_ctx* ctx);
  * chunk of the logistic-regression step (0 = from the budget), "ntt_generic"
  * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
  * one for N = 2^12 .. 2^16, "ks_row_ctas" = 2 or 3 (default) CTAs per SM for the
- * fused key-switch row pass (register budget 128 or 80 per thread).  HE_EINVAL for
- * an unknown key or a value out of range. */
+ * fused key-switch row pass (register budget 128 or 80 per thread),
+ * "ntt_shape" = 0 (default), 1 or 2 for the three NTT tile-shape pairs compiled
+ * per ring size (also used by the fused key switch), "ntt_pb_max" = at most this
+ * many polynomials of one limb per NTT CTA (default 8).  HE_EINVAL for an
+ * unknown key or a value out of range. */
 int he_set_tuning(he_ctx* ctx, const char* key, double value);
+/* Current value of a tuning knob (the keys above). */
+int he_get_tuning(he_ctx* ctx, const char* key, double* value);
+
+/* Autotuner (no counterpart in the paper; it serves the batched workers of
+ * Sec. 4): times the relinearisation key switch (iNTT, ModUp + NTT, inner
+ * product, ModDown) of `count` polynomials of uniform residues at `level`
+ * under every setting of "ntt_shape", "ks_row_ctas" and "ntt_pb_max" in
+ * {1, 4, 8}, keeps the fastest in the context and writes its time per key
+ * switch (ms) to *best_ms (may be NULL).  Synchronises the context's stream;
+ * results never depend on these knobs.  HE_EINVAL for level outside [1, L] or
+ * count outside [1, 4096]; on an error the knobs keep their previous values. */
+int he_autotune(he_ctx* ctx, uint32_t level, uint32_t count, double* best_ms);
 
 /* Context facts: N, L, alpha, beta (digits at the top level), and the
  * L + alpha primes (limbs first) into primes_out (may be NULL). */

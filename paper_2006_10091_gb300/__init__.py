@@ -126,6 +126,8 @@ def load():
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
+        "he_get_tuning": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
+        "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
@@ -268,6 +270,22 @@ def he_set_stream(ctx: Context, stream):
 
 def he_set_tuning(ctx: Context, key: str, value: float):
     _check(load().he_set_tuning(ctx.ptr, key.encode(), float(value)))
+
+
+def he_get_tuning(ctx: Context, key: str) -> float:
+    v = ctypes.c_double()
+    _check(load().he_get_tuning(ctx.ptr, key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def he_autotune(ctx: Context, level: int, count: int) -> dict:
+    """Time the kernel knobs on a key switch of `count` polynomials at `level`
+    and keep the fastest; returns the chosen knobs and the time (ms)."""
+    ms = ctypes.c_double()
+    _check(load().he_autotune(ctx.ptr, level, count, ctypes.byref(ms)))
+    out = {k: he_get_tuning(ctx, k) for k in ("ntt_shape", "ks_row_ctas", "ntt_pb_max")}
+    out["ms_per_keyswitch"] = ms.value
+    return out
 
 
 def he_sync(ctx: Context):

@@ -122,6 +122,8 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->lr_chunk = base->lr_chunk;
   v->ntt_generic = base->ntt_generic;
   v->ks_row_ctas = base->ks_row_ctas;
+  v->ntt_shape = base->ntt_shape;
+  v->ntt_pb_max = base->ntt_pb_max;
   v->P_mod_q = base->P_mod_q;
   v->d_s = base->d_s;
   v->d_pk = base->d_pk;
@@ -268,6 +270,13 @@ int he_set_tuning(he_ctx* c, const char* key, double value) {
   } else if (k == "ks_row_ctas") {
     if (value != 2.0 && value != 3.0) return fail(HE_EINVAL, "ks_row_ctas is 2 or 3");
     c->ks_row_ctas = (int)value;
+  } else if (k == "ntt_shape") {
+    if (value != 0.0 && value != 1.0 && value != 2.0) return fail(HE_EINVAL, "ntt_shape is 0, 1 or 2");
+    c->ntt_shape = (int)value;
+  } else if (k == "ntt_pb_max") {
+    if (!(value >= 1 && value <= 64) || value != (double)(uint32_t)value)
+      return fail(HE_EINVAL, "ntt_pb_max is an integer in [1, 64]");
+    c->ntt_pb_max = (uint32_t)value;
   } else {
     return fail(HE_EINVAL, "unknown tuning key " + k);
   }

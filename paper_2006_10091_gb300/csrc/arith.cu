@@ -9,10 +9,6 @@
 
 namespace he {
 
-__device__ __forceinline__ uint64_t* cpoly(const CtBatch& b, uint32_t i, uint32_t p, uint32_t t, uint32_t n) {
-  return b.base + (size_t)i * b.stride + ((size_t)p * b.cap + t) * n;
-}
-
 // ---- tensor product: (a0 b0, a0 b1 + a1 b0, a1 b1) ---------------------------
 __global__ void k_tensor(CtBatch A, CtBatch B, CtBatch D, uint64_t* d2, uint64_t d2_stride,
                          uint32_t level, uint32_t count, int log_n, const PrimeDev* primes) {

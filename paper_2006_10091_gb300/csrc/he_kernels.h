@@ -15,6 +15,11 @@ struct CtBatch {
   uint32_t pad;
 };
 
+// Ciphertext i, part p, limb t of a uniform batch.
+__device__ __forceinline__ uint64_t* cpoly(const CtBatch& b, uint32_t i, uint32_t p, uint32_t t, uint32_t n) {
+  return b.base + (size_t)i * b.stride + ((size_t)p * b.cap + t) * n;
+}
+
 struct ModUpArgs {
   uint32_t level, alpha, beta, L, np;
   uint32_t lo[HE_MAX_PRIMES], cnt[HE_MAX_PRIMES];

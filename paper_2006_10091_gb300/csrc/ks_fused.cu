@@ -167,6 +167,143 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
   }
 }
 
+// ---- ModDown, fused the same way ------------------------------------------
+// The P-part of the accumulators (coefficient form after its inverse NTT) is
+// converted to each target limb inside the load of the forward NTT's column
+// pass (as k_moddown_conv: conv = BConv(y + h) - h), and the row pass ends
+// with the combine of k_ks_combine: out = add + (acc_Q - NTT(conv)) * P^-1.
+// A CTA handles both parts of one ciphertext for one limb and tile, so the
+// staged twiddles serve two transforms.
+struct MdArgs {
+  const uint64_t* acc;  // count x [2][nt][N]: evaluation form on limbs < level, coefficient form on the P limbs
+  uint64_t acc_stride;
+  uint64_t* conv;       // count x [2][level][N]: column-pass outputs
+  CtBatch add, out;
+  int has_add;          // 0 none, 1 part 0 only, 2 both parts
+  uint32_t level, alpha, L, nt;
+  const PrimeDev* primes;
+  const ulonglong2* tw;
+  const uint64_t* md;   // ModDown tables (params.cu)
+};
+
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
+  constexpr uint32_t N = 1u << LOG_N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t t = b % a.level, i = b / a.level;
+  const PrimeDev pr = a.primes[t];
+  const uint64_t* mat = a.md + 2 * a.alpha;
+  const uint64_t* hP = mat + (size_t)a.alpha * a.L + 2 * a.L;
+  const uint64_t hQ = hP[a.alpha + t];
+  stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
+  for (uint32_t p = 0; p < 2; ++p) {
+    const uint64_t* yP = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + a.level) * N;
+#pragma unroll 2
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
+      const uint32_t e = S::gidx(tile, k, xx);
+      uint64_t acc = 0;
+      for (uint32_t u = 0; u < a.alpha; ++u) {
+        const uint64_t pu = a.primes[a.L + u].q;
+        const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pu);
+        const uint64_t v = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pu);
+        acc = add_mod(acc, mul_mod(reduce64(v, pr), mat[(size_t)u * a.L + t], pr), pr.q);
+      }
+      sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
+    }
+    __syncthreads();
+    if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+    uint64_t* out = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
+#pragma unroll 4
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
+      out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
+    }
+    // the next part rewrites only the words each thread has just read
+  }
+}
+
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_row_combine(MdArgs a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
+  constexpr uint32_t N = 1u << LOG_N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t t = b % a.level, i = b / a.level;
+  const PrimeDev pr = a.primes[t];
+  const uint64_t q = pr.q;
+  const bool lazy = q < (1ull << 58);
+  const uint64_t* pinv = a.md + 2 * a.alpha + (size_t)a.alpha * a.L;
+  const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
+  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)t * N, tile);
+  for (uint32_t p = 0; p < 2; ++p) {
+    const uint64_t* src = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
+#pragma unroll 4
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
+      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
+    }
+    __syncthreads();
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    const uint64_t* accq = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + t) * N;
+    const bool add = a.has_add == 2 || (a.has_add == 1 && p == 0);
+    const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
+    uint64_t* o = cpoly(a.out, i, p, t, N);
+#pragma unroll 4
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
+      const uint32_t e = S::gidx(tile, k, x);
+      const uint64_t v = sm[idx + (idx >> 3)];
+      const uint64_t cv = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
+      uint64_t r = mul_shoup(sub_mod(__ldg(accq + e), cv, q), w, wsh, q);
+      if (add) r = add_mod(r, ad[e], q);
+      o[e] = r;
+    }
+  }
+}
+
+template <int LOG_N, int M1, int K1, int M2, int K2>
+static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count) {
+  using SC = Shape<LOG_N, M1, K1, true>;
+  using SR = Shape<LOG_N, M2, K2, false>;
+  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
+  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
+  static unsigned long long attr_set = 0;
+  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
+    HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    HE_CUDA(cudaFuncSetAttribute(md_row_combine<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    attr_set |= 1ull << c->device;
+  }
+  const double n = (double)(1u << LOG_N);
+  const double polys = 2.0 * count * a.level;  // transformed limbs
+  {
+    const size_t blocks = (size_t)count * a.level * SC::TILES;
+    ProfScope prof(c, "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha), n * 8 * (2.0 * count * a.alpha + polys));
+    md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
+  }
+  HE_CUDA(cudaGetLastError());
+  {
+    const size_t blocks = (size_t)count * a.level * SR::TILES;
+    const double addw = a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
+    ProfScope prof(c, "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n), n * 8 * (3.0 * polys + addw));
+    md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
 template <int LOG_N, int M1, int K1, int M2, int K2>
 static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   using SC = Shape<LOG_N, M1, K1, true>;
@@ -236,12 +373,69 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
     a.off[j] = mc.off;
   }
   *handled = true;
+  const int sh = c->ntt_shape;  // the tile shapes of ntt2.cu
   switch (c->log_n) {
-    case 12: return ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
-    case 13: return ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
-    case 14: return ks_fused_run<14, 7, 4, 7, 4>(c, a, count);
-    case 15: return ks_fused_run<15, 8, 4, 7, 4>(c, a, count);
-    default: return ks_fused_run<16, 8, 4, 8, 3>(c, a, count);
+    case 12:
+      return sh == 1 ? ks_fused_run<12, 5, 6, 7, 4>(c, a, count)
+           : sh == 2 ? ks_fused_run<12, 3, 8, 9, 2>(c, a, count) : ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
+    case 13:
+      return sh == 1 ? ks_fused_run<13, 6, 5, 7, 4>(c, a, count)
+           : sh == 2 ? ks_fused_run<13, 4, 7, 9, 2>(c, a, count) : ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
+    case 14:
+      return sh == 1 ? ks_fused_run<14, 8, 3, 6, 5>(c, a, count)
+           : sh == 2 ? ks_fused_run<14, 5, 6, 9, 2>(c, a, count) : ks_fused_run<14, 7, 4, 7, 4>(c, a, count);
+    case 15:
+      return sh == 1 ? ks_fused_run<15, 7, 4, 8, 3>(c, a, count)
+           : sh == 2 ? ks_fused_run<15, 6, 5, 9, 2>(c, a, count) : ks_fused_run<15, 8, 4, 7, 4>(c, a, count);
+    default:
+      return sh == 1 ? ks_fused_run<16, 7, 4, 9, 2>(c, a, count)
+           : sh == 2 ? ks_fused_run<16, 6, 5, 10, 1>(c, a, count) : ks_fused_run<16, 8, 4, 8, 3>(c, a, count);
+  }
+}
+
+}  // namespace he
+
+namespace he {
+
+// Conversion -> NTT -> combine of keyswitch_batch's ModDown, fused.  acc's P
+// limbs must already be in coefficient form.  Sets *handled when N has
+// compiled shapes (the same ones as the NTT and ModUp).
+int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
+             CtBatch out, uint32_t level, uint32_t count, bool* handled) {
+  *handled = false;
+  if (c->ntt_generic || c->log_n < 12 || c->log_n > 16) return HE_OK;
+  MdArgs a;
+  a.acc = acc;
+  a.acc_stride = acc_stride;
+  a.conv = conv;
+  a.add = add;
+  a.out = out;
+  a.has_add = add_mode;
+  a.level = level;
+  a.alpha = (uint32_t)c->alpha;
+  a.L = (uint32_t)c->L;
+  a.nt = level + a.alpha;
+  a.primes = c->d_primes;
+  a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.md = c->d_moddown;
+  *handled = true;
+  const int sh = c->ntt_shape;
+  switch (c->log_n) {
+    case 12:
+      return sh == 1 ? md_fused_run<12, 5, 6, 7, 4>(c, a, count)
+           : sh == 2 ? md_fused_run<12, 3, 8, 9, 2>(c, a, count) : md_fused_run<12, 6, 5, 6, 5>(c, a, count);
+    case 13:
+      return sh == 1 ? md_fused_run<13, 6, 5, 7, 4>(c, a, count)
+           : sh == 2 ? md_fused_run<13, 4, 7, 9, 2>(c, a, count) : md_fused_run<13, 7, 4, 6, 5>(c, a, count);
+    case 14:
+      return sh == 1 ? md_fused_run<14, 8, 3, 6, 5>(c, a, count)
+           : sh == 2 ? md_fused_run<14, 5, 6, 9, 2>(c, a, count) : md_fused_run<14, 7, 4, 7, 4>(c, a, count);
+    case 15:
+      return sh == 1 ? md_fused_run<15, 7, 4, 8, 3>(c, a, count)
+           : sh == 2 ? md_fused_run<15, 6, 5, 9, 2>(c, a, count) : md_fused_run<15, 8, 4, 7, 4>(c, a, count);
+    default:
+      return sh == 1 ? md_fused_run<16, 7, 4, 9, 2>(c, a, count)
+           : sh == 2 ? md_fused_run<16, 6, 5, 10, 1>(c, a, count) : md_fused_run<16, 8, 4, 8, 3>(c, a, count);
   }
 }
 

@@ -122,7 +122,7 @@ static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t*
   // several polynomials of one limb per CTA share its staged twiddles, as
   // long as the grid keeps about four waves of CTAs
   const size_t tiles = (size_t)b.npolys * b.nl * S::TILES;
-  const size_t pb = std::max<size_t>(1, std::min<size_t>(8, tiles / (4 * 4 * 152)));
+  const size_t pb = std::max<size_t>(1, std::min<size_t>(c->ntt_pb_max, tiles / (4 * 4 * 152)));
   a.np = b.npolys;
   a.pb = (uint32_t)pb;
   const size_t blocks = (size_t)((b.npolys + pb - 1) / pb) * b.nl * S::TILES;
@@ -150,21 +150,40 @@ static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t*
 template <bool INV, int LOG_N, int M1, int K1, int M2, int K2>
 static int run2(he_ctx* c, const PolyBatch& b) {
   if (!INV) {
-    HE_TRY((launch2<false, LOG_N, M1, K1, true>(c, b, b.src, b.dst, b.src_stride, false)));
-    return launch2<false, LOG_N, M2, K2, false>(c, b, b.dst, b.dst, b.dst_stride, true);
+    const int rc = launch2<false, LOG_N, M1, K1, true>(c, b, b.src, b.dst, b.src_stride, false);
+    return rc != HE_OK ? rc : launch2<false, LOG_N, M2, K2, false>(c, b, b.dst, b.dst, b.dst_stride, true);
   }
-  HE_TRY((launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false)));
-  return launch2<true, LOG_N, M1, K1, true>(c, b, b.dst, b.dst, b.dst_stride, true);
+  const int rc = launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false);
+  return rc != HE_OK ? rc : launch2<true, LOG_N, M1, K1, true>(c, b, b.dst, b.dst, b.dst_stride, true);
 }
 
+template <int LOG_N, int M1, int K1, int M2, int K2>
+static int run2_dir(he_ctx* c, const PolyBatch& b, bool inv) {
+  return inv ? run2<true, LOG_N, M1, K1, M2, K2>(c, b) : run2<false, LOG_N, M1, K1, M2, K2>(c, b);
+}
+
+// Three tile shapes per ring size (column pass bits, rows per tile | row pass
+// bits, rows per tile); c->ntt_shape picks one (the autotuner times them).
+// The fused key-switching kernels use the same pairs.
 int ntt2(he_ctx* c, const PolyBatch& b, bool inv, bool* handled) {
   *handled = true;
+  const int sh = c->ntt_shape;
   switch (c->log_n) {
-    case 12: return inv ? run2<true, 12, 6, 5, 6, 5>(c, b) : run2<false, 12, 6, 5, 6, 5>(c, b);
-    case 13: return inv ? run2<true, 13, 7, 4, 6, 5>(c, b) : run2<false, 13, 7, 4, 6, 5>(c, b);
-    case 14: return inv ? run2<true, 14, 7, 4, 7, 4>(c, b) : run2<false, 14, 7, 4, 7, 4>(c, b);
-    case 15: return inv ? run2<true, 15, 8, 4, 7, 4>(c, b) : run2<false, 15, 8, 4, 7, 4>(c, b);
-    case 16: return inv ? run2<true, 16, 8, 4, 8, 3>(c, b) : run2<false, 16, 8, 4, 8, 3>(c, b);
+    case 12:
+      return sh == 1 ? run2_dir<12, 5, 6, 7, 4>(c, b, inv)
+           : sh == 2 ? run2_dir<12, 3, 8, 9, 2>(c, b, inv) : run2_dir<12, 6, 5, 6, 5>(c, b, inv);
+    case 13:
+      return sh == 1 ? run2_dir<13, 6, 5, 7, 4>(c, b, inv)
+           : sh == 2 ? run2_dir<13, 4, 7, 9, 2>(c, b, inv) : run2_dir<13, 7, 4, 6, 5>(c, b, inv);
+    case 14:
+      return sh == 1 ? run2_dir<14, 8, 3, 6, 5>(c, b, inv)
+           : sh == 2 ? run2_dir<14, 5, 6, 9, 2>(c, b, inv) : run2_dir<14, 7, 4, 7, 4>(c, b, inv);
+    case 15:
+      return sh == 1 ? run2_dir<15, 7, 4, 8, 3>(c, b, inv)
+           : sh == 2 ? run2_dir<15, 6, 5, 9, 2>(c, b, inv) : run2_dir<15, 8, 4, 7, 4>(c, b, inv);
+    case 16:
+      return sh == 1 ? run2_dir<16, 7, 4, 9, 2>(c, b, inv)
+           : sh == 2 ? run2_dir<16, 6, 5, 10, 1>(c, b, inv) : run2_dir<16, 8, 4, 8, 3>(c, b, inv);
     default: *handled = false; return HE_OK;
   }
 }

@@ -17,6 +17,8 @@
 namespace he {
 int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
              const uint64_t* evk, uint32_t level, uint32_t count, bool* handled);
+int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
+             CtBatch out, uint32_t level, uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -124,6 +126,9 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   // 4. ModDown
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
                            (size_t)nt * n, count * 2, alpha, level, level)));
+  bool md_done = false;
+  HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, out, level, count, &md_done));
+  if (md_done) return HE_OK;
   {
     ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
     k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(

@@ -51,16 +51,46 @@ def test_ntt_matches_oracle(he, log_n):
     n = 1 << log_n
     npolys = 3  # ragged: three polynomials of L + 1 limbs
     data = workloads.residues(log_n, ctx.primes, n, parts=npolys)  # [npolys][np][n]
-    t = torch.from_numpy(data.view(np.int64).copy()).cuda()
-    he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, False)
-    got = t.cpu().numpy().view(np.uint64)
-    for p in range(npolys):
-        for limb in range(L + 1):
-            q, psi = ctx.primes[limb], oracle.min_root(ctx.primes[limb], log_n)
-            want = oracle.ntt_r2(data[p, limb], log_n, q, psi)
-            assert np.array_equal(got[p, limb], want), (p, limb)
-    he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, True)
-    assert np.array_equal(t.cpu().numpy().view(np.uint64), data)
+    want = [[oracle.ntt_r2(data[p, limb], log_n, ctx.primes[limb], oracle.min_root(ctx.primes[limb], log_n))
+             for limb in range(L + 1)] for p in range(npolys)]
+    for shape in ((0, 1, 2) if log_n >= 12 else (0,)):  # every compiled tile shape
+        he.he_set_tuning(ctx, "ntt_shape", shape)
+        t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+        he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, False)
+        got = t.cpu().numpy().view(np.uint64)
+        for p in range(npolys):
+            for limb in range(L + 1):
+                assert np.array_equal(got[p, limb], want[p][limb]), (shape, p, limb)
+        he.he_ntt(ctx, t, npolys, (L + 1) * n, L + 1, 0, True)
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), data)
+    he.he_set_tuning(ctx, "ntt_shape", 0)
+
+
+@pytest.mark.parametrize("log_n", [13, 16])
+def test_ntt_several_polynomials_per_cta(he, log_n):
+    """Large ragged batches, where NTT CTAs transform several polynomials of
+    one limb: every shape and grouping agrees with the runtime-shaped kernel."""
+    import torch
+    ctx = he.Context(log_n, 3, 45, 1, 60, 2.0 ** 40, seed=4)
+    n = 1 << log_n
+    npolys = 321 if log_n == 13 else 41
+    data = workloads.residues(7 + log_n, ctx.primes, n, parts=npolys)
+    t0 = torch.from_numpy(data.view(np.int64).copy()).cuda()
+    he.he_set_tuning(ctx, "ntt_generic", True)
+    he.he_ntt(ctx, t0, npolys, 4 * n, 4, 0, False)
+    ref = t0.cpu().numpy()
+    he.he_set_tuning(ctx, "ntt_generic", False)
+    for shape in (0, 1, 2):
+        for pb in (1, 8):
+            he.he_set_tuning(ctx, "ntt_shape", shape)
+            he.he_set_tuning(ctx, "ntt_pb_max", pb)
+            t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+            he.he_ntt(ctx, t, npolys, 4 * n, 4, 0, False)
+            assert np.array_equal(t.cpu().numpy(), ref), (shape, pb)
+            he.he_ntt(ctx, t, npolys, 4 * n, 4, 0, True)
+            assert np.array_equal(t.cpu().numpy().view(np.uint64), data), (shape, pb)
+    he.he_set_tuning(ctx, "ntt_shape", 0)
+    he.he_set_tuning(ctx, "ntt_pb_max", 8)
 
 
 @pytest.mark.parametrize("log_n", [12, 13, 14, 15, 16])
@@ -379,16 +409,40 @@ def test_fused_keyswitch_bit_exact(wide, he, level):
     d = workloads.residues(500 + level, wide.o.primes[:level], wide.n)[0]
     k0, k1 = wide.o.keyswitch(d, level, -1)
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
-    # fused kernels (row pass compiled for 2 and for 3 CTAs per SM), then the unfused sequence
-    for generic, ctas in ((False, 2), (False, 3), (True, 2)):
+    # fused kernels (every tile shape, row pass compiled for 2 and for 3 CTAs
+    # per SM), then the unfused sequence
+    for generic, shape, ctas in ((False, 0, 2), (False, 0, 3), (False, 1, 2), (False, 1, 3), (False, 2, 2),
+                                 (False, 2, 3), (True, 0, 2)):
         he.he_set_tuning(wide.g, "ntt_generic", generic)
+        he.he_set_tuning(wide.g, "ntt_shape", shape)
         he.he_set_tuning(wide.g, "ks_row_ctas", ctas)
         o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
         he.he_keyswitch(wide.g, dt, level, 0, o0, o1)
         assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
         assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
     he.he_set_tuning(wide.g, "ntt_generic", False)
+    he.he_set_tuning(wide.g, "ntt_shape", 0)
     he.he_set_tuning(wide.g, "ks_row_ctas", 3)
+
+
+def test_autotune_keeps_results(wide, he):
+    """The autotuner picks knobs among its candidates; a rotation and a
+    multiplication after it still match the oracle bit for bit."""
+    res = he.he_autotune(wide.g, 6, 8)
+    assert res["ntt_shape"] in (0, 1, 2) and res["ks_row_ctas"] in (2, 3) and res["ntt_pb_max"] in (1, 4, 8)
+    assert res["ms_per_keyswitch"] > 0
+    m1, m2 = workloads.int_poly(81, wide.n, 1 << 36), workloads.int_poly(82, wide.n, 1 << 36)
+    ga, oa = wide.gpu_enc(m1, 6, 81), wide.orc_enc(m1, 6, 81)
+    gb, ob = wide.gpu_enc(m2, 6, 82), wide.orc_enc(m2, 6, 82)
+    out = wide.g.new_ct(6)
+    he.he_rotate(wide.g, ga, 5, out)
+    assert_same_residues(out, wide.o.rotate(oa, 5), he, wide.g)
+    he.he_mul_relin_rescale(wide.g, ga, gb, out)
+    assert_same_residues(out, wide.o.mul_relin_rescale(oa, ob), he, wide.g)
+    for k, v in (("ntt_shape", 0), ("ks_row_ctas", 3), ("ntt_pb_max", 8)):
+        he.he_set_tuning(wide.g, k, v)
+    with pytest.raises(he.HeError):
+        he.he_autotune(wide.g, 0, 8)
 
 
 def test_fused_keyswitch_reduced_accumulation(he):
