@@ -230,7 +230,6 @@ __global__ void k_rescale_final(CtBatch in, const uint64_t* corr, CtBatch out, u
 __global__ void k_automorph(CtBatch in, CtBatch out, uint32_t nparts, uint32_t level, uint64_t gal,
                             uint32_t count, int log_n) {
   const uint32_t n = 1u << log_n;
-  const uint32_t mask2n = 2 * n - 1;
   const size_t total = (size_t)count * nparts * level * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const uint32_t j = (uint32_t)(g % n);
@@ -238,10 +237,7 @@ __global__ void k_automorph(CtBatch in, CtBatch out, uint32_t nparts, uint32_t l
     const uint32_t t = (uint32_t)(r % level);
     r /= level;
     const uint32_t p = (uint32_t)(r % nparts), i = (uint32_t)(r / nparts);
-    const uint32_t e = 2 * brev_bits(j, log_n) + 1;
-    const uint32_t e2 = (uint32_t)(((uint64_t)e * gal) & mask2n);
-    const uint32_t js = brev_bits((e2 - 1) >> 1, log_n);
-    cpoly(out, i, p, t, n)[j] = cpoly(in, i, p, t, n)[js];
+    cpoly(out, i, p, t, n)[j] = cpoly(in, i, p, t, n)[automorph_src(j, gal, log_n)];
   }
 }
 

@@ -117,3 +117,12 @@ enum : uint32_t {
 __device__ __forceinline__ uint32_t brev_bits(uint32_t x, int bits) {
   return __brev(x) >> (32 - bits);
 }
+
+// The automorphism X -> X^gal (gal odd) in evaluation form: slot j of the
+// result is slot automorph_src(j) of the input, where slot j holds the value at
+// psi^(2 brv(j) + 1), so 2 brv(src) + 1 = (2 brv(j) + 1) * gal mod 2N.
+__device__ __forceinline__ uint32_t automorph_src(uint32_t j, uint64_t gal, int log_n) {
+  const uint32_t e = 2 * brev_bits(j, log_n) + 1;
+  const uint32_t e2 = (e * (uint32_t)gal) & ((2u << log_n) - 1);  // 2N divides 2^32
+  return brev_bits((e2 - 1) >> 1, log_n);
+}

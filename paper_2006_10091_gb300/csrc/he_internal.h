@@ -150,6 +150,7 @@ struct PolyBatch {
   uint64_t src_stride, dst_stride;
   uint32_t npolys, nl, limb0, level;
   uint32_t skip_alpha, skip_beta;
+  uint64_t gal = 0;  // inverse transforms: read the source through this automorphism (0: none)
 };
 int ntt_forward(he_ctx* c, const PolyBatch& b);
 int ntt_inverse(he_ctx* c, const PolyBatch& b);

@@ -42,9 +42,13 @@ size_t mul_words(const he_ctx* c, uint32_t level, uint32_t count, bool rescale);
 size_t rot_words(const he_ctx* c, uint32_t level, uint32_t count);
 size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count);
 
-// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts.
+// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts.  gal != 0:
+// d and the addend are read through the automorphism X -> X^gal (fused
+// kernels only; the output must not overlap them).
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
-                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar);
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal = 0);
+// Whether N has compiled shapes for the fused key-switching kernels.
+inline bool ks_fusable(const he_ctx* c) { return !c->ntt_generic && c->log_n >= 12 && c->log_n <= 16; }
 int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch out, Arena& ar);
 int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t count, CtBatch out,
                     bool rescale, Arena& ar);

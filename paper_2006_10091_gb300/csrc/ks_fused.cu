@@ -25,6 +25,7 @@ struct KsFusedArgs {
   const uint64_t* evk;   // [beta_top][2][np][N]
   const uint64_t* evk_sh;  // Shoup companions of evk, same layout
   uint64_t d_stride;
+  uint64_t gal;            // d is read through the automorphism X -> X^gal (0: none)
   uint32_t level, alpha, beta, L, np, nt;
   const PrimeDev* primes;
   const ulonglong2* tw;
@@ -58,7 +59,9 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFus
   stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
   const uint64_t* tab = a.consts + a.off[j];
   const uint64_t* mat = tab + 2 * cnt;
+  const uint64_t* mat_sh = mat + (size_t)cnt * a.np;
   const uint64_t* x = a.d2c + (size_t)i * a.level * N;
+  const uint64_t q2 = pr.q + pr.q;
 #pragma unroll 2
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
     const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
@@ -67,12 +70,15 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFus
     if (cnt == 1) {
       y = reduce64(__ldg(x + (size_t)lo * N + e), pr);  // Q_j / q_lo = 1
     } else {
+      // products by the constant (Q_j/q_i) mod q_t are Shoup products in [0, 2q), kept in [0, 2q)
       y = 0;
       for (uint32_t u = 0; u < cnt; ++u) {
         const uint64_t qa = a.primes[lo + u].q;
         const uint64_t v = mul_shoup(__ldg(x + (size_t)(lo + u) * N + e), tab[2 * u], tab[2 * u + 1], qa);
-        y = add_mod(y, mul_mod(reduce64(v, pr), mat[(size_t)u * a.np + prime], pr), pr.q);
+        y += mul_shoup_lazy(v, mat[(size_t)u * a.np + prime], mat_sh[(size_t)u * a.np + prime], pr.q);
+        y = y >= q2 ? y - q2 : y;
       }
+      y = y >= pr.q ? y - pr.q : y;
     }
     sm[idx + (idx >> 3)] = y;
   }
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
       for (int u = 0; u < PER; ++u) {
         const uint32_t idx = threadIdx.x + u * S::T;
         const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-        const uint64_t x = __ldg(dd + e);
+        const uint64_t x = __ldg(dd + (a.gal ? automorph_src(e, a.gal, LOG_N) : e));
         mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
         mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
       }
@@ -180,6 +186,7 @@ struct MdArgs {
   uint64_t* conv;       // count x [2][level][N]: column-pass outputs
   CtBatch add, out;
   int has_add;          // 0 none, 1 part 0 only, 2 both parts
+  uint64_t add_gal;     // the addend is read through the automorphism X -> X^add_gal (0: none)
   uint32_t level, alpha, L, nt;
   const PrimeDev* primes;
   const ulonglong2* tw;
@@ -198,9 +205,11 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   b /= S::TILES;
   const uint32_t t = b % a.level, i = b / a.level;
   const PrimeDev pr = a.primes[t];
+  const uint64_t q2 = pr.q + pr.q;
   const uint64_t* mat = a.md + 2 * a.alpha;
   const uint64_t* hP = mat + (size_t)a.alpha * a.L + 2 * a.L;
   const uint64_t hQ = hP[a.alpha + t];
+  const uint64_t* mat_sh = hP + a.alpha + a.L;
   stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
   for (uint32_t p = 0; p < 2; ++p) {
     const uint64_t* yP = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + a.level) * N;
@@ -208,13 +217,15 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
       const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
       const uint32_t e = S::gidx(tile, k, xx);
-      uint64_t acc = 0;
+      uint64_t acc = 0;  // Shoup products by (P/p_u) mod q_t, kept in [0, 2q)
       for (uint32_t u = 0; u < a.alpha; ++u) {
         const uint64_t pu = a.primes[a.L + u].q;
         const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pu);
         const uint64_t v = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pu);
-        acc = add_mod(acc, mul_mod(reduce64(v, pr), mat[(size_t)u * a.L + t], pr), pr.q);
+        acc += mul_shoup_lazy(v, mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t], pr.q);
+        acc = acc >= q2 ? acc - q2 : acc;
       }
+      acc = acc >= pr.q ? acc - pr.q : acc;
       sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
     }
     __syncthreads();
@@ -268,7 +279,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_row_combine(MdA
       const uint64_t v = sm[idx + (idx >> 3)];
       const uint64_t cv = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
       uint64_t r = mul_shoup(sub_mod(__ldg(accq + e), cv, q), w, wsh, q);
-      if (add) r = add_mod(r, ad[e], q);
+      if (add) r = add_mod(r, ad[a.add_gal ? automorph_src(e, a.add_gal, LOG_N) : e], q);
       o[e] = r;
     }
   }
@@ -346,10 +357,11 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
 // ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
 // sets *handled when N has a compiled shape.
 int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, bool* handled) {
+             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool* handled) {
   *handled = false;
-  if (c->ntt_generic || c->log_n < 12 || c->log_n > 16) return HE_OK;
+  if (!ks_fusable(c)) return HE_OK;
   KsFusedArgs a;
+  a.gal = gal;
   a.d = d;
   a.d2c = d2c;
   a.ext = ext;
@@ -401,10 +413,11 @@ namespace he {
 // limbs must already be in coefficient form.  Sets *handled when N has
 // compiled shapes (the same ones as the NTT and ModUp).
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-             CtBatch out, uint32_t level, uint32_t count, bool* handled) {
+             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
   *handled = false;
-  if (c->ntt_generic || c->log_n < 12 || c->log_n > 16) return HE_OK;
+  if (!ks_fusable(c)) return HE_OK;
   MdArgs a;
+  a.add_gal = add_gal;
   a.acc = acc;
   a.acc_stride = acc_stride;
   a.conv = conv;

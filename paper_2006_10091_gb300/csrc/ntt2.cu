@@ -27,6 +27,7 @@ struct Ntt2Args {
   uint32_t nl, limb0, level, L;
   uint32_t np, pb;  // polynomials; polynomials per CTA (same limb, so same twiddles)
   uint32_t skip_alpha, skip_beta;
+  uint64_t gal;  // first pass: load the source through the automorphism X -> X^gal (0: none)
   const ulonglong2* tw;
   const PrimeDev* primes;
   int last;
@@ -86,7 +87,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Ar
       uint32_t k, x;
       if (COL) { x = idx >> LOG_K; k = idx & (S::K - 1); }
       else { k = idx >> LOG_M; x = idx & (S::M - 1); }
-      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
+      const uint32_t e = S::gidx(tile, k, x);
+      sm[idx + (idx >> 3)] = __ldg(src + (a.gal ? automorph_src(e, a.gal, LOG_N) : e));
     }
     __syncthreads();
     if (!INV && pr.q < (1ull << 58)) pass_body<INV, true, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
@@ -96,9 +98,10 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Ar
 
 template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL>
 static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t* dst, uint64_t src_stride,
-                   bool last) {
+                   bool last, uint64_t gal = 0) {
   using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
   Ntt2Args a;
+  a.gal = gal;
   a.src = src;
   a.dst = dst;
   a.src_stride = src_stride;
@@ -153,7 +156,7 @@ static int run2(he_ctx* c, const PolyBatch& b) {
     const int rc = launch2<false, LOG_N, M1, K1, true>(c, b, b.src, b.dst, b.src_stride, false);
     return rc != HE_OK ? rc : launch2<false, LOG_N, M2, K2, false>(c, b, b.dst, b.dst, b.dst_stride, true);
   }
-  const int rc = launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false);
+  const int rc = launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
   return rc != HE_OK ? rc : launch2<true, LOG_N, M1, K1, true>(c, b, b.dst, b.dst, b.dst_stride, true);
 }
 

@@ -16,9 +16,9 @@
 
 namespace he {
 int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, bool* handled);
+             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool* handled);
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-             CtBatch out, uint32_t level, uint32_t count, bool* handled);
+             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -109,7 +109,8 @@ static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, co
 }
 
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
-                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar) {
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal) {
+  if (gal && !ks_fusable(c)) return fail(HE_EINVAL, "keyswitch_batch: automorphism needs the fused kernels");
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
   const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
   uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
@@ -118,16 +119,20 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
   // 1. coefficient form
-  HE_TRY(ntt_inverse(c, pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level)));
+  {
+    PolyBatch b = pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level);
+    b.gal = gal;
+    HE_TRY(ntt_inverse(c, b));
+  }
   // 2-3. fused ModUp + NTT + inner product where N has compiled shapes
   bool fused = false;
-  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, &fused));
+  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, gal, &fused));
   if (!fused) HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
   // 4. ModDown
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
                            (size_t)nt * n, count * 2, alpha, level, level)));
   bool md_done = false;
-  HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, out, level, count, &md_done));
+  HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, &md_done));
   if (md_done) return HE_OK;
   {
     ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
@@ -198,6 +203,14 @@ int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t 
   const uint32_t n = c->n;
   const uint64_t* key = galois_key(c, gal);
   if (!key) return fail(HE_ENOKEY, "no Galois key for this rotation");
+  // With the fused kernels the automorphism is applied as the key switch
+  // reads its input and addend, unless the output overlaps the input.
+  const char* a_lo = (const char*)A.base;
+  const char* a_hi = a_lo + sizeof(uint64_t) * ((size_t)(count - 1) * A.stride + (size_t)2 * A.cap * n);
+  const char* o_lo = (const char*)out.base;
+  const char* o_hi = o_lo + sizeof(uint64_t) * ((size_t)(count - 1) * out.stride + (size_t)2 * out.cap * n);
+  if (ks_fusable(c) && (o_hi <= a_lo || a_hi <= o_lo))
+    return keyswitch_batch(c, A.base + (size_t)A.cap * n, A.stride, level, count, key, A, 1, out, ar, gal);
   uint64_t* t = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!t) return fail(HE_ENOMEM, "rotation scratch too small");
   CtBatch T{t, (size_t)2 * level * n, level, 0};

@@ -202,7 +202,7 @@ int build_tables(he_ctx* c) {
 
   // ModUp constants per (level, digit): digit D_j = [j*alpha, min((j+1)*alpha, level)).
   // Table: [cnt] Shoup pairs (inv_i = (Q_j/q_i)^-1 mod q_i), then [cnt][np] values
-  // (Q_j/q_i) mod p for every prime index p.
+  // (Q_j/q_i) mod p for every prime index p, then their [cnt][np] Shoup companions.
   {
     std::vector<uint64_t> words;
     c->modup.assign(L + 1, {});
@@ -222,6 +222,7 @@ int build_tables(he_ctx* c) {
           words.push_back(inv);
           words.push_back(h_shoup(inv, qi));
         }
+        const size_t mat0 = words.size();
         for (uint32_t a = 0; a < mc.cnt; ++a) {
           for (int p = 0; p < np; ++p) {
             const uint64_t m = c->q[p];
@@ -231,6 +232,8 @@ int build_tables(he_ctx* c) {
             words.push_back(prod);
           }
         }
+        for (uint32_t a = 0; a < mc.cnt; ++a)
+          for (int p = 0; p < np; ++p) words.push_back(h_shoup(words[mat0 + (size_t)a * np + p], c->q[p]));
         c->modup[lv].push_back(mc);
       }
     }
@@ -240,7 +243,8 @@ int build_tables(he_ctx* c) {
 
   // ModDown constants: [alpha] Shoup pairs of (P/p_k)^-1 mod p_k; [alpha][L] values
   // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2 reduced:
-  // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds).
+  // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds); then the
+  // [alpha][L] Shoup companions of the (P/p_k) mod q_t values.
   {
     std::vector<uint64_t> words;
     for (int k = 0; k < alpha; ++k) {
@@ -278,6 +282,8 @@ int build_tables(he_ctx* c) {
     };
     for (int k = 0; k < alpha; ++k) words.push_back(half_P(c->q[L + k]));
     for (int t = 0; t < L; ++t) words.push_back(half_P(c->q[t]));
+    for (int k = 0; k < alpha; ++k)
+      for (int t = 0; t < L; ++t) words.push_back(h_shoup(words[2 * alpha + (size_t)k * L + t], c->q[t]));
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }

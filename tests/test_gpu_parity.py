@@ -473,6 +473,17 @@ def test_fused_rotation_and_mul_bit_exact(wide, he):
     assert_same_residues(out, wide.o.mul_relin_rescale(oa, ob), he, wide.g)
 
 
+def test_fused_rotation_in_place(wide, he):
+    """The fused rotation reads its input through the automorphism while it
+    writes the output; an output that overlaps the input takes the path with
+    a separate automorphism and gives the same residues."""
+    m = workloads.int_poly(63, wide.n, 1 << 36)
+    ga, oa = wide.gpu_enc(m, 5, 63), wide.orc_enc(m, 5, 63)
+    want = wide.o.rotate(oa, 5)
+    he.he_rotate(wide.g, ga, 5, ga)
+    assert_same_residues(ga, want, he, wide.g)
+
+
 def test_fused_single_special_prime_n13(he):
     p = Pair(13, 4, 40, 1, 60, 2.0 ** 40, seed=9, rots=[1])
     m1, m2 = workloads.int_poly(71, p.n, 1 << 30), workloads.int_poly(72, p.n, 1 << 30)
