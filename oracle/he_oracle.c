@@ -902,27 +902,36 @@ void orc_modup_coef(orc_ctx* c, const uint64_t* xcoef, int level, int j, int tp,
   modup_limb(c, xcoef, level, j, tp, y);
 }
 
-/* ModDown conversion [ext]: BConv from the special basis P to prime q_t of
- * coefficient residues ycoefP [alpha][N]:
- *   conv = sum_k [y_k * (P/p_k)^-1]_{p_k} * (P/p_k mod q_t)  mod q_t. */
+static uint64_t bn_mod_small(const bn* a, uint64_t m) {
+  u128 r = 0;
+  for (int i = BN_W - 1; i >= 0; i--) r = ((r << 64) | a->w[i]) % m;
+  return (uint64_t)r;
+}
+
+/* ModDown conversion [ext]: the exact basis conversion from the special basis
+ * P to prime q_t of coefficient residues ycoefP [alpha][N]: the integer
+ * Y in [0, P) with Y = y_k mod p_k for every k (CRT by Garner's mixed-radix
+ * digits), reduced mod q_t.  Exact, so that the division by P that follows
+ * rounds every coefficient (with one special prime Y = y_0). */
 static void moddown_conv(orc_ctx* c, const uint64_t* ycoefP, int t, uint64_t* out) {
   uint32_t n = c->n;
-  uint64_t qt = c->q[t];
-  for (uint32_t i = 0; i < n; i++) out[i] = 0;
-  for (int k = 0; k < c->alpha; k++) {
-    uint64_t pk = c->q[c->L + k];
-    uint64_t phat_k = 1 % pk, phat_t = 1 % qt;
-    for (int k2 = 0; k2 < c->alpha; k2++) {
-      if (k2 == k) continue;
-      phat_k = mulmod(phat_k, c->q[c->L + k2] % pk, pk);
-      phat_t = mulmod(phat_t, c->q[c->L + k2] % qt, qt);
+  int a = c->alpha;
+  const uint64_t* ps = c->q + c->L;
+  for (uint32_t i = 0; i < n; i++) {
+    uint64_t d[ORC_MAX_PRIMES];
+    for (int k = 0; k < a; k++) {
+      /* d_k = (y_k - (d_0 + d_1 p_0 + ...)) / (p_0 ... p_{k-1}) mod p_k */
+      uint64_t pk = ps[k], acc = 0, prod = 1 % pk;
+      for (int k2 = 0; k2 < k; k2++) {
+        acc = addmod(acc, mulmod(d[k2] % pk, prod, pk), pk);
+        prod = mulmod(prod, ps[k2] % pk, pk);
+      }
+      d[k] = mulmod(submod(ycoefP[(size_t)k * n + i] % pk, acc, pk), invmod(prod, pk), pk);
     }
-    uint64_t inv = invmod(phat_k, pk);
-    const uint64_t* y = POLY(ycoefP, k, n);
-    for (uint32_t i = 0; i < n; i++) {
-      uint64_t u = mulmod(y[i], inv, pk);
-      out[i] = addmod(out[i], mulmod(u % qt, phat_t, qt), qt);
-    }
+    bn y;
+    memset(&y, 0, sizeof y);
+    for (int k = a - 1; k >= 0; k--) bn_mul_small_add(&y, ps[k], d[k]); /* Horner */
+    out[i] = bn_mod_small(&y, c->q[t]);
   }
 }
 
@@ -944,9 +953,11 @@ static const uint64_t* find_key(orc_ctx* c, int key_id) {
  * rounding"; flooring would leave a -1/2 bias on every coefficient of both
  * parts, which concentrates in the lowest-frequency slot):
  *   y = INTT_P(acc_P) + h (every coefficient),  h = (P-1)/2,
- *   out_t = (acc_t - NTT_t(BConv_{P->q_t}(y) - h)) * P^-1  mod q_t,
- * i.e. round(acc / P) minus the conversion's small multiple of P (for one
- * special prime, BConv(y) - h is the centered residue of acc mod P). */
+ *   out_t = (acc_t - NTT_t(Conv_{P->q_t}(y) - h)) * P^-1  mod q_t,
+ * with the exact conversion Conv (the lift of y to [0, P)), i.e.
+ * out = round(acc / P): Conv(y) - h is the centered residue of acc mod P.  An
+ * approximate conversion would add v P, 0 <= v < alpha, and so a one-sided
+ * error of -v on every coefficient, the same drift as flooring. */
 static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key,
                       uint64_t* k0, uint64_t* k1) {
   uint32_t n = c->n;

@@ -130,10 +130,16 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
     uint64_t u[HE_MAX_DIGIT];
     const uint64_t* hP = md + 2 * alpha + (size_t)alpha * L + 2 * L;
     const uint64_t* hQ = hP + alpha;
+    const uint64_t* wlo = hQ + L + (size_t)alpha * L;
+    const uint64_t* p_mod_q = wlo + alpha;
+    // exact conversion: v = floor(sum_a u_a / p_a) multiples of P come off
+    uint64_t fs = 0;
+    uint32_t v = 0;
     for (uint32_t a = 0; a < alpha; ++a) {
-      const uint64_t pa = primes[L + a].q;
-      const uint64_t y = add_mod(acc[(size_t)i * acc_stride + ((size_t)p * nt + level + a) * n + k], hP[a], pa);
-      u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], pa);
+      const PrimeDev& pp = primes[L + a];
+      const uint64_t y = add_mod(acc[(size_t)i * acc_stride + ((size_t)p * nt + level + a) * n + k], hP[a], pp.q);
+      u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], pp.q);
+      if (alpha > 1) frac_acc(u[a], pp.one_sh, wlo[a], &fs, &v);
     }
     uint64_t* out = conv + (size_t)i * conv_stride + (size_t)p * level * n;
     for (uint32_t t = 0; t < level; ++t) {
@@ -141,6 +147,7 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
       uint64_t s = 0;
       for (uint32_t a = 0; a < alpha; ++a)
         s = add_mod(s, mul_mod(reduce64(u[a], pr), mat[(size_t)a * L + t], pr), pr.q);
+      if (v) s = sub_mod(s, reduce64((uint64_t)v * p_mod_q[t], pr), pr.q);
       out[(size_t)t * n + k] = sub_mod(s, hQ[t], pr.q);
     }
   }

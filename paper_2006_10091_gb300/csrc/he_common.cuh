@@ -72,6 +72,18 @@ __device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) 
   return a >= b ? a - b : a + q - b;
 }
 
+// One term of v = floor(sum_k u_k / p_k) for u_k < p_k: u_k 2^64 / p_k in
+// 64.64 fixed point from floor(2^128 / p_k) = (one_sh, wlo), at most 2 units
+// of 2^-64 below the exact value; the fractional parts accumulate in *s and
+// their carries (the integer part) in *v.
+__device__ __forceinline__ void frac_acc(uint64_t u, uint64_t one_sh, uint64_t wlo, uint64_t* s, uint32_t* v) {
+  const uint64_t t0 = u * one_sh;
+  const uint64_t t = t0 + __umul64hi(u, wlo);
+  *v += t < t0;
+  *s += t;
+  *v += *s < t;
+}
+
 // Signed integer to residue.
 __device__ __forceinline__ uint64_t from_signed(int64_t x, const PrimeDev& p) {
   if (x >= 0) return reduce64((uint64_t)x, p);

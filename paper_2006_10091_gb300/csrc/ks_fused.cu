@@ -12,10 +12,15 @@
 //    row pass of that digit's tile (or, on the digit's own limb, reads the
 //    input as it is) and adds its products with the two key polynomials; the
 //    transformed digits are never written.
+#include <algorithm>
+
 #include "he_ops.h"
 #include "ntt2.cuh"
 
 namespace he {
+
+// Dynamic shared memory the all-targets conversion kernels may take.
+constexpr size_t kModupAllSmem = 160 * 1024;
 
 struct KsFusedArgs {
   const uint64_t* d;     // input, evaluation form: count x [level][N] at d_stride
@@ -90,6 +95,73 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFus
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
     const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
     out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
+  }
+}
+
+// The same column pass for every target limb of one digit and tile in one
+// CTA: the digit's limbs are read once and their products by
+// (Q_j/q_i)^-1 mod q_i (or, for a one-limb digit, the limb itself) are kept
+// in shared memory for all targets.  Grid: count * beta * TILES; dynamic
+// shared memory holds cnt_max * TILE more words.
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(KsFusedArgs a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
+  constexpr uint32_t N = 1u << LOG_N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint64_t* wv = sm + S::TILE + S::TILE / 8;  // [cnt][TILE]
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t j = b % a.beta, i = b / a.beta;
+  const uint32_t lo = a.lo[j], cnt = a.cnt[j];
+  const uint64_t* tab = a.consts + a.off[j];
+  const uint64_t* mat = tab + 2 * cnt;
+  const uint64_t* mat_sh = mat + (size_t)cnt * a.np;
+  const uint64_t* x = a.d2c + (size_t)i * a.level * N;
+  for (uint32_t u = 0; u < cnt; ++u) {
+    const uint64_t qa = a.primes[lo + u].q;
+#pragma unroll 4
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
+      const uint64_t xv = __ldg(x + (size_t)(lo + u) * N + e);
+      wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], qa);
+    }
+  }
+  for (uint32_t t = 0; t < a.nt; ++t) {
+    if (t >= lo && t < lo + cnt) continue;  // the digit's own limbs are used as they are
+    const uint32_t prime = ks_prime(t, a.level, a.L);
+    const PrimeDev pr = a.primes[prime];
+    const uint64_t q2 = pr.q + pr.q;
+    // the previous target's rounds ended with a barrier, and its write-out
+    // reads only the words each thread rewrites below
+    stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
+#pragma unroll 2
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      uint64_t y;
+      if (cnt == 1) {
+        y = reduce64(wv[idx], pr);  // Q_j / q_lo = 1
+      } else {  // Shoup products by (Q_j/q_i) mod q_t, kept in [0, 2q)
+        y = 0;
+        for (uint32_t u = 0; u < cnt; ++u) {
+          y += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.np + prime],
+                              mat_sh[(size_t)u * a.np + prime], pr.q);
+          y = y >= q2 ? y - q2 : y;
+        }
+        y = y >= pr.q ? y - pr.q : y;
+      }
+      sm[idx + (idx >> 3)] = y;
+    }
+    __syncthreads();
+    uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+    if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
+#pragma unroll 4
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
+      out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
+    }
   }
 }
 
@@ -193,6 +265,9 @@ struct MdArgs {
   const uint64_t* md;   // ModDown tables (params.cu)
 };
 
+// Grid: count * 2 * TILES; the conversion's per-special-prime terms and the
+// multiple v of P are computed once per element and kept in shared memory
+// ([alpha][TILE] words and [TILE] counts) for all level target limbs.
 template <int LOG_N, int LOG_M, int LOG_K>
 __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs a) {
   using S = Shape<LOG_N, LOG_M, LOG_K, true>;
@@ -200,32 +275,48 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint64_t* wv = sm + S::TILE + S::TILE / 8;                          // [alpha][TILE]
+  uint32_t* vv = reinterpret_cast<uint32_t*>(wv + (size_t)a.alpha * S::TILE);  // [TILE]
   uint32_t b = blockIdx.x;
   const uint32_t tile = b % S::TILES;
   b /= S::TILES;
-  const uint32_t t = b % a.level, i = b / a.level;
-  const PrimeDev pr = a.primes[t];
-  const uint64_t q2 = pr.q + pr.q;
+  const uint32_t p = b % 2, i = b / 2;
   const uint64_t* mat = a.md + 2 * a.alpha;
   const uint64_t* hP = mat + (size_t)a.alpha * a.L + 2 * a.L;
-  const uint64_t hQ = hP[a.alpha + t];
   const uint64_t* mat_sh = hP + a.alpha + a.L;
-  stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
-  for (uint32_t p = 0; p < 2; ++p) {
-    const uint64_t* yP = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + a.level) * N;
+  const uint64_t* wlo = mat_sh + (size_t)a.alpha * a.L;
+  const uint64_t* yP = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + a.level) * N;
+  // exact conversion: sum_u w_u (P/p_u) - v P, w_u = [y_u (P/p_u)^-1]_{p_u},
+  // v = floor(sum_u w_u / p_u)
+#pragma unroll 2
+  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+    const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
+    uint64_t fs = 0;
+    uint32_t v = 0;
+    for (uint32_t u = 0; u < a.alpha; ++u) {
+      const PrimeDev& pp = a.primes[a.L + u];
+      const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pp.q);
+      const uint64_t w = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
+      wv[(size_t)u * S::TILE + idx] = w;
+      if (a.alpha > 1) frac_acc(w, pp.one_sh, wlo[u], &fs, &v);
+    }
+    vv[idx] = v;
+  }
+  for (uint32_t t = 0; t < a.level; ++t) {
+    const PrimeDev pr = a.primes[t];
+    const uint64_t q2 = pr.q + pr.q, hQ = hP[a.alpha + t], p_mod_q = wlo[a.alpha + t];
+    stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
 #pragma unroll 2
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
-      const uint32_t e = S::gidx(tile, k, xx);
       uint64_t acc = 0;  // Shoup products by (P/p_u) mod q_t, kept in [0, 2q)
       for (uint32_t u = 0; u < a.alpha; ++u) {
-        const uint64_t pu = a.primes[a.L + u].q;
-        const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pu);
-        const uint64_t v = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pu);
-        acc += mul_shoup_lazy(v, mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t], pr.q);
+        acc += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t],
+                              pr.q);
         acc = acc >= q2 ? acc - q2 : acc;
       }
       acc = acc >= pr.q ? acc - pr.q : acc;
+      const uint32_t v = vv[idx];
+      if (v) acc = sub_mod(acc, reduce64((uint64_t)v * p_mod_q, pr), pr.q);
       sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
     }
     __syncthreads();
@@ -237,12 +328,11 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
       const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
       out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
     }
-    // the next part rewrites only the words each thread has just read
   }
 }
 
 template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_row_combine(MdArgs a) {
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(MdArgs a) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
   constexpr uint32_t N = 1u << LOG_N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -258,6 +348,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_row_combine(MdA
   const uint64_t* pinv = a.md + 2 * a.alpha + (size_t)a.alpha * a.L;
   const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
   stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)t * N, tile);
+  constexpr int PER = S::TILE / S::T;
   for (uint32_t p = 0; p < 2; ++p) {
     const uint64_t* src = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
 #pragma unroll 4
@@ -265,21 +356,31 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_row_combine(MdA
       const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
       sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
     }
-    __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    // the epilogue's operands are loaded before the transform so that their
+    // latency overlaps its rounds
     const uint64_t* accq = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + t) * N;
     const bool add = a.has_add == 2 || (a.has_add == 1 && p == 0);
     const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
+    uint64_t av[PER], dv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+      av[u] = __ldg(accq + e);
+      dv[u] = add ? __ldg(ad + (a.add_gal ? automorph_src(e, a.add_gal, LOG_N) : e)) : 0;
+    }
+    __syncthreads();
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
     uint64_t* o = cpoly(a.out, i, p, t, N);
-#pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
-      const uint32_t e = S::gidx(tile, k, x);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       const uint64_t v = sm[idx + (idx >> 3)];
       const uint64_t cv = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
-      uint64_t r = mul_shoup(sub_mod(__ldg(accq + e), cv, q), w, wsh, q);
-      if (add) r = add_mod(r, ad[a.add_gal ? automorph_src(e, a.add_gal, LOG_N) : e], q);
+      uint64_t r = mul_shoup(sub_mod(av[u], cv, q), w, wsh, q);
+      if (add) r = add_mod(r, dv[u], q);
       o[e] = r;
     }
   }
@@ -289,18 +390,21 @@ template <int LOG_N, int M1, int K1, int M2, int K2>
 static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count) {
   using SC = Shape<LOG_N, M1, K1, true>;
   using SR = Shape<LOG_N, M2, K2, false>;
-  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
+  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
+                     (sizeof(uint64_t) * a.alpha + sizeof(uint32_t)) * SC::TILE;
   const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
+  if (smc > kModupAllSmem) return fail(HE_EINVAL, "ModDown tile too large for shared memory");
   static unsigned long long attr_set = 0;
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kModupAllSmem));
     HE_CUDA(cudaFuncSetAttribute(md_row_combine<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     attr_set |= 1ull << c->device;
   }
   const double n = (double)(1u << LOG_N);
   const double polys = 2.0 * count * a.level;  // transformed limbs
   {
-    const size_t blocks = (size_t)count * a.level * SC::TILES;
+    const size_t blocks = (size_t)count * 2 * SC::TILES;
     ProfScope prof(c, "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha), n * 8 * (2.0 * count * a.alpha + polys));
     md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
@@ -324,6 +428,8 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   static unsigned long long attr_set = 0;
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
     HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    HE_CUDA(cudaFuncSetAttribute(ks_modup_col_all<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kModupAllSmem));
     HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     attr_set |= 1ull << c->device;
@@ -337,10 +443,18 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
     if (a.cnt[j] > 1) conv_products += (double)(a.nt - a.cnt[j]) * a.cnt[j];
   // work = modular products: butterflies, conversion products, inner-product products
   {
-    const size_t blocks = (size_t)count * a.beta * a.nt * SC::TILES;
     ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n),
                    count * n * 8 * (a.level + conv));
-    ks_modup_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
+    uint32_t cnt_max = 0;
+    for (uint32_t j = 0; j < a.beta; ++j) cnt_max = std::max(cnt_max, a.cnt[j]);
+    const size_t sma = smc + sizeof(uint64_t) * (size_t)cnt_max * SC::TILE;
+    if (sma <= kModupAllSmem) {  // one CTA per digit and tile, all targets
+      const size_t blocks = (size_t)count * a.beta * SC::TILES;
+      ks_modup_col_all<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, sma, c->stream>>>(a);
+    } else {
+      const size_t blocks = (size_t)count * a.beta * a.nt * SC::TILES;
+      ks_modup_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
+    }
   }
   HE_CUDA(cudaGetLastError());
   {

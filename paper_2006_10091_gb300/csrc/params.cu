@@ -244,7 +244,10 @@ int build_tables(he_ctx* c) {
   // ModDown constants: [alpha] Shoup pairs of (P/p_k)^-1 mod p_k; [alpha][L] values
   // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2 reduced:
   // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds); then the
-  // [alpha][L] Shoup companions of the (P/p_k) mod q_t values.
+  // [alpha][L] Shoup companions of the (P/p_k) mod q_t values; [alpha] low
+  // words of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t.
+  // The last two make the conversion exact: v = floor(sum_k u_k / p_k) is
+  // evaluated in 64.64 fixed point and v P subtracted.
   {
     std::vector<uint64_t> words;
     for (int k = 0; k < alpha; ++k) {
@@ -284,6 +287,8 @@ int build_tables(he_ctx* c) {
     for (int t = 0; t < L; ++t) words.push_back(half_P(c->q[t]));
     for (int k = 0; k < alpha; ++k)
       for (int t = 0; t < L; ++t) words.push_back(h_shoup(words[2 * alpha + (size_t)k * L + t], c->q[t]));
+    for (int k = 0; k < alpha; ++k) words.push_back((uint64_t)(~(unsigned __int128)0 / c->q[L + k]));
+    for (int t = 0; t < L; ++t) words.push_back(c->P_mod_q[t]);
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }

@@ -173,16 +173,22 @@ def test_modup_is_x_plus_small_multiple_of_qj(tiny):
             assert len(us) == 1
 
 
-def test_moddown_conversion_is_y_plus_small_multiple_of_p(tiny):
+def test_moddown_conversion_is_exact(tiny):
+    """The P -> q_t conversion of ModDown is the exact lift to [0, P): the
+    CRT integer of the special residues, reduced mod q_t (no multiple of P),
+    including the residues that lift next to 0 and next to P."""
     o = tiny
     rng = np.random.default_rng(3)
-    P = o.primes[6] * o.primes[7]
-    y = np.stack([rng.integers(0, q, o.n, dtype=np.uint64) for q in o.primes[6:8]])
+    ps = o.primes[6:8]
+    P = ps[0] * ps[1]
+    ints = [int(v) for v in rng.integers(0, 2 ** 62, o.n - 4)] + [0, 1, P - 2, P - 1]
+    ints = [v % P for v in ints]
+    y = np.array([[v % p for v in ints] for p in ps], dtype=np.uint64)
     for t in range(6):
         conv = o.moddown_conv(y, t)
         for k in range(o.n):
-            yv = crt(y[:, k], o.primes[6:8])
-            assert any((yv + u * P) % o.primes[t] == int(conv[k]) for u in range(2))
+            assert crt(y[:, k], ps) == ints[k]
+            assert int(conv[k]) == ints[k] % o.primes[t]
 
 
 # ------------------------------------------------------------------ rescale
@@ -378,8 +384,8 @@ def test_keyswitch_equals_big_integer_definition(tiny):
     definition: per digit the approximate ModUp y_j = sum_i [x_i (Q_j/q_i)^-1]_{q_i}
     (Q_j/q_i) (an integer equal to [x]_{Q_j} + u Q_j), the products with the key
     over the integers mod X^N + 1, then the division by P with rounding:
-    out = floor((acc + h - conv) / P) with h = (P-1)/2 and conv the same
-    approximate conversion of [acc + h]_P.  Must equal the oracle's residues."""
+    out = floor((acc + h) / P) = round(acc / P), h = (P-1)/2.  Must equal the
+    oracle's residues."""
     o = tiny
     level, n, L, alpha = 5, o.n, o.L, o.alpha
     q = o.primes
@@ -409,13 +415,7 @@ def test_keyswitch_equals_big_integer_definition(tiny):
     for p, got in enumerate((k0, k1)):
         gotc = to_coef(o, got, level)
         for c in range(n):
-            v = acc[p][c] + h
-            conv = 0
-            for k in range(alpha):
-                pk = q[L + k]
-                phat = P // pk
-                conv += ((v % pk) * pow(phat, -1, pk) % pk) * phat
-            out = (v - conv) // P
+            out = (acc[p][c] + h) // P
             for t in range(level):
                 assert int(gotc[t][c]) == out % q[t], (p, c, t)
 
