@@ -117,6 +117,8 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->d_modup = base->d_modup;
   v->d_moddown = base->d_moddown;
   v->d_rescale = base->d_rescale;
+  v->d_rescale_md = base->d_rescale_md;
+  v->rescale_md_words = base->rescale_md_words;
   v->d_garner = base->d_garner;
   v->chunk_bytes = base->chunk_bytes;
   v->lr_chunk = base->lr_chunk;
@@ -152,6 +154,7 @@ static void destroy(he_ctx* c) {
   cudaFree(c->d_modup);
   cudaFree(c->d_moddown);
   cudaFree(c->d_rescale);
+  cudaFree(c->d_rescale_md);
   cudaFree(c->d_garner);
   cudaFree(c->d_s);
   cudaFree(c->d_pk);

@@ -72,8 +72,8 @@ struct he_ctx {
 
   // device tables
   PrimeDev* d_primes = nullptr;  // [np]
-  uint64_t* d_tw = nullptr;      // [np][N] psi^brv(m), then [np][N] Shoup companions
-  uint64_t* d_itw = nullptr;     // [np][N] psi^-brv(m), then companions
+  uint64_t* d_tw = nullptr;      // [np][N] pairs (psi^brv(m), its Shoup companion)
+  uint64_t* d_itw = nullptr;     // [np][N] pairs (psi^-brv(m), its Shoup companion)
   uint64_t* d_two64 = nullptr;   // [np] 2^64 mod q
   uint64_t* d_gauss = nullptr;   // Gaussian CDT
   int gK = 0;
@@ -85,6 +85,8 @@ struct he_ctx {
   uint64_t* d_moddown = nullptr;
   // Rescale: q_{l-1}^-1 mod q_t Shoup pairs [L][L][2]
   uint64_t* d_rescale = nullptr;
+  uint64_t* d_rescale_md = nullptr;  // per dropped limb l: the ModDown tables with q_l as the one special prime
+  size_t rescale_md_words = 0;       // words per l
   // Garner (decryption CRT): [L] Shoup pairs of (q_0..q_{i-1})^-1 mod q_i, then
   // [L][L] prefix products (q_0..q_{i'-1}) mod q_i
   uint64_t* d_garner = nullptr;

@@ -34,6 +34,8 @@ struct KsFusedArgs {
   uint32_t level, alpha, beta, L, np, nt;
   const PrimeDev* primes;
   const ulonglong2* tw;
+  const ulonglong2* itw;   // inverse twiddles
+  int half;                // d2c holds the inverse transform's row pass only (ks_modup_col_all finishes it)
   const uint64_t* consts;  // ModUp constant tables
   uint32_t lo[HE_MAX_PRIMES], cnt[HE_MAX_PRIMES];
   uint64_t off[HE_MAX_PRIMES];
@@ -121,13 +123,31 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
   const uint64_t* mat_sh = mat + (size_t)cnt * a.np;
   const uint64_t* x = a.d2c + (size_t)i * a.level * N;
   for (uint32_t u = 0; u < cnt; ++u) {
-    const uint64_t qa = a.primes[lo + u].q;
+    const PrimeDev pa = a.primes[lo + u];
+    if (a.half) {
+      // the inverse transform's column pass on this tile, then the scaling by N^-1
+      stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.itw + (size_t)(lo + u) * N, tile);
+#pragma unroll 4
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+        const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
+        sm[idx + (idx >> 3)] = __ldg(x + (size_t)(lo + u) * N + e);
+      }
+      __syncthreads();
+      run_rounds<true, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pa.q);
+    }
 #pragma unroll 4
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
-      const uint64_t xv = __ldg(x + (size_t)(lo + u) * N + e);
-      wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], qa);
+      uint64_t xv;
+      if (a.half) {
+        xv = mul_shoup(sm[idx + (idx >> 3)], pa.n_inv, pa.n_inv_sh, pa.q);
+      } else {
+        const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
+        xv = __ldg(x + (size_t)(lo + u) * N + e);
+      }
+      wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], pa.q);
     }
+    // the next limb's staging overwrites stw and sm: wait for every thread
+    __syncthreads();
   }
   for (uint32_t t = 0; t < a.nt; ++t) {
     if (t >= lo && t < lo + cnt) continue;  // the digit's own limbs are used as they are
@@ -253,13 +273,17 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
 // A CTA handles both parts of one ciphertext for one limb and tile, so the
 // staged twiddles serve two transforms.
 struct MdArgs {
-  const uint64_t* acc;  // count x [2][nt][N]: evaluation form on limbs < level, coefficient form on the P limbs
-  uint64_t acc_stride;
+  // The P part (coefficient form): ciphertext i, part p, special prime u at
+  // yP + i*yp_stride + p*yp_pstride + u*N.
+  const uint64_t* yP;
+  uint64_t yp_stride, yp_pstride;
+  CtBatch accq;         // the Q part (evaluation form), limbs 0 .. level-1
   uint64_t* conv;       // count x [2][level][N]: column-pass outputs
   CtBatch add, out;
   int has_add;          // 0 none, 1 part 0 only, 2 both parts
   uint64_t add_gal;     // the addend is read through the automorphism X -> X^add_gal (0: none)
-  uint32_t level, alpha, L, nt;
+  uint32_t level, alpha, L;
+  uint32_t sp0;         // prime index of the first special prime (L; l for a rescale by q_l)
   const PrimeDev* primes;
   const ulonglong2* tw;
   const uint64_t* md;   // ModDown tables (params.cu)
@@ -285,7 +309,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   const uint64_t* hP = mat + (size_t)a.alpha * a.L + 2 * a.L;
   const uint64_t* mat_sh = hP + a.alpha + a.L;
   const uint64_t* wlo = mat_sh + (size_t)a.alpha * a.L;
-  const uint64_t* yP = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + a.level) * N;
+  const uint64_t* yP = a.yP + (size_t)i * a.yp_stride + (size_t)p * a.yp_pstride;
   // exact conversion: sum_u w_u (P/p_u) - v P, w_u = [y_u (P/p_u)^-1]_{p_u},
   // v = floor(sum_u w_u / p_u)
 #pragma unroll 2
@@ -294,7 +318,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     uint64_t fs = 0;
     uint32_t v = 0;
     for (uint32_t u = 0; u < a.alpha; ++u) {
-      const PrimeDev& pp = a.primes[a.L + u];
+      const PrimeDev& pp = a.primes[a.sp0 + u];
       const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pp.q);
       const uint64_t w = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
       wv[(size_t)u * S::TILE + idx] = w;
@@ -304,7 +328,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   }
   for (uint32_t t = 0; t < a.level; ++t) {
     const PrimeDev pr = a.primes[t];
-    const uint64_t q2 = pr.q + pr.q, hQ = hP[a.alpha + t], p_mod_q = wlo[a.alpha + t];
+    const uint64_t q2 = pr.q + pr.q, hQ = hP[a.alpha + t];
+    const uint64_t* vP = wlo + a.alpha + a.L + (size_t)t * 8;  // v P mod q_t, v < 8
     stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
 #pragma unroll 2
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
@@ -315,8 +340,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
         acc = acc >= q2 ? acc - q2 : acc;
       }
       acc = acc >= pr.q ? acc - pr.q : acc;
-      const uint32_t v = vv[idx];
-      if (v) acc = sub_mod(acc, reduce64((uint64_t)v * p_mod_q, pr), pr.q);
+      acc = sub_mod(acc, vP[vv[idx]], pr.q);
       sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
     }
     __syncthreads();
@@ -358,7 +382,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
     }
     // the epilogue's operands are loaded before the transform so that their
     // latency overlaps its rounds
-    const uint64_t* accq = a.acc + (size_t)i * a.acc_stride + ((size_t)p * a.nt + t) * N;
+    const uint64_t* accq = cpoly(a.accq, i, p, t, N);
     const bool add = a.has_add == 2 || (a.has_add == 1 && p == 0);
     const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
     uint64_t av[PER], dv[PER];
@@ -403,20 +427,34 @@ static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count) {
   }
   const double n = (double)(1u << LOG_N);
   const double polys = 2.0 * count * a.level;  // transformed limbs
+  const bool rescale = a.sp0 != a.L;
   {
     const size_t blocks = (size_t)count * 2 * SC::TILES;
-    ProfScope prof(c, "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha), n * 8 * (2.0 * count * a.alpha + polys));
+    ProfScope prof(c, rescale ? "rescale_ntt" : "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha),
+                   n * 8 * (2.0 * count * a.alpha + polys));
     md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
   {
     const size_t blocks = (size_t)count * a.level * SR::TILES;
     const double addw = a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
-    ProfScope prof(c, "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n), n * 8 * (3.0 * polys + addw));
+    ProfScope prof(c, rescale ? "rescale_ntt_final" : "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n),
+                   n * 8 * (3.0 * polys + addw));
     md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
+}
+
+// Dynamic shared memory of ks_modup_col_all for these digits.
+template <int LOG_N, int M1, int K1>
+static size_t ks_all_smem(const he_ctx* c, uint32_t beta, const uint32_t* cnt) {
+  using SC = Shape<LOG_N, M1, K1, true>;
+  uint32_t cnt_max = 0;
+  for (uint32_t j = 0; j < beta; ++j) cnt_max = std::max(cnt_max, cnt[j]);
+  (void)c;
+  return sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
+         sizeof(uint64_t) * (size_t)cnt_max * SC::TILE;
 }
 
 template <int LOG_N, int M1, int K1, int M2, int K2>
@@ -443,11 +481,12 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
     if (a.cnt[j] > 1) conv_products += (double)(a.nt - a.cnt[j]) * a.cnt[j];
   // work = modular products: butterflies, conversion products, inner-product products
   {
-    ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n),
+    // with a half-transformed input the kernel also runs the inverse column pass of the level input limbs
+    const double inv_bfly = a.half ? (double)a.level * n / 2 * M1 + (double)a.level * n : 0.0;
+    ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n + inv_bfly),
                    count * n * 8 * (a.level + conv));
-    uint32_t cnt_max = 0;
-    for (uint32_t j = 0; j < a.beta; ++j) cnt_max = std::max(cnt_max, a.cnt[j]);
-    const size_t sma = smc + sizeof(uint64_t) * (size_t)cnt_max * SC::TILE;
+    const size_t sma = ks_all_smem<LOG_N, M1, K1>(c, a.beta, a.cnt);
+    if (a.half && sma > kModupAllSmem) return fail(HE_EINVAL, "ks_fused: half-transformed input needs the all-targets kernel");
     if (sma <= kModupAllSmem) {  // one CTA per digit and tile, all targets
       const size_t blocks = (size_t)count * a.beta * SC::TILES;
       ks_modup_col_all<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, sma, c->stream>>>(a);
@@ -471,11 +510,13 @@ static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
 // ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
 // sets *handled when N has a compiled shape.
 int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool* handled) {
+             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled) {
   *handled = false;
   if (!ks_fusable(c)) return HE_OK;
   KsFusedArgs a;
   a.gal = gal;
+  a.half = half ? 1 : 0;
+  a.itw = reinterpret_cast<const ulonglong2*>(c->d_itw);
   a.d = d;
   a.d2c = d2c;
   a.ext = ext;
@@ -526,14 +567,20 @@ namespace he {
 // Conversion -> NTT -> combine of keyswitch_batch's ModDown, fused.  acc's P
 // limbs must already be in coefficient form.  Sets *handled when N has
 // compiled shapes (the same ones as the NTT and ModUp).
+static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count);
+
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
   *handled = false;
   if (!ks_fusable(c)) return HE_OK;
+  const uint32_t nt = level + (uint32_t)c->alpha;
   MdArgs a;
   a.add_gal = add_gal;
-  a.acc = acc;
-  a.acc_stride = acc_stride;
+  a.yP = acc + (size_t)level * c->n;
+  a.yp_stride = acc_stride;
+  a.yp_pstride = (uint64_t)nt * c->n;
+  a.accq = CtBatch{const_cast<uint64_t*>(acc), acc_stride, nt, 0};
+  a.sp0 = (uint32_t)c->L;
   a.conv = conv;
   a.add = add;
   a.out = out;
@@ -541,11 +588,42 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
   a.level = level;
   a.alpha = (uint32_t)c->alpha;
   a.L = (uint32_t)c->L;
-  a.nt = level + a.alpha;
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
   a.md = c->d_moddown;
   *handled = true;
+  return md_dispatch(c, a, count);
+}
+
+// Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
+// last: the dropped limb of both parts in coefficient form, count x [2][N].
+int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
+             uint32_t count, bool* handled) {
+  *handled = false;
+  if (!ks_fusable(c) || level < 2) return HE_OK;
+  const uint32_t lt = level - 1;
+  MdArgs a;
+  a.add_gal = 0;
+  a.yP = last;
+  a.yp_stride = 2ull * c->n;
+  a.yp_pstride = c->n;
+  a.accq = in;
+  a.sp0 = lt;
+  a.conv = conv;
+  a.add = out;
+  a.out = out;
+  a.has_add = 0;
+  a.level = lt;
+  a.alpha = 1;
+  a.L = (uint32_t)c->L;
+  a.primes = c->d_primes;
+  a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.md = c->d_rescale_md + (size_t)lt * c->rescale_md_words;
+  *handled = true;
+  return md_dispatch(c, a, count);
+}
+
+static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count) {
   const int sh = c->ntt_shape;
   switch (c->log_n) {
     case 12:
@@ -564,6 +642,34 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
       return sh == 1 ? md_fused_run<16, 7, 4, 9, 2>(c, a, count)
            : sh == 2 ? md_fused_run<16, 6, 5, 10, 1>(c, a, count) : md_fused_run<16, 8, 4, 8, 3>(c, a, count);
   }
+}
+
+}  // namespace he
+
+namespace he {
+
+// Whether the fused key switch at this level converts each digit in one CTA
+// (then it can finish the inverse transform of its input itself).
+bool ks_converts_per_digit(const he_ctx* c, uint32_t level) {
+  if (!ks_fusable(c)) return false;
+  const uint32_t alpha = (uint32_t)c->alpha, beta = (level + alpha - 1) / alpha;
+  uint32_t cnt[HE_MAX_PRIMES];
+  for (uint32_t j = 0; j < beta; ++j) cnt[j] = c->modup[level][j].cnt;
+  const int sh = c->ntt_shape;
+  size_t smem = 0;
+  switch (c->log_n) {
+    case 12: smem = sh == 1 ? ks_all_smem<12, 5, 6>(c, beta, cnt) : sh == 2 ? ks_all_smem<12, 3, 8>(c, beta, cnt)
+                                                                  : ks_all_smem<12, 6, 5>(c, beta, cnt); break;
+    case 13: smem = sh == 1 ? ks_all_smem<13, 6, 5>(c, beta, cnt) : sh == 2 ? ks_all_smem<13, 4, 7>(c, beta, cnt)
+                                                                  : ks_all_smem<13, 7, 4>(c, beta, cnt); break;
+    case 14: smem = sh == 1 ? ks_all_smem<14, 8, 3>(c, beta, cnt) : sh == 2 ? ks_all_smem<14, 5, 6>(c, beta, cnt)
+                                                                  : ks_all_smem<14, 7, 4>(c, beta, cnt); break;
+    case 15: smem = sh == 1 ? ks_all_smem<15, 7, 4>(c, beta, cnt) : sh == 2 ? ks_all_smem<15, 6, 5>(c, beta, cnt)
+                                                                  : ks_all_smem<15, 8, 4>(c, beta, cnt); break;
+    default: smem = sh == 1 ? ks_all_smem<16, 7, 4>(c, beta, cnt) : sh == 2 ? ks_all_smem<16, 6, 5>(c, beta, cnt)
+                                                                  : ks_all_smem<16, 8, 4>(c, beta, cnt); break;
+  }
+  return smem <= kModupAllSmem;
 }
 
 }  // namespace he

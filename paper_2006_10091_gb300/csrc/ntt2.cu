@@ -165,6 +165,35 @@ static int run2_dir(he_ctx* c, const PolyBatch& b, bool inv) {
   return inv ? run2<true, LOG_N, M1, K1, M2, K2>(c, b) : run2<false, LOG_N, M1, K1, M2, K2>(c, b);
 }
 
+// Only the first pass (the row pass) of the inverse transform: the fused
+// key switch runs the column pass itself on the tiles it converts.
+template <int LOG_N, int M1, int K1, int M2, int K2>
+static int run2_inv_rows(he_ctx* c, const PolyBatch& b) {
+  return launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
+}
+
+int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b) {
+  const int sh = c->ntt_shape;
+  switch (c->log_n) {
+    case 12:
+      return sh == 1 ? run2_inv_rows<12, 5, 6, 7, 4>(c, b)
+           : sh == 2 ? run2_inv_rows<12, 3, 8, 9, 2>(c, b) : run2_inv_rows<12, 6, 5, 6, 5>(c, b);
+    case 13:
+      return sh == 1 ? run2_inv_rows<13, 6, 5, 7, 4>(c, b)
+           : sh == 2 ? run2_inv_rows<13, 4, 7, 9, 2>(c, b) : run2_inv_rows<13, 7, 4, 6, 5>(c, b);
+    case 14:
+      return sh == 1 ? run2_inv_rows<14, 8, 3, 6, 5>(c, b)
+           : sh == 2 ? run2_inv_rows<14, 5, 6, 9, 2>(c, b) : run2_inv_rows<14, 7, 4, 7, 4>(c, b);
+    case 15:
+      return sh == 1 ? run2_inv_rows<15, 7, 4, 8, 3>(c, b)
+           : sh == 2 ? run2_inv_rows<15, 6, 5, 9, 2>(c, b) : run2_inv_rows<15, 8, 4, 7, 4>(c, b);
+    case 16:
+      return sh == 1 ? run2_inv_rows<16, 7, 4, 9, 2>(c, b)
+           : sh == 2 ? run2_inv_rows<16, 6, 5, 10, 1>(c, b) : run2_inv_rows<16, 8, 4, 8, 3>(c, b);
+    default: return fail(HE_EINVAL, "ntt2_inverse_rows: no compiled shape");
+  }
+}
+
 // Three tile shapes per ring size (column pass bits, rows per tile | row pass
 // bits, rows per tile); c->ntt_shape picks one (the autotuner times them).
 // The fused key-switching kernels use the same pairs.

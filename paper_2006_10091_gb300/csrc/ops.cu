@@ -16,9 +16,13 @@
 
 namespace he {
 int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool* handled);
+             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled);
+bool ks_converts_per_digit(const he_ctx* c, uint32_t level);
+int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b);
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
+int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
+             uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -118,15 +122,17 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   uint64_t* acc = ar.take<uint64_t>((size_t)count * 2 * nt * n);
   uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
-  // 1. coefficient form
+  // 1. coefficient form (when each digit is converted in one CTA, only the
+  //    inverse transform's row pass here; the conversion kernel finishes it)
+  const bool half = ks_converts_per_digit(c, level);
   {
     PolyBatch b = pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level);
     b.gal = gal;
-    HE_TRY(ntt_inverse(c, b));
+    HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
   }
   // 2-3. fused ModUp + NTT + inner product where N has compiled shapes
   bool fused = false;
-  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, gal, &fused));
+  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, gal, half, &fused));
   if (!fused) HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
   // 4. ModDown
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
@@ -162,6 +168,9 @@ int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch
   for (uint32_t p = 0; p < 2; ++p)
     HE_TRY(ntt_inverse(c, pb(in.base + ((size_t)p * in.cap + lt) * n, last + (size_t)p * n, in.stride,
                              2ull * n, count, 1, lt, c->L)));
+  bool fused = false;  // correction, NTT and division fused like ModDown's
+  HE_TRY(rs_fused(c, in, last, corr, out, level, count, &fused));
+  if (fused) return HE_OK;
   {
     ProfScope prof(c, "rescale", (double)count * 2 * n * lt, (double)count * 2 * n * 8 * (1 + lt));
     k_rescale_corr<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(last, corr, level, count,

@@ -245,7 +245,8 @@ int build_tables(he_ctx* c) {
   // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2 reduced:
   // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds); then the
   // [alpha][L] Shoup companions of the (P/p_k) mod q_t values; [alpha] low
-  // words of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t.
+  // words of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t;
+  // [L][8] v P mod q_t.
   // The last two make the conversion exact: v = floor(sum_k u_k / p_k) is
   // evaluated in 64.64 fixed point and v P subtracted.
   {
@@ -289,6 +290,8 @@ int build_tables(he_ctx* c) {
       for (int t = 0; t < L; ++t) words.push_back(h_shoup(words[2 * alpha + (size_t)k * L + t], c->q[t]));
     for (int k = 0; k < alpha; ++k) words.push_back((uint64_t)(~(unsigned __int128)0 / c->q[L + k]));
     for (int t = 0; t < L; ++t) words.push_back(c->P_mod_q[t]);
+    for (int t = 0; t < L; ++t)  // [L][8]: v P mod q_t for v = 0 .. 7 (v < alpha <= 8)
+      for (uint64_t v = 0; v < 8; ++v) words.push_back(h_mulmod(v % c->q[t], c->P_mod_q[t], c->q[t]));
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }
@@ -305,6 +308,38 @@ int build_tables(he_ctx* c) {
       }
     HE_CUDA(cudaMalloc(&c->d_rescale, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_rescale, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
+  }
+  // The rescale is a ModDown by the single prime q_l (rounded the same way):
+  // per l, the ModDown table layout with alpha = 1 and q_l as the special
+  // prime (Shoup pairs of 1; [L] 1; [L] Shoup pairs of q_l^-1 mod q_t; h =
+  // (q_l - 1)/2 and [L] h mod q_t; [L] Shoup companions of 1; an unused word;
+  // [L] q_l mod q_t; [L][8] v q_l mod q_t), for the fused kernels.
+  {
+    const size_t W = 4 + 14 * (size_t)L;
+    std::vector<uint64_t> words(W * L, 0);
+    for (int l = 1; l < L; ++l) {
+      uint64_t* b = words.data() + (size_t)l * W;
+      const uint64_t ql = c->q[l], h = (ql - 1) / 2;
+      b[0] = 1;
+      b[1] = h_shoup(1, ql);
+      for (int t = 0; t < L; ++t) {
+        const uint64_t qt = c->q[t];
+        b[2 + t] = 1 % qt;
+        if (t < l) {
+          const uint64_t inv = h_invmod(ql % qt, qt);
+          b[2 + L + 2 * t] = inv;
+          b[2 + L + 2 * t + 1] = h_shoup(inv, qt);
+        }
+        b[3 + 3 * L + t] = h % qt;
+        b[3 + 4 * L + t] = h_shoup(1 % qt, qt);
+        b[4 + 5 * L + t] = ql % qt;
+        for (uint64_t v = 0; v < 8; ++v) b[4 + 6 * L + (size_t)t * 8 + v] = h_mulmod(v % qt, ql % qt, qt);
+      }
+      b[2 + 3 * L] = h;
+    }
+    c->rescale_md_words = W;
+    HE_CUDA(cudaMalloc(&c->d_rescale_md, sizeof(uint64_t) * words.size()));
+    HE_CUDA(cudaMemcpy(c->d_rescale_md, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }
   // Garner constants for decryption
   {

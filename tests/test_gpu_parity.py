@@ -473,6 +473,20 @@ def test_fused_rotation_and_mul_bit_exact(wide, he):
     assert_same_residues(out, wide.o.mul_relin_rescale(oa, ob), he, wide.g)
 
 
+@pytest.mark.parametrize("level", [6, 3, 2])
+def test_fused_rescale_bit_exact(wide, he, level):
+    """The rescale runs as a ModDown by q_{l-1} through the fused kernels at
+    N >= 2^12; out of place and in place."""
+    m = workloads.int_poly(64 + level, wide.n, 1 << 40)
+    ga, oa = wide.gpu_enc(m, level, 64 + level), wide.orc_enc(m, level, 64 + level)
+    want = wide.o.rescale(oa)
+    out = wide.g.new_ct(level)
+    he.he_rescale(wide.g, ga, out)
+    assert_same_residues(out, want, he, wide.g)
+    he.he_rescale(wide.g, ga, ga)
+    assert_same_residues(ga, want, he, wide.g)
+
+
 def test_fused_rotation_in_place(wide, he):
     """The fused rotation reads its input through the automorphism while it
     writes the output; an output that overlaps the input takes the path with
