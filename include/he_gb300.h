@@ -241,6 +241,21 @@ typedef struct he_lr_config {
 int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
                         const he_lr_config* cfg, he_ct* W_out);
 
+/* The same step (Eq. 7-8) with its inputs and result in host memory, the way
+ * a worker receives its encrypted shard (Algorithm 1): Z = nZ ciphertexts of
+ * [2][z_level][N] residues back to back, W = [2][w_level][N] (6 <= w_level <=
+ * z_level <= L); the result [2][w_level-5][N] goes to `out` (out_words >= its
+ * size), its level and scale to *out_level / *out_scale (may be NULL).  The
+ * weights and then pieces of 16 data ciphertexts are copied on a second
+ * stream while the circuit runs chunk by chunk on the context's stream, so
+ * the copies overlap the arithmetic; pinned host memory is needed for that
+ * overlap (pageable memory is copied synchronously).  Returns after the
+ * result is in `out`.  The device copy of the inputs is a context-owned
+ * buffer, grown on demand.  HE_ELEVEL if w_level < 6. */
+int he_lr_gradient_step_host(he_ctx* ctx, const uint64_t* Z, size_t nZ, uint32_t z_level, double z_scale,
+                             const uint64_t* W, uint32_t w_level, double w_scale, const he_lr_config* cfg,
+                             uint64_t* out, size_t out_words, uint32_t* out_level, double* out_scale);
+
 /* The paper's K workers (Sec. 4, Fig. 1; Algorithm 1) as independent
  * instances on one GPU, all stepped in one batched launch sequence.  Shard k
  * holds its own data ciphertexts Z[0..nZ) (one level, one scale), its weights

@@ -126,6 +126,9 @@ def load():
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
+        "he_lr_gradient_step_host": [VP, VP, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double, VP, ctypes.c_uint32,
+                                     ctypes.c_double, ctypes.POINTER(he_lr_config), VP, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)],
         "he_get_tuning": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
@@ -443,6 +446,19 @@ def _shards(shards, infer):
             arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w),
                                  ctypes.addressof(wo), None, cid, 0)
     return arr, keep
+
+
+def he_lr_gradient_step_host(ctx, Z_host, z_level: int, z_scale: float, W_host, w_level: int, w_scale: float,
+                             cfg: he_lr_config, out_host):
+    """The step on host buffers (numpy uint64 arrays or pinned CPU torch tensors):
+    Z_host [nZ][2][z_level][N], W_host [2][w_level][N], out_host >= [2][w_level-5][N].
+    Returns (level, scale) of the result."""
+    lv, sc = ctypes.c_uint32(), ctypes.c_double()
+    _check(load().he_lr_gradient_step_host(ctx.ptr, ctypes.c_void_p(_addr(Z_host)), Z_host.shape[0], z_level,
+                                           float(z_scale), ctypes.c_void_p(_addr(W_host)), w_level, float(w_scale),
+                                           ctypes.byref(cfg), ctypes.c_void_p(_addr(out_host)), _nwords(out_host),
+                                           ctypes.byref(lv), ctypes.byref(sc)))
+    return lv.value, sc.value
 
 
 def he_lr_gradient_step_workers(ctx, shards: list, cfg: he_lr_config, refresh_level: int = 0,

@@ -137,6 +137,10 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
 static void destroy(he_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  for (cudaEvent_t e : c->io_events) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  cudaFree(c->io.ptr);
   if (c->view) {  // only the view's own state
     for (auto& kv : c->lr_masks) cudaFree(kv.second);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -438,12 +442,28 @@ int he_ct_import(he_ctx* c, const uint64_t* host, uint32_t level, double scale, 
 int he_ct_import_batch(he_ctx* c, const uint64_t* host, uint32_t level, double scale, he_ct* out, size_t count) {
   if (!c || !host || !out) return fail(HE_EINVAL, "he_ct_import_batch: null argument");
   const size_t lw = (size_t)level * c->n;
-  for (size_t i = 0; i < count; ++i) {
-    HE_TRY(check_out(c, &out[i], level, "he_ct_import_batch"));
-    for (int p = 0; p < 2; ++p)
-      HE_CUDA(cudaMemcpyAsync(out[i].data + (size_t)p * out[i].cap * c->n, host + (i * 2 + p) * lw,
-                              sizeof(uint64_t) * lw, cudaMemcpyHostToDevice, c->stream));
-  }
+  for (size_t i = 0; i < count; ++i) HE_TRY(check_out(c, &out[i], level, "he_ct_import_batch"));
+  // one copy per run of polynomials that are contiguous on the device too
+  // (full-capacity ciphertexts back to back, as in a uniform batch)
+  size_t run_src = 0, run_len = 0;
+  uint64_t* run_dst = nullptr;
+  for (size_t i = 0; i < count; ++i)
+    for (int p = 0; p < 2; ++p) {
+      uint64_t* dst = out[i].data + (size_t)p * out[i].cap * c->n;
+      const size_t src = (i * 2 + p) * lw;
+      if (run_dst && dst == run_dst + run_len && src == run_src + run_len) {
+        run_len += lw;
+        continue;
+      }
+      if (run_dst)
+        HE_CUDA(cudaMemcpyAsync(run_dst, host + run_src, sizeof(uint64_t) * run_len, cudaMemcpyHostToDevice,
+                                c->stream));
+      run_dst = dst;
+      run_src = src;
+      run_len = lw;
+    }
+  if (run_dst)
+    HE_CUDA(cudaMemcpyAsync(run_dst, host + run_src, sizeof(uint64_t) * run_len, cudaMemcpyHostToDevice, c->stream));
   HE_CUDA(cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < count; ++i) {
     out[i].level = level;
@@ -457,13 +477,32 @@ int he_ct_export_batch(he_ctx* c, const he_ct* cts, size_t count, uint64_t* host
   size_t off = 0;
   for (size_t i = 0; i < count; ++i) {
     HE_TRY(check_ct(c, &cts[i], "he_ct_export_batch"));
-    const size_t lw = (size_t)cts[i].level * c->n;
-    if (off + 2 * lw > cap_words) return fail(HE_EINVAL, "he_ct_export_batch: host buffer too small");
-    for (int p = 0; p < 2; ++p)
-      HE_CUDA(cudaMemcpyAsync(host + off + p * lw, cts[i].data + (size_t)p * cts[i].cap * c->n,
-                              sizeof(uint64_t) * lw, cudaMemcpyDeviceToHost, c->stream));
-    off += 2 * lw;
+    off += 2 * (size_t)cts[i].level * c->n;
   }
+  if (off > cap_words) return fail(HE_EINVAL, "he_ct_export_batch: host buffer too small");
+  // one copy per run of polynomials that are contiguous on the device too
+  off = 0;
+  size_t run_dst = 0, run_len = 0;
+  const uint64_t* run_src = nullptr;
+  for (size_t i = 0; i < count; ++i) {
+    const size_t lw = (size_t)cts[i].level * c->n;
+    for (int p = 0; p < 2; ++p) {
+      const uint64_t* src = cts[i].data + (size_t)p * cts[i].cap * c->n;
+      if (run_src && src == run_src + run_len && off == run_dst + run_len) {
+        run_len += lw;
+      } else {
+        if (run_src)
+          HE_CUDA(cudaMemcpyAsync(host + run_dst, run_src, sizeof(uint64_t) * run_len, cudaMemcpyDeviceToHost,
+                                  c->stream));
+        run_src = src;
+        run_dst = off;
+        run_len = lw;
+      }
+      off += lw;
+    }
+  }
+  if (run_src)
+    HE_CUDA(cudaMemcpyAsync(host + run_dst, run_src, sizeof(uint64_t) * run_len, cudaMemcpyDeviceToHost, c->stream));
   HE_CUDA(cudaStreamSynchronize(c->stream));
   return HE_OK;
 }

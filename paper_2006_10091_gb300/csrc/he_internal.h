@@ -112,6 +112,13 @@ struct he_ctx {
   std::map<std::string, he::ProfClass> prof;
   uint64_t* h_stage = nullptr;  // pinned staging (host <-> device)
   size_t h_stage_size = 0;
+  // host-input step: device copy of the inputs, a copy stream and one event per
+  // piece of data ciphertexts; the step waits for a piece before its chunk
+  he::Workspace io;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> io_events;
+  size_t io_piece = 0;             // data ciphertexts per copied piece (0: no pipelined input)
+  size_t io_pieces_waited = 0;     // pieces the step's stream already waits for
 
   size_t key_words() const { return (size_t)beta * 2 * np * n; }
 };

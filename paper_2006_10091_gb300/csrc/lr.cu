@@ -358,6 +358,14 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
         Zc = b.Zcopy;
         Wc = b.Wrep;
       }
+      if (c->io_piece) {  // pipelined host input (one shard): wait for the pieces this chunk reads
+        const size_t last = seg.back().second.first + seg.back().second.second;  // ciphertexts [0, last) needed
+        const size_t need = (last + c->io_piece - 1) / c->io_piece;
+        if (need > c->io_pieces_waited) {
+          HE_CUDA(cudaStreamWaitEvent(c->stream, c->io_events[need - 1], 0));
+          c->io_pieces_waited = need;
+        }
+      }
       HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops, infer));
       size_t off = 0;
       if (infer) {  // copy S_k of each segment's ciphertexts to their outputs
@@ -571,6 +579,75 @@ extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const h
     if (Z[k].level != W->level) return fail(HE_EINVAL, "data and weights must share one level");
   he_lr_shard s{Z, nZ, W, W_out, nullptr, 0, 0};
   return lr_entry(c, &s, 1, cfg, 0, 0, false);
+}
+
+// The step with its inputs and output in host memory: the weights, then the
+// data ciphertexts in pieces, are copied on a second stream while the circuit
+// runs chunk by chunk on the context's stream, each chunk waiting only for the
+// pieces it reads; the new weights are copied back at the end.
+extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ, uint32_t z_level, double z_scale,
+                                        const uint64_t* W, uint32_t w_level, double w_scale,
+                                        const he_lr_config* cfg, uint64_t* out, size_t out_words,
+                                        uint32_t* out_level, double* out_scale) {
+  if (!c || !Z || !W || !cfg || !out || nZ == 0) return fail(HE_EINVAL, "he_lr_gradient_step_host: null argument");
+  if (z_level < 6 || z_level > (uint32_t)c->L || w_level < 6 || w_level > z_level)
+    return fail(w_level < 6 ? HE_ELEVEL : HE_EINVAL, "he_lr_gradient_step_host: bad levels");
+  const size_t n = c->n, zw = (size_t)2 * z_level * n, ww = (size_t)2 * w_level * n;
+  const uint32_t lo = w_level - 5;
+  if (out_words < (size_t)2 * lo * n) return fail(HE_EINVAL, "he_lr_gradient_step_host: output buffer too small");
+  const size_t words = zw * nZ + ww + 2 * (size_t)lo * n + 64;
+  if (c->io.size < words * sizeof(uint64_t)) {
+    HE_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->copy_stream) HE_CUDA(cudaStreamSynchronize(c->copy_stream));
+    cudaFree(c->io.ptr);
+    c->io.ptr = nullptr;
+    c->io.size = 0;
+    if (cudaMalloc(&c->io.ptr, words * sizeof(uint64_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HE_ENOMEM, "he_lr_gradient_step_host: device input buffer");
+    }
+    c->io.size = words * sizeof(uint64_t);
+  }
+  if (!c->copy_stream) HE_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  const size_t piece = 16;  // data ciphertexts per copy (32 MB at N = 2^14, 8 limbs)
+  const size_t pieces = (nZ + piece - 1) / piece;
+  while (c->io_events.size() < pieces + 1) {
+    cudaEvent_t e;
+    HE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->io_events.push_back(e);
+  }
+  uint64_t* dZ = (uint64_t*)c->io.ptr;
+  uint64_t* dW = dZ + zw * nZ;
+  uint64_t* dO = dW + ww;
+  // the copy stream may overwrite the buffers only after the previous step on c->stream is done with them
+  HE_CUDA(cudaEventRecord(c->io_events[pieces], c->stream));
+  HE_CUDA(cudaStreamWaitEvent(c->copy_stream, c->io_events[pieces], 0));
+  HE_CUDA(cudaMemcpyAsync(dW, W, sizeof(uint64_t) * ww, cudaMemcpyHostToDevice, c->copy_stream));
+  for (size_t k = 0; k < pieces; ++k) {
+    const size_t first = k * piece, cnt = std::min(piece, nZ - first);
+    HE_CUDA(cudaMemcpyAsync(dZ + first * zw, Z + first * zw, sizeof(uint64_t) * zw * cnt, cudaMemcpyHostToDevice,
+                            c->copy_stream));
+    HE_CUDA(cudaEventRecord(c->io_events[k], c->copy_stream));
+  }
+  std::vector<he_ct> zc(nZ);
+  for (size_t i = 0; i < nZ; ++i) zc[i] = he_ct{dZ + i * zw, z_level, z_level, z_scale};
+  he_ct wc{dW, w_level, w_level, w_scale}, oc{dO, 0, lo, 0.0};
+  he_lr_shard sh{zc.data(), nZ, &wc, &oc, nullptr, 0, 0};
+  // the weights arrive with the first piece's copy ordering: wait for it before the step
+  HE_CUDA(cudaStreamWaitEvent(c->stream, c->io_events[0], 0));
+  c->io_piece = piece;
+  c->io_pieces_waited = 1;
+  const int rc = lr_entry(c, &sh, 1, cfg, 0, 0, false);
+  c->io_piece = 0;
+  if (rc != HE_OK) {
+    cudaStreamSynchronize(c->copy_stream);
+    return rc;
+  }
+  HE_CUDA(cudaMemcpyAsync(out, dO, sizeof(uint64_t) * 2 * lo * n, cudaMemcpyDeviceToHost, c->stream));
+  HE_CUDA(cudaStreamSynchronize(c->stream));
+  if (out_level) *out_level = oc.level;
+  if (out_scale) *out_scale = oc.scale;
+  return HE_OK;
 }
 
 extern "C" int he_lr_gradient_step_workers(he_ctx* c, const he_lr_shard* shards, size_t count,

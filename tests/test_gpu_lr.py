@@ -240,3 +240,54 @@ def test_extreme_packings_bit_exact(g):
     want = pair.o.lr_inference(Zo, Wo, coeffs, 1.0, g)
     for k in range(2):
         assert_same_residues(S[k], want[k], he, pair.g)
+
+
+def test_host_input_step_matches_device_step():
+    """The step on host buffers (copies overlapped with the circuit, here in
+    many chunks) gives the residues of the step on device buffers, at a ring
+    size with the fused kernels and a ragged number of data ciphertexts."""
+    import torch
+    log_n, g = 12, 8
+    n_slots = (1 << log_n) // 2
+    he = gpu_lib()
+    ctx = he.Context(log_n, 7, 40, 2, 55, 2.0 ** 40, seed=21, rot_steps=rot_steps(n_slots, g))
+    nZ = 37
+    Z = ctx.new_ct(7, nZ)
+    for k in range(nZ):
+        he.he_encrypt_poly(ctx, workloads.int_poly(700 + k, ctx.n, 1 << 28), 2.0 ** 40, 7, Z[k], cid=700 + k)
+    W = ctx.new_ct(7)
+    he.he_encrypt_poly(ctx, workloads.int_poly(799, ctx.n, 1 << 28), 2.0 ** 40, 7, W, cid=799)
+    cfg = he.lr_config(table2()["binomial"], 1.0 / (nZ * g), g, 2.0 ** 27)
+    he.he_set_tuning(ctx, "lr_chunk", 5)
+    out = ctx.new_ct(7)
+    he.he_lr_gradient_step(ctx, Z, W, cfg, out)
+    want = he.he_ct_export(ctx, out)
+    zh = torch.empty((nZ, 2, 7, ctx.n), dtype=torch.int64, pin_memory=True)
+    he.he_ct_export_batch(ctx, Z, zh)
+    wh = he.he_ct_export(ctx, W)
+    oh = np.zeros((2, 2, ctx.n), dtype=np.uint64)
+    for _ in range(2):  # the second call reuses the device buffers and events
+        level, scale = he.he_lr_gradient_step_host(ctx, zh, 7, 2.0 ** 40, wh, 7, 2.0 ** 40, cfg, oh)
+        assert level == 2 and scale == out.scale
+        assert np.array_equal(oh, want)
+    with pytest.raises(he.HeError) as e:
+        he.he_lr_gradient_step_host(ctx, zh, 7, 2.0 ** 40, wh[:, :5].copy(), 5, 2.0 ** 40, cfg, oh)
+    assert e.value.code == he.HE_ELEVEL
+
+
+def test_batched_import_export_round_trip():
+    """Uniform batches move in one copy per contiguous run; ciphertexts with
+    spare capacity or in separate buffers still land limb by limb."""
+    he = gpu_lib()
+    ctx = he.Context(11, 5, 40, 1, 60, 2.0 ** 40, seed=22)
+    data = workloads.residues(5, ctx.primes[:4], ctx.n, parts=2 * 6).reshape(6, 2, 4, ctx.n)
+    uni = ctx.new_ct(4, 6)
+    he.he_ct_import_batch(ctx, data, 4, 2.0 ** 40, uni)
+    mixed = [ctx.new_ct(5) for _ in range(3)] + ctx.new_ct(4, 3)
+    he.he_ct_import_batch(ctx, data, 4, 2.0 ** 40, mixed)
+    for cts in (uni, mixed):
+        for i, ct in enumerate(cts):
+            assert np.array_equal(he.he_ct_export(ctx, ct), data[i])
+        back = np.zeros_like(data)
+        he.he_ct_export_batch(ctx, cts, back)
+        assert np.array_equal(back, data)
