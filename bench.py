@@ -133,7 +133,13 @@ def measured_peaks():
 # products/s.  A butterfly is one product; the key-switching kernels also
 # count their basis-conversion and inner-product products.
 ALU_MODMUL_PEAK = 152 * 2.070e9 * 64 / 17.3
-ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "moddown_ntt", "moddown_ntt_combine")
+ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "moddown_ntt", "moddown_ntt_combine",
+               "rescale_ntt", "rescale_ntt_final")
+# DRAM bytes (read + write) per modular product of the fused key-switch row
+# pass, from an ncu capture of one launch over 64 ciphertexts at level 7 of
+# these parameters (479.1 MB for 212.3 M products); the roofline scales it to
+# the step's average launch, whose traffic grows in proportion to its work.
+KS_ROW_TRAFFIC_PER_MODMUL = 479.085056e6 / 212336640
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
@@ -150,9 +156,14 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
     if name in ALU_CLASSES:
         rate = p["work"] / (p["ms"] * 1e-3)
         frac_alu = rate / ALU_MODMUL_PEAK
+        traffic = None
+        if name == "ks_ntt_inner_product":
+            traffic = KS_ROW_TRAFFIC_PER_MODMUL * p["work"] / max(1, p["launches"])
         if frac_alu >= frac_hbm:
             return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_MODMUL_PEAK / 1e9,
-                    "unit": "G modmul/s", "frac": frac_alu, "traffic": None,
+                    "unit": "G modmul/s", "frac": frac_alu, "traffic": traffic,
+                    "traffic_note": "bytes per launch, scaled from an ncu capture of a smaller launch" if traffic
+                    else None,
                     "per_launch_ms": per_launch_ms, "launches": p["launches"],
                     "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
                     "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots per 64-bit "

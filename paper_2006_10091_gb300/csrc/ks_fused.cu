@@ -411,13 +411,17 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
 }
 
 template <int LOG_N, int M1, int K1, int M2, int K2>
-static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count) {
+static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   using SC = Shape<LOG_N, M1, K1, true>;
   using SR = Shape<LOG_N, M2, K2, false>;
   const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
                      (sizeof(uint64_t) * a.alpha + sizeof(uint32_t)) * SC::TILE;
   const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
-  if (smc > kModupAllSmem) return fail(HE_EINVAL, "ModDown tile too large for shared memory");
+  if (smc > kModupAllSmem) {  // too many special primes for this tile: the caller runs the unfused sequence
+    *handled = false;
+    return HE_OK;
+  }
+  *handled = true;
   static unsigned long long attr_set = 0;
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
     HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -567,7 +571,7 @@ namespace he {
 // Conversion -> NTT -> combine of keyswitch_batch's ModDown, fused.  acc's P
 // limbs must already be in coefficient form.  Sets *handled when N has
 // compiled shapes (the same ones as the NTT and ModUp).
-static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count);
+static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);
 
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
@@ -591,8 +595,7 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
   a.md = c->d_moddown;
-  *handled = true;
-  return md_dispatch(c, a, count);
+  return md_dispatch(c, a, count, handled);
 }
 
 // Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
@@ -619,28 +622,27 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
   a.md = c->d_rescale_md + (size_t)lt * c->rescale_md_words;
-  *handled = true;
-  return md_dispatch(c, a, count);
+  return md_dispatch(c, a, count, handled);
 }
 
-static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count) {
+static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   const int sh = c->ntt_shape;
   switch (c->log_n) {
     case 12:
-      return sh == 1 ? md_fused_run<12, 5, 6, 7, 4>(c, a, count)
-           : sh == 2 ? md_fused_run<12, 3, 8, 9, 2>(c, a, count) : md_fused_run<12, 6, 5, 6, 5>(c, a, count);
+      return sh == 1 ? md_fused_run<12, 5, 6, 7, 4>(c, a, count, handled)
+           : sh == 2 ? md_fused_run<12, 3, 8, 9, 2>(c, a, count, handled) : md_fused_run<12, 6, 5, 6, 5>(c, a, count, handled);
     case 13:
-      return sh == 1 ? md_fused_run<13, 6, 5, 7, 4>(c, a, count)
-           : sh == 2 ? md_fused_run<13, 4, 7, 9, 2>(c, a, count) : md_fused_run<13, 7, 4, 6, 5>(c, a, count);
+      return sh == 1 ? md_fused_run<13, 6, 5, 7, 4>(c, a, count, handled)
+           : sh == 2 ? md_fused_run<13, 4, 7, 9, 2>(c, a, count, handled) : md_fused_run<13, 7, 4, 6, 5>(c, a, count, handled);
     case 14:
-      return sh == 1 ? md_fused_run<14, 8, 3, 6, 5>(c, a, count)
-           : sh == 2 ? md_fused_run<14, 5, 6, 9, 2>(c, a, count) : md_fused_run<14, 7, 4, 7, 4>(c, a, count);
+      return sh == 1 ? md_fused_run<14, 8, 3, 6, 5>(c, a, count, handled)
+           : sh == 2 ? md_fused_run<14, 5, 6, 9, 2>(c, a, count, handled) : md_fused_run<14, 7, 4, 7, 4>(c, a, count, handled);
     case 15:
-      return sh == 1 ? md_fused_run<15, 7, 4, 8, 3>(c, a, count)
-           : sh == 2 ? md_fused_run<15, 6, 5, 9, 2>(c, a, count) : md_fused_run<15, 8, 4, 7, 4>(c, a, count);
+      return sh == 1 ? md_fused_run<15, 7, 4, 8, 3>(c, a, count, handled)
+           : sh == 2 ? md_fused_run<15, 6, 5, 9, 2>(c, a, count, handled) : md_fused_run<15, 8, 4, 7, 4>(c, a, count, handled);
     default:
-      return sh == 1 ? md_fused_run<16, 7, 4, 9, 2>(c, a, count)
-           : sh == 2 ? md_fused_run<16, 6, 5, 10, 1>(c, a, count) : md_fused_run<16, 8, 4, 8, 3>(c, a, count);
+      return sh == 1 ? md_fused_run<16, 7, 4, 9, 2>(c, a, count, handled)
+           : sh == 2 ? md_fused_run<16, 6, 5, 10, 1>(c, a, count, handled) : md_fused_run<16, 8, 4, 8, 3>(c, a, count, handled);
   }
 }
 

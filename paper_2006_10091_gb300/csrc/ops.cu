@@ -140,6 +140,14 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   bool md_done = false;
   HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, &md_done));
   if (md_done) return HE_OK;
+  if (gal && add_mode) {  // the unfused combine reads its addend as it is: permute part 0 first
+    uint64_t* pa = ar.take<uint64_t>((size_t)count * level * n);
+    if (!pa) return fail(HE_ENOMEM, "key switch scratch too small");
+    CtBatch P{pa, (size_t)level * n, level, 0};
+    k_automorph<<<grid_for((size_t)count * level * n), 256, 0, c->stream>>>(add, P, 1, level, gal, count, c->log_n);
+    HE_CUDA(cudaGetLastError());
+    add = P;
+  }
   {
     ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
     k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(

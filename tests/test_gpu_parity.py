@@ -508,3 +508,34 @@ def test_fused_single_special_prime_n13(he):
     assert_same_residues(out, p.o.mul_relin_rescale(oa, ob), he, p.g)
     he.he_rotate(p.g, ga, 1, out)
     assert_same_residues(out, p.o.rotate(oa, 1), he, p.g)
+
+
+@pytest.mark.parametrize("log_n", [15, 16])
+def test_fused_matches_unfused_large(he, log_n):
+    """At the large ring sizes with four special primes (the tile shapes where
+    ModDown's conversion may not fit in shared memory) every fused variant
+    gives the residues of the unfused sequence, which the oracle pins at small
+    N; relinearisation and rotation."""
+    import torch
+    ctx = he.Context(log_n, 8, 50, 4, 60, 2.0 ** 50, seed=23, rot_steps=[3])
+    n = ctx.n
+    d = workloads.residues(31 + log_n, ctx.primes[:8], n)[0]
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    outs = {}
+    for generic, shape in ((True, 0), (False, 0), (False, 1), (False, 2)):
+        he.he_set_tuning(ctx, "ntt_generic", generic)
+        he.he_set_tuning(ctx, "ntt_shape", shape)
+        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+        he.he_keyswitch(ctx, dt, 8, 0, o0, o1)
+        outs[(generic, shape)] = (o0.cpu().numpy(), o1.cpu().numpy())
+        ct = ctx.new_ct(8)
+        he.he_encrypt_poly(ctx, workloads.int_poly(5, n, 1 << 40), 2.0 ** 50, 8, ct, cid=5)
+        rot = ctx.new_ct(8)
+        he.he_rotate(ctx, ct, 3, rot)
+        outs[(generic, shape, "rot")] = he.he_ct_export(ctx, rot)
+    he.he_set_tuning(ctx, "ntt_generic", False)
+    he.he_set_tuning(ctx, "ntt_shape", 0)
+    for shape in (0, 1, 2):
+        for k in range(2):
+            assert np.array_equal(outs[(False, shape)][k], outs[(True, 0)][k]), (shape, k)
+        assert np.array_equal(outs[(False, shape, "rot")], outs[(True, 0, "rot")]), shape
