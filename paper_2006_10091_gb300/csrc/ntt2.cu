@@ -33,12 +33,12 @@ struct Ntt2Args {
   int last;
 };
 
-template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL>
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V>
 __device__ __forceinline__ void pass_body(const Ntt2Args& a, uint64_t* sm, ulonglong2* stw, uint32_t tile,
                                           const uint64_t* src, uint64_t* dst, const PrimeDev& pr) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   const uint64_t q = pr.q;
-  run_rounds<INV, LAZY, LOG_N, LOG_M, LOG_K, COL>(sm, stw, q);
+  run_rounds<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, LOG_V>(sm, stw, q);
 #pragma unroll 4
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
     uint32_t k, x;
@@ -57,9 +57,9 @@ __device__ __forceinline__ void pass_body(const Ntt2Args& a, uint64_t* sm, ulong
   }
 }
 
-template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Args a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) >> LOG_V) ntt2_kernel(Ntt2Args a) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Ar
   const uint32_t prime = t < a.level ? t : a.L + t - a.level;
   const PrimeDev pr = a.primes[prime];
   const ulonglong2* tw = a.tw + (size_t)prime * (1u << LOG_N);
-  stage_twiddles<LOG_N, LOG_M, LOG_K, COL>(stw, tw, tile);
+  stage_twiddles<LOG_N, LOG_M, LOG_K, COL, LOG_V>(stw, tw, tile);
   const uint32_t p1 = min(pg * a.pb + a.pb, a.np);
   for (uint32_t p = pg * a.pb; p < p1; ++p) {
     if (a.skip_alpha) {
@@ -91,15 +91,17 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ntt2_kernel(Ntt2Ar
       sm[idx + (idx >> 3)] = __ldg(src + (a.gal ? automorph_src(e, a.gal, LOG_N) : e));
     }
     __syncthreads();
-    if (!INV && pr.q < (1ull << 58)) pass_body<INV, true, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
-    else pass_body<INV, false, LOG_N, LOG_M, LOG_K, COL>(a, sm, stw, tile, src, dst, pr);
+    if (!INV && pr.q < (1ull << 58))
+      pass_body<INV, true, LOG_N, LOG_M, LOG_K, COL, LOG_V>(a, sm, stw, tile, src, dst, pr);
+    else
+      pass_body<INV, false, LOG_N, LOG_M, LOG_K, COL, LOG_V>(a, sm, stw, tile, src, dst, pr);
   }
 }
 
-template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL>
+template <bool INV, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V>
 static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t* dst, uint64_t src_stride,
                    bool last, uint64_t gal = 0) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   Ntt2Args a;
   a.gal = gal;
   a.src = src;
@@ -118,7 +120,7 @@ static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t*
   const size_t smem = sizeof(ulonglong2) * S::NTW + sizeof(uint64_t) * (S::TILE + S::TILE / 8);
   static unsigned long long attr_set = 0;  // per instantiation: one bit per device
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL>,
+    HE_CUDA(cudaFuncSetAttribute(ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL, LOG_V>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr_set |= 1ull << c->device;
   }
@@ -143,33 +145,33 @@ static int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t*
   }
   const double nn = (double)(1u << LOG_N);
   ProfScope prof(c, INV ? "intt" : "ntt", transforms * nn / 2 * LOG_M, transforms * nn * 16);
-  ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL><<<(unsigned)blocks, S::T, smem, c->stream>>>(a);
+  ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL, LOG_V><<<(unsigned)blocks, S::T, smem, c->stream>>>(a);
   HE_CUDA(cudaGetLastError());
   return HE_OK;
 }
 
 // Forward: column pass over the top n1 bits, then row pass; inverse: the
 // reverse.  Returns 1 if N has no compiled shape (the caller falls back).
-template <bool INV, int LOG_N, int M1, int K1, int M2, int K2>
+template <bool INV, int LOG_N, int M1, int K1, int M2, int K2, int LOG_V>
 static int run2(he_ctx* c, const PolyBatch& b) {
   if (!INV) {
-    const int rc = launch2<false, LOG_N, M1, K1, true>(c, b, b.src, b.dst, b.src_stride, false);
-    return rc != HE_OK ? rc : launch2<false, LOG_N, M2, K2, false>(c, b, b.dst, b.dst, b.dst_stride, true);
+    const int rc = launch2<false, LOG_N, M1, K1, true, LOG_V>(c, b, b.src, b.dst, b.src_stride, false);
+    return rc != HE_OK ? rc : launch2<false, LOG_N, M2, K2, false, LOG_V>(c, b, b.dst, b.dst, b.dst_stride, true);
   }
-  const int rc = launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
-  return rc != HE_OK ? rc : launch2<true, LOG_N, M1, K1, true>(c, b, b.dst, b.dst, b.dst_stride, true);
+  const int rc = launch2<true, LOG_N, M2, K2, false, LOG_V>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
+  return rc != HE_OK ? rc : launch2<true, LOG_N, M1, K1, true, LOG_V>(c, b, b.dst, b.dst, b.dst_stride, true);
 }
 
-template <int LOG_N, int M1, int K1, int M2, int K2>
+template <int LOG_N, int M1, int K1, int M2, int K2, int LOG_V = 3>
 static int run2_dir(he_ctx* c, const PolyBatch& b, bool inv) {
-  return inv ? run2<true, LOG_N, M1, K1, M2, K2>(c, b) : run2<false, LOG_N, M1, K1, M2, K2>(c, b);
+  return inv ? run2<true, LOG_N, M1, K1, M2, K2, LOG_V>(c, b) : run2<false, LOG_N, M1, K1, M2, K2, LOG_V>(c, b);
 }
 
 // Only the first pass (the row pass) of the inverse transform: the fused
 // key switch runs the column pass itself on the tiles it converts.
-template <int LOG_N, int M1, int K1, int M2, int K2>
+template <int LOG_N, int M1, int K1, int M2, int K2, int LOG_V = 3>
 static int run2_inv_rows(he_ctx* c, const PolyBatch& b) {
-  return launch2<true, LOG_N, M2, K2, false>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
+  return launch2<true, LOG_N, M2, K2, false, LOG_V>(c, b, b.src, b.dst, b.src_stride, false, b.gal);
 }
 
 int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b) {
@@ -196,7 +198,8 @@ int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b) {
 
 // Three tile shapes per ring size (column pass bits, rows per tile | row pass
 // bits, rows per tile); c->ntt_shape picks one (the autotuner times them).
-// The fused key-switching kernels use the same pairs.
+// The fused key-switching kernels use the same pairs.  (Radix-16 rounds,
+// Shape's LOG_V = 4 with 128-thread CTAs, measured slower than these.)
 int ntt2(he_ctx* c, const PolyBatch& b, bool inv, bool* handled) {
   *handled = true;
   const int sh = c->ntt_shape;

@@ -6,9 +6,11 @@
 
 namespace he {
 
-template <int LOG_N, int LOG_M, int LOG_K, bool COL>
+// A pass over tiles of 2^LOG_M transform positions x 2^LOG_K rows; each of
+// the T threads holds 2^LOG_V elements in registers per round (radix 2^LOG_V).
+template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
 struct Shape {
-  static constexpr int M = 1 << LOG_M, K = 1 << LOG_K, TILE = M * K, T = TILE / 8;
+  static constexpr int M = 1 << LOG_M, K = 1 << LOG_K, TILE = M * K, T = TILE >> LOG_V;
   static constexpr int BIT_LO = COL ? LOG_N - LOG_M : 0;  // lowest index bit this pass transforms
   static constexpr int S0 = LOG_N - BIT_LO - LOG_M;      // global stage of local stage 0
   static constexpr int TILES = 1 << (LOG_N - LOG_M - LOG_K);
@@ -36,10 +38,10 @@ struct Shape {
 // unevenly), so only the first offset is computed.  At stage st the group
 // needs 2^st distinct twiddles, one per value of the top st bits of j; each
 // is loaded once.
-template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R>
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R, int LOG_V = 3>
 __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int sig0, uint64_t q) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
-  constexpr int G = 1 << R, GPT = 8 >> R;
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
+  constexpr int G = 1 << R, GPT = (1 << LOG_V) >> R;
   const uint64_t q2 = q + q;
   const int lo_bits = LOG_M - sig0 - R;
   const uint32_t lo_mask = (1u << lo_bits) - 1;
@@ -99,9 +101,9 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
 // Stage the twiddle pairs of one pass into shared memory: a column pass
 // needs tw[0 .. M), a row pass for rows f0 .. f0+K-1 needs, per local stage
 // sigma, the K*2^sigma entries from 2^(S0+sigma) + f0*2^sigma on.
-template <int LOG_N, int LOG_M, int LOG_K, bool COL>
+template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
 __device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, COL>;
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   if (COL) {
     for (uint32_t e = threadIdx.x; e < (uint32_t)S::M; e += S::T) stw[e] = __ldg(tw + e);
   } else {
@@ -117,17 +119,18 @@ __device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2
 }
 
 // All rounds of one pass on the tile in shared memory (ends with a barrier).
-template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL>
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
 __device__ __forceinline__ void run_rounds(uint64_t* sm, const ulonglong2* stw, uint64_t q) {
-  constexpr int NR = (LOG_M + 2) / 3;
+  constexpr int NR = (LOG_M + LOG_V - 1) / LOG_V;
 #pragma unroll
   for (int rr = 0; rr < NR; ++rr) {
     const int r = INV ? NR - 1 - rr : rr;
-    const int sig0 = 3 * r;
-    const int R = LOG_M - sig0 < 3 ? LOG_M - sig0 : 3;
-    if (R == 3) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3>(sm, stw, sig0, q);
-    else if (R == 2) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2>(sm, stw, sig0, q);
-    else round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1>(sm, stw, sig0, q);
+    const int sig0 = LOG_V * r;
+    const int R = LOG_M - sig0 < LOG_V ? LOG_M - sig0 : LOG_V;
+    if (R == 4) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, (LOG_V >= 4 ? 4 : 1), LOG_V>(sm, stw, sig0, q);
+    else if (R == 3) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3, LOG_V>(sm, stw, sig0, q);
+    else if (R == 2) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2, LOG_V>(sm, stw, sig0, q);
+    else round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1, LOG_V>(sm, stw, sig0, q);
     __syncthreads();
   }
 }
