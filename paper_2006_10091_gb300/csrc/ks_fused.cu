@@ -1,515 +1,8 @@
-// ks_fused.cu -- hybrid key switching with ModUp fused into the NTT's first
-// pass and the key inner product fused into its second pass (N = 2^12 ..
-// 2^16).  Same arithmetic and the same residues as the unfused sequence in
-// ops.cu (iNTT, k_modup, NTT, k_inner_product); what it saves is the round
-// trips of the converted digits through memory:
-//  * ks_modup_col: a CTA of digit j and target limb t builds its column tile
-//    straight from the coefficient-form input (the digit's limbs, converted
-//    to prime t as in k_modup) and runs the column pass; the ModUp output is
-//    never written;
-//  * ks_row_ip: a CTA of target limb t and one row tile keeps two
-//    accumulators per residue in registers, and for every digit finishes the
-//    row pass of that digit's tile (or, on the digit's own limb, reads the
-//    input as it is) and adds its products with the two key polynomials; the
-//    transformed digits are never written.
-#include <algorithm>
-
-#include "he_ops.h"
-#include "ntt2.cuh"
+// ks_fused.cu -- entry points of the fused key-switching kernels (kernels in
+// ks_fused.cuh, instantiated per ring size in ks_fused_n12.cu .. n16.cu).
+#include "ks_fused.cuh"
 
 namespace he {
-
-// Dynamic shared memory the all-targets conversion kernels may take.
-constexpr size_t kModupAllSmem = 160 * 1024;
-
-struct KsFusedArgs {
-  const uint64_t* d;     // input, evaluation form: count x [level][N] at d_stride
-  const uint64_t* d2c;   // input, coefficient form: count x [level][N]
-  uint64_t* ext;         // column-pass outputs: count x [beta][nt][N]
-  uint64_t* acc;         // accumulators: count x [2][nt][N]
-  const uint64_t* evk;   // [beta_top][2][np][N]
-  const uint64_t* evk_sh;  // Shoup companions of evk, same layout
-  uint64_t d_stride;
-  uint64_t gal;            // d is read through the automorphism X -> X^gal (0: none)
-  uint32_t level, alpha, beta, L, np, nt;
-  const PrimeDev* primes;
-  const ulonglong2* tw;
-  const ulonglong2* itw;   // inverse twiddles
-  int half;                // d2c holds the inverse transform's row pass only (ks_modup_col_all finishes it)
-  const uint64_t* consts;  // ModUp constant tables
-  uint32_t lo[HE_MAX_PRIMES], cnt[HE_MAX_PRIMES];
-  uint64_t off[HE_MAX_PRIMES];
-};
-
-__device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level, uint32_t L) {
-  return t < level ? t : L + t - level;
-}
-
-// Column pass with the ModUp conversion in its load.  Grid: count * beta * nt * TILES.
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFusedArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
-  constexpr uint32_t N = 1u << LOG_N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t t = b % a.nt;
-  b /= a.nt;
-  const uint32_t j = b % a.beta, i = b / a.beta;
-  const uint32_t lo = a.lo[j], cnt = a.cnt[j];
-  if (t >= lo && t < lo + cnt) return;  // the digit's own limbs are used as they are
-  const uint32_t prime = ks_prime(t, a.level, a.L);
-  const PrimeDev pr = a.primes[prime];
-  stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
-  const uint64_t* tab = a.consts + a.off[j];
-  const uint64_t* mat = tab + 2 * cnt;
-  const uint64_t* mat_sh = mat + (size_t)cnt * a.np;
-  const uint64_t* x = a.d2c + (size_t)i * a.level * N;
-  const uint64_t q2 = pr.q + pr.q;
-#pragma unroll 2
-  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-    const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
-    const uint32_t e = S::gidx(tile, k, xx);
-    uint64_t y;
-    if (cnt == 1) {
-      y = reduce64(__ldg(x + (size_t)lo * N + e), pr);  // Q_j / q_lo = 1
-    } else {
-      // products by the constant (Q_j/q_i) mod q_t are Shoup products in [0, 2q), kept in [0, 2q)
-      y = 0;
-      for (uint32_t u = 0; u < cnt; ++u) {
-        const uint64_t qa = a.primes[lo + u].q;
-        const uint64_t v = mul_shoup(__ldg(x + (size_t)(lo + u) * N + e), tab[2 * u], tab[2 * u + 1], qa);
-        y += mul_shoup_lazy(v, mat[(size_t)u * a.np + prime], mat_sh[(size_t)u * a.np + prime], pr.q);
-        y = y >= q2 ? y - q2 : y;
-      }
-      y = y >= pr.q ? y - pr.q : y;
-    }
-    sm[idx + (idx >> 3)] = y;
-  }
-  __syncthreads();
-  uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
-  if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-  else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-#pragma unroll 4
-  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-    const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
-    out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
-  }
-}
-
-// The same column pass for every target limb of one digit and tile in one
-// CTA: the digit's limbs are read once and their products by
-// (Q_j/q_i)^-1 mod q_i (or, for a one-limb digit, the limb itself) are kept
-// in shared memory for all targets.  Grid: count * beta * TILES; dynamic
-// shared memory holds cnt_max * TILE more words.
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(KsFusedArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
-  constexpr uint32_t N = 1u << LOG_N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint64_t* wv = sm + S::TILE + S::TILE / 8;  // [cnt][TILE]
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t j = b % a.beta, i = b / a.beta;
-  const uint32_t lo = a.lo[j], cnt = a.cnt[j];
-  const uint64_t* tab = a.consts + a.off[j];
-  const uint64_t* mat = tab + 2 * cnt;
-  const uint64_t* mat_sh = mat + (size_t)cnt * a.np;
-  const uint64_t* x = a.d2c + (size_t)i * a.level * N;
-  for (uint32_t u = 0; u < cnt; ++u) {
-    const PrimeDev pa = a.primes[lo + u];
-    if (a.half) {
-      // the inverse transform's column pass on this tile, then the scaling by N^-1
-      stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.itw + (size_t)(lo + u) * N, tile);
-#pragma unroll 4
-      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-        const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
-        sm[idx + (idx >> 3)] = __ldg(x + (size_t)(lo + u) * N + e);
-      }
-      __syncthreads();
-      run_rounds<true, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pa.q);
-    }
-#pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t xv;
-      if (a.half) {
-        xv = mul_shoup(sm[idx + (idx >> 3)], pa.n_inv, pa.n_inv_sh, pa.q);
-      } else {
-        const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
-        xv = __ldg(x + (size_t)(lo + u) * N + e);
-      }
-      wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], pa.q);
-    }
-    // the next limb's staging overwrites stw and sm: wait for every thread
-    __syncthreads();
-  }
-  for (uint32_t t = 0; t < a.nt; ++t) {
-    if (t >= lo && t < lo + cnt) continue;  // the digit's own limbs are used as they are
-    const uint32_t prime = ks_prime(t, a.level, a.L);
-    const PrimeDev pr = a.primes[prime];
-    const uint64_t q2 = pr.q + pr.q;
-    // the previous target's rounds ended with a barrier, and its write-out
-    // reads only the words each thread rewrites below
-    stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
-#pragma unroll 2
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t y;
-      if (cnt == 1) {
-        y = reduce64(wv[idx], pr);  // Q_j / q_lo = 1
-      } else {  // Shoup products by (Q_j/q_i) mod q_t, kept in [0, 2q)
-        y = 0;
-        for (uint32_t u = 0; u < cnt; ++u) {
-          y += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.np + prime],
-                              mat_sh[(size_t)u * a.np + prime], pr.q);
-          y = y >= q2 ? y - q2 : y;
-        }
-        y = y >= pr.q ? y - pr.q : y;
-      }
-      sm[idx + (idx >> 3)] = y;
-    }
-    __syncthreads();
-    uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
-    if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-#pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
-      out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
-    }
-  }
-}
-
-// Row pass of every digit's tile fused with the key inner product.
-// Grid: count * nt * TILES.  Each thread owns residues idx = tid + u*T.
-// MINB: CTAs per SM the register allocation must allow (2: no spills, 128
-// registers; 3: 80 registers with a few spilled words), chosen at run time.
-template <int LOG_N, int LOG_M, int LOG_K, int MINB>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(KsFusedArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
-  constexpr uint32_t N = 1u << LOG_N;
-  constexpr int PER = S::TILE / S::T;  // 8
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t t = b % a.nt, i = b / a.nt;
-  const uint32_t prime = ks_prime(t, a.level, a.L);
-  const PrimeDev pr = a.primes[prime];
-  const uint64_t q = pr.q, q2 = q + q;
-  const bool lazy = q < (1ull << 58);
-  // Products by key words are Shoup products in [0, 2q); they are summed
-  // without reduction while beta of them stay below 2^64, else kept in [0, 2q).
-  const bool acc_lazy = q < ~0ull / (2ull * a.beta);
-  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
-  uint64_t acc0[PER], acc1[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) acc0[u] = acc1[u] = 0;
-  auto mac = [&](uint64_t& acc, uint64_t x, uint64_t k, uint64_t ksh) {
-    acc += mul_shoup_lazy(x, k, ksh, q);
-    if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
-  };
-  for (uint32_t j = 0; j < a.beta; ++j) {
-    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
-    const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
-    const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
-    const uint64_t *kb = a.evk + kb_off, *ka = a.evk + ka_off;
-    const uint64_t *kbs = a.evk_sh + kb_off, *kas = a.evk_sh + ka_off;
-    if (own) {
-      const uint64_t* dd = a.d + (size_t)i * a.d_stride + (size_t)t * N;
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const uint32_t idx = threadIdx.x + u * S::T;
-        const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-        const uint64_t x = __ldg(dd + (a.gal ? automorph_src(e, a.gal, LOG_N) : e));
-        mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
-        mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
-      }
-      continue;
-    }
-    const uint64_t* src = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
-    }
-    __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      const uint64_t v = sm[idx + (idx >> 3)];
-      const uint64_t x = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
-      mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
-      mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
-    }
-    __syncthreads();  // the tile buffer is reused by the next digit
-  }
-  uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
-  uint64_t* o1 = a.acc + ((size_t)i * 2 * a.nt + a.nt + t) * N;
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const uint32_t idx = threadIdx.x + u * S::T;
-    const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-    o0[e] = reduce64(acc0[u], pr);
-    o1[e] = reduce64(acc1[u], pr);
-  }
-}
-
-// ---- ModDown, fused the same way ------------------------------------------
-// The P-part of the accumulators (coefficient form after its inverse NTT) is
-// converted to each target limb inside the load of the forward NTT's column
-// pass (as k_moddown_conv: conv = BConv(y + h) - h), and the row pass ends
-// with the combine of k_ks_combine: out = add + (acc_Q - NTT(conv)) * P^-1.
-// A CTA handles both parts of one ciphertext for one limb and tile, so the
-// staged twiddles serve two transforms.
-struct MdArgs {
-  // The P part (coefficient form): ciphertext i, part p, special prime u at
-  // yP + i*yp_stride + p*yp_pstride + u*N.
-  const uint64_t* yP;
-  uint64_t yp_stride, yp_pstride;
-  CtBatch accq;         // the Q part (evaluation form), limbs 0 .. level-1
-  uint64_t* conv;       // count x [2][level][N]: column-pass outputs
-  CtBatch add, out;
-  int has_add;          // 0 none, 1 part 0 only, 2 both parts
-  uint64_t add_gal;     // the addend is read through the automorphism X -> X^add_gal (0: none)
-  uint32_t level, alpha, L;
-  uint32_t sp0;         // prime index of the first special prime (L; l for a rescale by q_l)
-  const PrimeDev* primes;
-  const ulonglong2* tw;
-  const uint64_t* md;   // ModDown tables (params.cu)
-};
-
-// Grid: count * 2 * TILES; the conversion's per-special-prime terms and the
-// multiple v of P are computed once per element and kept in shared memory
-// ([alpha][TILE] words and [TILE] counts) for all level target limbs.
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, true>;
-  constexpr uint32_t N = 1u << LOG_N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint64_t* wv = sm + S::TILE + S::TILE / 8;                          // [alpha][TILE]
-  uint32_t* vv = reinterpret_cast<uint32_t*>(wv + (size_t)a.alpha * S::TILE);  // [TILE]
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t p = b % 2, i = b / 2;
-  const uint64_t* mat = a.md + 2 * a.alpha;
-  const uint64_t* hP = mat + (size_t)a.alpha * a.L + 2 * a.L;
-  const uint64_t* mat_sh = hP + a.alpha + a.L;
-  const uint64_t* wlo = mat_sh + (size_t)a.alpha * a.L;
-  const uint64_t* yP = a.yP + (size_t)i * a.yp_stride + (size_t)p * a.yp_pstride;
-  // exact conversion: sum_u w_u (P/p_u) - v P, w_u = [y_u (P/p_u)^-1]_{p_u},
-  // v = floor(sum_u w_u / p_u)
-#pragma unroll 2
-  for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-    const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
-    uint64_t fs = 0;
-    uint32_t v = 0;
-    for (uint32_t u = 0; u < a.alpha; ++u) {
-      const PrimeDev& pp = a.primes[a.sp0 + u];
-      const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pp.q);
-      const uint64_t w = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
-      wv[(size_t)u * S::TILE + idx] = w;
-      if (a.alpha > 1) frac_acc(w, pp.one_sh, wlo[u], &fs, &v);
-    }
-    vv[idx] = v;
-  }
-  for (uint32_t t = 0; t < a.level; ++t) {
-    const PrimeDev pr = a.primes[t];
-    const uint64_t q2 = pr.q + pr.q, hQ = hP[a.alpha + t];
-    const uint64_t* vP = wlo + a.alpha + a.L + (size_t)t * 8;  // v P mod q_t, v < 8
-    stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
-#pragma unroll 2
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t acc = 0;  // Shoup products by (P/p_u) mod q_t, kept in [0, 2q)
-      for (uint32_t u = 0; u < a.alpha; ++u) {
-        acc += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t],
-                              pr.q);
-        acc = acc >= q2 ? acc - q2 : acc;
-      }
-      acc = acc >= pr.q ? acc - pr.q : acc;
-      acc = sub_mod(acc, vP[vv[idx]], pr.q);
-      sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
-    }
-    __syncthreads();
-    if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-    uint64_t* out = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
-#pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
-      out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
-    }
-  }
-}
-
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(MdArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
-  constexpr uint32_t N = 1u << LOG_N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t t = b % a.level, i = b / a.level;
-  const PrimeDev pr = a.primes[t];
-  const uint64_t q = pr.q;
-  const bool lazy = q < (1ull << 58);
-  const uint64_t* pinv = a.md + 2 * a.alpha + (size_t)a.alpha * a.L;
-  const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
-  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)t * N, tile);
-  constexpr int PER = S::TILE / S::T;
-  for (uint32_t p = 0; p < 2; ++p) {
-    const uint64_t* src = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
-#pragma unroll 4
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
-      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
-    }
-    // the epilogue's operands are loaded before the transform so that their
-    // latency overlaps its rounds
-    const uint64_t* accq = cpoly(a.accq, i, p, t, N);
-    const bool add = a.has_add == 2 || (a.has_add == 1 && p == 0);
-    const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
-    uint64_t av[PER], dv[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      av[u] = __ldg(accq + e);
-      dv[u] = add ? __ldg(ad + (a.add_gal ? automorph_src(e, a.add_gal, LOG_N) : e)) : 0;
-    }
-    __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
-    uint64_t* o = cpoly(a.out, i, p, t, N);
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      const uint64_t v = sm[idx + (idx >> 3)];
-      const uint64_t cv = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
-      uint64_t r = mul_shoup(sub_mod(av[u], cv, q), w, wsh, q);
-      if (add) r = add_mod(r, dv[u], q);
-      o[e] = r;
-    }
-  }
-}
-
-template <int LOG_N, int M1, int K1, int M2, int K2>
-static int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
-  using SC = Shape<LOG_N, M1, K1, true>;
-  using SR = Shape<LOG_N, M2, K2, false>;
-  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
-                     (sizeof(uint64_t) * a.alpha + sizeof(uint32_t)) * SC::TILE;
-  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
-  if (smc > kModupAllSmem) {  // too many special primes for this tile: the caller runs the unfused sequence
-    *handled = false;
-    return HE_OK;
-  }
-  *handled = true;
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kModupAllSmem));
-    HE_CUDA(cudaFuncSetAttribute(md_row_combine<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    attr_set |= 1ull << c->device;
-  }
-  const double n = (double)(1u << LOG_N);
-  const double polys = 2.0 * count * a.level;  // transformed limbs
-  const bool rescale = a.sp0 != a.L;
-  {
-    const size_t blocks = (size_t)count * 2 * SC::TILES;
-    ProfScope prof(c, rescale ? "rescale_ntt" : "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha),
-                   n * 8 * (2.0 * count * a.alpha + polys));
-    md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
-  }
-  HE_CUDA(cudaGetLastError());
-  {
-    const size_t blocks = (size_t)count * a.level * SR::TILES;
-    const double addw = a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
-    ProfScope prof(c, rescale ? "rescale_ntt_final" : "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n),
-                   n * 8 * (3.0 * polys + addw));
-    md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
-  }
-  HE_CUDA(cudaGetLastError());
-  return HE_OK;
-}
-
-// Dynamic shared memory of ks_modup_col_all for these digits.
-template <int LOG_N, int M1, int K1>
-static size_t ks_all_smem(const he_ctx* c, uint32_t beta, const uint32_t* cnt) {
-  using SC = Shape<LOG_N, M1, K1, true>;
-  uint32_t cnt_max = 0;
-  for (uint32_t j = 0; j < beta; ++j) cnt_max = std::max(cnt_max, cnt[j]);
-  (void)c;
-  return sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
-         sizeof(uint64_t) * (size_t)cnt_max * SC::TILE;
-}
-
-template <int LOG_N, int M1, int K1, int M2, int K2>
-static int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  using SC = Shape<LOG_N, M1, K1, true>;
-  using SR = Shape<LOG_N, M2, K2, false>;
-  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
-  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-    HE_CUDA(cudaFuncSetAttribute(ks_modup_col_all<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kModupAllSmem));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    attr_set |= 1ull << c->device;
-  }
-  const double n = (double)(1u << LOG_N);
-  double own = 0;  // limbs each ciphertext takes as they are
-  for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
-  const double conv = (double)a.beta * a.nt - own;  // converted limbs per ciphertext
-  double conv_products = 0;  // basis-conversion products (none when a digit is one limb)
-  for (uint32_t j = 0; j < a.beta; ++j)
-    if (a.cnt[j] > 1) conv_products += (double)(a.nt - a.cnt[j]) * a.cnt[j];
-  // work = modular products: butterflies, conversion products, inner-product products
-  {
-    // with a half-transformed input the kernel also runs the inverse column pass of the level input limbs
-    const double inv_bfly = a.half ? (double)a.level * n / 2 * M1 + (double)a.level * n : 0.0;
-    ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n + inv_bfly),
-                   count * n * 8 * (a.level + conv));
-    const size_t sma = ks_all_smem<LOG_N, M1, K1>(c, a.beta, a.cnt);
-    if (a.half && sma > kModupAllSmem) return fail(HE_EINVAL, "ks_fused: half-transformed input needs the all-targets kernel");
-    if (sma <= kModupAllSmem) {  // one CTA per digit and tile, all targets
-      const size_t blocks = (size_t)count * a.beta * SC::TILES;
-      ks_modup_col_all<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, sma, c->stream>>>(a);
-    } else {
-      const size_t blocks = (size_t)count * a.beta * a.nt * SC::TILES;
-      ks_modup_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
-    }
-  }
-  HE_CUDA(cudaGetLastError());
-  {
-    const size_t blocks = (size_t)count * a.nt * SR::TILES;
-    ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * a.beta * a.nt * n),
-                   count * n * 8 * (conv + own + 2.0 * a.beta * a.nt + 2.0 * a.nt));
-    if (c->ks_row_ctas == 3) ks_row_ip<LOG_N, M2, K2, 3><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
-    else ks_row_ip<LOG_N, M2, K2, 2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
-  }
-  HE_CUDA(cudaGetLastError());
-  return HE_OK;
-}
 
 // ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
 // sets *handled when N has a compiled shape.
@@ -544,23 +37,12 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
     a.off[j] = mc.off;
   }
   *handled = true;
-  const int sh = c->ntt_shape;  // the tile shapes of ntt2.cu
-  switch (c->log_n) {
-    case 12:
-      return sh == 1 ? ks_fused_run<12, 5, 6, 7, 4>(c, a, count)
-           : sh == 2 ? ks_fused_run<12, 3, 8, 9, 2>(c, a, count) : ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
-    case 13:
-      return sh == 1 ? ks_fused_run<13, 6, 5, 7, 4>(c, a, count)
-           : sh == 2 ? ks_fused_run<13, 4, 7, 9, 2>(c, a, count) : ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
-    case 14:
-      return sh == 1 ? ks_fused_run<14, 8, 3, 6, 5>(c, a, count)
-           : sh == 2 ? ks_fused_run<14, 5, 6, 9, 2>(c, a, count) : ks_fused_run<14, 7, 4, 7, 4>(c, a, count);
-    case 15:
-      return sh == 1 ? ks_fused_run<15, 7, 4, 8, 3>(c, a, count)
-           : sh == 2 ? ks_fused_run<15, 6, 5, 9, 2>(c, a, count) : ks_fused_run<15, 8, 4, 7, 4>(c, a, count);
-    default:
-      return sh == 1 ? ks_fused_run<16, 7, 4, 9, 2>(c, a, count)
-           : sh == 2 ? ks_fused_run<16, 6, 5, 10, 1>(c, a, count) : ks_fused_run<16, 8, 4, 8, 3>(c, a, count);
+  switch (c->log_n) {  // the tile shapes of ntt2.cu
+    case 12: return ks_fused_n12(c, a, count);
+    case 13: return ks_fused_n13(c, a, count);
+    case 14: return ks_fused_n14(c, a, count);
+    case 15: return ks_fused_n15(c, a, count);
+    default: return ks_fused_n16(c, a, count);
   }
 }
 
@@ -626,23 +108,12 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
 }
 
 static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
-  const int sh = c->ntt_shape;
   switch (c->log_n) {
-    case 12:
-      return sh == 1 ? md_fused_run<12, 5, 6, 7, 4>(c, a, count, handled)
-           : sh == 2 ? md_fused_run<12, 3, 8, 9, 2>(c, a, count, handled) : md_fused_run<12, 6, 5, 6, 5>(c, a, count, handled);
-    case 13:
-      return sh == 1 ? md_fused_run<13, 6, 5, 7, 4>(c, a, count, handled)
-           : sh == 2 ? md_fused_run<13, 4, 7, 9, 2>(c, a, count, handled) : md_fused_run<13, 7, 4, 6, 5>(c, a, count, handled);
-    case 14:
-      return sh == 1 ? md_fused_run<14, 8, 3, 6, 5>(c, a, count, handled)
-           : sh == 2 ? md_fused_run<14, 5, 6, 9, 2>(c, a, count, handled) : md_fused_run<14, 7, 4, 7, 4>(c, a, count, handled);
-    case 15:
-      return sh == 1 ? md_fused_run<15, 7, 4, 8, 3>(c, a, count, handled)
-           : sh == 2 ? md_fused_run<15, 6, 5, 9, 2>(c, a, count, handled) : md_fused_run<15, 8, 4, 7, 4>(c, a, count, handled);
-    default:
-      return sh == 1 ? md_fused_run<16, 7, 4, 9, 2>(c, a, count, handled)
-           : sh == 2 ? md_fused_run<16, 6, 5, 10, 1>(c, a, count, handled) : md_fused_run<16, 8, 4, 8, 3>(c, a, count, handled);
+    case 12: return md_fused_n12(c, a, count, handled);
+    case 13: return md_fused_n13(c, a, count, handled);
+    case 14: return md_fused_n14(c, a, count, handled);
+    case 15: return md_fused_n15(c, a, count, handled);
+    default: return md_fused_n16(c, a, count, handled);
   }
 }
 
@@ -657,19 +128,13 @@ bool ks_converts_per_digit(const he_ctx* c, uint32_t level) {
   const uint32_t alpha = (uint32_t)c->alpha, beta = (level + alpha - 1) / alpha;
   uint32_t cnt[HE_MAX_PRIMES];
   for (uint32_t j = 0; j < beta; ++j) cnt[j] = c->modup[level][j].cnt;
-  const int sh = c->ntt_shape;
   size_t smem = 0;
   switch (c->log_n) {
-    case 12: smem = sh == 1 ? ks_all_smem<12, 5, 6>(c, beta, cnt) : sh == 2 ? ks_all_smem<12, 3, 8>(c, beta, cnt)
-                                                                  : ks_all_smem<12, 6, 5>(c, beta, cnt); break;
-    case 13: smem = sh == 1 ? ks_all_smem<13, 6, 5>(c, beta, cnt) : sh == 2 ? ks_all_smem<13, 4, 7>(c, beta, cnt)
-                                                                  : ks_all_smem<13, 7, 4>(c, beta, cnt); break;
-    case 14: smem = sh == 1 ? ks_all_smem<14, 8, 3>(c, beta, cnt) : sh == 2 ? ks_all_smem<14, 5, 6>(c, beta, cnt)
-                                                                  : ks_all_smem<14, 7, 4>(c, beta, cnt); break;
-    case 15: smem = sh == 1 ? ks_all_smem<15, 7, 4>(c, beta, cnt) : sh == 2 ? ks_all_smem<15, 6, 5>(c, beta, cnt)
-                                                                  : ks_all_smem<15, 8, 4>(c, beta, cnt); break;
-    default: smem = sh == 1 ? ks_all_smem<16, 7, 4>(c, beta, cnt) : sh == 2 ? ks_all_smem<16, 6, 5>(c, beta, cnt)
-                                                                  : ks_all_smem<16, 8, 4>(c, beta, cnt); break;
+    case 12: smem = ks_all_smem_n12(c, beta, cnt); break;
+    case 13: smem = ks_all_smem_n13(c, beta, cnt); break;
+    case 14: smem = ks_all_smem_n14(c, beta, cnt); break;
+    case 15: smem = ks_all_smem_n15(c, beta, cnt); break;
+    default: smem = ks_all_smem_n16(c, beta, cnt); break;
   }
   return smem <= kModupAllSmem;
 }
