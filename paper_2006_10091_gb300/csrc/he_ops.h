@@ -42,7 +42,9 @@ size_t mul_words(const he_ctx* c, uint32_t level, uint32_t count, bool rescale);
 size_t rot_words(const he_ctx* c, uint32_t level, uint32_t count);
 size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count);
 
-// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts.  gal != 0:
+// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts, 3 (with gal)
+// add the addend permuted to part 0 and the addend itself to both parts
+// (out = add + rotate(add) for a rotation of add).  gal != 0:
 // d and the addend are read through the automorphism X -> X^gal (fused
 // kernels only; the output must not overlap them).
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
@@ -55,6 +57,7 @@ int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t co
 int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out,
                  Arena& ar);
 int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count);
+int rotate_add_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out, Arena& ar);
 int mul_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int add_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int copy_batch(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, uint32_t count);

@@ -281,7 +281,7 @@ struct MdArgs {
   CtBatch accq;         // the Q part (evaluation form), limbs 0 .. level-1
   uint64_t* conv;       // count x [2][level][N]: column-pass outputs
   CtBatch add, out;
-  int has_add;          // 0 none, 1 part 0 only, 2 both parts
+  int has_add;          // 0 none, 1 part 0 only, 2 both parts, 3 permuted on part 0 plus plain on both
   uint64_t add_gal;     // the addend is read through the automorphism X -> X^add_gal (0: none)
   uint32_t level, alpha, L;
   uint32_t sp0;         // prime index of the first special prime (L; l for a rescale by q_l)
@@ -384,7 +384,9 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
     // the epilogue's operands are loaded before the transform so that their
     // latency overlaps its rounds
     const uint64_t* accq = cpoly(a.accq, i, p, t, N);
-    const bool add = a.has_add == 2 || (a.has_add == 1 && p == 0);
+    const bool add = a.has_add >= 2 || (a.has_add == 1 && p == 0);
+    const bool add_perm = (a.has_add == 1 || a.has_add == 3) && p == 0 && a.add_gal;  // part 0 through the automorphism
+    const bool add_plain = a.has_add == 3 || (add && !add_perm);                     // the addend as it is
     const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
     uint64_t av[PER], dv[PER];
 #pragma unroll
@@ -392,7 +394,9 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
       const uint32_t idx = threadIdx.x + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       av[u] = __ldg(accq + e);
-      dv[u] = add ? __ldg(ad + (a.add_gal ? automorph_src(e, a.add_gal, LOG_N) : e)) : 0;
+      uint64_t d = add_plain ? __ldg(ad + e) : 0;
+      if (add_perm) d = add_mod(d, __ldg(ad + automorph_src(e, a.add_gal, LOG_N)), q);
+      dv[u] = d;
     }
     __syncthreads();
     if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
@@ -442,7 +446,7 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   HE_CUDA(cudaGetLastError());
   {
     const size_t blocks = (size_t)count * a.level * SR::TILES;
-    const double addw = a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
+    const double addw = a.has_add == 3 ? 1.5 * polys : a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
     ProfScope prof(c, rescale ? "rescale_ntt_final" : "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n),
                    n * 8 * (3.0 * polys + addw));
     md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);

@@ -182,9 +182,9 @@ static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtB
   };
   // U = Z_k * W, then the rotate-and-sum over the F feature positions
   HE_TRY(mul_relin_batch(c, Zc, Wc, l0, m, b.U, true, fresh()));
-  for (uint32_t t = 0; t < P.logF; ++t) {
-    HE_TRY(rotate_batch(c, b.U, l0 - 1, m, gl.in[t], b.Tmp, fresh()));
-    HE_TRY(addsub_batch(c, b.U, b.Tmp, b.U, 0, l0 - 1, m));
+  for (uint32_t t = 0; t < P.logF; ++t) {  // U <- U + rotate(U), alternating buffers
+    HE_TRY(rotate_add_batch(c, b.U, l0 - 1, m, gl.in[t], b.Tmp, fresh()));
+    std::swap(b.U, b.Tmp);
   }
   // T = M^2; A = c3 M; C = T A
   HE_TRY(mul_relin_batch(c, b.U, b.U, l0 - 1, m, b.T, true, fresh()));
@@ -216,16 +216,18 @@ static int lr_finish(he_ctx* c, const LrPlan& P, const LrGal& gl, const int64_t*
     ops.off = 0;
     return ops;
   };
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    HE_TRY(rotate_batch(c, G, l0 - 4, count, gl.up[t], H1, fresh()));
-    HE_TRY(addsub_batch(c, G, H1, G, 0, l0 - 4, count));
+  for (uint32_t t = 0; t < P.logg; ++t) {  // G <- G + rotate(G), alternating buffers
+    HE_TRY(rotate_add_batch(c, G, l0 - 4, count, gl.up[t], H1, fresh()));
+    std::swap(G, H1);
   }
   HE_TRY(mul_plain_dev(c, G, mask, H1, l0 - 4, count, fresh()));
   HE_TRY(rescale_batch(c, H1, l0 - 4, count, R, fresh()));
+  const CtBatch R_out = R;
   for (uint32_t t = 0; t < P.logg; ++t) {
-    HE_TRY(rotate_batch(c, R, l0 - 5, count, gl.down[t], H1, fresh()));
-    HE_TRY(addsub_batch(c, R, H1, R, 0, l0 - 5, count));
+    HE_TRY(rotate_add_batch(c, R, l0 - 5, count, gl.down[t], H1, fresh()));
+    std::swap(R, H1);
   }
+  if (R.base != R_out.base) HE_TRY(copy_batch(c, R, R_out, l0 - 5, count));
   return HE_OK;
 }
 

@@ -140,6 +140,7 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   bool md_done = false;
   HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, &md_done));
   if (md_done) return HE_OK;
+  const CtBatch add_in = add;
   if (gal && add_mode) {  // the unfused combine reads its addend as it is: permute part 0 first
     uint64_t* pa = ar.take<uint64_t>((size_t)count * level * n);
     if (!pa) return fail(HE_ENOMEM, "key switch scratch too small");
@@ -148,6 +149,7 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
     HE_CUDA(cudaGetLastError());
     add = P;
   }
+  const int combine_mode = add_mode == 3 ? 1 : add_mode;  // mode 3 adds the unpermuted input afterwards
   {
     ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
     k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
@@ -160,10 +162,11 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   {
     ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
     k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha, L,
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, combine_mode, out, 0, 2, level, alpha, L,
         count, c->log_n, c->d_primes, pinv);
   }
   HE_CUDA(cudaGetLastError());
+  if (add_mode == 3) return addsub_batch(c, out, add_in, out, 0, level, count);
   return HE_OK;
 }
 
@@ -238,6 +241,24 @@ int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t 
   }
   HE_CUDA(cudaGetLastError());
   return keyswitch_batch(c, t + (size_t)level * n, (size_t)2 * level * n, level, count, key, T, 1, out, ar);
+}
+
+// out = A + rotate(A): with the fused kernels the sum is formed in the key
+// switch's last kernel (add_mode 3), otherwise a rotation and an addition.
+// out must not overlap A.
+int rotate_add_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out, Arena& ar) {
+  const uint32_t n = c->n;
+  const uint64_t* key = galois_key(c, gal);
+  if (!key) return fail(HE_ENOKEY, "no Galois key for this rotation");
+  const char* a_lo = (const char*)A.base;
+  const char* a_hi = a_lo + sizeof(uint64_t) * ((size_t)(count - 1) * A.stride + (size_t)2 * A.cap * n);
+  const char* o_lo = (const char*)out.base;
+  const char* o_hi = o_lo + sizeof(uint64_t) * ((size_t)(count - 1) * out.stride + (size_t)2 * out.cap * n);
+  if (!(o_hi <= a_lo || a_hi <= o_lo)) return fail(HE_EINVAL, "rotate_add_batch: output overlaps the input");
+  if (ks_fusable(c))
+    return keyswitch_batch(c, A.base + (size_t)A.cap * n, A.stride, level, count, key, A, 3, out, ar, gal);
+  HE_TRY(rotate_batch(c, A, level, count, gal, out, ar));
+  return addsub_batch(c, out, A, out, 0, level, count);
 }
 
 int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count) {

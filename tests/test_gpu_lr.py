@@ -291,3 +291,30 @@ def test_batched_import_export_round_trip():
         back = np.zeros_like(data)
         he.he_ct_export_batch(ctx, cts, back)
         assert np.array_equal(back, data)
+
+
+def test_lr_step_and_inference_bit_exact_fused_kernels():
+    """At N = 2^12 the step runs on the fused kernels (key switch, ModDown,
+    rescale, rotate-and-add) with two special primes: residues equal the
+    oracle's op-for-op evaluation."""
+    log_n, g = 12, 8
+    n_slots = (1 << log_n) // 2
+    pair = Pair(log_n, 7, 40, 2, 55, 2.0 ** 40, seed=13, rots=rot_steps(n_slots, g))
+    he = pair.he
+    coeffs = table2()["huber"]
+    ms = [workloads.int_poly(600 + k, pair.n, 1 << 28) for k in range(3)]
+    mw = workloads.int_poly(609, pair.n, 1 << 28)
+    Zg = pair.g.new_ct(7, 3)
+    for k, m in enumerate(ms):
+        he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 7, Zg[k], cid=600 + k)
+    Wg = pair.gpu_enc(mw, 7, 609, scale=2.0 ** 40)
+    Zo = [pair.orc_enc(m, 7, 600 + k, scale=2.0 ** 40) for k, m in enumerate(ms)]
+    Wo = pair.orc_enc(mw, 7, 609, scale=2.0 ** 40)
+    out = pair.g.new_ct(7)
+    he.he_lr_gradient_step(pair.g, Zg, Wg, he.lr_config(coeffs, 0.125, g, 2.0 ** 30), out)
+    assert_same_residues(out, pair.o.lr_gradient_step(Zo, Wo, coeffs, 0.125, g, 2.0 ** 30), he, pair.g)
+    S = pair.g.new_ct(7, 3)
+    he.he_lr_inference_workers(pair.g, [(Zg, Wg, S)], he.lr_config(coeffs, 1.0, g, 2.0 ** 40))
+    want = pair.o.lr_inference(Zo, Wo, coeffs, 1.0, g)
+    for k in range(3):
+        assert_same_residues(S[k], want[k], he, pair.g)
