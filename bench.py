@@ -777,8 +777,10 @@ def run_micro(args):
 
 def run_micro_keyswitch(args):
     """Rotation by 8 slots (automorphism + key switching) of `--polys`
-    ciphertexts at level 7 of the benchmark parameters, with the per-class
-    kernel times of the batch."""
+    ciphertexts, with the per-class kernel times of the batch: at level 7 of
+    the step's parameters (N = 2^14), or with --log-n 16 at the top level of
+    the large parameters (24 x ~50-bit limbs, 4 special primes, dnum 6).
+    --tune autotune runs the autotuner on this batch first."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -786,15 +788,24 @@ def run_micro_keyswitch(args):
     from paper_2006_10091_gb300 import workloads
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=[8],
-                     stream=stream.cuda_stream)
+    if args.log_n == 16:
+        ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=0, rot_steps=[8], stream=stream.cuda_stream)
+        level = 24
+    else:
+        ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=[8],
+                         stream=stream.cuda_stream)
+        level = L - 1
+    count = args.polys
+    tuned = None
     for kv in args.tune or []:
+        if kv == "autotune":
+            tuned = he.he_autotune(ctx, level, count)
+            continue
         key, val = kv.split("=")
         he.he_set_tuning(ctx, key, float(val))
-    level, count = L - 1, args.polys
     host = workloads.residues(2, ctx.primes[:level], ctx.n, parts=2 * count).reshape(count, 2, level, ctx.n)
     A, O = ctx.new_ct(level, count), ctx.new_ct(level, count)
-    he.he_ct_import_batch(ctx, host, level, SCALE, A)
+    he.he_ct_import_batch(ctx, host, level, ctx.scale, A)
     for _ in range(args.warmup):
         he.he_rotate_batch(ctx, A, 8, O)
     torch.cuda.synchronize()
@@ -809,8 +820,11 @@ def run_micro_keyswitch(args):
     he.he_rotate_batch(ctx, A, 8, O)
     prof = {k: he.he_profile_read(ctx, k) for k in he.he_profile_names(ctx)}
     he.he_profile_enable(ctx, False)
-    print(json.dumps({"micro": "keyswitch", "N": ctx.n, "level": level, "ciphertexts": count,
+    total_work = sum(v["work"] for v in prof.values())
+    print(json.dumps({"micro": "keyswitch", "N": ctx.n, "level": level, "ciphertexts": count, "autotune": tuned,
                       "ms_per_batch": ms, "rotations_per_s": count * 1000.0 / ms,
+                      "modmul_per_s": total_work / (ms * 1e-3),
+                      "alu_frac": total_work / (ms * 1e-3) / ALU_MODMUL_PEAK,
                       "kernels": {k: {"ms": v["ms"], "GBs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
                                       "work_per_s": v["work"] / max(v["ms"], 1e-9) * 1e3}
                                   for k, v in prof.items()}}))
