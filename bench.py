@@ -208,6 +208,8 @@ def run_ours(args, rank: int, world: int):
     lr = 1.0 / N_SAMPLES
     cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
     tuned = he.he_autotune(ctx, L - 1, 64)  # kernel knobs by timing, before any timed step
+    if args.chunk_bytes:
+        he.he_set_tuning(ctx, "chunk_bytes", args.chunk_bytes)
     Z, W = build_inputs(he, ctx, data, L)
     out = ctx.new_ct(L)
     step = lambda: he.he_lr_gradient_step(ctx, Z, W, cfg, out)  # noqa: E731
@@ -858,6 +860,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk-bytes", type=float, default=0, help="scratch budget of one batched operation")
     ap.add_argument("--alpha", type=int, default=None, help="special primes of the step's parameters")
     ap.add_argument("--special-bits", type=int, default=None)
     args = ap.parse_args()

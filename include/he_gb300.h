@@ -95,7 +95,7 @@ int he_set_stream(he_ctx* ctx, void* stream);
 int he_sync(he_ctx* ctx);
 
 /* Tuning knobs (results never depend on them): "chunk_bytes" = scratch budget
- * of one batched operation (default 2^31), "lr_chunk" = data ciphertexts per
+ * of one batched operation (default 2^34), "lr_chunk" = data ciphertexts per
  * chunk of the logistic-regression step (0 = from the budget), "ntt_generic"
  * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
  * one for N = 2^12 .. 2^16, "ks_row_ctas" = 2 or 3 (default) CTAs per SM for the

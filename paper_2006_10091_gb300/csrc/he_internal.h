@@ -90,7 +90,7 @@ struct he_ctx {
   // Garner (decryption CRT): [L] Shoup pairs of (q_0..q_{i-1})^-1 mod q_i, then
   // [L][L] prefix products (q_0..q_{i'-1}) mod q_i
   uint64_t* d_garner = nullptr;
-  size_t chunk_bytes = (size_t)1 << 31;  // scratch budget of one batched operation
+  size_t chunk_bytes = (size_t)1 << 34;  // scratch budget of one batched operation (16 GiB)
   uint32_t lr_chunk = 0;                 // data ciphertexts per chunk of the LR step (0: from the budget)
   bool ntt_generic = false;              // force the runtime-shaped NTT kernel (tuning)
   int ks_row_ctas = 3;                   // CTAs per SM the key-switch row pass is compiled for (2 or 3)
