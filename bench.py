@@ -173,6 +173,27 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
             "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over the ranks (each rank runs its own
+    independent step: the job takes as long as its slowest rank); a barrier
+    follows so that no rank starts its next timed region early."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def build_inputs(he, ctx, data, level):
@@ -240,13 +261,7 @@ def run_ours(args, rank: int, world: int):
             torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     ms_per_step = ms / args.steps
 
     # kernel-class timing over a profiled region of the same step
@@ -279,7 +294,7 @@ def run_ours(args, rank: int, world: int):
     for _ in range(e2e_steps):
         host_step()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     got_e2e = host_out.numpy().view(np.uint64)
     he.he_lr_gradient_step(ctx, Z, W, cfg, out)
     e2e_same = bool(np.array_equal(got_e2e, he.he_ct_export(ctx, out)))
@@ -294,7 +309,7 @@ def run_ours(args, rank: int, world: int):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(data, coeffs, lr)
-    value = world * 1000.0 / ms_per_step
+    value = weak_scaling_value(1.0, world, ms_per_step * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -305,7 +320,7 @@ def run_ours(args, rank: int, world: int):
                    "l2": "inputs larger than L2 (1.07 GB of ciphertexts per step)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "accuracy": {"max_rel_err_vs_fp64": rel_err, "gate": 2.0 ** -20, "ok": rel_err < 2.0 ** -20},
-        "e2e": {"value": world / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": weak_scaling_value(1.0, world, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "he_lr_gradient_step_host (pinned host buffers)",
                 "same_residues_as_device_step": e2e_same},
         "gpu_launches": int(sum(v["launches"] for v in prof.values()) // prof_steps),
