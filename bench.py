@@ -69,7 +69,9 @@ class ClockSampler:
     def __init__(self, device_uuid: str | None):
         self.uuid = device_uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: $HE_BENCH_CLOCKS_DIR if set, else the system's temporary directory
+        out_dir = os.environ.get("HE_BENCH_CLOCKS_DIR") or __import__("tempfile").gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
