@@ -308,7 +308,13 @@ int he_lr_inference_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count
  * while waves run join the next free slot without waiting for the others, and
  * waves on different streams overlap on the device.  A request whose weights
  * have too few limbs is refreshed in-process to the data's level first, with
- * random stream refresh_cid, so its result does not depend on its wave. */
+ * random stream refresh_cid, so its result does not depend on its wave.
+ * Calls return HE_OK or an error code: HE_EINVAL for null or inconsistent
+ * arguments (context index, kind, levels, output size), HE_ELEVEL at submit
+ * for data below the circuit's depth, HE_ETIMEOUT from drain; a failure while
+ * running a wave (HE_ENOMEM, HE_ECUDA, ...) is reported in the status of each
+ * of its requests' results.  The server owns its streams, slot views and
+ * scheduler thread; destroy joins the thread after the queued work. */
 enum { HE_REQ_GRADIENT = 0, HE_REQ_INFERENCE = 1 };
 
 typedef struct he_server he_server;
