@@ -235,7 +235,10 @@ def run_ours(args, rank: int, world: int):
         he.he_set_tuning(ctx, "chunk_bytes", args.chunk_bytes)
     Z, W = build_inputs(he, ctx, data, L)
     out = ctx.new_ct(L)
-    step = lambda: he.he_lr_gradient_step(ctx, Z, W, cfg, out)  # noqa: E731
+    if args.graph:  # the same step through the workers entry point, replayed as one CUDA graph
+        step = lambda: he.he_lr_gradient_step_workers(ctx, [(Z, W, out)], cfg, graph=True)  # noqa: E731
+    else:
+        step = lambda: he.he_lr_gradient_step(ctx, Z, W, cfg, out)  # noqa: E731
 
     for _ in range(args.warmup):
         step()
@@ -509,7 +512,8 @@ SERVE_MASK_SCALE = 2.0 ** 34
 SERVE_MIN_STEP_LEVEL = 7
 
 
-def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, budget=48 << 30):
+def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, budget=48 << 30,
+            inflight=4, wave=16):
     """A Poisson stream (mean `rate` req/s) of encrypted gradient-step and
     inference requests over ring sizes N = 2^13..2^16 (20 limbs of ~50 bits,
     4 special primes, scale 2^50; at 2^40 the encryption noise summed over
@@ -622,7 +626,7 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
                 "arrival_window_s": t_sub, "span_s": span, "waves": stats["waves"],
                 "peak_running_waves": stats["peak_running"], "peak_device_bytes": stats["peak_used"]}
 
-    srv = he.Server(ctxs, budget, max_inflight=4, max_wave=16)
+    srv = he.Server(ctxs, budget, max_inflight=inflight, max_wave=wave)
     try:
         cont = run(srv)
     finally:
@@ -679,7 +683,7 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
            "gradient_share": sum(1 for r in reqs[n_warm:] if r["kind"] == he.HE_REQ_GRADIENT) / n_requests,
            "refreshed": sum(1 for r in reqs[n_warm:] if r["wl"] < r["need"]),
            "data_ciphertexts": int(sum(r["nz"] for r in reqs[n_warm:])), "budget_bytes": budget}
-    return {"continuous": cont, "one_at_a_time": one,
+    return {"server": {"max_inflight": inflight, "max_wave": wave}, "continuous": cont, "one_at_a_time": one,
             "throughput_ratio": cont["requests_per_s"] / one["requests_per_s"], "mix": mix, "accuracy": acc,
             "setup_s": setup_s,
             "params": "N=2^13..2^16, 20x50-bit limbs + 4x60-bit special primes (dnum 5), scale 2^50; "
@@ -860,7 +864,8 @@ def run_part(args):
     if args.micro == "workers":
         print(json.dumps({"part": "batched_workers", **batched_workers(he, torch, stream)}))
     else:
-        print(json.dumps({"part": "serving", **serving(he, torch, stream, n_requests=args.requests)}))
+        print(json.dumps({"part": "serving", **serving(he, torch, stream, n_requests=args.requests,
+                                                       inflight=args.serve_inflight, wave=args.serve_wave)}))
 
 
 def main():
@@ -869,6 +874,8 @@ def main():
                     help="time one kernel class or one extra measurement alone")
     ap.add_argument("--requests", type=int, default=400, help="timed requests of --micro serving")
     ap.add_argument("--tune", action="append", help="key=value tuning of --micro keyswitch")
+    ap.add_argument("--serve-inflight", type=int, default=4, help="waves per context in --micro serving")
+    ap.add_argument("--serve-wave", type=int, default=16, help="requests per wave in --micro serving")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--polys", type=int, default=256)
     ap.add_argument("--gpus", type=int, default=1)
@@ -878,6 +885,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chunk-bytes", type=float, default=0, help="scratch budget of one batched operation")
+    ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
     ap.add_argument("--alpha", type=int, default=None, help="special primes of the step's parameters")
     ap.add_argument("--special-bits", type=int, default=None)
     args = ap.parse_args()
