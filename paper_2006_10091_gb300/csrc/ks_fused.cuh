@@ -188,8 +188,9 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
 
 // Row pass of every digit's tile fused with the key inner product.
 // Grid: count * nt * TILES.  Each thread owns residues idx = tid + u*T.
-// MINB: CTAs per SM the register allocation must allow (2: no spills, 128
-// registers; 3: 80 registers with a few spilled words), chosen at run time.
+// MINB: CTAs per SM the register allocation must allow (2: 128 registers,
+// with the next digit's tile prefetched into registers; 3: 80 registers with
+// a few spilled words, no prefetch), chosen at run time.
 template <int LOG_N, int LOG_M, int LOG_K, int MINB>
 __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(KsFusedArgs a) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
@@ -217,8 +218,30 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
     acc += mul_shoup_lazy(x, k, ksh, q);
     if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
   };
+  // With room for the registers (MINB 2) the next converted digit's tile is
+  // loaded while the current one is transformed, so its memory latency
+  // overlaps the rounds and the products.
+  constexpr bool PIPE = MINB <= 2;
+  auto own_of = [&](uint32_t j) { return t >= a.lo[j] && t < a.lo[j] + a.cnt[j]; };
+  auto next_conv = [&](uint32_t j) {  // first digit >= j whose limb t was converted
+    while (j < a.beta && own_of(j)) ++j;
+    return j;
+  };
+  auto tile_src = [&](uint32_t j) { return a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N; };
+  uint64_t nxt[PER];
+  if (PIPE) {
+    const uint32_t j0 = next_conv(0);
+    if (j0 < a.beta) {
+      const uint64_t* src = tile_src(j0);
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const uint32_t idx = threadIdx.x + u * S::T;
+        nxt[u] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+      }
+    }
+  }
   for (uint32_t j = 0; j < a.beta; ++j) {
-    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
+    const bool own = own_of(j);
     const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
     const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
     const uint64_t *kb = a.evk + kb_off, *ka = a.evk + ka_off;
@@ -235,11 +258,28 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
       }
       continue;
     }
-    const uint64_t* src = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+    if (PIPE) {
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+      for (int u = 0; u < PER; ++u) {
+        const uint32_t idx = threadIdx.x + u * S::T;
+        sm[idx + (idx >> 3)] = nxt[u];
+      }
+      const uint32_t jn = next_conv(j + 1);
+      if (jn < a.beta) {
+        const uint64_t* src = tile_src(jn);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const uint32_t idx = threadIdx.x + u * S::T;
+          nxt[u] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+        }
+      }
+    } else {
+      const uint64_t* src = tile_src(j);
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const uint32_t idx = threadIdx.x + u * S::T;
+        sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+      }
     }
     __syncthreads();
     if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
