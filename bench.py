@@ -128,13 +128,29 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# Integer-pipe roof: 152 SMs x 2070 MHz x 64 32-bit multiply-adds per clock per
-# SM (a register-resident IMAD chain reaches 60.4/clk/SM), divided by the 17.3
-# IMAD-pipe slots one 64-bit Shoup product takes (a register-resident chain of
-# Shoup products reaches 64/17.3 = 3.69 per clock per SM): 1.16 T modular
-# products/s.  A butterfly is one product; the key-switching kernels also
-# count their basis-conversion and inner-product products.
+# Integer-pipe roof: the rate of a register-resident chain of 64-bit Shoup
+# products (he_probe_alu kind 1), measured on the GPU at the start of the run
+# (ALU_PEAK below is replaced by that measurement); the fallback is 152 SMs x
+# 2070 MHz x 3.69 products per clock per SM (64 IMAD slots / 17.3 per product,
+# an earlier measurement on this kind of GPU): 1.16 T modular products/s.  A
+# butterfly is one product; the key-switching kernels also count their
+# basis-conversion and inner-product products.
 ALU_MODMUL_PEAK = 152 * 2.070e9 * 64 / 17.3
+ALU_PEAK = {"per_second": ALU_MODMUL_PEAK, "note": "fallback: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots "
+                                                  "per 64-bit Shoup product"}
+
+
+def measure_alu_peak(he) -> None:
+    """Replace the fallback integer roof by this GPU's measured Shoup-product rate."""
+    try:
+        r = he.he_probe_alu(1)
+    except Exception:  # keep the fallback
+        return
+    ALU_PEAK["per_second"] = r["per_second"]
+    ALU_PEAK["note"] = (f"measured: register-resident 64-bit Shoup product chain on this GPU "
+                        f"({r['per_clock_per_sm']:.2f} per clock per SM)")
+
+
 ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "moddown_ntt", "moddown_ntt_combine",
                "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes (read + write) per modular product of the fused key-switch row
@@ -157,19 +173,18 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
     frac_hbm = gbs / hbm_peak
     if name in ALU_CLASSES:
         rate = p["work"] / (p["ms"] * 1e-3)
-        frac_alu = rate / ALU_MODMUL_PEAK
+        frac_alu = rate / ALU_PEAK["per_second"]
         traffic = None
         if name == "ks_ntt_inner_product":
             traffic = KS_ROW_TRAFFIC_PER_MODMUL * p["work"] / max(1, p["launches"])
         if frac_alu >= frac_hbm:
-            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_MODMUL_PEAK / 1e9,
+            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_PEAK["per_second"] / 1e9,
                     "unit": "G modmul/s", "frac": frac_alu, "traffic": traffic,
                     "traffic_note": "bytes per launch, scaled from an ncu capture of a smaller launch" if traffic
                     else None,
                     "per_launch_ms": per_launch_ms, "launches": p["launches"],
                     "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
-                    "peak_note": "derived: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots per 64-bit "
-                                 "Shoup product (probe-measured)"}
+                    "peak_note": ALU_PEAK["note"]}
     return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
             "frac": frac_hbm, "traffic": None, "per_launch_ms": per_launch_ms,
             "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
@@ -216,6 +231,7 @@ def run_ours(args, rank: int, world: int):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_10091_gb300 as he
+    measure_alu_peak(he)
     from paper_2006_10091_gb300 import workloads
     from tests.lr_reference import lr_step_fp64
 
@@ -767,6 +783,7 @@ def run_micro(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_10091_gb300 as he
+    measure_alu_peak(he)
     from paper_2006_10091_gb300 import workloads
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -792,7 +809,7 @@ def run_micro(args):
         limbs = args.polys * nl
         bfly = limbs * (n / 2) * log_n
         out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else f"_shape{shape}" if shape else "")] = {
-            "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_MODMUL_PEAK,
+            "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_PEAK["per_second"],
             "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
     he.he_set_tuning(ctx, "ntt_generic", False)
     print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
@@ -808,6 +825,7 @@ def run_micro_keyswitch(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_10091_gb300 as he
+    measure_alu_peak(he)
     from paper_2006_10091_gb300 import workloads
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -847,7 +865,7 @@ def run_micro_keyswitch(args):
     print(json.dumps({"micro": "keyswitch", "N": ctx.n, "level": level, "ciphertexts": count, "autotune": tuned,
                       "ms_per_batch": ms, "rotations_per_s": count * 1000.0 / ms,
                       "modmul_per_s": total_work / (ms * 1e-3),
-                      "alu_frac": total_work / (ms * 1e-3) / ALU_MODMUL_PEAK,
+                      "alu_frac": total_work / (ms * 1e-3) / ALU_PEAK["per_second"],
                       "kernels": {k: {"ms": v["ms"], "GBs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
                                       "work_per_s": v["work"] / max(v["ms"], 1e-9) * 1e3}
                                   for k, v in prof.items()}}))
@@ -870,7 +888,7 @@ def run_part(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "keyswitch", "workers", "serving"], default=None,
+    ap.add_argument("--micro", choices=["ntt", "keyswitch", "workers", "serving", "alu"], default=None,
                     help="time one kernel class or one extra measurement alone")
     ap.add_argument("--requests", type=int, default=400, help="timed requests of --micro serving")
     ap.add_argument("--tune", action="append", help="key=value tuning of --micro keyswitch")
@@ -902,6 +920,15 @@ def main():
         return
     if args.micro in ("workers", "serving"):
         run_part(args)
+        return
+    if args.micro == "alu":
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_2006_10091_gb300 as he
+        names = ("imad_32", "shoup_product_64", "lazy_butterfly_radix8")
+        print(json.dumps({"micro": "alu", **{n: he.he_probe_alu(k) for k, n in enumerate(names)},
+                          "fallback_roof": {"per_second": ALU_MODMUL_PEAK,
+                                            "note": "152 SMs x 2070 MHz x 64 / 17.3 (Shoup product)"}}))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -108,6 +108,14 @@ int he_set_tuning(he_ctx* ctx, const char* key, double value);
 /* Current value of a tuning knob (the keys above). */
 int he_get_tuning(he_ctx* ctx, const char* key, double* value);
 
+/* Measurement utility (no counterpart in the paper): register-resident
+ * throughput on the current device of kind 0 = 32-bit multiply-adds, 1 =
+ * 64-bit Shoup modular products (the integer roof of the transforms), 2 =
+ * radix-8 rounds of the lazy forward butterfly; per clock per SM (at the
+ * device's maximum clock) and per second.  Runs two short kernels on the
+ * default stream and synchronises. */
+int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second);
+
 /* Autotuner (no counterpart in the paper; it serves the batched workers of
  * Sec. 4): times the relinearisation key switch (iNTT, ModUp + NTT, inner
  * product, ModDown) of `count` polynomials of uniform residues at `level`

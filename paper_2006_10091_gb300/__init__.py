@@ -130,6 +130,7 @@ def load():
                                      ctypes.c_double, ctypes.POINTER(he_lr_config), VP, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)],
         "he_get_tuning": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
+        "he_probe_alu": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
@@ -279,6 +280,13 @@ def he_get_tuning(ctx: Context, key: str) -> float:
     v = ctypes.c_double()
     _check(load().he_get_tuning(ctx.ptr, key.encode(), ctypes.byref(v)))
     return v.value
+
+
+def he_probe_alu(kind: int) -> dict:
+    """Register-resident integer throughput: kind 0 IMAD, 1 Shoup product, 2 lazy butterfly."""
+    pc, ps = ctypes.c_double(), ctypes.c_double()
+    _check(load().he_probe_alu(kind, ctypes.byref(pc), ctypes.byref(ps)))
+    return {"per_clock_per_sm": pc.value, "per_second": ps.value}
 
 
 def he_autotune(ctx: Context, level: int, count: int) -> dict:

@@ -539,3 +539,13 @@ def test_fused_matches_unfused_large(he, log_n):
         for k in range(2):
             assert np.array_equal(outs[(False, shape)][k], outs[(True, 0)][k]), (shape, k)
         assert np.array_equal(outs[(False, shape, "rot")], outs[(True, 0, "rot")]), shape
+
+
+def test_alu_probes_run(he):
+    """The throughput probes behind the integer roof return positive rates in
+    the expected order (a Shoup product costs several multiply-adds)."""
+    r = [he.he_probe_alu(k) for k in range(3)]
+    assert all(x["per_second"] > 0 and x["per_clock_per_sm"] > 0 for x in r)
+    assert r[0]["per_clock_per_sm"] > 4 * r[1]["per_clock_per_sm"]
+    with pytest.raises(he.HeError):
+        he.he_probe_alu(7)
