@@ -613,14 +613,14 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
         return srv.submit(r["ci"], r["kind"], r["Z"], SERVE_L, SERVE_SCALE, r["W"], r["wl"], SERVE_SCALE, r["cfg"],
                           r["out"], refresh_cid=r["cid"], min_w_level=r["need"])
 
-    def run(srv):
-        for r in reqs[:n_warm]:  # warm-up: plans, masks and workspaces
-            submit(srv, r)
-        srv.drain(1200)
-        srv.poll(cap=n_warm + 16)
-        timed = reqs[n_warm:]
+    def run(srv, arr, timed, warm=True):
+        if warm:
+            for r in reqs[:n_warm]:  # warm-up: plans, masks and workspaces
+                submit(srv, r)
+            srv.drain(1200)
+            srv.poll(cap=n_warm + 16)
         t0 = time.perf_counter()
-        for r, ta in zip(timed, arrivals):
+        for r, ta in zip(timed, arr):
             while True:
                 dt = ta - (time.perf_counter() - t0)
                 if dt <= 0:
@@ -631,27 +631,33 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
         t_sub = time.perf_counter() - t0
         srv.drain(1200)
         span = time.perf_counter() - t0
-        res = srv.poll(cap=n_requests + 16)
+        res = srv.poll(cap=len(timed) + 16)
         stats = srv.stats()
         bad = [x for x in res if x["status"] != 0]
-        if bad or len(res) != n_requests:
-            raise RuntimeError(f"serving: {len(bad)} failed requests, {len(res)} of {n_requests} returned")
+        if bad or len(res) != len(timed):
+            raise RuntimeError(f"serving: {len(bad)} failed requests, {len(res)} of {len(timed)} returned")
         lat = np.array([x["latency_ms"] for x in res])
-        return {"requests_per_s": n_requests / span, "p50_ms": float(np.percentile(lat, 50)),
+        return {"requests": len(timed), "offered_per_s": len(timed) / float(arr[len(timed) - 1]),
+                "requests_per_s": len(timed) / span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                 "arrival_window_s": t_sub, "span_s": span, "waves": stats["waves"],
                 "peak_running_waves": stats["peak_running"], "peak_device_bytes": stats["peak_used"]}
 
-    srv = he.Server(ctxs, budget, max_inflight=inflight, max_wave=wave)
+    timed = reqs[n_warm:]
+    srv_c = he.Server(ctxs, budget, max_inflight=inflight, max_wave=wave)
+    srv_o = he.Server(ctxs, budget, max_inflight=1, max_wave=1, max_running=1)
     try:
-        cont = run(srv)
+        cont = run(srv_c, arrivals, timed)
+        one = run(srv_o, arrivals, timed)
+        # the same servers under a load both sustain (80% of the one-at-a-time
+        # throughput): latency without a backlog
+        n_s = min(150, len(timed))
+        arr_s = workloads.poisson_arrivals(seed + 1, 0.8 * one["requests_per_s"], n_s)
+        cont_s = run(srv_c, arr_s, timed[:n_s], warm=False)
+        one_s = run(srv_o, arr_s, timed[:n_s], warm=False)
     finally:
-        srv.close()
-    srv = he.Server(ctxs, budget, max_inflight=1, max_wave=1, max_running=1)
-    try:
-        one = run(srv)
-    finally:
-        srv.close()
+        srv_c.close()
+        srv_o.close()
     # accuracy: the first request of every (ring, kind) class, served alone and decrypted
     acc = {}
     srv = he.Server(ctxs, budget, max_inflight=1, max_wave=1, max_running=1)
@@ -700,7 +706,8 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
            "refreshed": sum(1 for r in reqs[n_warm:] if r["wl"] < r["need"]),
            "data_ciphertexts": int(sum(r["nz"] for r in reqs[n_warm:])), "budget_bytes": budget}
     return {"server": {"max_inflight": inflight, "max_wave": wave}, "continuous": cont, "one_at_a_time": one,
-            "throughput_ratio": cont["requests_per_s"] / one["requests_per_s"], "mix": mix, "accuracy": acc,
+            "throughput_ratio": cont["requests_per_s"] / one["requests_per_s"],
+            "sustained_load": {"continuous": cont_s, "one_at_a_time": one_s}, "mix": mix, "accuracy": acc,
             "setup_s": setup_s,
             "params": "N=2^13..2^16, 20x50-bit limbs + 4x60-bit special primes (dnum 5), scale 2^50; "
                       "not 128-bit secure at N<=2^15 (benchmark parameters)"}
