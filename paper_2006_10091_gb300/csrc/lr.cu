@@ -639,7 +639,12 @@ extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ,
   HE_CUDA(cudaStreamWaitEvent(c->stream, c->io_events[0], 0));
   c->io_piece = piece;
   c->io_pieces_waited = 1;
+  // unless the caller chose a chunk, run the data in two chunks so that the
+  // second half's copy overlaps the first half's arithmetic
+  const uint32_t saved_chunk = c->lr_chunk;
+  if (!saved_chunk && nZ > 2 * piece) c->lr_chunk = (uint32_t)(((nZ + 1) / 2 + piece - 1) / piece * piece);
   const int rc = lr_entry(c, &sh, 1, cfg, 0, 0, false);
+  c->lr_chunk = saved_chunk;
   c->io_piece = 0;
   if (rc != HE_OK) {
     cudaStreamSynchronize(c->copy_stream);
