@@ -139,7 +139,7 @@ int he_ctx_info(const he_ctx* ctx, uint32_t* n, uint32_t* n_limbs, uint32_t* n_s
 int he_encode(he_ctx* ctx, const double* slots, size_t n_slots, double scale, int64_t* coeffs_out);
 
 /* Encrypt integer coefficients (host, N of them) at `level` (Sec. 3;
- * Algorithm 1 line 4 uses pk, Algorithm 2 line 4 encrypts with sk).
+ * Algorithm 1 uses pk, Algorithm 2 encrypts with sk).
  * use_sk = 0: (v*b + e0 + m, v*a + e1); use_sk = 1: (-a*s + e + m, a).  The
  * randomness is the stream of ciphertext id `cid`, so equal inputs give
  * equal residues.  out->data must be allocated; sets level and scale. */
@@ -232,7 +232,7 @@ int he_mul_relin_rescale_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, he_c
 int he_rotate_batch(he_ctx* ctx, const he_ct* a, int32_t steps, he_ct* out, size_t count);
 
 /* Encrypted logistic-regression gradient step (Sec. 4: Eq. 5-8 with a Table 2
- * polynomial; Algorithm 1 line 7).  Z[k] hold g samples each, slot g*f + s =
+ * polynomial; Algorithm 1).  Z[k] hold g samples each, slot g*f + s =
  * y_s*x_{s,f}; W holds w_f in slots g*f + s for every s.  Computes
  * w' = w + lr * sum_k sum_s p(y_s w.x_s) y_s x_s with p(x) = c0 + c1 x +
  * c2 x^2 + c3 x^3, replicated over the g slots of each feature.  Consumes 5
@@ -269,7 +269,7 @@ int he_lr_gradient_step_host(he_ctx* ctx, const uint64_t* Z, size_t nZ, uint32_t
  * holds its own data ciphertexts Z[0..nZ) (one level, one scale), its weights
  * W and an output buffer W_out.  A shard whose weights sit below level 6 (too
  * few limbs for the step's five rescales) first goes through the in-process
- * key-holder refresh (Algorithm 1 lines 8-10) to refresh_level (0 = refuse
+ * key-holder refresh (Algorithm 1) to refresh_level (0 = refuse
  * with HE_ELEVEL); the step then runs at the weights' level l with the data
  * taken at l, and W_out receives level l - 5 and W's scale.  Shards with the
  * same level and scales share every kernel launch; their data ciphertexts
@@ -294,6 +294,21 @@ typedef struct he_lr_shard {
 int he_lr_gradient_step_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count,
                                 const he_lr_config* cfg, uint32_t refresh_level, int flags);
 
+/* The training loop of Algorithms 1 and 2 in one process: worker k (shard
+ * k: data Z[0..nZ), initial weights W at top_level, all at one scale; W_out
+ * and S_out unused) runs `iterations` gradient steps (Eq. 7-8, this cfg) on
+ * its own data from its own weights; after every `refresh_every` steps and
+ * after the last, the key holder (Algorithm 2) decrypts all
+ * workers' weights, averages them slot by slot (the paper leaves its update
+ * rule open), encodes the average at the weights' scale and encrypts it once
+ * at top_level (random stream cid0 + iteration), and every worker continues
+ * from that ciphertext.  W_final (cap >= top_level) receives the last
+ * average.  Needs top_level >= 5 * refresh_every + 1 (a step consumes 5
+ * limbs), else HE_ELEVEL; HE_EINVAL for weights not at top_level; HE_ESCALE
+ * for different scales.  Weight buffers are allocated for the call. */
+int he_lr_train(he_ctx* ctx, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
+                uint32_t iterations, uint32_t refresh_every, uint32_t top_level, uint32_t cid0, he_ct* W_final);
+
 /* Encrypted inference of the same model (the first half of the step): for
  * every data ciphertext Z_k of every shard, S_k = p(M_k) with M_k = the
  * per-sample inner products y_s w.x_s replicated over each sample's slots
@@ -305,7 +320,7 @@ int he_lr_inference_workers(he_ctx* ctx, const he_lr_shard* shards, size_t count
                             const he_lr_config* cfg, uint32_t refresh_level, int flags);
 
 /* ---- Serving: a continuous-batching request loop ----------------------------
- * The paper's workers answer gradient steps (Algorithm 1 line 7) and, with
+ * The paper's workers answer gradient steps (Algorithm 1) and, with
  * the same model, inference.  A server holds contexts of several ring sizes
  * (keys resident in HBM) and a scheduler thread.  Requests carry host
  * residues; the scheduler admits them oldest first while their device memory
@@ -377,7 +392,7 @@ int he_server_drain(he_server* s, double timeout_s);
 int he_server_stats(he_server* s, size_t* used, size_t* peak_used, size_t* waves, size_t* peak_running);
 int he_server_destroy(he_server* s);
 
-/* The key holder's refresh (Algorithm 1 lines 8-10, Algorithm 2 lines 8-11),
+/* The key holder's refresh (Algorithm 1, Algorithm 2),
  * simulated in-process: decrypt, decode, re-encode at out_scale and encrypt
  * at `level` with ciphertext id cid.  Synchronous. */
 int he_refresh(he_ctx* ctx, const he_ct* a, uint32_t level, double out_scale, uint32_t cid,

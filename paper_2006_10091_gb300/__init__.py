@@ -126,6 +126,8 @@ def load():
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
+        "he_lr_train": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config), ctypes.c_uint32, ctypes.c_uint32,
+                        ctypes.c_uint32, ctypes.c_uint32, CTP],
         "he_lr_gradient_step_host": [VP, VP, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double, VP, ctypes.c_uint32,
                                      ctypes.c_double, ctypes.POINTER(he_lr_config), VP, ctypes.c_size_t,
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)],
@@ -454,6 +456,19 @@ def _shards(shards, infer):
             arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w),
                                  ctypes.addressof(wo), None, cid, 0)
     return arr, keep
+
+
+def he_lr_train(ctx, workers: list, cfg: he_lr_config, iterations: int, refresh_every: int, top_level: int,
+                W_final, cid0: int = 1 << 20):
+    """workers: list of (Z list, W at top_level).  Returns W_final (the last
+    averaged weights, re-encrypted at top_level)."""
+    shards = [(Z, W, W) for Z, W in workers]  # W_out is not used by the loop
+    arr, keep = _shards(shards, False)
+    f = W_final.c()
+    _check(load().he_lr_train(ctx.ptr, arr, len(workers), ctypes.byref(cfg), iterations, refresh_every, top_level,
+                              cid0, ctypes.byref(f)))
+    W_final.update(f)
+    return W_final
 
 
 def he_lr_gradient_step_host(ctx, Z_host, z_level: int, z_scale: float, W_host, w_level: int, w_scale: float,

@@ -1,6 +1,6 @@
 // keys.cu -- random streams, key generation and encryption (Sec. 3:
 // "Encrypt/Decrypt ... the public key and private key ... R-LWE";
-// Algorithm 2 line 4: the parameter server generates the keys and encrypts).
+// Algorithm 2: the parameter server generates the keys and encrypts).
 //
 // Random streams: Philox4x32-10 with key (seed low, seed high) and counter
 // (coefficient index, prime index or 0, stream id, domain).  Samplers:

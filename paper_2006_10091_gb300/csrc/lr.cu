@@ -1,5 +1,5 @@
 // lr.cu -- the encrypted logistic-regression gradient step of a worker
-// (Sec. 4: Eq. 5-8 with a Table 2 polynomial; Algorithm 1 line 7).
+// (Sec. 4: Eq. 5-8 with a Table 2 polynomial; Algorithm 1).
 //
 // Packing: each data ciphertext holds g samples interleaved, slot g*f + s =
 // y_s * x_{s,f}; W holds w_f in slots g*f + s for every s.  Because slot
@@ -253,7 +253,7 @@ static int check_aligned(const void* p) { return ((uintptr_t)p & 15) == 0 ? HE_O
 static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, uint32_t refresh_level,
                   Arena& pool, bool infer) {
   const uint32_t n = c->n;
-  // in-process refresh of weights below the circuit's depth (Algorithm 1 lines 8-10)
+  // in-process refresh of weights below the circuit's depth (Algorithm 1)
   for (size_t k = 0; k < sh.size(); ++k) {
     if (!sh[k].refresh) continue;
     const size_t words = (size_t)sh[k].W_in->level * n + 2 * n + 2 * n * 2 + n + 4 * (size_t)refresh_level * n;
@@ -665,4 +665,119 @@ extern "C" int he_lr_gradient_step_workers(he_ctx* c, const he_lr_shard* shards,
 extern "C" int he_lr_inference_workers(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
                                        uint32_t refresh_level, int flags) {
   return lr_entry(c, shards, count, cfg, refresh_level, flags, true);
+}
+
+// ---- the training loop of Algorithms 1 and 2 ---------------------------------
+
+namespace he {
+
+__global__ void k_slots_accumulate(double* acc, const double* x, size_t n, int first, double scale_after) {
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < n; g += (size_t)gridDim.x * blockDim.x) {
+    const double v = first ? x[g] : acc[g] + x[g];
+    acc[g] = scale_after != 0.0 ? v * scale_after : v;
+  }
+}
+
+// The key holder's round (Algorithm 2): decrypt every worker's
+// weights, average them slot by slot (in worker order), encode the average at
+// `scale` and encrypt it once at `level` (stream cid) into W[0], then copy it
+// to every other worker.
+static int lr_aggregate(he_ctx* c, std::vector<he_ct>& W, uint32_t level, double scale, uint32_t cid) {
+  const size_t n = c->n, ns = n / 2;
+  size_t lmax = 0;
+  for (const he_ct& w : W) lmax = std::max<size_t>(lmax, w.level);
+  HE_TRY(ws_reserve(c, sizeof(uint64_t) * lmax * n + sizeof(double) * (n + 2 * ns) + sizeof(double2) * 2 * n +
+                           sizeof(int64_t) * n + sizeof(uint64_t) * 4 * level * n + 16384));
+  Arena ar;
+  ar.base = (char*)c->ws.ptr;
+  ar.size = c->ws.size;
+  ar.off = 0;
+  uint64_t* m = ar.take<uint64_t>(lmax * n);
+  double* d = ar.take<double>(n);
+  double* re = ar.take<double>(ns);
+  double* avg = ar.take<double>(ns);
+  double2* fft = ar.take<double2>(2 * n);
+  int64_t* coeffs = ar.take<int64_t>(n);
+  int* ovf = ar.take<int>(1);
+  uint64_t* scratch = ar.take<uint64_t>((size_t)4 * level * n);
+  if (!scratch) return fail(HE_ENOMEM, "aggregation scratch too small");
+  for (size_t k = 0; k < W.size(); ++k) {
+    HE_TRY(decrypt_dev(c, &W[k], m, d));
+    HE_TRY(decode_dev(c, d, W[k].scale, re, ns, fft));
+    const bool last = k + 1 == W.size();
+    k_slots_accumulate<<<grid_for(ns), 256, 0, c->stream>>>(avg, re, ns, k == 0, last ? 1.0 / (double)W.size() : 0.0);
+    HE_CUDA(cudaGetLastError());
+  }
+  HE_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c->stream));
+  HE_TRY(encode_dev(c, avg, ns, scale, coeffs, fft, ovf));
+  HE_TRY(encrypt_dev(c, coeffs, level, 0, cid, &W[0], scratch));
+  W[0].level = level;
+  W[0].scale = scale;
+  for (size_t k = 1; k < W.size(); ++k) {
+    HE_TRY(copy_batch(c, CtBatch{W[0].data, 0, W[0].cap, 0}, CtBatch{W[k].data, 0, W[k].cap, 0}, level, 1));
+    W[k].level = level;
+    W[k].scale = scale;
+  }
+  HE_TRY(stage_reserve(c, 64));
+  HE_CUDA(cudaMemcpyAsync(c->h_stage, ovf, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HE_CUDA(cudaStreamSynchronize(c->stream));
+  int flag = 0;
+  memcpy(&flag, c->h_stage, sizeof(int));
+  return flag ? fail(HE_EINVAL, "aggregation: encoded coefficient beyond int64") : HE_OK;
+}
+
+}  // namespace he
+
+// Algorithms 1 and 2 in one process: every worker k runs `iterations`
+// gradient steps (Eq. 7-8) on its own data Z_k from its own weights; after
+// every `refresh_every` steps, and after the last, the key holder replaces
+// all workers' weights by the re-encrypted slot-wise average of their
+// weights (the paper leaves the parameter server's update rule open).
+extern "C" int he_lr_train(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_config* cfg,
+                           uint32_t iterations, uint32_t refresh_every, uint32_t top_level, uint32_t cid0,
+                           he_ct* W_final) {
+  if (!c || !shards || !cfg || !W_final || count == 0 || iterations == 0 || refresh_every == 0)
+    return fail(HE_EINVAL, "he_lr_train: null argument or zero count");
+  if (top_level < 6 || top_level > (uint32_t)c->L) return fail(HE_EINVAL, "he_lr_train: top level out of range");
+  if (top_level < 5 * refresh_every + 1)
+    return fail(HE_ELEVEL, "he_lr_train: the weights run out of limbs before the refresh");
+  if (!W_final->data || W_final->cap < top_level) return fail(HE_EINVAL, "he_lr_train: output capacity too small");
+  const size_t n = c->n, words = (size_t)2 * top_level * n;
+  double scale = 0.0;
+  for (size_t k = 0; k < count; ++k) {
+    const he_ct* w = shards[k].W;
+    if (!w || !w->data || w->level != top_level) return fail(HE_EINVAL, "he_lr_train: weights must be at the top level");
+    if (k == 0) scale = w->scale;
+    else if (w->scale != scale) return fail(HE_ESCALE, "he_lr_train: workers' weights at different scales");
+  }
+  uint64_t* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(uint64_t) * words * 2 * count) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HE_ENOMEM, "he_lr_train: weight buffers");
+  }
+  std::vector<he_ct> cur(count), nxt(count);
+  int rc = HE_OK;
+  for (size_t k = 0; k < count && rc == HE_OK; ++k) {
+    cur[k] = he_ct{buf + 2 * k * words, top_level, top_level, scale};
+    nxt[k] = he_ct{buf + (2 * k + 1) * words, 0, top_level, 0.0};
+    rc = copy_batch(c, CtBatch{shards[k].W->data, 0, shards[k].W->cap, 0}, CtBatch{cur[k].data, 0, top_level, 0},
+                    top_level, 1);
+  }
+  std::vector<he_lr_shard> sh(count);
+  for (uint32_t it = 1; it <= iterations && rc == HE_OK; ++it) {
+    for (size_t k = 0; k < count; ++k) sh[k] = he_lr_shard{shards[k].Z, shards[k].nZ, &cur[k], &nxt[k], nullptr, 0, 0};
+    rc = lr_entry(c, sh.data(), count, cfg, 0, 0, false);
+    if (rc != HE_OK) break;
+    std::swap(cur, nxt);
+    if (it % refresh_every == 0 || it == iterations) rc = lr_aggregate(c, cur, top_level, scale, cid0 + it);
+  }
+  if (rc == HE_OK)
+    rc = copy_batch(c, CtBatch{cur[0].data, 0, top_level, 0}, CtBatch{W_final->data, 0, W_final->cap, 0}, top_level, 1);
+  if (rc == HE_OK) {
+    W_final->level = top_level;
+    W_final->scale = scale;
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  return rc;
 }

@@ -1,7 +1,7 @@
 // serve.cu -- a continuous-batching request loop for encrypted
 // logistic-regression gradient and inference requests over several ring
 // sizes (the paper's workers serving requests, Sec. 4; the key holder's
-// refresh of Algorithm 1 lines 8-10 runs in-process when a request's weights
+// refresh of Algorithm 1 runs in-process when a request's weights
 // have too few limbs left).
 //
 // One scheduler thread owns every CUDA call.  Each context (one ring size

@@ -148,7 +148,7 @@ def test_workers_match_separate_calls(lr_pair, graph):
 
 def test_workers_refresh_low_levels(lr_pair):
     """A worker whose weights have too few limbs left is refreshed by the
-    in-process key holder first (Algorithm 1 lines 8-10); the decrypted
+    in-process key holder first (Algorithm 1); the decrypted
     result still matches the FP64 update."""
     pair, g = lr_pair
     he = pair.he
@@ -318,3 +318,43 @@ def test_lr_step_and_inference_bit_exact_fused_kernels():
     want = pair.o.lr_inference(Zo, Wo, coeffs, 1.0, g)
     for k in range(3):
         assert_same_residues(S[k], want[k], he, pair.g)
+
+
+@pytest.mark.parametrize("refresh_every", [1, 2])
+def test_training_loop_matches_fp64_algorithm(refresh_every):
+    """Algorithms 1 and 2: two workers with their own data run three steps,
+    the key holder averages their weights every `refresh_every` steps and
+    after the last; the decrypted result equals the same procedure in FP64
+    within 2^-20 of the weights."""
+    he = gpu_lib()
+    log_n, g = 12, 8
+    n_slots = (1 << log_n) // 2
+    ctx = he.Context(log_n, 11, 40, 2, 55, 2.0 ** 40, seed=17, rot_steps=rot_steps(n_slots, g))
+    coeffs = table2()["binomial"]
+    lr = 1.0 / 16
+    w0 = workloads.LRData(seed=40, n_samples=16, n_features=200).w0
+    datas = [workloads.LRData(seed=41 + k, n_samples=16, n_features=200) for k in range(2)]
+    workers = []
+    for k, d in enumerate(datas):
+        zs = workloads.pack_samples(d.X, d.y, n_slots, g)
+        Z = ctx.new_ct(11, len(zs))
+        for i, v in enumerate(zs):
+            he.he_encode_encrypt(ctx, v, 2.0 ** 40, 11, Z[i], cid=100 * k + i)
+        W = ctx.new_ct(11)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(w0, n_slots, g), 2.0 ** 40, 11, W, cid=100 * k + 99)
+        workers.append((Z, W))
+    out = ctx.new_ct(11)
+    he.he_lr_train(ctx, workers, he.lr_config(coeffs, lr, g, 2.0 ** 27), 3, refresh_every, 11, out)
+    assert out.level == 11
+    ws = [w0.copy() for _ in datas]
+    for it in range(1, 4):
+        ws = [lr_step_fp64(d.X, d.y, w, coeffs, lr) for d, w in zip(datas, ws)]
+        if it % refresh_every == 0 or it == 3:
+            avg = sum(ws) / len(ws)
+            ws = [avg.copy() for _ in ws]
+    want = workloads.pack_weights(ws[0], n_slots, g)
+    got = he.he_decrypt_decode(ctx, out)
+    assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20
+    with pytest.raises(he.HeError) as e:  # 11 limbs hold two steps, not three
+        he.he_lr_train(ctx, workers, he.lr_config(coeffs, lr, g, 2.0 ** 27), 3, 3, 11, out)
+    assert e.value.code == he.HE_ELEVEL
