@@ -93,6 +93,7 @@ def _load():
             lib.orc_mul_relin_rescale.argtypes = [VP, VP, VP, ctypes.c_int, VP]
             lib.orc_mul_relin.argtypes = [VP, VP, VP, ctypes.c_int, VP]
             lib.orc_rotate.argtypes = [VP, VP, ctypes.c_int, ctypes.c_int32, VP]
+            lib.orc_rotate_sum.argtypes = [VP, VP, ctypes.c_int, VP, ctypes.c_int, VP]
             lib.orc_automorph.argtypes = [VP, VP, VP, ctypes.c_int, ctypes.c_uint64]
             lib.orc_get_primes.argtypes = [VP, VP]
             lib.orc_get_roots.argtypes = [VP, VP]
@@ -410,6 +411,16 @@ class Oracle:
         rc = self._lib.orc_rotate(self.ptr, _p(_u64(a.data)), a.level, r, _p(out))
         if rc:
             raise KeyError(f"no Galois key for rotation {r}")
+        return Ciphertext(out, a.level, a.scale)
+
+    def rotate_sum(self, a: Ciphertext, steps) -> Ciphertext:
+        """a + sum_s rot(a, s) with one shared decomposition of a's second part
+        (orc_rotate_sum)."""
+        st = np.ascontiguousarray(steps, dtype=np.int32)
+        out = self._new(a.level)
+        rc = self._lib.orc_rotate_sum(self.ptr, _p(_u64(a.data)), a.level, _p(st), len(st), _p(out))
+        if rc:
+            raise KeyError(f"rotate_sum {list(steps)} failed ({rc})")
         return Ciphertext(out, a.level, a.scale)
 
     def automorph(self, polys, nlimbs: int, k: int) -> np.ndarray:

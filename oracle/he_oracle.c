@@ -945,6 +945,39 @@ static const uint64_t* find_key(orc_ctx* c, int key_id) {
   return NULL;
 }
 
+/* ModDown of a key switch's two accumulators acc [2][level + alpha][N]
+ * (evaluation form over Q_level and P) to (k0, k1) [level][N]: division by P
+ * with rounding, as described at keyswitch below. */
+static void moddown_pair(orc_ctx* c, const uint64_t* acc, int level, uint64_t* k0, uint64_t* k1) {
+  uint32_t n = c->n;
+  int nt = level + c->alpha;
+  uint64_t* yP = malloc(sizeof(uint64_t) * (size_t)c->alpha * n);
+  uint64_t* conv = malloc(sizeof(uint64_t) * n);
+  for (int p = 0; p < 2; p++) {
+    const uint64_t* ap = acc + (size_t)p * nt * n;
+    for (int k = 0; k < c->alpha; k++) {
+      uint64_t pk = c->q[c->L + k];
+      uint64_t hk = half_P_mod(c, pk);
+      memcpy(POLY(yP, k, n), POLY(ap, level + k, n), sizeof(uint64_t) * n);
+      intt_limb(c, c->L + k, POLY(yP, k, n));
+      for (uint32_t i = 0; i < n; i++) yP[(size_t)k * n + i] = addmod(yP[(size_t)k * n + i], hk, pk);
+    }
+    uint64_t* dst = p == 0 ? k0 : k1;
+    for (int t = 0; t < level; t++) {
+      uint64_t q = c->q[t];
+      uint64_t ht = half_P_mod(c, q);
+      moddown_conv(c, yP, t, conv);
+      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
+      ntt_limb(c, t, conv);
+      uint64_t pinv = invmod(P_mod(c, q), q);
+      const uint64_t* at = POLY(ap, t, n);
+      uint64_t* o = POLY(dst, t, n);
+      for (uint32_t i = 0; i < n; i++) o[i] = mulmod(submod(at[i], conv[i], q), pinv, q);
+    }
+  }
+  free(yP); free(conv);
+}
+
 /* Hybrid key switching [ext], at `level`: input d (evaluation form [level][N]),
  * key for s' -> s; output (k0, k1) [level][N] each, with k0 + k1 s ~ d s'.
  * Steps in order: d to coefficients; per digit ModUp to Q_level + P and back
@@ -990,32 +1023,8 @@ static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* 
       }
     }
   }
-  /* ModDown of both accumulators */
-  uint64_t* yP = malloc(sizeof(uint64_t) * (size_t)c->alpha * n);
-  uint64_t* conv = malloc(sizeof(uint64_t) * n);
-  for (int p = 0; p < 2; p++) {
-    uint64_t* ap = acc + (size_t)p * nt * n;
-    for (int k = 0; k < c->alpha; k++) {
-      uint64_t pk = c->q[c->L + k];
-      uint64_t hk = half_P_mod(c, pk);
-      memcpy(POLY(yP, k, n), POLY(ap, level + k, n), sizeof(uint64_t) * n);
-      intt_limb(c, c->L + k, POLY(yP, k, n));
-      for (uint32_t i = 0; i < n; i++) yP[(size_t)k * n + i] = addmod(yP[(size_t)k * n + i], hk, pk);
-    }
-    uint64_t* dst = p == 0 ? k0 : k1;
-    for (int t = 0; t < level; t++) {
-      uint64_t q = c->q[t];
-      uint64_t ht = half_P_mod(c, q);
-      moddown_conv(c, yP, t, conv);
-      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
-      ntt_limb(c, t, conv);
-      uint64_t pinv = invmod(P_mod(c, q), q);
-      const uint64_t* at = POLY(ap, t, n);
-      uint64_t* o = POLY(dst, t, n);
-      for (uint32_t i = 0; i < n; i++) o[i] = mulmod(submod(at[i], conv[i], q), pinv, q);
-    }
-  }
-  free(dc); free(acc); free(ext); free(yP); free(conv);
+  moddown_pair(c, acc, level, k0, k1);
+  free(dc); free(acc); free(ext);
 }
 
 /* key_id: -1 relinearisation key, i >= 0 Galois key i (in creation order). */
@@ -1135,6 +1144,90 @@ int orc_rotate(orc_ctx* c, const uint64_t* a, int level, int32_t r, uint64_t* ou
   return 0;
 }
 
+/* Sum of rotations with one shared decomposition (hoisting) [ext]:
+ *   out = a + sum_{s < ns} rot(a, r_s),   k_s = 5^{r_s} mod 2N.
+ * The paper leaves the evaluation of rotations to HEAAN; this is the standard
+ * hoisted form of a rotate-and-sum.  The digits of a1 are raised once,
+ *   y_j = ModUp_j(a1)  (coefficient form over Q_level and P; on the digit's
+ *                       own limbs the limb itself),
+ * rotation s takes kappa_{k_s}(y_j) (the coefficient automorphism applied to
+ * every limb) as its extended digit, the inner products of all rotations with
+ * their Galois keys are summed over Q_level * P, and one ModDown (division by
+ * P with rounding, as in keyswitch) gives (k0, k1):
+ *   out0 = a0 + sum_s kappa_{k_s}(a0) + k0,   out1 = a1 + k1.
+ * The approximate conversion is not odd (it maps -x to |D_j| Q_j - y, not to
+ * -y), so kappa(y_j) and ModUp_j(kappa(a1)) may differ by multiples of Q_j:
+ * the result encrypts the same sum as rotating and adding one at a time, with
+ * residues of its own.  Returns -2 when a Galois key is missing, -3 for a
+ * rotation by 0 slots. */
+#define ORC_MAX_ROT 16
+int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* steps, int ns, uint64_t* out) {
+  uint32_t n = c->n;
+  if (level < 1 || level > c->L || ns < 1 || ns > ORC_MAX_ROT) return -1;
+  int nt = level + c->alpha, beta_l = (level + c->alpha - 1) / c->alpha;
+  uint64_t ks[ORC_MAX_ROT];
+  const uint64_t* keys[ORC_MAX_ROT];
+  for (int s = 0; s < ns; s++) {
+    ks[s] = orc_galois_elt(c->log_n, steps[s]);
+    if (ks[s] == 1) return -3;
+    int gi = find_gal(c, ks[s]);
+    if (gi < 0) return -2;
+    keys[s] = c->gal[gi].key;
+  }
+  const uint64_t* a0 = a;
+  const uint64_t* a1 = a + (size_t)level * n;
+  uint64_t* dc = malloc(sizeof(uint64_t) * (size_t)level * n);
+  for (int t = 0; t < level; t++) {
+    memcpy(POLY(dc, t, n), POLY(a1, t, n), sizeof(uint64_t) * n);
+    intt_limb(c, t, POLY(dc, t, n));
+  }
+  uint64_t* acc = calloc((size_t)2 * nt * n, sizeof(uint64_t)); /* [2][nt][N], summed over rotations */
+  uint64_t* y = malloc(sizeof(uint64_t) * n);
+  uint64_t* z = malloc(sizeof(uint64_t) * n);
+  for (int j = 0; j < beta_l; j++) {
+    for (int ti = 0; ti < nt; ti++) {
+      int tp = ti < level ? ti : c->L + (ti - level);
+      uint64_t q = c->q[tp];
+      if (tp < level && tp >= digit_lo(c, j) && tp < digit_hi(c, j, level))
+        memcpy(y, POLY(dc, tp, n), sizeof(uint64_t) * n);
+      else
+        modup_limb(c, dc, level, j, tp, y);
+      for (int s = 0; s < ns; s++) {
+        orc_automorph_coef(y, z, c->log_n, q, ks[s]);
+        ntt_limb(c, tp, z);
+        const uint64_t* kb = keys[s] + ((size_t)(j * 2 + 0) * c->np + tp) * n;
+        const uint64_t* ka = keys[s] + ((size_t)(j * 2 + 1) * c->np + tp) * n;
+        uint64_t* s0 = POLY(acc, ti, n);
+        uint64_t* s1 = POLY(acc, nt + ti, n);
+        for (uint32_t i = 0; i < n; i++) {
+          s0[i] = addmod(s0[i], mulmod(z[i], kb[i], q), q);
+          s1[i] = addmod(s1[i], mulmod(z[i], ka[i], q), q);
+        }
+      }
+    }
+  }
+  uint64_t* k0 = malloc(sizeof(uint64_t) * (size_t)level * n);
+  uint64_t* k1 = malloc(sizeof(uint64_t) * (size_t)level * n);
+  moddown_pair(c, acc, level, k0, k1);
+  uint64_t* res = malloc(sizeof(uint64_t) * 2 * (size_t)level * n);
+  for (int t = 0; t < level; t++) {
+    uint64_t q = c->q[t];
+    uint64_t* r0 = POLY(res, t, n);
+    uint64_t* r1 = POLY(res, level + t, n);
+    for (uint32_t i = 0; i < n; i++) {
+      r0[i] = addmod(a0[(size_t)t * n + i], k0[(size_t)t * n + i], q);
+      r1[i] = addmod(a1[(size_t)t * n + i], k1[(size_t)t * n + i], q);
+    }
+    for (int s = 0; s < ns; s++) {
+      automorph_eval(c, POLY(a0, t, n), z, ks[s]);
+      for (uint32_t i = 0; i < n; i++) r0[i] = addmod(r0[i], z[i], q);
+    }
+  }
+  memcpy(out, res, sizeof(uint64_t) * 2 * (size_t)level * n);
+  free(dc); free(acc); free(y); free(z); free(k0); free(k1); free(res);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Encrypted logistic-regression gradient step (Sec. 4, Eq. 5-8, Table 2).   */
 /* ------------------------------------------------------------------------ */
@@ -1150,7 +1243,7 @@ int orc_rotate(orc_ctx* c, const uint64_t* a, int level, int32_t r, uint64_t* ou
  * Op sequence and scale plan (all scales IEEE doubles, computed in this exact
  * order on both implementations; l0 = input level; q[i] the limb primes):
  *   U  = HMult(Z_k, W)                 level l0-1, sU = sZ*sW/q[l0-1]
- *   M  = U + rot(., g), + rot(., 2g) ... + rot(., N/4)   (log2 F rotations)
+ *   M  = sum over o < F of rot(U, o*g)   (rotsum: hoisted stages of radix 4)
  *   T  = HMult(M, M)                   level l0-2, sT = sU*sU/q[l0-2]
  *   sS = ((sW*q[l0-5])*q[l0-4]) / (maskscale*sZ)         (target scale of S)
  *   sA = (sS*q[l0-3])/sT ;  A = rescale(M * round(c3*lr * sA*q[l0-2]/sU))
@@ -1162,9 +1255,9 @@ int orc_rotate(orc_ctx* c, const uint64_t* a, int level, int32_t r, uint64_t* ou
  *   S  = C + B (+ Q) + round(c0*lr * scale(C))
  *   G_k = HMult(S, drop(Z_k, l0-3))    level l0-4
  *   G  = sum_k G_k
- *   H  = G + rot(., 1) + rot(., 2) ... + rot(., g/2)
+ *   H  = sum over o < g of rot(G, o)     (rotsum)
  *   H' = rescale(H (x) mask), mask = 1 on slots = 0 mod g, encoded at maskscale
- *   R  = H' + rot(., -1) + rot(., -2) ... + rot(., -g/2)
+ *   R  = sum over o < g of rot(H', -o)   (rotsum)
  *   W' = drop(W, l0-5) + R             level l0-5
  * Additions require scales equal to within a relative 2^-40.
  */
@@ -1181,15 +1274,20 @@ static int scales_match(double a, double b) { return fabs(a / b - 1.0) < ldexp(1
 
 static int64_t round_const(double v) { return (int64_t)llround(v); }
 
+/* x <- sum over o = 0 .. 2^count - 1 of rot(x, o * step), in hoisted stages
+ * (orc_rotate_sum): while two or more doublings remain, one stage of radix 4
+ * (rotations by s, 2s, 3s, then s <- 4s); a last stage of radix 2 (rotation
+ * by s) when count is odd. */
 static int rotsum(orc_ctx* c, orc_ct* x, int32_t step, int count) {
-  /* x <- x + rot(x, step) + ... doubling: for i < count: x += rot(x, step << i) */
-  uint64_t* tmp = malloc(sizeof(uint64_t) * 2 * (size_t)x->level * c->n);
+  int32_t s = step;
   int rc = 0;
-  for (int i = 0; i < count && rc == 0; i++) {
-    rc = orc_rotate(c, x->d, x->level, step * (1 << i), tmp);
-    if (rc == 0) orc_add(c, x->d, tmp, x->level, x->d);
+  while (count > 0 && rc == 0) {
+    int32_t st[3] = {s, 2 * s, 3 * s};
+    int ns = count >= 2 ? 3 : 1;
+    rc = orc_rotate_sum(c, x->d, x->level, st, ns, x->d);
+    s *= ns + 1;
+    count -= count >= 2 ? 2 : 1;
   }
-  free(tmp);
   return rc;
 }
 

@@ -426,6 +426,32 @@ def he_rotate_batch(ctx, a: list, steps: int, out: list):
     return out
 
 
+def rotsum_stages(step: int, count: int) -> list:
+    """The stages in which a rotate-and-sum over the 2^count offsets 0, step,
+    2 step, ... is evaluated: one he_rotate_sum per stage, with rotations by
+    s, 2s, 3s (radix 4, then s <- 4s) while two or more doublings remain, and a
+    last stage with the rotation by s alone when count is odd."""
+    out, s = [], step
+    while count > 0:
+        ns = 3 if count >= 2 else 1
+        out.append([s * m for m in range(1, ns + 1)])
+        s *= ns + 1
+        count -= 2 if ns == 3 else 1
+    return out
+
+
+def lr_rot_steps(n_slots: int, g: int) -> list:
+    """Rotation steps whose Galois keys the gradient step and inference need
+    for g samples per ciphertext: the feature sum (stages of step g over
+    n_slots / g positions), the sample sum (step 1) and the replication
+    (step -1), each over g positions."""
+    log_f, log_g = (n_slots // g).bit_length() - 1, g.bit_length() - 1
+    steps = []
+    for st in rotsum_stages(g, log_f) + rotsum_stages(1, log_g) + rotsum_stages(-1, log_g):
+        steps += [r for r in st if r not in steps]
+    return steps
+
+
 def lr_config(coeffs, lr: float, g: int, mask_scale: float) -> he_lr_config:
     return he_lr_config((ctypes.c_double * 4)(*coeffs), float(lr), g, 0, float(mask_scale))
 

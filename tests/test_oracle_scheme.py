@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+import paper_2006_10091_gb300 as he
 from paper_2006_10091_gb300 import workloads
 from tests.lr_reference import lr_step_fp64, table2
 
@@ -364,8 +365,7 @@ def test_lr_step_matches_fp64_update(loss):
     n_slots = (1 << log_n) // 2
     F = n_slots // g
     data = workloads.LRData(seed=0, n_samples=16, n_features=100)
-    rots = [g << t for t in range(int(math.log2(F)))] + [1, 2, -1, -2]
-    o = oracle.Oracle(log_n, 7, 40, 1, 60, 2.0 ** 40, seed=1, rot_steps=rots)
+    o = oracle.Oracle(log_n, 7, 40, 1, 60, 2.0 ** 40, seed=1, rot_steps=he.lr_rot_steps(n_slots, g))
     coeffs = table2()[loss]
     lr = 1.0 / data.n
     Z = [_enc(o, v, 7, 100 + k) for k, v in enumerate(workloads.pack_samples(data.X, data.y, n_slots, g))]
@@ -420,13 +420,91 @@ def test_keyswitch_equals_big_integer_definition(tiny):
                 assert int(gotc[t][c]) == out % q[t], (p, c, t)
 
 
+def _kappa_int(y, k, n):
+    """X -> X^k on integer coefficients, X^N = -1."""
+    z = [0] * n
+    for i, v in enumerate(y):
+        e = i * k % (2 * n)
+        if e < n:
+            z[e] += v
+        else:
+            z[e - n] -= v
+    return z
+
+
+@pytest.mark.parametrize("steps", [[1, 3], [-1], [3, 1, -1]])
+def test_rotate_sum_equals_big_integer_definition(tiny, steps):
+    """The hoisted rotate-and-sum recomputed with Python integers: the digits
+    y_j of a1 are raised once (the integer ModUp of the key-switch pin above),
+    rotation s puts kappa_s(y_j) (X -> X^k_s over the integers) into its
+    products with its Galois key, all products are summed mod Q_level P and
+    divided by P once, with rounding; the addends are a0 + sum_s kappa_s(a0)
+    and a1.  Must equal the oracle's residues."""
+    o = tiny
+    level, n, L, alpha = 5, o.n, o.L, o.alpha
+    q = o.primes
+    P = math.prod(q[L:L + alpha])
+    h = (P - 1) // 2
+    a = workloads.residues(94, q[:level], n, parts=2)
+    out = o.rotate_sum(oracle.Ciphertext(a, level, o.scale), steps)
+    dc = [to_coef(o, a[p], level) for p in range(2)]
+    targets = list(range(level)) + list(range(L, L + alpha))
+    mod = math.prod(q[t] for t in targets)
+    ks = [oracle.galois_elt(o.log_n, s) for s in steps]
+    acc = [[0] * n, [0] * n]
+    for k in ks:
+        key = o.key(2 + o.gal_order.index(k))
+        for j in range((level + alpha - 1) // alpha):
+            digit = list(range(j * alpha, min((j + 1) * alpha, level)))
+            Qj = math.prod(q[i] for i in digit)
+            y = [0] * n
+            for i in digit:
+                qhat = Qj // q[i]
+                inv = pow(qhat, -1, q[i])
+                for c in range(n):
+                    y[c] += (int(dc[1][i][c]) * inv % q[i]) * qhat
+            yk = _kappa_int(y, k, n)
+            for p in range(2):
+                kc = [oracle.intt_def(key[j, p, t], o.log_n, q[t], o.roots[t]) for t in targets]
+                kint = [crt([kc[ti][c] for ti in range(len(targets))], [q[t] for t in targets]) for c in range(n)]
+                prod = negacyclic(yk, kint)
+                acc[p] = [(x + v) % mod for x, v in zip(acc[p], prod)]
+    for p in range(2):
+        gotc = to_coef(o, out.data[p], level)
+        for t in range(level):
+            addend = [int(v) for v in dc[p][t]]
+            if p == 0:
+                for k in ks:
+                    addend = [x + v for x, v in zip(addend, _kappa_int([int(v) for v in dc[0][t]], k, n))]
+            for c in range(n):
+                want = ((acc[p][c] + h) // P + addend[c]) % q[t]
+                assert int(gotc[t][c]) == want, (p, t, c)
+
+
+@pytest.mark.parametrize("steps", [[1, 2], [5, -7, -1], [2]])
+def test_rotate_sum_decrypts_to_the_sum_of_shifts(mid, steps):
+    o = mid
+    z = workloads.uniform_slots(7, o.n // 2)
+    a = _enc(o, z, 4, 8)
+    re, _ = o.decrypt(o.rotate_sum(a, steps))
+    want = z + sum(np.roll(z, -s) for s in steps)
+    assert np.max(np.abs(re - want)) < 2.0 ** -20
+
+
+def test_rotate_sum_refuses_missing_keys_and_zero_steps(mid):
+    a = _enc(mid, workloads.uniform_slots(8, mid.n // 2), 3, 9)
+    with pytest.raises(KeyError):
+        mid.rotate_sum(a, [3])
+    with pytest.raises(KeyError):
+        mid.rotate_sum(a, [1, 0])
+
+
 def test_lr_inference_matches_fp64_polynomial():
     log_n, g = 10, 4
     n_slots = (1 << log_n) // 2
     F = n_slots // g
     data = workloads.LRData(seed=2, n_samples=8, n_features=90)
-    rots = [g << t for t in range(int(math.log2(F)))]
-    o = oracle.Oracle(log_n, 6, 40, 1, 60, 2.0 ** 40, seed=4, rot_steps=rots)
+    o = oracle.Oracle(log_n, 6, 40, 1, 60, 2.0 ** 40, seed=4, rot_steps=he.lr_rot_steps(n_slots, g))
     coeffs = table2()["binomial"]
     Z = [_enc(o, v, 5, 300 + k) for k, v in enumerate(workloads.pack_samples(data.X, data.y, n_slots, g))]
     W = _enc(o, workloads.pack_weights(data.w0, n_slots, g), 5, 299)
