@@ -40,13 +40,13 @@ N_SAMPLES, N_FEATURES, G = 4096, 784, 8
 MASK_SCALE = 2.0 ** 27
 WORKLOAD = ("enc-LR gradient step (Eq. 7-8, Table 2 binomial): N=2^14, 8x40-bit limbs + 2x59-bit "
             "special primes (dnum 4), scale 2^40; 4096 samples x 784 features, 8 samples per ciphertext "
-            "(512 data ciphertexts); one step = 2048 mul+relin+rescale + 5126 rotations")
+            "(512 data ciphertexts); one step = 2048 mul+relin+rescale + 7688 rotations in 2564 hoisted "
+            "rotate-and-sum stages")
 
 
 def rot_steps(n_slots: int, g: int) -> list[int]:
-    F = n_slots // g
-    return ([g << t for t in range(int(math.log2(F)))] + [1 << t for t in range(int(math.log2(g)))]
-            + [-(1 << t) for t in range(int(math.log2(g)))])
+    import paper_2006_10091_gb300 as he
+    return he.lr_rot_steps(n_slots, g)
 
 
 def table2_binomial():
@@ -362,7 +362,10 @@ def hmult_rates(he, torch, stream):
     for name, (log_n, nl, bits, alpha, sbits, scale, count) in {
             "hmult_small": (12, 3, 40, 1, 60, 2.0 ** 30, 16),
             "hmult_large": (16, 24, 50, 4, 60, 2.0 ** 50, 64)}.items():
-        rots = [1 << t for t in range(10)] if name == "hmult_large" else []
+        rots = []
+        if name == "hmult_large":
+            rots = [1 << t for t in range(10)]
+            rots += [r for st in he.rotsum_stages(1, 10) for r in st if r not in rots]
         ctx = he.Context(log_n, nl, bits, alpha, sbits, scale, seed=0, stream=stream.cuda_stream, rot_steps=rots)
         n = 1 << log_n
         A, B, O = ctx.new_ct(nl, count), ctx.new_ct(nl, count), ctx.new_ct(nl, count)
@@ -393,21 +396,30 @@ def hmult_rates(he, torch, stream):
         out[name] = {"per_s_batched": batched, "per_s_plain": plain, "count": count, "N": n, "limbs": nl,
                      "max_abs_err": err}
         if name == "hmult_large":
-            # 1024-slot rotate-and-sum: ten rotations by 1, 2, ..., 512, each batched over the 64
+            # 1024-slot rotate-and-sum over the 64: hoisted stages (five of rotations
+            # by s, 2s, 3s), and as ten rotations by 1, 2, ..., 512 with additions
             T = ctx.new_ct(nl, count)
+            stages = he.rotsum_stages(1, 10)
+
             def rotsum():
+                for st in stages:
+                    he.he_rotate_sum_batch(ctx, O, st, T)
+                    O[:], T[:] = T[:], O[:]
+
+            def rotsum_sequential():
                 for t in range(10):
                     he.he_rotate_batch(ctx, O, 1 << t, T)
                     for i in range(count):
                         he.he_add(ctx, O[i], T[i], O[i])
-            rotsum()
-            torch.cuda.synchronize()
-            e0.record(stream)
-            rotsum()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            out[name]["rotate_and_sum_per_s"] = count * 1000.0 / e0.elapsed_time(e1)
-            out[name]["rotations_per_s"] = 10 * count * 1000.0 / e0.elapsed_time(e1)
+            for fn, key in ((rotsum, "rotate_and_sum_per_s"), (rotsum_sequential, "rotate_and_sum_sequential_per_s")):
+                fn()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                out[name][key] = count * 1000.0 / e0.elapsed_time(e1)
+            out[name]["rotate_and_sum_stages"] = [list(st) for st in stages]
         ctx.close()
         del A, B, O
         torch.cuda.empty_cache()
@@ -547,8 +559,11 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
     t_setup = time.perf_counter()
     ctxs = []
     for log_n in SERVE_LOG_NS:
-        k = log_n - 1
-        rots = [1 << t for t in range(k)] + [-(1 << t) for t in range(k - 6)]
+        n_slots = 1 << (log_n - 1)
+        rots = []  # every sample count per ciphertext the feature counts 64..4096 give
+        for F in (64 << t for t in range(7)):
+            if F <= n_slots:
+                rots += [r for r in he.lr_rot_steps(n_slots, n_slots // F) if r not in rots]
         ctxs.append(he.Context(log_n, SERVE_L, SERVE_BITS, SERVE_ALPHA, 60, SERVE_SCALE, seed=0, rot_steps=rots,
                                stream=stream.cuda_stream))
     classes, wbuf, obuf = {}, {}, {}

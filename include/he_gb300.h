@@ -231,13 +231,35 @@ int he_mul_relin_rescale_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, he_c
                                size_t count);
 int he_rotate_batch(he_ctx* ctx, const he_ct* a, int32_t steps, he_ct* out, size_t count);
 
+/* Rotate-and-sum with one shared decomposition: out = a + sum_{r < nsteps}
+ * rotate(a, steps[r]), 1 <= nsteps <= 8, the sums over slot positions that
+ * the packing of Sec. 3-4 reads inner products from.  The key switches of all
+ * nsteps rotations share the ModUp of a's second part (each rotation applies
+ * its automorphism to the raised digits) and one ModDown of their summed
+ * inner products, so a stage of three rotations costs about one and a half
+ * key switches instead of three.  Its residues differ from those of
+ * he_rotate + he_add (the approximate basis conversion does not commute with
+ * the automorphism's sign flips) but it decrypts to the same sum with the
+ * noise of one key switch.  out (level and scale of a) may be a; other
+ * overlaps of inputs and outputs are refused (HE_EINVAL).  HE_ENOKEY if a
+ * step has no Galois key, HE_EINVAL for a step of 0 slots.  The batched form
+ * takes count ciphertexts of one level. */
+int he_rotate_sum(he_ctx* ctx, const he_ct* a, const int32_t* steps, uint32_t nsteps, he_ct* out);
+int he_rotate_sum_batch(he_ctx* ctx, const he_ct* a, const int32_t* steps, uint32_t nsteps, he_ct* out,
+                        size_t count);
+
 /* Encrypted logistic-regression gradient step (Sec. 4: Eq. 5-8 with a Table 2
  * polynomial; Algorithm 1).  Z[k] hold g samples each, slot g*f + s =
  * y_s*x_{s,f}; W holds w_f in slots g*f + s for every s.  Computes
  * w' = w + lr * sum_k sum_s p(y_s w.x_s) y_s x_s with p(x) = c0 + c1 x +
  * c2 x^2 + c3 x^3, replicated over the g slots of each feature.  Consumes 5
  * levels: Z and W at the same level l >= 6; W_out at l - 5 with W's scale.
- * Needs Galois keys for steps g*2^i (i < log2(N/(2g))), 2^i and -2^i (i < log2 g). */
+ * Each of its three rotate-and-sums (over F = N/(2g) feature positions of
+ * step g, and over the g samples with steps 1 and -1) runs as he_rotate_sum
+ * stages: steps s, 2s, 3s while two or more doublings remain (then s <- 4s),
+ * and a stage of step s alone when the number of doublings is odd.  Needs
+ * Galois keys for all those steps (e.g. for g = 8, F = 1024: 8, 16, 24, 32,
+ * ..., 6144 and 1, 2, 3, 4, -1, -2, -3, -4). */
 typedef struct he_lr_config {
   double coeffs[4];     /* c0..c3 */
   double lr;            /* learning rate, e.g. eta / n */

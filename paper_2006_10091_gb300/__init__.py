@@ -116,6 +116,8 @@ def load():
         "he_rotate": [VP, CTP, ctypes.c_int32, CTP],
         "he_mul_relin_rescale_batch": [VP, CTP, CTP, CTP, ctypes.c_size_t],
         "he_rotate_batch": [VP, CTP, ctypes.c_int32, CTP, ctypes.c_size_t],
+        "he_rotate_sum": [VP, CTP, VP, ctypes.c_uint32, CTP],
+        "he_rotate_sum_batch": [VP, CTP, VP, ctypes.c_uint32, CTP, ctypes.c_size_t],
         "he_lr_gradient_step": [VP, CTP, ctypes.c_size_t, CTP, ctypes.POINTER(he_lr_config), CTP],
         "he_refresh": [VP, CTP, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32, CTP],
         "he_ntt": [VP, VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
@@ -407,6 +409,23 @@ def he_mul_relin(ctx, a, b, out):
 
 def he_rotate(ctx, a, steps: int, out):
     _run(load().he_rotate, ctx, [out], a, steps, out)
+    return out
+
+
+def he_rotate_sum(ctx, a, steps, out):
+    """out = a + sum of rotate(a, s) over steps (1 to 8 steps), one shared
+    decomposition; out may be a."""
+    st = (ctypes.c_int32 * len(steps))(*steps)
+    _run(load().he_rotate_sum, ctx, [out], a, st, len(steps), out)
+    return out
+
+
+def he_rotate_sum_batch(ctx, a: list, steps, out: list):
+    st = (ctypes.c_int32 * len(steps))(*steps)
+    A, O = _batch(a), _batch(out)
+    _check(load().he_rotate_sum_batch(ctx.ptr, A, st, len(steps), O, len(a)))
+    for o, s in zip(out, O):
+        o.update(s)
     return out
 
 

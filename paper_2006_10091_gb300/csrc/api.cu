@@ -708,6 +708,82 @@ int he_rotate_batch(he_ctx* c, const he_ct* a, int32_t steps, he_ct* out, size_t
   return HE_OK;
 }
 
+static int rotsum_chunks(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, size_t count, const uint64_t* gals,
+                         uint32_t nrot) {
+  const size_t per = rotsum_words(c, level, 1, nrot) * sizeof(uint64_t);
+  size_t chunk = std::max<size_t>(1, c->chunk_bytes / per);
+  chunk = std::min(chunk, count);
+  HE_TRY(ws_reserve(c, rotsum_words(c, level, (uint32_t)chunk, nrot) * sizeof(uint64_t) + 8192));
+  for (size_t i0 = 0; i0 < count; i0 += chunk) {
+    const uint32_t m = (uint32_t)std::min(chunk, count - i0);
+    CtBatch a = A, o = O;
+    a.base += i0 * A.stride;
+    o.base += i0 * O.stride;
+    Arena ar = arena(c);
+    HE_TRY(rotsum_batch(c, a, level, m, gals, nrot, o, ar));
+  }
+  return HE_OK;
+}
+
+int he_rotate_sum(he_ctx* c, const he_ct* a, const int32_t* steps, uint32_t nsteps, he_ct* out) {
+  return he_rotate_sum_batch(c, a, steps, nsteps, out, 1);
+}
+
+int he_rotate_sum_batch(he_ctx* c, const he_ct* a, const int32_t* steps, uint32_t nsteps, he_ct* out,
+                        size_t count) {
+  if (!c || !a || !out || !steps) return fail(HE_EINVAL, "he_rotate_sum: null argument");
+  if (nsteps < 1 || nsteps > HE_MAX_ROT) return fail(HE_EINVAL, "he_rotate_sum: 1 to 8 steps");
+  if (count == 0) return HE_OK;
+  for (size_t i = 0; i < count; ++i) {
+    HE_TRY(check_ct(c, &a[i], "he_rotate_sum"));
+    if (a[i].level != a[0].level) return fail(HE_EINVAL, "batched operands must share one level");
+    HE_TRY(check_out(c, &out[i], a[i].level, "he_rotate_sum"));
+  }
+  const uint32_t level = a[0].level;
+  uint64_t gals[HE_MAX_ROT];
+  for (uint32_t r = 0; r < nsteps; ++r) {
+    gals[r] = h_galois_elt(c->log_n, steps[r]);
+    if (gals[r] == 1) return fail(HE_EINVAL, "he_rotate_sum: a rotation by 0 slots");
+    if (!galois_key(c, gals[r])) return fail(HE_ENOKEY, "no Galois key for this rotation");
+  }
+  // out[i] may be a[i] (then through a copy of the input); no other overlap
+  bool overlap = false;
+  for (size_t i = 0; i < count; ++i)
+    for (size_t k = 0; k < count; ++k) {
+      const char* a_lo = (const char*)a[i].data;
+      const char* a_hi = a_lo + sizeof(uint64_t) * 2 * (size_t)a[i].cap * c->n;
+      const char* o_lo = (const char*)out[k].data;
+      const char* o_hi = o_lo + sizeof(uint64_t) * 2 * (size_t)out[k].cap * c->n;
+      if (o_hi <= a_lo || a_hi <= o_lo) continue;
+      if (i != k) return fail(HE_EINVAL, "he_rotate_sum: an output overlaps another ciphertext's input");
+      overlap = true;
+    }
+  CtBatch A, O;
+  if (!overlap && uniform_view(a, count, &A) && uniform_view(out, count, &O)) {
+    HE_TRY(rotsum_chunks(c, A, O, level, count, gals, nsteps));
+  } else {
+    uint64_t* tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(uint64_t) * 2 * (size_t)level * c->n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HE_ENOMEM, "he_rotate_sum: copy of the input");
+    }
+    int rc = HE_OK;
+    const CtBatch T{tmp, 0, level, 0};
+    for (size_t i = 0; i < count && rc == HE_OK; ++i) {
+      rc = copy_batch(c, one(&a[i]), T, level, 1);
+      if (rc == HE_OK) rc = rotsum_chunks(c, T, one(&out[i]), level, 1, gals, nsteps);
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    HE_TRY(rc);
+  }
+  for (size_t i = 0; i < count; ++i) {
+    out[i].level = level;
+    out[i].scale = a[i].scale;
+  }
+  return HE_OK;
+}
+
 int he_refresh(he_ctx* c, const he_ct* a, uint32_t level, double out_scale, uint32_t cid, he_ct* out) {
   if (!c) return fail(HE_EINVAL, "null context");
   HE_TRY(check_ct(c, a, "he_refresh"));

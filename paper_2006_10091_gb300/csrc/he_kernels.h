@@ -3,6 +3,7 @@
 #include "he_common.cuh"
 
 #define HE_MAX_DIGIT 8
+#define HE_MAX_ROT 8  // rotations one hoisted rotate-and-sum stage may take
 
 namespace he {
 
@@ -26,6 +27,13 @@ struct ModUpArgs {
   uint64_t off[HE_MAX_PRIMES];
 };
 
+// The rotations of one hoisted rotate-and-sum: Galois elements and keys.
+struct RotSet {
+  uint32_t n;
+  uint64_t gal[HE_MAX_ROT];
+  const uint64_t* evk[HE_MAX_ROT];
+};
+
 struct LimbConsts {
   uint64_t w[HE_MAX_PRIMES];
   uint64_t wsh[HE_MAX_PRIMES];
@@ -41,6 +49,15 @@ __global__ void k_inner_product(const uint64_t* ext, uint64_t ext_stride, const 
                                 uint64_t acc_stride, uint32_t level, uint32_t alpha, uint32_t beta,
                                 uint32_t L, uint32_t np, uint32_t count, int log_n,
                                 const PrimeDev* primes);
+__global__ void k_inner_product_rot(const uint64_t* ext, uint64_t ext_stride, const uint64_t* d,
+                                    uint64_t d_stride, RotSet rs, uint64_t* acc, uint64_t acc_stride,
+                                    uint64_t acc_rstride, uint32_t level, uint32_t alpha, uint32_t beta,
+                                    uint32_t L, uint32_t np, uint32_t count, int log_n, const PrimeDev* primes);
+__global__ void k_sum_acc(uint64_t* acc, uint64_t acc_stride, uint64_t acc_rstride, uint32_t nsum, uint32_t t0,
+                          uint32_t t1, uint32_t nt, uint32_t level, uint32_t L, uint32_t count, int log_n,
+                          const PrimeDev* primes);
+__global__ void k_add_automorphs(CtBatch A, CtBatch O, RotSet rs, uint32_t level, uint32_t count, int log_n,
+                                 const PrimeDev* primes);
 __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_t* conv,
                                uint64_t conv_stride, uint32_t level, uint32_t alpha, uint32_t L,
                                uint32_t count, int log_n, const PrimeDev* primes,

@@ -57,7 +57,11 @@ int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t co
 int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out,
                  Arena& ar);
 int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count);
-int rotate_add_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out, Arena& ar);
+// out = A + sum_r rotate(A, gals[r]) (1 <= nrot <= HE_MAX_ROT), one hoisted
+// decomposition and one ModDown; out must not overlap A.
+int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uint64_t* gals, uint32_t nrot,
+                 CtBatch out, Arena& ar);
+size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count, uint32_t nrot);
 int mul_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int add_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int copy_batch(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, uint32_t count);

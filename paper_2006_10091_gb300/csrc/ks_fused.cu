@@ -6,10 +6,8 @@ namespace he {
 
 // ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
 // sets *handled when N has a compiled shape.
-int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled) {
-  *handled = false;
-  if (!ks_fusable(c)) return HE_OK;
+static KsFusedArgs ks_args(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext,
+                           uint64_t* acc, const uint64_t* evk, uint32_t level, uint64_t gal, bool half) {
   KsFusedArgs a;
   a.gal = gal;
   a.half = half ? 1 : 0;
@@ -19,7 +17,7 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
   a.ext = ext;
   a.acc = acc;
   a.evk = evk;
-  a.evk_sh = evk + c->key_words();
+  a.evk_sh = evk ? evk + c->key_words() : nullptr;
   a.d_stride = d_stride;
   a.level = level;
   a.alpha = (uint32_t)c->alpha;
@@ -36,6 +34,14 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
     a.cnt[j] = mc.cnt;
     a.off[j] = mc.off;
   }
+  return a;
+}
+
+int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
+             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled) {
+  *handled = false;
+  if (!ks_fusable(c)) return HE_OK;
+  const KsFusedArgs a = ks_args(c, d, d_stride, d2c, ext, acc, evk, level, gal, half);
   *handled = true;
   switch (c->log_n) {  // the tile shapes of ntt2.cu
     case 12: return ks_fused_n12(c, a, count);
@@ -43,6 +49,53 @@ int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2
     case 14: return ks_fused_n14(c, a, count);
     case 15: return ks_fused_n15(c, a, count);
     default: return ks_fused_n16(c, a, count);
+  }
+}
+
+// Inverse of an odd Galois element modulo 2N (Newton's iteration for the
+// inverse modulo 2^64, then reduced).
+static uint64_t gal_inverse(uint64_t gal, int log_n) {
+  uint64_t x = gal;  // correct to 3 bits
+  for (int i = 0; i < 5; ++i) x *= 2 - gal * x;
+  return x & ((2ull << log_n) - 1);
+}
+
+bool ks_rot_fits(const he_ctx* c, uint32_t level) {
+  if (!ks_fusable(c)) return false;
+  const uint32_t beta = (level + (uint32_t)c->alpha - 1) / (uint32_t)c->alpha;
+  size_t smem = 0;
+  switch (c->log_n) {
+    case 12: smem = ks_rot_smem_n12(c, beta); break;
+    case 13: smem = ks_rot_smem_n13(c, beta); break;
+    case 14: smem = ks_rot_smem_n14(c, beta); break;
+    case 15: smem = ks_rot_smem_n15(c, beta); break;
+    default: smem = ks_rot_smem_n16(c, beta); break;
+  }
+  return smem <= kRotSmemMax;
+}
+
+// ModUp -> NTT -> the inner products of every rotation of a hoisted
+// rotate-and-sum, fused; rotation r's accumulators at acc + r*acc_rstride.
+int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
+           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled) {
+  *handled = false;
+  if (!ks_rot_fits(c, level)) return HE_OK;
+  KsRotArgs ra;
+  ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
+  ra.nrot = rs.n;
+  ra.acc_rstride = acc_rstride;
+  for (uint32_t r = 0; r < rs.n; ++r) {
+    ra.gal[r] = rs.gal[r];
+    ra.gal_inv[r] = gal_inverse(rs.gal[r], c->log_n);
+    ra.evk[r] = rs.evk[r];
+    ra.evk_sh[r] = rs.evk[r] + c->key_words();
+  }
+  switch (c->log_n) {
+    case 12: return ks_rot_n12(c, ra, count, handled);
+    case 13: return ks_rot_n13(c, ra, count, handled);
+    case 14: return ks_rot_n14(c, ra, count, handled);
+    case 15: return ks_rot_n15(c, ra, count, handled);
+    default: return ks_rot_n16(c, ra, count, handled);
   }
 }
 
@@ -55,13 +108,17 @@ namespace he {
 // compiled shapes (the same ones as the NTT and ModUp).
 static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);
 
-int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
+int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t nsum, uint64_t sum_stride,
+                 uint64_t* conv, CtBatch add, int add_mode, const uint64_t* gals, uint32_t n_gal, CtBatch out,
+                 uint32_t level, uint32_t count, bool* handled) {
   *handled = false;
-  if (!ks_fusable(c)) return HE_OK;
+  if (!ks_fusable(c) || n_gal > HE_MAX_ROT) return HE_OK;
   const uint32_t nt = level + (uint32_t)c->alpha;
   MdArgs a;
-  a.add_gal = add_gal;
+  a.n_gal = n_gal;
+  for (uint32_t g = 0; g < n_gal; ++g) a.gal[g] = gals[g];
+  a.nsum = nsum;
+  a.sum_stride = sum_stride;
   a.yP = acc + (size_t)level * c->n;
   a.yp_stride = acc_stride;
   a.yp_pstride = (uint64_t)nt * c->n;
@@ -80,6 +137,12 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
   return md_dispatch(c, a, count, handled);
 }
 
+int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
+             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
+  return md_fused_sum(c, acc, acc_stride, 1, 0, conv, add, add_mode, &add_gal, add_gal ? 1 : 0, out, level, count,
+                      handled);
+}
+
 // Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
 // last: the dropped limb of both parts in coefficient form, count x [2][N].
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
@@ -88,7 +151,9 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
   if (!ks_fusable(c) || level < 2) return HE_OK;
   const uint32_t lt = level - 1;
   MdArgs a;
-  a.add_gal = 0;
+  a.n_gal = 0;
+  a.nsum = 1;
+  a.sum_stride = 0;
   a.yP = last;
   a.yp_stride = 2ull * c->n;
   a.yp_pstride = c->n;

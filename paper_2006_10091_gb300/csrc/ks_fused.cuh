@@ -22,6 +22,8 @@ namespace he {
 
 // Dynamic shared memory the all-targets conversion kernels may take.
 constexpr size_t kModupAllSmem = 160 * 1024;
+// ... and the hoisted rotate-and-sum's row pass (every digit's tile).
+constexpr size_t kRotSmemMax = 200 * 1024;
 
 struct KsFusedArgs {
   const uint64_t* d;     // input, evaluation form: count x [level][N] at d_stride
@@ -306,6 +308,120 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
   }
 }
 
+// ---- hoisted rotate-and-sum ------------------------------------------------
+// The rotations of one rotate-and-sum stage share the decomposition of the
+// input: the column pass (ks_modup_col[_all], run once) and the row pass of
+// every digit.  Rotation r then needs the products of the permuted digits,
+//   acc_r[e] = sum_j D_j[src_r(e)] * evk_r[j][e],  src_r = automorph_src(., gal_r),
+// with a permutation of the evaluation points that maps rows to rows: in
+// bit-reversed order a row of M points is a residue class of the natural
+// index modulo N/M, and X -> X^gal maps residue classes onto residue
+// classes.  So the CTA that holds input row c after the row pass can write
+// the whole of output row c' = src_{gal^-1}(c M) / M with coalesced stores and
+// key loads, reading its sources from shared memory.
+struct KsRotArgs {
+  KsFusedArgs k;           // k.acc: the accumulators of rotation 0
+  uint32_t nrot;
+  uint64_t acc_rstride;    // words between the accumulators of consecutive rotations
+  uint64_t gal[HE_MAX_ROT], gal_inv[HE_MAX_ROT];
+  const uint64_t* evk[HE_MAX_ROT];
+  const uint64_t* evk_sh[HE_MAX_ROT];
+};
+
+// Grid: count * nt * TILES.  Shared memory: the tile's twiddles and every
+// digit's transformed tile ([beta][TILE + TILE/8] words).
+template <int LOG_N, int LOG_M, int LOG_K>
+__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRotArgs ra) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
+  constexpr uint32_t N = 1u << LOG_N;
+  constexpr int PER = S::TILE / S::T;  // 8
+  constexpr uint32_t TW = S::TILE + S::TILE / 8;
+  const KsFusedArgs& a = ra.k;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
+  uint64_t* dig = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
+  uint32_t b = blockIdx.x;
+  const uint32_t tile = b % S::TILES;
+  b /= S::TILES;
+  const uint32_t t = b % a.nt, i = b / a.nt;
+  const uint32_t prime = ks_prime(t, a.level, a.L);
+  const PrimeDev pr = a.primes[prime];
+  const uint64_t q = pr.q, q2 = q + q;
+  const bool lazy = q < (1ull << 58);
+  const bool acc_lazy = q < ~0ull / (2ull * a.beta);
+  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
+  // 1. every digit's tile in evaluation form, canonical residues
+  for (uint32_t j = 0; j < a.beta; ++j) {
+    uint64_t* sm = dig + (size_t)j * TW;
+    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
+    const uint64_t* src = own ? a.d + (size_t)i * a.d_stride + (size_t)t * N
+                              : a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+    }
+    if (own) continue;
+    __syncthreads();
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint64_t v = sm[idx + (idx >> 3)];
+      sm[idx + (idx >> 3)] = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
+    }
+  }
+  __syncthreads();
+  // 2. per rotation, the products of the permuted digits with its key
+  auto mac = [&](uint64_t& acc, uint64_t x, uint64_t k, uint64_t ksh) {
+    acc += mul_shoup_lazy(x, k, ksh, q);
+    if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
+  };
+  const uint32_t row0 = (uint32_t)tile << LOG_K;
+  constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
+  for (uint32_t r = 0; r < ra.nrot; ++r) {
+    const uint64_t* ev = ra.evk[r];
+    const uint64_t* es = ra.evk_sh[r];
+    uint64_t* o0 = a.acc + (size_t)r * ra.acc_rstride + ((size_t)i * 2 * a.nt + t) * N;
+    uint64_t* o1 = o0 + (size_t)a.nt * N;
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += GRP) {
+      uint32_t so[GRP], eo[GRP];
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) {
+        const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
+        const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
+        const uint32_t row = row0 + k;
+        const uint32_t orow = automorph_src(row << LOG_M, ra.gal_inv[r], LOG_N) >> LOG_M;
+        const uint32_t e = (orow << LOG_M) | x;
+        const uint32_t sl = (k << LOG_M) | (automorph_src(e, ra.gal[r], LOG_N) & (S::M - 1));
+        so[u] = sl + (sl >> 3);
+        eo[u] = e;
+      }
+      uint64_t acc0[GRP], acc1[GRP];
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) acc0[u] = acc1[u] = 0;
+      for (uint32_t j = 0; j < a.beta; ++j) {
+        const uint64_t* sm = dig + (size_t)j * TW;
+        const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
+        const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
+#pragma unroll
+        for (int u = 0; u < GRP; ++u) {
+          const uint64_t x = sm[so[u]];
+          mac(acc0[u], x, __ldg(ev + kb_off + eo[u]), __ldg(es + kb_off + eo[u]));
+          mac(acc1[u], x, __ldg(ev + ka_off + eo[u]), __ldg(es + ka_off + eo[u]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) {
+        o0[eo[u]] = reduce64(acc0[u], pr);
+        o1[eo[u]] = reduce64(acc1[u], pr);
+      }
+    }
+  }
+}
+
 // ---- ModDown, fused the same way ------------------------------------------
 // The P-part of the accumulators (coefficient form after its inverse NTT) is
 // converted to each target limb inside the load of the forward NTT's column
@@ -319,10 +435,13 @@ struct MdArgs {
   const uint64_t* yP;
   uint64_t yp_stride, yp_pstride;
   CtBatch accq;         // the Q part (evaluation form), limbs 0 .. level-1
+  uint32_t nsum;        // accq is the sum of nsum accumulators, sum_stride words apart
+  uint64_t sum_stride;
   uint64_t* conv;       // count x [2][level][N]: column-pass outputs
   CtBatch add, out;
   int has_add;          // 0 none, 1 part 0 only, 2 both parts, 3 permuted on part 0 plus plain on both
-  uint64_t add_gal;     // the addend is read through the automorphism X -> X^add_gal (0: none)
+  uint32_t n_gal;       // part 0 of the addend is added through each automorphism X -> X^gal[g]
+  uint64_t gal[HE_MAX_ROT];
   uint32_t level, alpha, L;
   uint32_t sp0;         // prime index of the first special prime (L; l for a rescale by q_l)
   const PrimeDev* primes;
@@ -425,7 +544,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
     // latency overlaps its rounds
     const uint64_t* accq = cpoly(a.accq, i, p, t, N);
     const bool add = a.has_add >= 2 || (a.has_add == 1 && p == 0);
-    const bool add_perm = (a.has_add == 1 || a.has_add == 3) && p == 0 && a.add_gal;  // part 0 through the automorphism
+    const bool add_perm = (a.has_add == 1 || a.has_add == 3) && p == 0 && a.n_gal;  // part 0 through the automorphisms
     const bool add_plain = a.has_add == 3 || (add && !add_perm);                     // the addend as it is
     const uint64_t* ad = add ? cpoly(a.add, i, p, t, N) : nullptr;
     uint64_t av[PER], dv[PER];
@@ -433,9 +552,12 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = threadIdx.x + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      av[u] = __ldg(accq + e);
+      uint64_t x = __ldg(accq + e);
+      for (uint32_t s = 1; s < a.nsum; ++s) x = add_mod(x, __ldg(accq + s * a.sum_stride + e), q);
+      av[u] = x;
       uint64_t d = add_plain ? __ldg(ad + e) : 0;
-      if (add_perm) d = add_mod(d, __ldg(ad + automorph_src(e, a.add_gal, LOG_N)), q);
+      if (add_perm)
+        for (uint32_t g = 0; g < a.n_gal; ++g) d = add_mod(d, __ldg(ad + automorph_src(e, a.gal[g], LOG_N)), q);
       dv[u] = d;
     }
     __syncthreads();
@@ -506,19 +628,17 @@ size_t ks_all_smem(const he_ctx* c, uint32_t beta, const uint32_t* cnt) {
          sizeof(uint64_t) * (size_t)cnt_max * SC::TILE;
 }
 
-template <int LOG_N, int M1, int K1, int M2, int K2>
-int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
+// The ModUp + column-pass launch shared by the key switch and the hoisted
+// rotate-and-sum.
+template <int LOG_N, int M1, int K1>
+int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   using SC = Shape<LOG_N, M1, K1, true>;
-  using SR = Shape<LOG_N, M2, K2, false>;
   const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
-  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
   static unsigned long long attr_set = 0;
   if (c->device < 64 && !(attr_set & (1ull << c->device))) {
     HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
     HE_CUDA(cudaFuncSetAttribute(ks_modup_col_all<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kModupAllSmem));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
     attr_set |= 1ull << c->device;
   }
   const double n = (double)(1u << LOG_N);
@@ -528,7 +648,7 @@ int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   double conv_products = 0;  // basis-conversion products (none when a digit is one limb)
   for (uint32_t j = 0; j < a.beta; ++j)
     if (a.cnt[j] > 1) conv_products += (double)(a.nt - a.cnt[j]) * a.cnt[j];
-  // work = modular products: butterflies, conversion products, inner-product products
+  // work = modular products: butterflies, conversion products
   {
     // with a half-transformed input the kernel also runs the inverse column pass of the level input limbs
     const double inv_bfly = a.half ? (double)a.level * n / 2 * M1 + (double)a.level * n : 0.0;
@@ -545,6 +665,24 @@ int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
     }
   }
   HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+template <int LOG_N, int M1, int K1, int M2, int K2>
+int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
+  using SR = Shape<LOG_N, M2, K2, false>;
+  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
+  static unsigned long long attr_set = 0;
+  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
+    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    attr_set |= 1ull << c->device;
+  }
+  const double n = (double)(1u << LOG_N);
+  double own = 0;  // limbs each ciphertext takes as they are
+  for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
+  const double conv = (double)a.beta * a.nt - own;  // converted limbs per ciphertext
+  HE_TRY((ks_modup_launch<LOG_N, M1, K1>(c, a, count)));
   {
     const size_t blocks = (size_t)count * a.nt * SR::TILES;
     ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * a.beta * a.nt * n),
@@ -556,11 +694,52 @@ int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   return HE_OK;
 }
 
+// Dynamic shared memory of ks_row_rot (row tiles of half the row pass's
+// tile: M2 x 2^(K2-1)) for beta digits.
+template <int LOG_N, int M2, int K2>
+size_t ks_rot_smem(uint32_t beta) {
+  using SR = Shape<LOG_N, M2, K2 - 1, false>;
+  return sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8) * beta;
+}
+
+// The hoisted rotate-and-sum's ModUp, column pass and row pass with the
+// inner products of every rotation.  *handled = false (nothing launched)
+// when the digits' tiles do not fit in shared memory.
+template <int LOG_N, int M1, int K1, int M2, int K2>
+int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled) {
+  using SR = Shape<LOG_N, M2, K2 - 1, false>;
+  const KsFusedArgs& a = ra.k;
+  const size_t smr = ks_rot_smem<LOG_N, M2, K2>(a.beta);
+  *handled = smr <= kRotSmemMax;
+  if (!*handled) return HE_OK;
+  static unsigned long long attr_set = 0;
+  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
+    HE_CUDA(cudaFuncSetAttribute(ks_row_rot<LOG_N, M2, K2 - 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRotSmemMax));
+    attr_set |= 1ull << c->device;
+  }
+  HE_TRY((ks_modup_launch<LOG_N, M1, K1>(c, a, count)));
+  const double n = (double)(1u << LOG_N);
+  double own = 0;
+  for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
+  const double conv = (double)a.beta * a.nt - own;
+  {
+    const size_t blocks = (size_t)count * a.nt * SR::TILES;
+    ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * ra.nrot * a.beta * a.nt * n),
+                   count * n * 8 * (conv + own + 2.0 * ra.nrot * a.nt));
+    ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(ra);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
 // Per ring size (ks_fused_n12.cu .. ks_fused_n16.cu: one translation unit
 // each, so that the template instances compile in parallel): the launches
 // for the tile shape c->ntt_shape.
 #define HE_KS_FUSED_DECL(NN)                                                         \
   int ks_fused_n##NN(he_ctx* c, const KsFusedArgs& a, uint32_t count);               \
+  int ks_rot_n##NN(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled);    \
+  size_t ks_rot_smem_n##NN(const he_ctx* c, uint32_t beta);                          \
   int md_fused_n##NN(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);     \
   size_t ks_all_smem_n##NN(const he_ctx* c, uint32_t beta, const uint32_t* cnt);
 HE_KS_FUSED_DECL(12)

@@ -10,6 +10,17 @@ int ks_fused_n13(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
        : sh == 2 ? ks_fused_run<13, 4, 7, 9, 2>(c, a, count) : ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
 }
 
+int ks_rot_n13(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled) {
+  const int sh = c->ntt_shape;
+  return sh == 1 ? ks_rot_run<13, 6, 5, 7, 4>(c, a, count, handled)
+       : sh == 2 ? ks_rot_run<13, 4, 7, 9, 2>(c, a, count, handled) : ks_rot_run<13, 7, 4, 6, 5>(c, a, count, handled);
+}
+
+size_t ks_rot_smem_n13(const he_ctx* c, uint32_t beta) {
+  const int sh = c->ntt_shape;
+  return sh == 1 ? ks_rot_smem<13, 7, 4>(beta) : sh == 2 ? ks_rot_smem<13, 9, 2>(beta) : ks_rot_smem<13, 6, 5>(beta);
+}
+
 int md_fused_n13(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   const int sh = c->ntt_shape;
   return sh == 1 ? md_fused_run<13, 6, 5, 7, 4>(c, a, count, handled)

@@ -3,17 +3,20 @@
 //
 // Packing: each data ciphertext holds g samples interleaved, slot g*f + s =
 // y_s * x_{s,f}; W holds w_f in slots g*f + s for every s.  Because slot
-// rotations are cyclic over all N/2 slots, summing rotations by g, 2g, ...,
-// N/4 leaves in every slot g*f + s the full inner product m_s = w . z_s of
-// its own sample, so no mask is needed before the polynomial.  After the
-// polynomial, rotations by 1, 2, ..., g/2 collect the per-feature sum on
-// slots = 0 mod g, a 0/1 mask keeps those, and rotations by -1, ..., -g/2
-// copy it back to all g slots.
+// rotations are cyclic over all N/2 slots, the sum of the rotations by o*g
+// for o < F = N/(2g) leaves in every slot g*f + s the full inner product
+// m_s = w . z_s of its own sample, so no mask is needed before the
+// polynomial.  After the polynomial, the sum of the rotations by o < g
+// collects the per-feature sum on slots = 0 mod g, a 0/1 mask keeps those,
+// and the sum of the rotations by -o copies it back to all g slots.  Each
+// rotate-and-sum runs in hoisted stages of three rotations (rotsum_batch;
+// offsets s, 2s, 3s, then s <- 4s) and one of a single rotation when its
+// number of doublings is odd.
 //
 // Op sequence and scale plan (doubles, same order as the CPU oracle; l0 the
 // input level, q[i] the limb primes):
 //   U  = HMult(Z_k, W)                      sU = sZ*sW/q[l0-1]
-//   M  = U + rot(U, g) + ... (log2 F doublings)
+//   M  = sum over o < F of rot(U, o*g)       (hoisted stages)
 //   T  = HMult(M, M)                        sT = sU*sU/q[l0-2]
 //   sS = ((sW*q[l0-5])*q[l0-4]) / (mask_scale*sZ)
 //   A  = rescale(M * round(c3*lr*sigA)),    sigA = ((sS*q[l0-3])/sT * q[l0-2])/sU
@@ -22,7 +25,7 @@
 //   Q  = rescale(T * round(c2*lr*sigQ)),    sigQ = (sS*q[l0-3])/sT   (c2 != 0)
 //   S  = C + B (+ Q) + round(c0*lr*scale(C))
 //   G  = sum_k HMult(S, drop(Z_k))
-//   H  = G + rot(G, 1) + ... ;  R = rescale(H (x) mask) ;  R += rot(R, -1) + ...
+//   H  = sum over o < g of rot(G, o) ;  R = rescale(H (x) mask) ;  R <- sum over o < g of rot(R, -o)
 //   W' = drop(W) + R                        (scale sW, level l0-5)
 #include <math.h>
 #include <stdio.h>
@@ -136,29 +139,48 @@ static size_t lr_ct_words(const he_ctx* c, uint32_t l0) {
          10 * 32;
 }
 
-static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk) {
+// Scratch words of one operation of the step: those of the per-ciphertext
+// part over `chunk` ciphertexts and those of the finish over `ns` sums.
+static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk, uint32_t ns) {
   size_t w = mul_words(c, l0, chunk, true);
-  w = std::max(w, rot_words(c, l0 - 1, chunk));
+  w = std::max(w, rotsum_words(c, l0 - 1, chunk, 3));
   w = std::max(w, rescale_words(c, l0 - 1, chunk));
+  w = std::max(w, rotsum_words(c, l0 - 4, ns, 3));
+  w = std::max(w, rescale_words(c, l0 - 4, ns) + (size_t)ns * 2 * (l0 - 4) * c->n);
   return w + 64;
 }
 
+// Galois elements of the step's three rotate-and-sums, stage by stage.
 struct LrGal {
-  std::vector<uint64_t> in, up, down;
+  std::vector<std::vector<uint64_t>> in, up, down;
 };
+
+// The stages of a rotate-and-sum over offsets 0, step, ..., (2^count - 1) step:
+// while two or more doublings remain, rotations by s, 2s, 3s in one hoisted
+// stage (then s <- 4s); a last stage with the rotation by s when count is odd.
+static void rotsum_stages(int log_n, int32_t step, uint32_t count, std::vector<std::vector<uint64_t>>* out) {
+  int32_t s = step;
+  while (count > 0) {
+    const uint32_t ns = count >= 2 ? 3 : 1;
+    std::vector<uint64_t> st;
+    for (uint32_t m = 1; m <= ns; ++m) st.push_back(h_galois_elt(log_n, s * (int32_t)m));
+    out->push_back(st);
+    s *= (int32_t)ns + 1;
+    count -= ns == 3 ? 2 : 1;
+  }
+}
 
 static int lr_gal(he_ctx* c, const LrPlan& P, LrGal* gl) {
   gl->in.clear();
   gl->up.clear();
   gl->down.clear();
-  for (uint32_t t = 0; t < P.logF; ++t) gl->in.push_back(h_galois_elt(c->log_n, (int32_t)(P.g << t)));
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    gl->up.push_back(h_galois_elt(c->log_n, (int32_t)(1u << t)));
-    gl->down.push_back(h_galois_elt(c->log_n, -(int32_t)(1u << t)));
-  }
+  rotsum_stages(c->log_n, (int32_t)P.g, P.logF, &gl->in);
+  rotsum_stages(c->log_n, 1, P.logg, &gl->up);
+  rotsum_stages(c->log_n, -1, P.logg, &gl->down);
   for (auto* v : {&gl->in, &gl->up, &gl->down})
-    for (uint64_t e : *v)
-      if (e != 1 && !galois_key(c, e)) return fail(HE_ENOKEY, "missing Galois key for the step's rotations");
+    for (const auto& st : *v)
+      for (uint64_t e : st)
+        if (e == 1 || !galois_key(c, e)) return fail(HE_ENOKEY, "missing Galois key for the step's rotations");
   return HE_OK;
 }
 
@@ -182,8 +204,8 @@ static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtB
   };
   // U = Z_k * W, then the rotate-and-sum over the F feature positions
   HE_TRY(mul_relin_batch(c, Zc, Wc, l0, m, b.U, true, fresh()));
-  for (uint32_t t = 0; t < P.logF; ++t) {  // U <- U + rotate(U), alternating buffers
-    HE_TRY(rotate_add_batch(c, b.U, l0 - 1, m, gl.in[t], b.Tmp, fresh()));
+  for (const auto& st : gl.in) {  // U <- U + its rotations, alternating buffers
+    HE_TRY(rotsum_batch(c, b.U, l0 - 1, m, st.data(), (uint32_t)st.size(), b.Tmp, fresh()));
     std::swap(b.U, b.Tmp);
   }
   // T = M^2; A = c3 M; C = T A
@@ -216,15 +238,15 @@ static int lr_finish(he_ctx* c, const LrPlan& P, const LrGal& gl, const int64_t*
     ops.off = 0;
     return ops;
   };
-  for (uint32_t t = 0; t < P.logg; ++t) {  // G <- G + rotate(G), alternating buffers
-    HE_TRY(rotate_add_batch(c, G, l0 - 4, count, gl.up[t], H1, fresh()));
+  for (const auto& st : gl.up) {  // G <- G + its rotations, alternating buffers
+    HE_TRY(rotsum_batch(c, G, l0 - 4, count, st.data(), (uint32_t)st.size(), H1, fresh()));
     std::swap(G, H1);
   }
   HE_TRY(mul_plain_dev(c, G, mask, H1, l0 - 4, count, fresh()));
   HE_TRY(rescale_batch(c, H1, l0 - 4, count, R, fresh()));
   const CtBatch R_out = R;
-  for (uint32_t t = 0; t < P.logg; ++t) {
-    HE_TRY(rotate_add_batch(c, R, l0 - 5, count, gl.down[t], H1, fresh()));
+  for (const auto& st : gl.down) {
+    HE_TRY(rotsum_batch(c, R, l0 - 5, count, st.data(), (uint32_t)st.size(), H1, fresh()));
     std::swap(R, H1);
   }
   if (R.base != R_out.base) HE_TRY(copy_batch(c, R, R_out, l0 - 5, count));
@@ -295,7 +317,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     const uint32_t ns = (uint32_t)grp.size();
     Arena a = pool;
     CtBatch G = carve(a, ns, l0 - 4, n), H1 = carve(a, ns, l0 - 4, n), R = carve(a, ns, l0 - 4, n);
-    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1)) * sizeof(uint64_t);
+    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1, 1)) * sizeof(uint64_t);
     size_t chunk = std::max<size_t>(1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, total));
     LrBufs b;
     b.U = carve(a, chunk, l0 - 1, n);
@@ -311,7 +333,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     Arena ops;
     ops.base = a.base + a.off;
     ops.size = a.size > a.off ? a.size - a.off : 0;
-    if (!b.Wrep.base || ops.size < lr_op_words(c, l0, (uint32_t)chunk) * sizeof(uint64_t))
+    if (!b.Wrep.base || ops.size < lr_op_words(c, l0, (uint32_t)chunk, ns) * sizeof(uint64_t))
       return fail(HE_ENOMEM, "step scratch too small");
     HE_CUDA(cudaMemsetAsync(G.base, 0, sizeof(uint64_t) * G.stride * ns, c->stream));
     // walk the group's data ciphertexts chunk by chunk
@@ -415,11 +437,11 @@ static size_t lr_words(he_ctx* c, const LrShape* sh, size_t count, uint32_t refr
   }
   for (auto& kv : groups) {
     const uint32_t l0 = kv.first;
-    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1)) * sizeof(uint64_t);
+    const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1, 1)) * sizeof(uint64_t);
     const size_t chunk = std::max<size_t>(
         1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, kv.second.second));
     const size_t w = 3 * kv.second.first * 2 * (l0 - 4) * n + chunk * lr_ct_words(c, l0) +
-                     lr_op_words(c, l0, (uint32_t)chunk) + 4096;
+                     lr_op_words(c, l0, (uint32_t)chunk, (uint32_t)kv.second.first) + 4096;
     need = std::max(need, w);
   }
   const size_t ref = (size_t)c->L * n + 2 * n + 4 * n + n + 4 * (size_t)refresh_level * n + 4096;

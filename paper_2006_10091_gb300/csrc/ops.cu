@@ -23,6 +23,12 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
              uint32_t count, bool* handled);
+bool ks_rot_fits(const he_ctx* c, uint32_t level);
+int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
+           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled);
+int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t nsum, uint64_t sum_stride,
+                 uint64_t* conv, CtBatch add, int add_mode, const uint64_t* gals, uint32_t n_gal, CtBatch out,
+                 uint32_t level, uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -73,10 +79,9 @@ const uint64_t* galois_key(const he_ctx* c, uint64_t gal) {
   return it == c->gal.end() ? nullptr : it->second;
 }
 
-// ModUp, NTT of the converted limbs and the key inner product as separate
-// kernels (any N).
-static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext,
-                             uint64_t* acc, const uint64_t* evk, uint32_t level, uint32_t count) {
+// ModUp and the NTT of the converted limbs as separate kernels (any N):
+// ext = count x [beta][nt][N], evaluation form (a digit's own limbs unset).
+static int modup_unfused(he_ctx* c, const uint64_t* d2c, uint64_t* ext, uint32_t level, uint32_t count) {
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
   const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
   ModUpArgs m;
@@ -100,13 +105,47 @@ static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, co
   PolyBatch e = pb(ext, ext, (size_t)nt * n, (size_t)nt * n, count * beta, nt, 0, level);
   e.skip_alpha = alpha;
   e.skip_beta = beta;
-  HE_TRY(ntt_forward(c, e));
+  return ntt_forward(c, e);
+}
+
+// ModUp, NTT of the converted limbs and the key inner product as separate
+// kernels (any N).
+static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext,
+                             uint64_t* acc, const uint64_t* evk, uint32_t level, uint32_t count) {
+  const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
+  const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
+  HE_TRY(modup_unfused(c, d2c, ext, level, count));
   // 3. inner product with the key
   {
     ProfScope prof(c, "inner_product", 2.0 * count * beta * nt * n, (double)n * 8 * ((double)count * beta * nt + 2.0 * beta * nt * count + 2.0 * count * nt));
     k_inner_product<<<grid_for((size_t)count * nt * n / 2), 256, 0, c->stream>>>(
         ext, (size_t)beta * nt * n, d, d_stride, evk, acc, (size_t)2 * nt * n, level, alpha, beta, L, np,
         count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+// The ModDown of a key switch as separate kernels: conversion of the P limbs
+// (already in coefficient form), NTT, combine (add_mode 0 none, 1 part 0,
+// 2 both parts).
+static int moddown_unfused(he_ctx* c, const uint64_t* acc, uint64_t* conv, CtBatch add, int add_mode, CtBatch out,
+                           uint32_t level, uint32_t count) {
+  const uint32_t n = c->n, alpha = c->alpha, L = c->L, nt = level + alpha;
+  {
+    ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
+    k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, level, alpha, L, count, c->log_n,
+        c->d_primes, c->d_moddown);
+  }
+  HE_CUDA(cudaGetLastError());
+  HE_TRY(ntt_forward(c, pb(conv, conv, (size_t)level * n, (size_t)level * n, count * 2, level, 0, level)));
+  const uint64_t* pinv = c->d_moddown + 2 * alpha + (size_t)alpha * L;
+  {
+    ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
+    k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
+        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha, L,
+        count, c->log_n, c->d_primes, pinv);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
@@ -150,22 +189,7 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
     add = P;
   }
   const int combine_mode = add_mode == 3 ? 1 : add_mode;  // mode 3 adds the unpermuted input afterwards
-  {
-    ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
-    k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, level, alpha, L, count, c->log_n,
-        c->d_primes, c->d_moddown);
-  }
-  HE_CUDA(cudaGetLastError());
-  HE_TRY(ntt_forward(c, pb(conv, conv, (size_t)level * n, (size_t)level * n, count * 2, level, 0, level)));
-  const uint64_t* pinv = c->d_moddown + 2 * alpha + (size_t)alpha * L;
-  {
-    ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
-    k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, combine_mode, out, 0, 2, level, alpha, L,
-        count, c->log_n, c->d_primes, pinv);
-  }
-  HE_CUDA(cudaGetLastError());
+  HE_TRY(moddown_unfused(c, acc, conv, add, combine_mode, out, level, count));
   if (add_mode == 3) return addsub_batch(c, out, add_in, out, 0, level, count);
   return HE_OK;
 }
@@ -243,22 +267,85 @@ int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t 
   return keyswitch_batch(c, t + (size_t)level * n, (size_t)2 * level * n, level, count, key, T, 1, out, ar);
 }
 
-// out = A + rotate(A): with the fused kernels the sum is formed in the key
-// switch's last kernel (add_mode 3), otherwise a rotation and an addition.
+// out = A + sum_r rotate(A, gal_r) with one decomposition of A's second part
+// and one ModDown for all rotations (hoisting): iNTT of A1, ModUp + NTT
+// once, the inner product of the permuted digits with each rotation's key,
+// the sum of those products, ModDown, plus A0 + sum_r kappa_r(A0) and A1.
 // out must not overlap A.
-int rotate_add_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out, Arena& ar) {
-  const uint32_t n = c->n;
-  const uint64_t* key = galois_key(c, gal);
-  if (!key) return fail(HE_ENOKEY, "no Galois key for this rotation");
+int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uint64_t* gals, uint32_t nrot,
+                 CtBatch out, Arena& ar) {
+  if (nrot < 1 || nrot > HE_MAX_ROT) return fail(HE_EINVAL, "rotate-and-sum: 1 to 8 rotations per stage");
+  RotSet rs;
+  rs.n = nrot;
+  for (uint32_t r = 0; r < nrot; ++r) {
+    if (gals[r] == 1) return fail(HE_EINVAL, "rotate-and-sum: a rotation by 0 slots");
+    rs.gal[r] = gals[r];
+    rs.evk[r] = galois_key(c, gals[r]);
+    if (!rs.evk[r]) return fail(HE_ENOKEY, "no Galois key for this rotation");
+  }
+  const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
+  const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
   const char* a_lo = (const char*)A.base;
   const char* a_hi = a_lo + sizeof(uint64_t) * ((size_t)(count - 1) * A.stride + (size_t)2 * A.cap * n);
   const char* o_lo = (const char*)out.base;
   const char* o_hi = o_lo + sizeof(uint64_t) * ((size_t)(count - 1) * out.stride + (size_t)2 * out.cap * n);
-  if (!(o_hi <= a_lo || a_hi <= o_lo)) return fail(HE_EINVAL, "rotate_add_batch: output overlaps the input");
-  if (ks_fusable(c))
-    return keyswitch_batch(c, A.base + (size_t)A.cap * n, A.stride, level, count, key, A, 3, out, ar, gal);
-  HE_TRY(rotate_batch(c, A, level, count, gal, out, ar));
-  return addsub_batch(c, out, A, out, 0, level, count);
+  if (!(o_hi <= a_lo || a_hi <= o_lo)) return fail(HE_EINVAL, "rotate-and-sum: output overlaps the input");
+  const uint64_t acc_stride = (uint64_t)2 * nt * n, rstride = (uint64_t)count * acc_stride;
+  uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
+  uint64_t* ext = ar.take<uint64_t>((size_t)count * beta * nt * n);
+  uint64_t* acc = ar.take<uint64_t>((size_t)nrot * rstride);
+  uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
+  const uint64_t* d = A.base + (size_t)A.cap * n;
+  const bool fits = ks_rot_fits(c, level);
+  const bool half = fits && ks_converts_per_digit(c, level);
+  {
+    const PolyBatch b = pb(d, d2c, A.stride, (size_t)level * n, count, level, 0, level);
+    HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
+  }
+  bool fused = false;
+  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rstride, rs, level, count, half, &fused));
+  if (!fused) {
+    if (half) return fail(HE_ECUDA, "rotate-and-sum: fused kernels declined a half-transformed input");
+    HE_TRY(modup_unfused(c, d2c, ext, level, count));
+    {
+      ProfScope prof(c, "inner_product", 2.0 * nrot * count * beta * nt * n,
+                     (double)n * 8 * ((double)count * beta * nt * (1 + 2.0 * nrot) + 2.0 * nrot * count * nt));
+      k_inner_product_rot<<<grid_for((size_t)nrot * count * nt * n), 256, 0, c->stream>>>(
+          ext, (size_t)beta * nt * n, d, A.stride, rs, acc, acc_stride, rstride, level, alpha, beta, L, np, count,
+          c->log_n, c->d_primes);
+    }
+    HE_CUDA(cudaGetLastError());
+  }
+  // the P limbs of all rotations' accumulators summed, to coefficient form
+  if (nrot > 1) {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * alpha * n * 8 * (nrot + 1));
+    k_sum_acc<<<grid_for((size_t)count * 2 * alpha * n), 256, 0, c->stream>>>(
+        acc, acc_stride, rstride, nrot, level, nt, nt, level, L, count, c->log_n, c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
+                           count * 2, alpha, level, level)));
+  bool md_done = false;  // the Q limbs are summed as the combine reads them
+  HE_TRY(md_fused_sum(c, acc, acc_stride, nrot, rstride, conv, A, 3, gals, nrot, out, level, count, &md_done));
+  if (md_done) return HE_OK;
+  if (nrot > 1) {
+    k_sum_acc<<<grid_for((size_t)count * 2 * level * n), 256, 0, c->stream>>>(
+        acc, acc_stride, rstride, nrot, 0, level, nt, level, L, count, c->log_n, c->d_primes);
+    HE_CUDA(cudaGetLastError());
+  }
+  uint64_t* sa = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!sa) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
+  const CtBatch S{sa, (uint64_t)2 * level * n, level, 0};
+  k_add_automorphs<<<grid_for((size_t)count * 2 * level * n), 256, 0, c->stream>>>(A, S, rs, level, count, c->log_n,
+                                                                                   c->d_primes);
+  HE_CUDA(cudaGetLastError());
+  return moddown_unfused(c, acc, conv, S, 2, out, level, count);
+}
+
+size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count, uint32_t nrot) {
+  const size_t n = c->n, a = c->alpha, beta = (level + a - 1) / a, nt = level + a;
+  return count * n * (level + beta * nt + 2 * nt * nrot + 2 * level + 2 * level) + 6 * 32;
 }
 
 int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count) {

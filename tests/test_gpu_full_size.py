@@ -25,8 +25,7 @@ def test_full_size_step_accuracy_and_entry_points_agree():
     log_n, L, g = 14, 8, 8
     n_slots = (1 << log_n) // 2
     F = n_slots // g
-    rots = [g << t for t in range(int(math.log2(F)))] + [1 << t for t in range(3)] + [-(1 << t) for t in range(3)]
-    ctx = he.Context(log_n, L, 40, 2, 59, 2.0 ** 40, seed=0, rot_steps=rots)
+    ctx = he.Context(log_n, L, 40, 2, 59, 2.0 ** 40, seed=0, rot_steps=he.lr_rot_steps(n_slots, g))
     he.he_autotune(ctx, L - 1, 64)
     data = workloads.LRData(seed=0, n_samples=4096, n_features=784)
     zs = workloads.pack_samples(data.X, data.y, n_slots, g)
@@ -67,7 +66,10 @@ def test_large_parameters_mul_rotate_accuracy():
     mul+relin+rescale and a 1024-slot rotate-and-sum decrypt within 1e-8 of
     FP64 at the top level and after several levels."""
     he = gpu_lib()
-    ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=1, rot_steps=[1 << t for t in range(10)])
+    stages = he.rotsum_stages(1, 10)
+    rots = [1 << t for t in range(10)]
+    rots += [r for st in stages for r in st if r not in rots]
+    ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=1, rot_steps=rots)
     n_slots = ctx.n // 2
     za, zb = workloads.uniform_slots(1, n_slots), workloads.uniform_slots(2, n_slots)
     a, b, c = ctx.new_ct(24), ctx.new_ct(24), ctx.new_ct(24)
@@ -76,13 +78,19 @@ def test_large_parameters_mul_rotate_accuracy():
     he.he_mul_relin_rescale(ctx, a, b, c)
     assert c.level == 23
     assert float(np.max(np.abs(he.he_decrypt_decode(ctx, c) - za * zb))) < 1e-8
-    # rotate-and-sum over 1024 positions at level 23
+    # rotate-and-sum over 1024 positions at level 23: one rotation and one
+    # addition at a time, and in hoisted stages (in place)
+    c2 = ctx.new_ct(24)
+    he.he_ct_import(ctx, he.he_ct_export(ctx, c), 23, c.scale, c2)
     t = ctx.new_ct(24)
     for s in range(10):
         he.he_rotate(ctx, c, 1 << s, t)
         he.he_add(ctx, c, t, c)
     want = sum(np.roll(za * zb, -k) for k in range(1024))
     assert float(np.max(np.abs(he.he_decrypt_decode(ctx, c) - want))) < 1e-7
+    for st in stages:
+        he.he_rotate_sum(ctx, c2, st, c2)
+    assert float(np.max(np.abs(he.he_decrypt_decode(ctx, c2) - want))) < 1e-7
 
 
 def test_full_size_keyswitch_matches_oracle():

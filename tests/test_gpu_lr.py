@@ -14,9 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 def rot_steps(n_slots, g):
-    F = n_slots // g
-    return [g << t for t in range(int(math.log2(F)))] + \
-        [1 << t for t in range(int(math.log2(g)))] + [-(1 << t) for t in range(int(math.log2(g)))]
+    return gpu_lib().lr_rot_steps(n_slots, g)
 
 
 @pytest.fixture(scope="module")

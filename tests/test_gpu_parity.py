@@ -517,7 +517,7 @@ def test_fused_matches_unfused_large(he, log_n):
     gives the residues of the unfused sequence, which the oracle pins at small
     N; relinearisation and rotation."""
     import torch
-    ctx = he.Context(log_n, 8, 50, 4, 60, 2.0 ** 50, seed=23, rot_steps=[3])
+    ctx = he.Context(log_n, 8, 50, 4, 60, 2.0 ** 50, seed=23, rot_steps=[3, 1, 2])
     n = ctx.n
     d = workloads.residues(31 + log_n, ctx.primes[:8], n)[0]
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
@@ -533,12 +533,83 @@ def test_fused_matches_unfused_large(he, log_n):
         rot = ctx.new_ct(8)
         he.he_rotate(ctx, ct, 3, rot)
         outs[(generic, shape, "rot")] = he.he_ct_export(ctx, rot)
+        he.he_rotate_sum(ctx, ct, [1, 2, 3], rot)
+        outs[(generic, shape, "rotsum")] = he.he_ct_export(ctx, rot)
     he.he_set_tuning(ctx, "ntt_generic", False)
     he.he_set_tuning(ctx, "ntt_shape", 0)
     for shape in (0, 1, 2):
         for k in range(2):
             assert np.array_equal(outs[(False, shape)][k], outs[(True, 0)][k]), (shape, k)
         assert np.array_equal(outs[(False, shape, "rot")], outs[(True, 0, "rot")]), shape
+        assert np.array_equal(outs[(False, shape, "rotsum")], outs[(True, 0, "rotsum")]), shape
+
+
+@pytest.fixture(scope="module")
+def hoist():
+    # N = 2^12, six 45-bit limbs, two 55-bit special primes
+    return Pair(12, 6, 45, 2, 55, 2.0 ** 45, seed=14, rots=[1, 2, 3, 5, -3, -1, -2])
+
+
+@pytest.mark.parametrize("level,steps", [(6, [1, 2, 3]), (5, [5, -3]), (2, [-1, -2, 5]), (1, [3])])
+def test_rotate_sum_bit_exact(hoist, he, level, steps):
+    """The hoisted rotate-and-sum against the oracle's: fused kernels in every
+    tile shape, the unfused sequence, and in place."""
+    m = workloads.int_poly(90 + level, hoist.n, 1 << 36)
+    ga, oa = hoist.gpu_enc(m, level, 90 + level), hoist.orc_enc(m, level, 90 + level)
+    want = hoist.o.rotate_sum(oa, steps)
+    for generic, shape in ((False, 0), (False, 1), (False, 2), (True, 0)):
+        he.he_set_tuning(hoist.g, "ntt_generic", generic)
+        he.he_set_tuning(hoist.g, "ntt_shape", shape)
+        out = hoist.g.new_ct(level)
+        he.he_rotate_sum(hoist.g, ga, steps, out)
+        assert_same_residues(out, want, he, hoist.g)
+    he.he_set_tuning(hoist.g, "ntt_generic", False)
+    he.he_set_tuning(hoist.g, "ntt_shape", 0)
+    he.he_rotate_sum(hoist.g, ga, steps, ga)
+    assert_same_residues(ga, want, he, hoist.g)
+
+
+def test_rotate_sum_batch_and_errors(hoist, he):
+    count, level = 5, 4
+    ms = [workloads.int_poly(950 + i, hoist.n, 1 << 30) for i in range(count)]
+    A = hoist.g.new_ct(level, count)
+    for i in range(count):
+        he.he_encrypt_poly(hoist.g, ms[i], hoist.g.scale, level, A[i], cid=950 + i)
+    O = hoist.g.new_ct(level, count)
+    he.he_rotate_sum_batch(hoist.g, A, [1, 2, 3], O)
+    for i in range(count):
+        want = hoist.o.rotate_sum(hoist.orc_enc(ms[i], level, cid=950 + i), [1, 2, 3])
+        assert_same_residues(O[i], want, he, hoist.g)
+    for steps, code in (([7], he.HE_ENOKEY), ([1, 0], he.HE_EINVAL), ([1] * 9, he.HE_EINVAL)):
+        with pytest.raises(he.HeError) as e:
+            he.he_rotate_sum(hoist.g, A[0], steps, O[0])
+        assert e.value.code == code
+    with pytest.raises(he.HeError) as e:  # an output over another input
+        he.he_rotate_sum_batch(hoist.g, [A[0], A[1]], [1], [A[1], O[1]])
+    assert e.value.code == he.HE_EINVAL
+
+
+def test_rotate_sum_accuracy(hoist, he):
+    z = workloads.uniform_slots(96, hoist.n // 2)
+    a = hoist.g.new_ct(4)
+    he.he_encode_encrypt(hoist.g, z, 2.0 ** 45, 4, a, cid=96)
+    out = hoist.g.new_ct(4)
+    he.he_rotate_sum(hoist.g, a, [1, 2, 3], out)
+    got = he.he_decrypt_decode(hoist.g, out)
+    want = z + np.roll(z, -1) + np.roll(z, -2) + np.roll(z, -3)
+    assert np.max(np.abs(got - want)) < 2.0 ** -20
+
+
+def test_rotate_sum_many_digits_unfused(he):
+    """Twenty-two one-limb digits: their row tiles exceed the shared memory
+    of the fused hoisted row pass, so the stage runs the unfused ModUp and
+    inner products; same residues as the oracle."""
+    p = Pair(12, 22, 40, 1, 60, 2.0 ** 40, seed=15, rots=[1, 2])
+    m = workloads.int_poly(97, p.n, 1 << 30)
+    ga, oa = p.gpu_enc(m, 22, 97), p.orc_enc(m, 22, 97)
+    out = p.g.new_ct(22)
+    he.he_rotate_sum(p.g, ga, [1, 2], out)
+    assert_same_residues(out, p.o.rotate_sum(oa, [1, 2]), he, p.g)
 
 
 def test_alu_probes_run(he):

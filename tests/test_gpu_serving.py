@@ -16,16 +16,16 @@ from tests.lr_reference import lr_step_fp64, table2
 pytestmark = pytest.mark.gpu
 
 
-def rots(n_slots):
-    k = int(math.log2(n_slots))
-    return [1 << t for t in range(k)] + [-(1 << t) for t in range(k)]
+def rots(he, n_slots, g):
+    return he.lr_rot_steps(n_slots, g)
 
 
 @pytest.fixture(scope="module")
 def setup():
     he = gpu_lib()
-    ctxs = [he.Context(11, 7, 40, 1, 60, 2.0 ** 40, seed=31, rot_steps=rots(1 << 10)),
-            he.Context(12, 7, 40, 2, 50, 2.0 ** 40, seed=32, rot_steps=rots(1 << 11))]
+    # 16 samples of 64 (N = 2^11) or 128 (N = 2^12) feature positions per ciphertext
+    ctxs = [he.Context(11, 7, 40, 1, 60, 2.0 ** 40, seed=31, rot_steps=rots(he, 1 << 10, 16)),
+            he.Context(12, 7, 40, 2, 50, 2.0 ** 40, seed=32, rot_steps=rots(he, 1 << 11, 16))]
     coeffs = table2()["binomial"]
     reqs = []
     for r in range(10):
