@@ -151,8 +151,8 @@ def measure_alu_peak(he) -> None:
                         f"({r['per_clock_per_sm']:.2f} per clock per SM)")
 
 
-ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "moddown_ntt", "moddown_ntt_combine",
-               "rescale_ntt", "rescale_ntt_final")
+ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "ks_ntt_rot_products", "moddown_ntt",
+               "moddown_ntt_combine", "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes (read + write) per modular product of the fused key-switch row
 # pass, from an ncu capture of one launch over 64 ciphertexts at level 7 of
 # these parameters (479.1 MB for 212.3 M products); the roofline scales it to
@@ -842,7 +842,9 @@ def run_micro_keyswitch(args):
     ciphertexts, with the per-class kernel times of the batch: at level 7 of
     the step's parameters (N = 2^14), or with --log-n 16 at the top level of
     the large parameters (24 x ~50-bit limbs, 4 special primes, dnum 6).
-    --tune autotune runs the autotuner on this batch first."""
+    --micro rotsum times one hoisted rotate-and-sum stage instead (rotations
+    by 8, 16 and 24 sharing one decomposition).  --tune autotune runs the
+    autotuner on this batch first."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -851,13 +853,21 @@ def run_micro_keyswitch(args):
     from paper_2006_10091_gb300 import workloads
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    hoisted = args.micro == "rotsum"
+    steps = [8, 16, 24] if hoisted else [8]
     if args.log_n == 16:
-        ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=0, rot_steps=[8], stream=stream.cuda_stream)
+        ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=0, rot_steps=steps, stream=stream.cuda_stream)
         level = 24
     else:
-        ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=[8],
+        ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=steps,
                          stream=stream.cuda_stream)
         level = L - 1
+
+    def op(A, O):
+        if hoisted:
+            he.he_rotate_sum_batch(ctx, A, steps, O)
+        else:
+            he.he_rotate_batch(ctx, A, 8, O)
     count = args.polys
     tuned = None
     for kv in args.tune or []:
@@ -870,22 +880,22 @@ def run_micro_keyswitch(args):
     A, O = ctx.new_ct(level, count), ctx.new_ct(level, count)
     he.he_ct_import_batch(ctx, host, level, ctx.scale, A)
     for _ in range(args.warmup):
-        he.he_rotate_batch(ctx, A, 8, O)
+        op(A, O)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        he.he_rotate_batch(ctx, A, 8, O)
+        op(A, O)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     he.he_profile_enable(ctx, True)
-    he.he_rotate_batch(ctx, A, 8, O)
+    op(A, O)
     prof = {k: he.he_profile_read(ctx, k) for k in he.he_profile_names(ctx)}
     he.he_profile_enable(ctx, False)
     total_work = sum(v["work"] for v in prof.values())
-    print(json.dumps({"micro": "keyswitch", "N": ctx.n, "level": level, "ciphertexts": count, "autotune": tuned,
-                      "ms_per_batch": ms, "rotations_per_s": count * 1000.0 / ms,
+    print(json.dumps({"micro": args.micro, "N": ctx.n, "level": level, "ciphertexts": count, "autotune": tuned,
+                      "steps": steps, "ms_per_batch": ms, "rotations_per_s": len(steps) * count * 1000.0 / ms,
                       "modmul_per_s": total_work / (ms * 1e-3),
                       "alu_frac": total_work / (ms * 1e-3) / ALU_PEAK["per_second"],
                       "kernels": {k: {"ms": v["ms"], "GBs": v["bytes"] / max(v["ms"], 1e-9) / 1e6,
@@ -910,7 +920,7 @@ def run_part(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "keyswitch", "workers", "serving", "alu"], default=None,
+    ap.add_argument("--micro", choices=["ntt", "keyswitch", "rotsum", "workers", "serving", "alu"], default=None,
                     help="time one kernel class or one extra measurement alone")
     ap.add_argument("--requests", type=int, default=400, help="timed requests of --micro serving")
     ap.add_argument("--tune", action="append", help="key=value tuning of --micro keyswitch")
@@ -937,7 +947,7 @@ def main():
     if args.micro == "ntt":
         run_micro(args)
         return
-    if args.micro == "keyswitch":
+    if args.micro in ("keyswitch", "rotsum"):
         run_micro_keyswitch(args)
         return
     if args.micro in ("workers", "serving"):

@@ -75,14 +75,20 @@ bool ks_rot_fits(const he_ctx* c, uint32_t level) {
 }
 
 // ModUp -> NTT -> the inner products of every rotation of a hoisted
-// rotate-and-sum, fused; rotation r's accumulators at acc + r*acc_rstride.
+// rotate-and-sum, fused; rotation r's accumulators at acc + r*acc_rstride,
+// or (*nacc = 1) all rotations summed in the first when each rotation maps
+// the kernel's row tiles onto themselves.
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled) {
+           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled,
+           uint32_t* nacc) {
   *handled = false;
+  *nacc = rs.n;
   if (!ks_rot_fits(c, level)) return HE_OK;
   KsRotArgs ra;
   ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
   ra.nrot = rs.n;
+  ra.count = count;
+  ra.closed = 0;
   ra.acc_rstride = acc_rstride;
   for (uint32_t r = 0; r < rs.n; ++r) {
     ra.gal[r] = rs.gal[r];
@@ -90,13 +96,16 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
     ra.evk[r] = rs.evk[r];
     ra.evk_sh[r] = rs.evk[r] + c->key_words();
   }
+  int closed = 0, rc;
   switch (c->log_n) {
-    case 12: return ks_rot_n12(c, ra, count, handled);
-    case 13: return ks_rot_n13(c, ra, count, handled);
-    case 14: return ks_rot_n14(c, ra, count, handled);
-    case 15: return ks_rot_n15(c, ra, count, handled);
-    default: return ks_rot_n16(c, ra, count, handled);
+    case 12: rc = ks_rot_n12(c, ra, count, handled, &closed); break;
+    case 13: rc = ks_rot_n13(c, ra, count, handled, &closed); break;
+    case 14: rc = ks_rot_n14(c, ra, count, handled, &closed); break;
+    case 15: rc = ks_rot_n15(c, ra, count, handled, &closed); break;
+    default: rc = ks_rot_n16(c, ra, count, handled, &closed); break;
   }
+  if (*handled && closed) *nacc = 1;
+  return rc;
 }
 
 }  // namespace he

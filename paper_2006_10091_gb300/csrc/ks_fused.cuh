@@ -321,15 +321,19 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
 // key loads, reading its sources from shared memory.
 struct KsRotArgs {
   KsFusedArgs k;           // k.acc: the accumulators of rotation 0
-  uint32_t nrot;
+  uint32_t nrot, count;
+  int closed;              // every rotation maps each tile's rows onto themselves: one summed accumulator
   uint64_t acc_rstride;    // words between the accumulators of consecutive rotations
   uint64_t gal[HE_MAX_ROT], gal_inv[HE_MAX_ROT];
   const uint64_t* evk[HE_MAX_ROT];
   const uint64_t* evk_sh[HE_MAX_ROT];
 };
 
-// Grid: count * nt * TILES.  Shared memory: the tile's twiddles and every
-// digit's transformed tile ([beta][TILE + TILE/8] words).
+// Grid: nt * count * TILES, target limb slowest and row tile fastest, so
+// that the CTAs resident at one time share their keys (one limb of each
+// rotation's key) in L2 and finish each ciphertext's limb together.  Shared
+// memory: the tile's twiddles and every digit's transformed tile
+// ([beta][TILE + TILE/8] words).
 template <int LOG_N, int LOG_M, int LOG_K>
 __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRotArgs ra) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
@@ -343,12 +347,13 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   uint32_t b = blockIdx.x;
   const uint32_t tile = b % S::TILES;
   b /= S::TILES;
-  const uint32_t t = b % a.nt, i = b / a.nt;
+  const uint32_t i = b % ra.count, t = b / ra.count;
   const uint32_t prime = ks_prime(t, a.level, a.L);
   const PrimeDev pr = a.primes[prime];
   const uint64_t q = pr.q, q2 = q + q;
   const bool lazy = q < (1ull << 58);
-  const bool acc_lazy = q < ~0ull / (2ull * a.beta);
+  // products summed unreduced while all of them stay below 2^64
+  const bool acc_lazy = q < ~0ull / (2ull * a.beta * (ra.closed ? ra.nrot : 1));
   stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
   // 1. every digit's tile in evaluation form, canonical residues
   for (uint32_t j = 0; j < a.beta; ++j) {
@@ -380,6 +385,50 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   };
   const uint32_t row0 = (uint32_t)tile << LOG_K;
   constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
+  if (ra.closed) {
+    // each thread sums every rotation's products for its own positions
+    uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
+    uint64_t* o1 = o0 + (size_t)a.nt * N;
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += GRP) {
+      uint32_t eo[GRP];
+      uint64_t acc0[GRP], acc1[GRP];
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) {
+        const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
+        eo[u] = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+        acc0[u] = acc1[u] = 0;
+      }
+      for (uint32_t r = 0; r < ra.nrot; ++r) {
+        uint32_t so[GRP];
+#pragma unroll
+        for (int u = 0; u < GRP; ++u) {
+          const uint32_t p = automorph_src(eo[u], ra.gal[r], LOG_N);
+          const uint32_t sl = (((p >> LOG_M) - row0) << LOG_M) | (p & (S::M - 1));
+          so[u] = sl + (sl >> 3);
+        }
+        const uint64_t* ev = ra.evk[r];
+        const uint64_t* es = ra.evk_sh[r];
+        for (uint32_t j = 0; j < a.beta; ++j) {
+          const uint64_t* sm = dig + (size_t)j * TW;
+          const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
+          const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
+#pragma unroll
+          for (int u = 0; u < GRP; ++u) {
+            const uint64_t x = sm[so[u]];
+            mac(acc0[u], x, __ldg(ev + kb_off + eo[u]), __ldg(es + kb_off + eo[u]));
+            mac(acc1[u], x, __ldg(ev + ka_off + eo[u]), __ldg(es + ka_off + eo[u]));
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) {
+        o0[eo[u]] = reduce64(acc0[u], pr);
+        o1[eo[u]] = reduce64(acc1[u], pr);
+      }
+    }
+    return;
+  }
   for (uint32_t r = 0; r < ra.nrot; ++r) {
     const uint64_t* ev = ra.evk[r];
     const uint64_t* es = ra.evk_sh[r];
@@ -705,8 +754,27 @@ size_t ks_rot_smem(uint32_t beta) {
 // The hoisted rotate-and-sum's ModUp, column pass and row pass with the
 // inner products of every rotation.  *handled = false (nothing launched)
 // when the digits' tiles do not fit in shared memory.
+inline uint32_t brev_host(uint32_t x, int bits) {
+  uint32_t r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+// Whether X -> X^gal maps every row tile of the hoisted row pass (2^LOG_K
+// rows of 2^LOG_M evaluation points) onto itself.
+template <int LOG_N, int LOG_M, int LOG_K>
+bool rot_closed(uint64_t gal_inv) {
+  for (uint32_t row = 0; row < (1u << (LOG_N - LOG_M)); ++row) {
+    const uint32_t e = 2 * brev_host(row << LOG_M, LOG_N) + 1;
+    const uint32_t e2 = (uint32_t)(((uint64_t)e * gal_inv) & ((2ull << LOG_N) - 1));
+    const uint32_t orow = brev_host((e2 - 1) >> 1, LOG_N) >> LOG_M;
+    if ((orow >> LOG_K) != (row >> LOG_K)) return false;
+  }
+  return true;
+}
+
 template <int LOG_N, int M1, int K1, int M2, int K2>
-int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled) {
+int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, int* closed_out) {
   using SR = Shape<LOG_N, M2, K2 - 1, false>;
   const KsFusedArgs& a = ra.k;
   const size_t smr = ks_rot_smem<LOG_N, M2, K2>(a.beta);
@@ -725,9 +793,14 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled) {
   const double conv = (double)a.beta * a.nt - own;
   {
     const size_t blocks = (size_t)count * a.nt * SR::TILES;
-    ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * ra.nrot * a.beta * a.nt * n),
+    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * ra.nrot * a.beta * a.nt * n),
                    count * n * 8 * (conv + own + 2.0 * ra.nrot * a.nt));
-    ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(ra);
+    KsRotArgs rc = ra;
+    rc.count = count;
+    rc.closed = 1;
+    for (uint32_t r = 0; r < ra.nrot; ++r) rc.closed &= rot_closed<LOG_N, M2, K2 - 1>(ra.gal_inv[r]) ? 1 : 0;
+    *closed_out = rc.closed;
+    ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(rc);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
@@ -738,7 +811,7 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled) {
 // for the tile shape c->ntt_shape.
 #define HE_KS_FUSED_DECL(NN)                                                         \
   int ks_fused_n##NN(he_ctx* c, const KsFusedArgs& a, uint32_t count);               \
-  int ks_rot_n##NN(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled);    \
+  int ks_rot_n##NN(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed); \
   size_t ks_rot_smem_n##NN(const he_ctx* c, uint32_t beta);                          \
   int md_fused_n##NN(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);     \
   size_t ks_all_smem_n##NN(const he_ctx* c, uint32_t beta, const uint32_t* cnt);

@@ -10,10 +10,10 @@ int ks_fused_n12(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
        : sh == 2 ? ks_fused_run<12, 3, 8, 9, 2>(c, a, count) : ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
 }
 
-int ks_rot_n12(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled) {
+int ks_rot_n12(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
-  return sh == 1 ? ks_rot_run<12, 5, 6, 7, 4>(c, a, count, handled)
-       : sh == 2 ? ks_rot_run<12, 3, 8, 9, 2>(c, a, count, handled) : ks_rot_run<12, 6, 5, 6, 5>(c, a, count, handled);
+  return sh == 1 ? ks_rot_run<12, 5, 6, 7, 4>(c, a, count, handled, closed)
+       : sh == 2 ? ks_rot_run<12, 3, 8, 9, 2>(c, a, count, handled, closed) : ks_rot_run<12, 6, 5, 6, 5>(c, a, count, handled, closed);
 }
 
 size_t ks_rot_smem_n12(const he_ctx* c, uint32_t beta) {

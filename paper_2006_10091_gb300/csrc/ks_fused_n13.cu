@@ -10,10 +10,10 @@ int ks_fused_n13(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
        : sh == 2 ? ks_fused_run<13, 4, 7, 9, 2>(c, a, count) : ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
 }
 
-int ks_rot_n13(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled) {
+int ks_rot_n13(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
-  return sh == 1 ? ks_rot_run<13, 6, 5, 7, 4>(c, a, count, handled)
-       : sh == 2 ? ks_rot_run<13, 4, 7, 9, 2>(c, a, count, handled) : ks_rot_run<13, 7, 4, 6, 5>(c, a, count, handled);
+  return sh == 1 ? ks_rot_run<13, 6, 5, 7, 4>(c, a, count, handled, closed)
+       : sh == 2 ? ks_rot_run<13, 4, 7, 9, 2>(c, a, count, handled, closed) : ks_rot_run<13, 7, 4, 6, 5>(c, a, count, handled, closed);
 }
 
 size_t ks_rot_smem_n13(const he_ctx* c, uint32_t beta) {

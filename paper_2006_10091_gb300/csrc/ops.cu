@@ -25,7 +25,8 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
              uint32_t count, bool* handled);
 bool ks_rot_fits(const he_ctx* c, uint32_t level);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled);
+           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled,
+           uint32_t* nacc);
 int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t nsum, uint64_t sum_stride,
                  uint64_t* conv, CtBatch add, int add_mode, const uint64_t* gals, uint32_t n_gal, CtBatch out,
                  uint32_t level, uint32_t count, bool* handled);
@@ -304,7 +305,8 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
   }
   bool fused = false;
-  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rstride, rs, level, count, half, &fused));
+  uint32_t nacc = nrot;  // accumulators to sum (1 when the fused kernel summed the rotations)
+  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rstride, rs, level, count, half, &fused, &nacc));
   if (!fused) {
     if (half) return fail(HE_ECUDA, "rotate-and-sum: fused kernels declined a half-transformed input");
     HE_TRY(modup_unfused(c, d2c, ext, level, count));
@@ -318,20 +320,20 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     HE_CUDA(cudaGetLastError());
   }
   // the P limbs of all rotations' accumulators summed, to coefficient form
-  if (nrot > 1) {
-    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * alpha * n * 8 * (nrot + 1));
+  if (nacc > 1) {
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * alpha * n * 8 * (nacc + 1));
     k_sum_acc<<<grid_for((size_t)count * 2 * alpha * n), 256, 0, c->stream>>>(
-        acc, acc_stride, rstride, nrot, level, nt, nt, level, L, count, c->log_n, c->d_primes);
+        acc, acc_stride, rstride, nacc, level, nt, nt, level, L, count, c->log_n, c->d_primes);
   }
   HE_CUDA(cudaGetLastError());
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
                            count * 2, alpha, level, level)));
   bool md_done = false;  // the Q limbs are summed as the combine reads them
-  HE_TRY(md_fused_sum(c, acc, acc_stride, nrot, rstride, conv, A, 3, gals, nrot, out, level, count, &md_done));
+  HE_TRY(md_fused_sum(c, acc, acc_stride, nacc, rstride, conv, A, 3, gals, nrot, out, level, count, &md_done));
   if (md_done) return HE_OK;
-  if (nrot > 1) {
+  if (nacc > 1) {
     k_sum_acc<<<grid_for((size_t)count * 2 * level * n), 256, 0, c->stream>>>(
-        acc, acc_stride, rstride, nrot, 0, level, nt, level, L, count, c->log_n, c->d_primes);
+        acc, acc_stride, rstride, nacc, 0, level, nt, level, L, count, c->log_n, c->d_primes);
     HE_CUDA(cudaGetLastError());
   }
   uint64_t* sa = ar.take<uint64_t>((size_t)count * 2 * level * n);

@@ -517,7 +517,7 @@ def test_fused_matches_unfused_large(he, log_n):
     gives the residues of the unfused sequence, which the oracle pins at small
     N; relinearisation and rotation."""
     import torch
-    ctx = he.Context(log_n, 8, 50, 4, 60, 2.0 ** 50, seed=23, rot_steps=[3, 1, 2])
+    ctx = he.Context(log_n, 8, 50, 4, 60, 2.0 ** 50, seed=23, rot_steps=[3, 1, 2, 64, 128, 192])
     n = ctx.n
     d = workloads.residues(31 + log_n, ctx.primes[:8], n)[0]
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
@@ -535,6 +535,8 @@ def test_fused_matches_unfused_large(he, log_n):
         outs[(generic, shape, "rot")] = he.he_ct_export(ctx, rot)
         he.he_rotate_sum(ctx, ct, [1, 2, 3], rot)
         outs[(generic, shape, "rotsum")] = he.he_ct_export(ctx, rot)
+        he.he_rotate_sum(ctx, ct, [64, 128, 192], rot)
+        outs[(generic, shape, "rotsum64")] = he.he_ct_export(ctx, rot)
     he.he_set_tuning(ctx, "ntt_generic", False)
     he.he_set_tuning(ctx, "ntt_shape", 0)
     for shape in (0, 1, 2):
@@ -542,18 +544,23 @@ def test_fused_matches_unfused_large(he, log_n):
             assert np.array_equal(outs[(False, shape)][k], outs[(True, 0)][k]), (shape, k)
         assert np.array_equal(outs[(False, shape, "rot")], outs[(True, 0, "rot")]), shape
         assert np.array_equal(outs[(False, shape, "rotsum")], outs[(True, 0, "rotsum")]), shape
+        assert np.array_equal(outs[(False, shape, "rotsum64")], outs[(True, 0, "rotsum64")]), shape
 
 
 @pytest.fixture(scope="module")
 def hoist():
     # N = 2^12, six 45-bit limbs, two 55-bit special primes
-    return Pair(12, 6, 45, 2, 55, 2.0 ** 45, seed=14, rots=[1, 2, 3, 5, -3, -1, -2])
+    return Pair(12, 6, 45, 2, 55, 2.0 ** 45, seed=14, rots=[1, 2, 3, 5, -3, -1, -2, 4, 6, 8, 16, 24])
 
 
-@pytest.mark.parametrize("level,steps", [(6, [1, 2, 3]), (5, [5, -3]), (2, [-1, -2, 5]), (1, [3])])
+@pytest.mark.parametrize("level,steps", [(6, [1, 2, 3]), (5, [5, -3]), (2, [-1, -2, 5]), (1, [3]), (4, [2, 4, 6]),
+                                         (6, [8, 16, 24]), (3, [16])])
 def test_rotate_sum_bit_exact(hoist, he, level, steps):
     """The hoisted rotate-and-sum against the oracle's: fused kernels in every
-    tile shape, the unfused sequence, and in place."""
+    tile shape, the unfused sequence, and in place.  Even steps map every row
+    tile of the fused row pass at N = 2^12 onto itself (the kernel then sums
+    the rotations in registers); odd ones move rows between tiles (one
+    accumulator per rotation)."""
     m = workloads.int_poly(90 + level, hoist.n, 1 << 36)
     ga, oa = hoist.gpu_enc(m, level, 90 + level), hoist.orc_enc(m, level, 90 + level)
     want = hoist.o.rotate_sum(oa, steps)
