@@ -116,6 +116,17 @@ int he_get_tuning(he_ctx* ctx, const char* key, double* value);
  * default stream and synchronises. */
 int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second);
 
+/* Least-squares polynomial fit of a nonlinearity from samples (Sec. 3,
+ * Eq. 3), the host utility behind gradient polynomials such as Table 2's:
+ * coeffs[0..degree] minimise sum_i (y_i - sum_k coeffs[k] x_i^k)^2 over the n
+ * samples (x_i, y_i).  Host memory, host computation (no device, no context);
+ * degree <= 16, n > degree.  HE_EINVAL for null pointers, a non-finite sample,
+ * too few samples or samples that do not determine the polynomial (fewer
+ * than degree + 1 distinct abscissas).  Table 2's binomial row is the fit of
+ * the negated logistic-loss derivative 1/(1+e^x) on samples uniform in
+ * [-16, 16], to its printed digits. */
+int he_fit_poly(const double* x, const double* y, size_t n, uint32_t degree, double* coeffs);
+
 /* Autotuner (no counterpart in the paper; it serves the batched workers of
  * Sec. 4): times the relinearisation key switch (iNTT, ModUp + NTT, inner
  * product, ModDown) of `count` polynomials of uniform residues at `level`

@@ -202,6 +202,16 @@ def automorph_coef(a, log_n: int, q: int, k: int) -> np.ndarray:
 # Context
 # --------------------------------------------------------------------------
 
+def fit_poly(x, y, degree: int) -> np.ndarray:
+    """Least-squares polynomial fit (Sec. 3, Eq. 3), by its definition: the
+    coefficients c minimising ||V c - y||_2 for the Vandermonde matrix
+    V[i, k] = x_i^k, from numpy's least-squares solver (SVD based)."""
+    x = np.asarray(x, dtype=np.float64)
+    V = np.vander(x, degree + 1, increasing=True)
+    c, *_ = np.linalg.lstsq(V, np.asarray(y, dtype=np.float64), rcond=None)
+    return c
+
+
 class Ciphertext:
     """Residues [2][level][N] (uint64, evaluation form), level and scale."""
 

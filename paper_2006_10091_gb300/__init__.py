@@ -135,6 +135,7 @@ def load():
                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_double)],
         "he_get_tuning": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
         "he_probe_alu": [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "he_fit_poly": [VP, VP, ctypes.c_size_t, ctypes.c_uint32, VP],
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
@@ -443,6 +444,33 @@ def he_rotate_batch(ctx, a: list, steps: int, out: list):
     for o, s in zip(out, O):
         o.update(s)
     return out
+
+
+def he_fit_poly(x, y, degree: int) -> np.ndarray:
+    """Least-squares polynomial coefficients c_0 .. c_degree of samples
+    (x_i, y_i) (Eq. 3); host computation."""
+    xs = np.ascontiguousarray(x, dtype=np.float64)
+    ys = np.ascontiguousarray(y, dtype=np.float64)
+    if xs.shape != ys.shape or xs.ndim != 1:
+        raise ValueError("x and y must be 1-D arrays of one length")
+    c = np.zeros(degree + 1, dtype=np.float64)
+    _check(load().he_fit_poly(ctypes.c_void_p(xs.ctypes.data), ctypes.c_void_p(ys.ctypes.data), len(xs), degree,
+                              ctypes.c_void_p(c.ctypes.data)))
+    return c
+
+
+def fit_gradient_polynomial(f, a: float, degree: int = 3, n: int = 200001, seed=None) -> np.ndarray:
+    """Eq. 3: fit f by least squares on n samples of [-a, a]: random samples
+    uniform in the interval with a seed, or (seed None) n evenly spaced
+    points, the limit of many random samples.  With f(x) = 1/(1+e^x) (the
+    negated logistic-loss derivative), a = 16 and degree 3 the latter gives
+    Table 2's binomial row to its printed digits."""
+    if seed is None:
+        x = np.linspace(-a, a, n)
+    else:
+        from . import workloads
+        x = workloads.uniform_slots(seed, n, -a, a)
+    return he_fit_poly(x, f(x), degree)
 
 
 def rotsum_stages(step: int, count: int) -> list:
