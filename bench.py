@@ -903,6 +903,62 @@ def run_micro_keyswitch(args):
                                   for k, v in prof.items()}}))
 
 
+def run_micro_train(args):
+    """Algorithms 1 and 2 as one loop (he_lr_train) at the step's parameters:
+    K = 4 workers of 1024 samples x 784 features (128 data ciphertexts each),
+    refresh (decrypt, average, re-encrypt) after every step (l = 1), `--steps`
+    iterations timed; the decrypted weights against the same procedure in
+    FP64."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2006_10091_gb300 as he
+    from paper_2006_10091_gb300 import workloads
+    from tests.lr_reference import lr_step_fp64
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n_slots = (1 << LOG_N) // 2
+    ctx = he.Context(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0, rot_steps=rot_steps(n_slots, G),
+                     stream=stream.cuda_stream)
+    he.he_autotune(ctx, L - 1, 64)
+    coeffs = table2_binomial()
+    K, ns = 4, 1024
+    datas = [workloads.LRData(seed=500 + k, n_samples=ns, n_features=N_FEATURES) for k in range(K)]
+    w0 = datas[0].w0
+    lr = 1.0 / (K * ns)
+    workers = []
+    for k, d in enumerate(datas):
+        zs = workloads.pack_samples(d.X, d.y, n_slots, G)
+        Z = ctx.new_ct(L, len(zs))
+        for i, v in enumerate(zs):
+            he.he_encode_encrypt(ctx, v, SCALE, L, Z[i], cid=(k << 16) + i)
+        W = ctx.new_ct(L)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(w0, n_slots, G), SCALE, L, W, cid=(k << 16) + 9999)
+        workers.append((Z, W))
+    cfg = he.lr_config(coeffs, lr, G, MASK_SCALE)
+    out = ctx.new_ct(L)
+    he.he_lr_train(ctx, workers, cfg, 1, 1, L, out)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    he.he_lr_train(ctx, workers, cfg, args.steps, 1, L, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ws = [w0.copy() for _ in datas]
+    for _ in range(args.steps):
+        ws = [lr_step_fp64(d.X, d.y, w, coeffs, lr) for d, w in zip(datas, ws)]
+        avg = sum(ws) / len(ws)
+        ws = [avg.copy() for _ in ws]
+    want = workloads.pack_weights(ws[0], n_slots, G)
+    got = he.he_decrypt_decode(ctx, out)
+    print(json.dumps({"micro": "train", "workers": K, "samples_per_worker": ns, "features": N_FEATURES,
+                      "refresh_every": 1, "iterations": args.steps, "ms": ms,
+                      "iterations_per_s": args.steps * 1000.0 / ms,
+                      "worker_steps_per_s": K * args.steps * 1000.0 / ms,
+                      "max_rel_err_vs_fp64": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}))
+
+
 def run_part(args):
     """One of the extra measurements alone (batched workers or serving)."""
     import torch
@@ -920,7 +976,8 @@ def run_part(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "keyswitch", "rotsum", "workers", "serving", "alu"], default=None,
+    ap.add_argument("--micro", choices=["ntt", "keyswitch", "rotsum", "workers", "serving", "alu", "train"],
+                    default=None,
                     help="time one kernel class or one extra measurement alone")
     ap.add_argument("--requests", type=int, default=400, help="timed requests of --micro serving")
     ap.add_argument("--tune", action="append", help="key=value tuning of --micro keyswitch")
@@ -949,6 +1006,9 @@ def main():
         return
     if args.micro in ("keyswitch", "rotsum"):
         run_micro_keyswitch(args)
+        return
+    if args.micro == "train":
+        run_micro_train(args)
         return
     if args.micro in ("workers", "serving"):
         run_part(args)

@@ -318,16 +318,16 @@ def test_lr_step_and_inference_bit_exact_fused_kernels():
         assert_same_residues(S[k], want[k], he, pair.g)
 
 
-@pytest.mark.parametrize("refresh_every", [1, 2])
-def test_training_loop_matches_fp64_algorithm(refresh_every):
-    """Algorithms 1 and 2: two workers with their own data run three steps,
-    the key holder averages their weights every `refresh_every` steps and
-    after the last; the decrypted result equals the same procedure in FP64
-    within 2^-20 of the weights."""
+@pytest.mark.parametrize("refresh_every,top,iterations", [(1, 11, 3), (2, 11, 3), (3, 16, 6), (5, 26, 5)])
+def test_training_loop_matches_fp64_algorithm(refresh_every, top, iterations):
+    """Algorithms 1 and 2: two workers with their own data run their steps,
+    the key holder averages their weights every `refresh_every` steps (the
+    paper's l = 1, 3, 5) and after the last; the decrypted result equals the
+    same procedure in FP64 within 2^-20 of the weights."""
     he = gpu_lib()
     log_n, g = 12, 8
     n_slots = (1 << log_n) // 2
-    ctx = he.Context(log_n, 11, 40, 2, 55, 2.0 ** 40, seed=17, rot_steps=rot_steps(n_slots, g))
+    ctx = he.Context(log_n, top, 40, 2, 55, 2.0 ** 40, seed=17, rot_steps=rot_steps(n_slots, g))
     coeffs = table2()["binomial"]
     lr = 1.0 / 16
     w0 = workloads.LRData(seed=40, n_samples=16, n_features=200).w0
@@ -335,24 +335,25 @@ def test_training_loop_matches_fp64_algorithm(refresh_every):
     workers = []
     for k, d in enumerate(datas):
         zs = workloads.pack_samples(d.X, d.y, n_slots, g)
-        Z = ctx.new_ct(11, len(zs))
+        Z = ctx.new_ct(top, len(zs))
         for i, v in enumerate(zs):
-            he.he_encode_encrypt(ctx, v, 2.0 ** 40, 11, Z[i], cid=100 * k + i)
-        W = ctx.new_ct(11)
-        he.he_encode_encrypt(ctx, workloads.pack_weights(w0, n_slots, g), 2.0 ** 40, 11, W, cid=100 * k + 99)
+            he.he_encode_encrypt(ctx, v, 2.0 ** 40, top, Z[i], cid=100 * k + i)
+        W = ctx.new_ct(top)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(w0, n_slots, g), 2.0 ** 40, top, W, cid=100 * k + 99)
         workers.append((Z, W))
-    out = ctx.new_ct(11)
-    he.he_lr_train(ctx, workers, he.lr_config(coeffs, lr, g, 2.0 ** 27), 3, refresh_every, 11, out)
-    assert out.level == 11
+    out = ctx.new_ct(top)
+    cfg = he.lr_config(coeffs, lr, g, 2.0 ** 27)
+    he.he_lr_train(ctx, workers, cfg, iterations, refresh_every, top, out)
+    assert out.level == top
     ws = [w0.copy() for _ in datas]
-    for it in range(1, 4):
+    for it in range(1, iterations + 1):
         ws = [lr_step_fp64(d.X, d.y, w, coeffs, lr) for d, w in zip(datas, ws)]
-        if it % refresh_every == 0 or it == 3:
+        if it % refresh_every == 0 or it == iterations:
             avg = sum(ws) / len(ws)
             ws = [avg.copy() for _ in ws]
     want = workloads.pack_weights(ws[0], n_slots, g)
     got = he.he_decrypt_decode(ctx, out)
     assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20
-    with pytest.raises(he.HeError) as e:  # 11 limbs hold two steps, not three
-        he.he_lr_train(ctx, workers, he.lr_config(coeffs, lr, g, 2.0 ** 27), 3, 3, 11, out)
+    with pytest.raises(he.HeError) as e:  # the limbs hold fewer steps than that between refreshes
+        he.he_lr_train(ctx, workers, cfg, iterations, (top - 1) // 5 + 1, top, out)
     assert e.value.code == he.HE_ELEVEL
