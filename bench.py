@@ -815,6 +815,9 @@ def run_micro(args):
     host = workloads.residues(1, ctx.primes[:nl], n, parts=args.polys)
     t = torch.from_numpy(host.view(np.int64)).cuda()
     out = {}
+    for kv in args.tune or []:
+        key, val = kv.split("=")
+        he.he_set_tuning(ctx, key, float(val))
     for shape, generic, inverse in ((0, False, False), (0, False, True), (1, False, False), (1, False, True),
                                     (2, False, False), (2, False, True), (0, True, False), (0, True, True)):
         he.he_set_tuning(ctx, "ntt_generic", generic)
@@ -822,11 +825,13 @@ def run_micro(args):
         for _ in range(args.warmup):
             he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(f"{'intt' if inverse else 'ntt'}_{'generic' if generic else f's{shape}'}")
         e0.record(stream)
         for _ in range(args.steps):
             he.he_ntt(ctx, t, args.polys, nl * n, nl, 0, inverse)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1) / args.steps
         limbs = args.polys * nl
         bfly = limbs * (n / 2) * log_n
