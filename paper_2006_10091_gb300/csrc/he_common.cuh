@@ -23,6 +23,8 @@ struct PrimeDev {
   uint64_t n_inv;     // N^-1 mod q
   uint64_t n_inv_sh;  // its Shoup companion
   uint64_t one_sh;    // Shoup companion of 1: floor(2^64 / q)
+  uint64_t r64;       // 2^64 mod q
+  uint64_t r64_sh;    // its Shoup companion
 };
 
 __device__ __forceinline__ uint64_t shoup_companion_dev(uint64_t w, uint64_t q) {
@@ -89,6 +91,20 @@ __device__ __forceinline__ uint64_t from_signed(int64_t x, const PrimeDev& p) {
   if (x >= 0) return reduce64((uint64_t)x, p);
   uint64_t r = reduce64((uint64_t)(-x), p);
   return r ? p.q - r : 0;
+}
+
+// (hi:lo) += a*b, the full 128-bit product (no reduction).
+__device__ __forceinline__ void mac128(uint64_t& lo, uint64_t& hi, uint64_t a, uint64_t b) {
+  asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
+}
+
+// (hi:lo) mod q for any 128-bit value: hi * (2^64 mod q) by a Shoup product
+// (any 64-bit hi, result in [0, 2q)) plus lo mod q, corrected once.
+__device__ __forceinline__ uint64_t reduce128_any(uint64_t hi, uint64_t lo, const PrimeDev& p) {
+  const uint64_t q = p.q;
+  uint64_t r = mul_shoup_lazy(hi, p.r64, p.r64_sh, q) + reduce64(lo, p);
+  r = r >= q + q ? r - q - q : r;
+  return r >= q ? r - q : r;
 }
 
 // 128-bit word (w3:w2:w1:w0) mod q, by Horner on 64-bit halves:

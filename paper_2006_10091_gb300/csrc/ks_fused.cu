@@ -1,5 +1,7 @@
 // ks_fused.cu -- entry points of the fused key-switching kernels (kernels in
 // ks_fused.cuh, instantiated per ring size in ks_fused_n12.cu .. n16.cu).
+#include <algorithm>
+
 #include "ks_fused.cuh"
 
 namespace he {
@@ -88,13 +90,18 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
   ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
   ra.nrot = rs.n;
   ra.count = count;
-  ra.closed = 0;
+  // the summed path adds nrot * beta products below q^2 in 128 bits (the
+  // other path beta of them)
+  uint32_t bits = 0;
+  for (uint32_t t = 0; t < level; ++t) bits = std::max(bits, (uint32_t)(64 - __builtin_clzll(c->q[t])));
+  for (uint32_t u = 0; u < (uint32_t)c->alpha; ++u) bits = std::max(bits, (uint32_t)(64 - __builtin_clzll(c->q[c->L + u])));
+  const uint32_t nprod = rs.n * ((level + (uint32_t)c->alpha - 1) / (uint32_t)c->alpha);
+  ra.closed = 2 * bits + (32 - __builtin_clz(nprod)) <= 128 ? 1 : 0;
   ra.acc_rstride = acc_rstride;
   for (uint32_t r = 0; r < rs.n; ++r) {
     ra.gal[r] = rs.gal[r];
     ra.gal_inv[r] = gal_inverse(rs.gal[r], c->log_n);
     ra.evk[r] = rs.evk[r];
-    ra.evk_sh[r] = rs.evk[r] + c->key_words();
   }
   int closed = 0, rc;
   switch (c->log_n) {

@@ -326,7 +326,6 @@ struct KsRotArgs {
   uint64_t acc_rstride;    // words between the accumulators of consecutive rotations
   uint64_t gal[HE_MAX_ROT], gal_inv[HE_MAX_ROT];
   const uint64_t* evk[HE_MAX_ROT];
-  const uint64_t* evk_sh[HE_MAX_ROT];
 };
 
 // Grid: nt * count * TILES, target limb slowest and row tile fastest, so
@@ -350,10 +349,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   const uint32_t i = b % ra.count, t = b / ra.count;
   const uint32_t prime = ks_prime(t, a.level, a.L);
   const PrimeDev pr = a.primes[prime];
-  const uint64_t q = pr.q, q2 = q + q;
+  const uint64_t q = pr.q;
   const bool lazy = q < (1ull << 58);
-  // products summed unreduced while all of them stay below 2^64
-  const bool acc_lazy = q < ~0ull / (2ull * a.beta * (ra.closed ? ra.nrot : 1));
   stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
   // 1. every digit's tile in evaluation form, canonical residues
   for (uint32_t j = 0; j < a.beta; ++j) {
@@ -378,11 +375,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
     }
   }
   __syncthreads();
-  // 2. per rotation, the products of the permuted digits with its key
-  auto mac = [&](uint64_t& acc, uint64_t x, uint64_t k, uint64_t ksh) {
-    acc += mul_shoup_lazy(x, k, ksh, q);
-    if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
-  };
+  // 2. the products of the permuted digits with each rotation's key, summed
+  // as full 128-bit products and reduced once per residue
   const uint32_t row0 = (uint32_t)tile << LOG_K;
   constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
   if (ra.closed) {
@@ -392,12 +386,12 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
 #pragma unroll 1
     for (int u0 = 0; u0 < PER; u0 += GRP) {
       uint32_t eo[GRP];
-      uint64_t acc0[GRP], acc1[GRP];
+      uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
 #pragma unroll
       for (int u = 0; u < GRP; ++u) {
         const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
         eo[u] = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-        acc0[u] = acc1[u] = 0;
+        a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
       }
       for (uint32_t r = 0; r < ra.nrot; ++r) {
         uint32_t so[GRP];
@@ -408,30 +402,28 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
           so[u] = sl + (sl >> 3);
         }
         const uint64_t* ev = ra.evk[r];
-        const uint64_t* es = ra.evk_sh[r];
         for (uint32_t j = 0; j < a.beta; ++j) {
           const uint64_t* sm = dig + (size_t)j * TW;
-          const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
-          const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
+          const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
+          const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
 #pragma unroll
           for (int u = 0; u < GRP; ++u) {
             const uint64_t x = sm[so[u]];
-            mac(acc0[u], x, __ldg(ev + kb_off + eo[u]), __ldg(es + kb_off + eo[u]));
-            mac(acc1[u], x, __ldg(ev + ka_off + eo[u]), __ldg(es + ka_off + eo[u]));
+            mac128(a0l[u], a0h[u], x, __ldg(kb + eo[u]));
+            mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
           }
         }
       }
 #pragma unroll
       for (int u = 0; u < GRP; ++u) {
-        o0[eo[u]] = reduce64(acc0[u], pr);
-        o1[eo[u]] = reduce64(acc1[u], pr);
+        o0[eo[u]] = reduce128_any(a0h[u], a0l[u], pr);
+        o1[eo[u]] = reduce128_any(a1h[u], a1l[u], pr);
       }
     }
     return;
   }
   for (uint32_t r = 0; r < ra.nrot; ++r) {
     const uint64_t* ev = ra.evk[r];
-    const uint64_t* es = ra.evk_sh[r];
     uint64_t* o0 = a.acc + (size_t)r * ra.acc_rstride + ((size_t)i * 2 * a.nt + t) * N;
     uint64_t* o1 = o0 + (size_t)a.nt * N;
 #pragma unroll 1
@@ -448,24 +440,24 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
         so[u] = sl + (sl >> 3);
         eo[u] = e;
       }
-      uint64_t acc0[GRP], acc1[GRP];
+      uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
 #pragma unroll
-      for (int u = 0; u < GRP; ++u) acc0[u] = acc1[u] = 0;
+      for (int u = 0; u < GRP; ++u) a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
       for (uint32_t j = 0; j < a.beta; ++j) {
         const uint64_t* sm = dig + (size_t)j * TW;
-        const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
-        const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
+        const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
+        const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
 #pragma unroll
         for (int u = 0; u < GRP; ++u) {
           const uint64_t x = sm[so[u]];
-          mac(acc0[u], x, __ldg(ev + kb_off + eo[u]), __ldg(es + kb_off + eo[u]));
-          mac(acc1[u], x, __ldg(ev + ka_off + eo[u]), __ldg(es + ka_off + eo[u]));
+          mac128(a0l[u], a0h[u], x, __ldg(kb + eo[u]));
+          mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
         }
       }
 #pragma unroll
       for (int u = 0; u < GRP; ++u) {
-        o0[eo[u]] = reduce64(acc0[u], pr);
-        o1[eo[u]] = reduce64(acc1[u], pr);
+        o0[eo[u]] = reduce128_any(a0h[u], a0l[u], pr);
+        o1[eo[u]] = reduce128_any(a1h[u], a1l[u], pr);
       }
     }
   }
@@ -797,7 +789,7 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
                    count * n * 8 * (conv + own + 2.0 * ra.nrot * a.nt));
     KsRotArgs rc = ra;
     rc.count = count;
-    rc.closed = 1;
+    rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits
     for (uint32_t r = 0; r < ra.nrot; ++r) rc.closed &= rot_closed<LOG_N, M2, K2 - 1>(ra.gal_inv[r]) ? 1 : 0;
     *closed_out = rc.closed;
     ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(rc);

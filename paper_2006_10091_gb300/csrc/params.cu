@@ -159,6 +159,8 @@ int build_tables(he_ctx* c) {
     p.n_inv_sh = h_shoup(p.n_inv, q);
     p.one_sh = h_shoup(1, q);
     two64[t] = (uint64_t)(((u128)1 << 64) % q);
+    p.r64 = two64[t];
+    p.r64_sh = h_shoup(p.r64, q);
   }
   HE_CUDA(cudaMalloc(&c->d_primes, sizeof(PrimeDev) * np));
   HE_CUDA(cudaMemcpy(c->d_primes, pd.data(), sizeof(PrimeDev) * np, cudaMemcpyHostToDevice));
