@@ -1069,16 +1069,14 @@ int orc_rescale(orc_ctx* c, const uint64_t* a, int level, uint64_t* out) {
   return 0;
 }
 
-/* HMult: tensor, relinearise d2 with the s^2 key, add, rescale.  out has
- * level - 1 limbs.  scale_out = scale_a * scale_b / q[level-1]. */
-int orc_mul_relin_rescale(orc_ctx* c, const uint64_t* a, const uint64_t* b, int level, uint64_t* out) {
-  if (level < 2 || level > c->L) return -1;
+/* Relinearise a three-part ciphertext d = (d0, d1, d2) [3][level][N]: switch
+ * d2 with the s^2 key and add, (d0 + k0, d1 + k1); then rescale.  out has
+ * level - 1 limbs. */
+static void relin_rescale(orc_ctx* c, const uint64_t* d, int level, uint64_t* out) {
   uint32_t n = c->n;
-  uint64_t* d = malloc(sizeof(uint64_t) * 3 * (size_t)level * n);
   uint64_t* k0 = malloc(sizeof(uint64_t) * (size_t)level * n);
   uint64_t* k1 = malloc(sizeof(uint64_t) * (size_t)level * n);
   uint64_t* r = malloc(sizeof(uint64_t) * 2 * (size_t)level * n);
-  orc_tensor(c, a, b, level, d);
   keyswitch(c, POLY(d, 2 * level, n), level, c->rlk, k0, k1);
   for (int t = 0; t < level; t++) {
     uint64_t q = c->q[t];
@@ -1088,7 +1086,18 @@ int orc_mul_relin_rescale(orc_ctx* c, const uint64_t* a, const uint64_t* b, int 
     }
   }
   orc_rescale(c, r, level, out);
-  free(d); free(k0); free(k1); free(r);
+  free(k0); free(k1); free(r);
+}
+
+/* HMult: tensor, relinearise d2 with the s^2 key, add, rescale.  out has
+ * level - 1 limbs.  scale_out = scale_a * scale_b / q[level-1]. */
+int orc_mul_relin_rescale(orc_ctx* c, const uint64_t* a, const uint64_t* b, int level, uint64_t* out) {
+  if (level < 2 || level > c->L) return -1;
+  uint32_t n = c->n;
+  uint64_t* d = malloc(sizeof(uint64_t) * 3 * (size_t)level * n);
+  orc_tensor(c, a, b, level, d);
+  relin_rescale(c, d, level, out);
+  free(d);
   return 0;
 }
 
@@ -1253,8 +1262,11 @@ int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* step
  *   B  = rescale(M * round(c1*lr * sigB)), sigB = (sS*q[l0-2])/sU, dropped to l0-3
  *   Q  = rescale(T * round(c2*lr * sigQ)), sigQ = (sS*q[l0-3])/sT  (if c2 != 0)
  *   S  = C + B (+ Q) + round(c0*lr * scale(C))
- *   G_k = HMult(S, drop(Z_k, l0-3))    level l0-4
- *   G  = sum_k G_k
+ *   D  = sum_k tensor(S_k, drop(Z_k, l0-3))   three parts, level l0-3
+ *   G  = rescale(relinearise(D))       level l0-4, sG = scale(C)*sZ/q[l0-4]
+ *        (one relinearisation and one rescale for all k: both are linear,
+ *        so this encrypts sum_k S_k Z_k as the sum of nZ HMults would, with
+ *        1/nZ of their key switches and less noise)
  *   H  = sum over o < g of rot(G, o)     (rotsum)
  *   H' = rescale(H (x) mask), mask = 1 on slots = 0 mod g, encoded at maskscale
  *   R  = sum over o < g of rot(H', -o)   (rotsum)
@@ -1329,8 +1341,12 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
   memset(G.d, 0, sizeof(uint64_t) * 2 * (size_t)G.level * n);
   orc_ct U = ct_new(c, l0 - 1, sU), T = ct_new(c, l0 - 2, sT), A = ct_new(c, l0 - 2, 0.0);
   orc_ct Cc = ct_new(c, l0 - 3, 0.0), B = ct_new(c, l0 - 2, 0.0), Qq = ct_new(c, l0 - 3, 0.0);
-  orc_ct Zd = ct_new(c, l0 - 3, sZ), Gk = ct_new(c, l0 - 4, 0.0);
+  orc_ct Zd = ct_new(c, l0 - 3, sZ);
   uint64_t* tmp = malloc(sizeof(uint64_t) * 2 * (size_t)l0 * n);
+  const size_t w3 = 3 * (size_t)(l0 - 3) * n;
+  uint64_t* D = calloc(w3, sizeof(uint64_t));  /* sum_k tensor(S_k, Z_k) */
+  uint64_t* Dk = malloc(sizeof(uint64_t) * w3);
+  double sD = 0.0;
   for (int k = 0; k < nZ && rc == 0; k++) {
     /* U = HMult(Z_k, W); M = rotate-and-sum over the F features */
     orc_mul_relin_rescale(c, Z[k], Wd, l0, U.d);
@@ -1360,15 +1376,22 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
       orc_add(c, Cc.d, Qq.d, l0 - 3, Cc.d);
     }
     orc_add_int(c, Cc.d, l0 - 3, round_const(coeffs[0] * lr * Cc.scale), Cc.d);
-    /* G_k = S * Z_k */
+    /* D += tensor(S_k, Z_k) */
     orc_drop(c, Z[k], l0, l0 - 3, Zd.d);
-    orc_mul_relin_rescale(c, Cc.d, Zd.d, l0 - 3, Gk.d);
-    Gk.scale = Cc.scale * sZ / (double)q[l0 - 4];
-    if (k == 0) G.scale = Gk.scale;
-    else if (!scales_match(G.scale, Gk.scale)) { rc = -3; break; }
-    orc_add(c, G.d, Gk.d, l0 - 4, G.d);
+    orc_tensor(c, Cc.d, Zd.d, l0 - 3, Dk);
+    if (k == 0) sD = Cc.scale * sZ;
+    else if (!scales_match(sD, Cc.scale * sZ)) { rc = -3; break; }
+    for (int p = 0; p < 3; p++)
+      for (int t = 0; t < l0 - 3; t++) {
+        uint64_t* dst = POLY(D, p * (l0 - 3) + t, n);
+        const uint64_t* src = POLY(Dk, p * (l0 - 3) + t, n);
+        for (uint32_t i = 0; i < n; i++) dst[i] = addmod(dst[i], src[i], q[t]);
+      }
   }
   if (rc == 0) {
+    /* G = rescale(relinearise(D)) */
+    relin_rescale(c, D, l0 - 3, G.d);
+    G.scale = sD / (double)q[l0 - 4];
     /* H = sum over the g samples of each feature (lands on slots = 0 mod g) */
     rc = rotsum(c, &G, 1, logg);
   }
@@ -1393,7 +1416,7 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
   }
   free(tmp);
   free(G.d); free(U.d); free(T.d); free(A.d); free(Cc.d); free(B.d); free(Qq.d);
-  free(Zd.d); free(Gk.d); free(R.d);
+  free(Zd.d); free(D); free(Dk); free(R.d);
   return rc;
 }
 

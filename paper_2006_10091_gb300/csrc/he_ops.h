@@ -67,6 +67,11 @@ int add_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, ui
 int copy_batch(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, uint32_t count);
 // acc += sum_i in[i] over `count` ciphertexts.
 int accumulate_batch(he_ctx* c, CtBatch in, uint32_t count, CtBatch acc, uint32_t level);
+// acc ([3][level][N]) += sum_i tensor(A[i], B[i]) over `count` pairs.
+int tensor_acc_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t count, uint64_t* acc, uint32_t level);
+// out = rescale(relinearise(D)) for three-part D (count x [3][level][N] at d_stride).
+int relin_rescale_batch(he_ctx* c, uint64_t* D, uint64_t d_stride, uint32_t level, uint32_t count, CtBatch out,
+                        Arena& ar);
 
 const uint64_t* galois_key(const he_ctx* c, uint64_t gal);
 bool uniform_view(const he_ct* a, size_t count, CtBatch* out);

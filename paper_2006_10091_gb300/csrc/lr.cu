@@ -24,7 +24,7 @@
 //   B  = rescale(M * round(c1*lr*sigB)),    sigB = (sS*q[l0-2])/sU, dropped one level
 //   Q  = rescale(T * round(c2*lr*sigQ)),    sigQ = (sS*q[l0-3])/sT   (c2 != 0)
 //   S  = C + B (+ Q) + round(c0*lr*scale(C))
-//   G  = sum_k HMult(S, drop(Z_k))
+//   D  = sum_k tensor(S_k, drop(Z_k)) ;  G = rescale(relinearise(D))   (one key switch per shard)
 //   H  = sum over o < g of rot(G, o) ;  R = rescale(H (x) mask) ;  R <- sum over o < g of rot(R, -o)
 //   W' = drop(W) + R                        (scale sW, level l0-5)
 #include <math.h>
@@ -132,11 +132,10 @@ static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_
 }
 
 // Per-ciphertext words of the circuit's intermediates at input level l0:
-// U, T, A, C, B, Q, Gk, Tmp, and the gathered copies of Z and W.
+// U, T, A, C, B, Q, Tmp, and the gathered copies of Z and W.
 static size_t lr_ct_words(const he_ctx* c, uint32_t l0) {
   const size_t n = c->n;
-  return n * 2 * ((l0 - 1) + (l0 - 2) + (l0 - 2) + (l0 - 3) + (l0 - 2) + (l0 - 3) + (l0 - 4) + (l0 - 1) + 2 * l0) +
-         10 * 32;
+  return n * 2 * ((l0 - 1) + (l0 - 2) + (l0 - 2) + (l0 - 3) + (l0 - 2) + (l0 - 3) + (l0 - 1) + 2 * l0) + 9 * 32;
 }
 
 // Scratch words of one operation of the step: those of the per-ciphertext
@@ -146,6 +145,7 @@ static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk, uint32_t
   w = std::max(w, rotsum_words(c, l0 - 1, chunk, 3));
   w = std::max(w, rescale_words(c, l0 - 1, chunk));
   w = std::max(w, rotsum_words(c, l0 - 4, ns, 3));
+  w = std::max(w, ks_words(c, l0 - 3, ns) + (size_t)ns * 2 * (l0 - 3) * c->n + rescale_words(c, l0 - 3, ns) + 64);
   w = std::max(w, rescale_words(c, l0 - 4, ns) + (size_t)ns * 2 * (l0 - 4) * c->n);
   return w + 64;
 }
@@ -185,7 +185,7 @@ static int lr_gal(he_ctx* c, const LrPlan& P, LrGal* gl) {
 }
 
 struct LrBufs {
-  CtBatch U, T, A, Cc, B, Q, Gk, Tmp, Zcopy, Wrep;
+  CtBatch U, T, A, Cc, B, Q, Tmp, Zcopy, Wrep;
 };
 
 static CtBatch carve(Arena& a, size_t count, uint32_t cap, uint32_t n) {
@@ -194,7 +194,7 @@ static CtBatch carve(Arena& a, size_t count, uint32_t cap, uint32_t n) {
 }
 
 // The per-ciphertext part of the step for m data ciphertexts Zc with weights
-// Wc (stride 0: one W for all): G_k = p(M_k) * Z_k in b.Gk.
+// Wc (stride 0: one W for all): S_k = p(M_k) in b.Cc.
 static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtBatch Wc, uint32_t m, LrBufs& b,
                     Arena& ops, bool infer) {
   const uint32_t l0 = P.l0;
@@ -223,9 +223,7 @@ static int lr_chunk(he_ctx* c, const LrPlan& P, const LrGal& gl, CtBatch Zc, CtB
     HE_TRY(addsub_batch(c, b.Cc, b.Q, b.Cc, 0, l0 - 3, m));
   }
   HE_TRY(add_int_batch(c, b.Cc, b.Cc, P.k0, l0 - 3, m));
-  if (infer) return HE_OK;  // S_k = p(M_k) is in b.Cc
-  // G_k = S * Z_k
-  HE_TRY(mul_relin_batch(c, b.Cc, Zc, l0 - 3, m, b.Gk, true, fresh()));
+  (void)infer;  // S_k = p(M_k) is in b.Cc
   return HE_OK;
 }
 
@@ -317,6 +315,9 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     const uint32_t ns = (uint32_t)grp.size();
     Arena a = pool;
     CtBatch G = carve(a, ns, l0 - 4, n), H1 = carve(a, ns, l0 - 4, n), R = carve(a, ns, l0 - 4, n);
+    // three-part sums D = sum_k tensor(S_k, Z_k) per shard, relinearised once
+    const uint64_t d3_stride = (uint64_t)3 * (l0 - 3) * n;
+    uint64_t* D3 = a.take<uint64_t>((size_t)ns * d3_stride);
     const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1, 1)) * sizeof(uint64_t);
     size_t chunk = std::max<size_t>(1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, total));
     LrBufs b;
@@ -326,7 +327,6 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     b.Cc = carve(a, chunk, l0 - 3, n);
     b.B = carve(a, chunk, l0 - 2, n);
     b.Q = carve(a, chunk, l0 - 3, n);
-    b.Gk = carve(a, chunk, l0 - 4, n);
     b.Tmp = carve(a, chunk, l0 - 1, n);
     b.Zcopy = carve(a, chunk, l0, n);
     b.Wrep = carve(a, chunk, l0, n);
@@ -335,7 +335,8 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     ops.size = a.size > a.off ? a.size - a.off : 0;
     if (!b.Wrep.base || ops.size < lr_op_words(c, l0, (uint32_t)chunk, ns) * sizeof(uint64_t))
       return fail(HE_ENOMEM, "step scratch too small");
-    HE_CUDA(cudaMemsetAsync(G.base, 0, sizeof(uint64_t) * G.stride * ns, c->stream));
+    if (!D3) return fail(HE_ENOMEM, "step scratch too small");
+    HE_CUDA(cudaMemsetAsync(D3, 0, sizeof(uint64_t) * d3_stride * ns, c->stream));
     // walk the group's data ciphertexts chunk by chunk
     size_t gi = 0, idx = 0;  // shard position in grp, ciphertext index in that shard
     while (gi < grp.size()) {
@@ -405,15 +406,20 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
         }
         continue;
       }
-      for (auto& sg : seg) {
-        CtBatch gk = b.Gk, gs = G;
-        gk.base += off * b.Gk.stride;
-        gs.base += sg.first * G.stride;
-        HE_TRY(accumulate_batch(c, gk, (uint32_t)sg.second.second, gs, l0 - 4));
+      for (auto& sg : seg) {  // D += tensor(S_k, Z_k) of each segment's ciphertexts
+        CtBatch sk = b.Cc, zk = Zc;
+        sk.base += off * b.Cc.stride;
+        zk.base += off * Zc.stride;
+        HE_TRY(tensor_acc_batch(c, sk, zk, (uint32_t)sg.second.second, D3 + sg.first * d3_stride, l0 - 3));
         off += sg.second.second;
       }
     }
     if (infer) continue;
+    {  // G = rescale(relinearise(D))
+      Arena ar = ops;
+      ar.off = 0;
+      HE_TRY(relin_rescale_batch(c, D3, d3_stride, l0 - 3, ns, G, ar));
+    }
     HE_TRY(lr_finish(c, P, gl, mask, G, ns, H1, R, ops));
     for (uint32_t i = 0; i < ns; ++i) {
       Shard& s = sh[grp[i]];
@@ -440,7 +446,8 @@ static size_t lr_words(he_ctx* c, const LrShape* sh, size_t count, uint32_t refr
     const size_t per = (lr_ct_words(c, l0) + lr_op_words(c, l0, 1, 1)) * sizeof(uint64_t);
     const size_t chunk = std::max<size_t>(
         1, std::min(c->lr_chunk ? (size_t)c->lr_chunk : c->chunk_bytes / per, kv.second.second));
-    const size_t w = 3 * kv.second.first * 2 * (l0 - 4) * n + chunk * lr_ct_words(c, l0) +
+    const size_t w = 3 * kv.second.first * 2 * (l0 - 4) * n + kv.second.first * 3 * (l0 - 3) * n + 32 +
+                     chunk * lr_ct_words(c, l0) +
                      lr_op_words(c, l0, (uint32_t)chunk, (uint32_t)kv.second.first) + 4096;
     need = std::max(need, w);
   }

@@ -429,4 +429,53 @@ int accumulate_batch(he_ctx* c, CtBatch in, uint32_t count, CtBatch acc, uint32_
   return HE_OK;
 }
 
+// acc += sum over i < count of tensor(A_i, B_i): the three parts
+// (a0 b0, a0 b1 + a1 b0, a1 b1) of each product summed into the three-part
+// accumulator acc [3][level][N] (limbs below level of A and B).
+__global__ void k_tensor_acc(CtBatch A, CtBatch B, uint32_t count, uint64_t* acc, uint32_t level, int log_n,
+                             const PrimeDev* primes) {
+  const uint32_t n = 1u << log_n;
+  const size_t total = (size_t)level * n;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(g % n), t = (uint32_t)(g / n);
+    const PrimeDev pr = primes[t];
+    uint64_t* a0p = acc + (size_t)t * n + k;
+    uint64_t* a1p = a0p + (size_t)level * n;
+    uint64_t* a2p = a1p + (size_t)level * n;
+    uint64_t s0 = *a0p, s1 = *a1p, s2 = *a2p;
+    for (uint32_t i = 0; i < count; ++i) {
+      const uint64_t x0 = cpoly(A, i, 0, t, n)[k], x1 = cpoly(A, i, 1, t, n)[k];
+      const uint64_t y0 = cpoly(B, i, 0, t, n)[k], y1 = cpoly(B, i, 1, t, n)[k];
+      s0 = add_mod(s0, mul_mod(x0, y0, pr), pr.q);
+      s1 = add_mod(s1, add_mod(mul_mod(x0, y1, pr), mul_mod(x1, y0, pr), pr.q), pr.q);
+      s2 = add_mod(s2, mul_mod(x1, y1, pr), pr.q);
+    }
+    *a0p = s0;
+    *a1p = s1;
+    *a2p = s2;
+  }
+}
+
+int tensor_acc_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t count, uint64_t* acc, uint32_t level) {
+  {
+    ProfScope prof(c, "tensor", 4.0 * count * level * c->n, (double)(4 * count + 6) * level * c->n * 8);
+    k_tensor_acc<<<grid_for((size_t)level * c->n), 256, 0, c->stream>>>(A, B, count, acc, level, c->log_n,
+                                                                       c->d_primes);
+  }
+  HE_CUDA(cudaGetLastError());
+  return HE_OK;
+}
+
+// Relinearise three-part ciphertexts D (count x [3][level][N] at d_stride)
+// and rescale: out (level - 1 limbs) = rescale((d0, d1) + KS(d2)).
+int relin_rescale_batch(he_ctx* c, uint64_t* D, uint64_t d_stride, uint32_t level, uint32_t count, CtBatch out,
+                        Arena& ar) {
+  const uint32_t n = c->n;
+  uint64_t* r = ar.take<uint64_t>((size_t)count * 2 * level * n);
+  if (!r) return fail(HE_ENOMEM, "relinearisation scratch too small");
+  const CtBatch D01{D, d_stride, level, 0}, R{r, (uint64_t)2 * level * n, level, 0};
+  HE_TRY(keyswitch_batch(c, D + (size_t)2 * level * n, d_stride, level, count, c->d_rlk, D01, 2, R, ar));
+  return rescale_batch(c, R, level, count, out, ar);
+}
+
 }  // namespace he
