@@ -40,7 +40,8 @@ N_SAMPLES, N_FEATURES, G = 4096, 784, 8
 MASK_SCALE = 2.0 ** 27
 WORKLOAD = ("enc-LR gradient step (Eq. 7-8, Table 2 binomial): N=2^14, 8x40-bit limbs + 2x59-bit "
             "special primes (dnum 4), scale 2^40; 4096 samples x 784 features, 8 samples per ciphertext "
-            "(512 data ciphertexts); one step = 2048 mul+relin+rescale + 7688 rotations in 2564 hoisted "
+            "(512 data ciphertexts); one step = 1537 relinearised multiplications (3 per data ciphertext + 1 "
+            "for the gradient sum), 512 tensor accumulations and 14862 rotations in 1538 hoisted "
             "rotate-and-sum stages")
 
 
@@ -859,7 +860,7 @@ def run_micro_keyswitch(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     hoisted = args.micro == "rotsum"
-    steps = [8, 16, 24] if hoisted else [8]
+    steps = [8 * m for m in range(1, args.radix)] if hoisted else [8]
     if args.log_n == 16:
         ctx = he.Context(16, 24, 50, 4, 60, 2.0 ** 50, seed=0, rot_steps=steps, stream=stream.cuda_stream)
         level = 24
@@ -989,6 +990,7 @@ def main():
     ap.add_argument("--serve-inflight", type=int, default=4, help="waves per context in --micro serving")
     ap.add_argument("--serve-wave", type=int, default=16, help="requests per wave in --micro serving")
     ap.add_argument("--log-n", type=int, default=14)
+    ap.add_argument("--radix", type=int, default=4, help="--micro rotsum: rotations by 8, 16, ..., 8*(radix-1)")
     ap.add_argument("--polys", type=int, default=256)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)

@@ -243,7 +243,7 @@ int he_mul_relin_rescale_batch(he_ctx* ctx, const he_ct* a, const he_ct* b, he_c
 int he_rotate_batch(he_ctx* ctx, const he_ct* a, int32_t steps, he_ct* out, size_t count);
 
 /* Rotate-and-sum with one shared decomposition: out = a + sum_{r < nsteps}
- * rotate(a, steps[r]), 1 <= nsteps <= 8, the sums over slot positions that
+ * rotate(a, steps[r]), 1 <= nsteps <= 16, the sums over slot positions that
  * the packing of Sec. 3-4 reads inner products from.  The key switches of all
  * nsteps rotations share the ModUp of a's second part (each rotation applies
  * its automorphism to the raised digits) and one ModDown of their summed
@@ -267,10 +267,12 @@ int he_rotate_sum_batch(he_ctx* ctx, const he_ct* a, const int32_t* steps, uint3
  * levels: Z and W at the same level l >= 6; W_out at l - 5 with W's scale.
  * Each of its three rotate-and-sums (over F = N/(2g) feature positions of
  * step g, and over the g samples with steps 1 and -1) runs as he_rotate_sum
- * stages: steps s, 2s, 3s while two or more doublings remain (then s <- 4s),
- * and a stage of step s alone when the number of doublings is odd.  Needs
- * Galois keys for all those steps (e.g. for g = 8, F = 1024: 8, 16, 24, 32,
- * ..., 6144 and 1, 2, 3, 4, -1, -2, -3, -4). */
+ * stages of k doublings each -- steps s, 2s, ..., (2^k - 1)s, then s <- 2^k s
+ * -- with k = 3, except k = 4 for the first stage when the number of
+ * doublings is 1 mod 3 (k = 1 if it is 1) and k = 2 for a last stage when it
+ * is 2 mod 3.  Needs Galois keys for all those steps (lr_rot_steps in the
+ * Python binding lists them; e.g. g = 8, F = 1024: 8, 16, ..., 120, then
+ * 128, ..., 896, then 1024, ..., 7168, and 1, ..., 7 and -1, ..., -7). */
 typedef struct he_lr_config {
   double coeffs[4];     /* c0..c3 */
   double lr;            /* learning rate, e.g. eta / n */

@@ -1252,7 +1252,7 @@ int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* step
  * Op sequence and scale plan (all scales IEEE doubles, computed in this exact
  * order on both implementations; l0 = input level; q[i] the limb primes):
  *   U  = HMult(Z_k, W)                 level l0-1, sU = sZ*sW/q[l0-1]
- *   M  = sum over o < F of rot(U, o*g)   (rotsum: hoisted stages of radix 4)
+ *   M  = sum over o < F of rot(U, o*g)   (rotsum: hoisted stages)
  *   T  = HMult(M, M)                   level l0-2, sT = sU*sU/q[l0-2]
  *   sS = ((sW*q[l0-5])*q[l0-4]) / (maskscale*sZ)         (target scale of S)
  *   sA = (sS*q[l0-3])/sT ;  A = rescale(M * round(c3*lr * sA*q[l0-2]/sU))
@@ -1287,18 +1287,27 @@ static int scales_match(double a, double b) { return fabs(a / b - 1.0) < ldexp(1
 static int64_t round_const(double v) { return (int64_t)llround(v); }
 
 /* x <- sum over o = 0 .. 2^count - 1 of rot(x, o * step), in hoisted stages
- * (orc_rotate_sum): while two or more doublings remain, one stage of radix 4
- * (rotations by s, 2s, 3s, then s <- 4s); a last stage of radix 2 (rotation
- * by s) when count is odd. */
+ * (orc_rotate_sum) of k doublings each -- rotations by s, 2s, ..., (2^k - 1) s,
+ * then s <- 2^k s -- with k = 3, except k = 4 for the first stage when
+ * count = 1 mod 3 (k = 1 when count = 1) and k = 2 for a last stage when
+ * count = 2 mod 3. */
 static int rotsum(orc_ctx* c, orc_ct* x, int32_t step, int count) {
+  int sizes[32], ns = 0;
+  for (int i = 0; i < count / 3; i++) sizes[ns++] = 3;
+  if (count % 3 == 1) {
+    if (ns == 0) sizes[ns++] = 1;
+    else sizes[0] = 4;
+  } else if (count % 3 == 2) {
+    sizes[ns++] = 2;
+  }
   int32_t s = step;
   int rc = 0;
-  while (count > 0 && rc == 0) {
-    int32_t st[3] = {s, 2 * s, 3 * s};
-    int ns = count >= 2 ? 3 : 1;
-    rc = orc_rotate_sum(c, x->d, x->level, st, ns, x->d);
-    s *= ns + 1;
-    count -= count >= 2 ? 2 : 1;
+  for (int i = 0; i < ns && rc == 0; i++) {
+    int32_t st[15];
+    int nr = (1 << sizes[i]) - 1;
+    for (int m = 1; m <= nr; m++) st[m - 1] = s * m;
+    rc = orc_rotate_sum(c, x->d, x->level, st, nr, x->d);
+    s *= 1 << sizes[i];
   }
   return rc;
 }

@@ -414,7 +414,7 @@ def he_rotate(ctx, a, steps: int, out):
 
 
 def he_rotate_sum(ctx, a, steps, out):
-    """out = a + sum of rotate(a, s) over steps (1 to 8 steps), one shared
+    """out = a + sum of rotate(a, s) over steps (1 to 16 steps), one shared
     decomposition; out may be a."""
     st = (ctypes.c_int32 * len(steps))(*steps)
     _run(load().he_rotate_sum, ctx, [out], a, st, len(steps), out)
@@ -473,17 +473,32 @@ def fit_gradient_polynomial(f, a: float, degree: int = 3, n: int = 200001, seed=
     return he_fit_poly(x, f(x), degree)
 
 
+def rotsum_stage_sizes(count: int) -> list:
+    """Doublings per stage of a rotate-and-sum over 2^count offsets: stages of
+    three (radix 8, seven rotations), the first of four (radix 16) when count
+    = 1 mod 3 and a last one of two (radix 4) when count = 2 mod 3.  Every
+    stage pays one ModUp and one ModDown and each of its rotations one inner
+    product, so stages of three doublings are the cheapest split."""
+    if count <= 0:
+        return []
+    r = count % 3
+    sizes = [3] * (count // 3)
+    if r == 1:
+        sizes = [4] + sizes[1:] if sizes else [1]
+    elif r == 2:
+        sizes = sizes + [2]
+    return sizes
+
+
 def rotsum_stages(step: int, count: int) -> list:
     """The stages in which a rotate-and-sum over the 2^count offsets 0, step,
-    2 step, ... is evaluated: one he_rotate_sum per stage, with rotations by
-    s, 2s, 3s (radix 4, then s <- 4s) while two or more doublings remain, and a
-    last stage with the rotation by s alone when count is odd."""
+    2 step, ... is evaluated: one he_rotate_sum per stage of k doublings
+    (rotsum_stage_sizes), with rotations by s, 2s, ..., (2^k - 1) s, then
+    s <- 2^k s."""
     out, s = [], step
-    while count > 0:
-        ns = 3 if count >= 2 else 1
-        out.append([s * m for m in range(1, ns + 1)])
-        s *= ns + 1
-        count -= 2 if ns == 3 else 1
+    for k in rotsum_stage_sizes(count):
+        out.append([s * m for m in range(1, 1 << k)])
+        s <<= k
     return out
 
 

@@ -710,10 +710,10 @@ int he_rotate_batch(he_ctx* c, const he_ct* a, int32_t steps, he_ct* out, size_t
 
 static int rotsum_chunks(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, size_t count, const uint64_t* gals,
                          uint32_t nrot) {
-  const size_t per = rotsum_words(c, level, 1, nrot) * sizeof(uint64_t);
+  const size_t per = rotsum_words(c, level, 1) * sizeof(uint64_t);
   size_t chunk = std::max<size_t>(1, c->chunk_bytes / per);
   chunk = std::min(chunk, count);
-  HE_TRY(ws_reserve(c, rotsum_words(c, level, (uint32_t)chunk, nrot) * sizeof(uint64_t) + 8192));
+  HE_TRY(ws_reserve(c, rotsum_words(c, level, (uint32_t)chunk) * sizeof(uint64_t) + 8192));
   for (size_t i0 = 0; i0 < count; i0 += chunk) {
     const uint32_t m = (uint32_t)std::min(chunk, count - i0);
     CtBatch a = A, o = O;
@@ -732,7 +732,7 @@ int he_rotate_sum(he_ctx* c, const he_ct* a, const int32_t* steps, uint32_t nste
 int he_rotate_sum_batch(he_ctx* c, const he_ct* a, const int32_t* steps, uint32_t nsteps, he_ct* out,
                         size_t count) {
   if (!c || !a || !out || !steps) return fail(HE_EINVAL, "he_rotate_sum: null argument");
-  if (nsteps < 1 || nsteps > HE_MAX_ROT) return fail(HE_EINVAL, "he_rotate_sum: 1 to 8 steps");
+  if (nsteps < 1 || nsteps > HE_MAX_ROT) return fail(HE_EINVAL, "he_rotate_sum: 1 to 16 steps");
   if (count == 0) return HE_OK;
   for (size_t i = 0; i < count; ++i) {
     HE_TRY(check_ct(c, &a[i], "he_rotate_sum"));

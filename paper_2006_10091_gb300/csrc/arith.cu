@@ -111,60 +111,57 @@ __global__ void k_inner_product(const uint64_t* ext, uint64_t ext_stride, const 
 }
 
 // ---- hoisted rotate-and-sum (unfused form, any N) --------------------------------
-// The inner products of several rotations sharing one decomposition: ext
-// holds the extended digits of d (evaluation form, d itself on each digit's
-// own limbs) and rotation r uses them through its automorphism,
-//   acc_r[i][p][t][e] = sum_j X_j[automorph_src(e, gal_r)] * evk_r[j][p][prime(t)][e],
+// The inner products of several rotations sharing one decomposition, summed:
+// ext holds the extended digits of d (evaluation form, d itself on each
+// digit's own limbs) and rotation r uses them through its automorphism,
+//   acc[i][p][t][e] = sum_r sum_j X_j[automorph_src(e, gal_r)] * evk_r[j][p][prime(t)][e],
 // which permutes the evaluation points of every limb alike.
 __global__ void k_inner_product_rot(const uint64_t* ext, uint64_t ext_stride, const uint64_t* d,
                                     uint64_t d_stride, RotSet rs, uint64_t* acc, uint64_t acc_stride,
-                                    uint64_t acc_rstride, uint32_t level, uint32_t alpha, uint32_t beta,
-                                    uint32_t L, uint32_t np, uint32_t count, int log_n, const PrimeDev* primes) {
+                                    uint32_t level, uint32_t alpha, uint32_t beta, uint32_t L, uint32_t np,
+                                    uint32_t count, int log_n, const PrimeDev* primes) {
   const uint32_t n = 1u << log_n;
   const uint32_t nt = level + alpha;
-  const size_t total = (size_t)rs.n * count * nt * n;
+  const size_t total = (size_t)count * nt * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const uint32_t e = (uint32_t)(g % n);
-    size_t r2 = g / n;
-    const uint32_t t = (uint32_t)(r2 % nt);
-    r2 /= nt;
-    const uint32_t i = (uint32_t)(r2 % count), r = (uint32_t)(r2 / count);
+    const size_t r2 = g / n;
+    const uint32_t t = (uint32_t)(r2 % nt), i = (uint32_t)(r2 / nt);
     const uint32_t p = t < level ? t : L + t - level;
     const PrimeDev pr = primes[p];
-    const uint32_t src = automorph_src(e, rs.gal[r], log_n);
-    const uint64_t* evk = rs.evk[r];
     uint64_t s0 = 0, s1 = 0;
-    for (uint32_t j = 0; j < beta; ++j) {
-      const uint32_t lo = j * alpha;
-      const bool own = t >= lo && t < lo + alpha && t < level;
-      const uint64_t x = own ? d[(size_t)i * d_stride + (size_t)t * n + src]
-                             : ext[(size_t)i * ext_stride + ((size_t)j * nt + t) * n + src];
-      s0 = add_mod(s0, mul_mod(x, __ldg(evk + (((size_t)j * 2 + 0) * np + p) * n + e), pr), pr.q);
-      s1 = add_mod(s1, mul_mod(x, __ldg(evk + (((size_t)j * 2 + 1) * np + p) * n + e), pr), pr.q);
+    for (uint32_t r = 0; r < rs.n; ++r) {
+      const uint32_t src = automorph_src(e, rs.gal[r], log_n);
+      const uint64_t* evk = rs.evk[r];
+      for (uint32_t j = 0; j < beta; ++j) {
+        const uint32_t lo = j * alpha;
+        const bool own = t >= lo && t < lo + alpha && t < level;
+        const uint64_t x = own ? d[(size_t)i * d_stride + (size_t)t * n + src]
+                               : ext[(size_t)i * ext_stride + ((size_t)j * nt + t) * n + src];
+        s0 = add_mod(s0, mul_mod(x, __ldg(evk + (((size_t)j * 2 + 0) * np + p) * n + e), pr), pr.q);
+        s1 = add_mod(s1, mul_mod(x, __ldg(evk + (((size_t)j * 2 + 1) * np + p) * n + e), pr), pr.q);
+      }
     }
-    uint64_t* a = acc + (size_t)r * acc_rstride + (size_t)i * acc_stride;
+    uint64_t* a = acc + (size_t)i * acc_stride;
     a[(size_t)t * n + e] = s0;
     a[((size_t)nt + t) * n + e] = s1;
   }
 }
 
-// acc_0 += acc_1 + ... + acc_{nsum-1} on limbs t0 <= t < t1 of both parts.
-__global__ void k_sum_acc(uint64_t* acc, uint64_t acc_stride, uint64_t acc_rstride, uint32_t nsum, uint32_t t0,
-                          uint32_t t1, uint32_t nt, uint32_t level, uint32_t L, uint32_t count, int log_n,
-                          const PrimeDev* primes) {
-  const uint32_t n = 1u << log_n, nl = t1 - t0;
-  const size_t total = (size_t)count * 2 * nl * n;
+// Accumulators of both parts (limbs 0 .. nt-1, limb t over prime(t)) reduced
+// to [0, q) from sums of a few residues.
+__global__ void k_reduce_acc(uint64_t* acc, uint64_t acc_stride, uint32_t nt, uint32_t level, uint32_t L,
+                             uint32_t count, int log_n, const PrimeDev* primes) {
+  const uint32_t n = 1u << log_n;
+  const size_t total = (size_t)count * 2 * nt * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const uint32_t e = (uint32_t)(g % n);
     size_t r = g / n;
-    const uint32_t t = t0 + (uint32_t)(r % nl);
-    r /= nl;
+    const uint32_t t = (uint32_t)(r % nt);
+    r /= nt;
     const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
-    const uint64_t q = primes[t < level ? t : L + t - level].q;
     uint64_t* a = acc + (size_t)i * acc_stride + ((size_t)p * nt + t) * n + e;
-    uint64_t v = *a;
-    for (uint32_t s = 1; s < nsum; ++s) v = add_mod(v, a[(size_t)s * acc_rstride], q);
-    *a = v;
+    *a = reduce64(*a, primes[t < level ? t : L + t - level]);
   }
 }
 

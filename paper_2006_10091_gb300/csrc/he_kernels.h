@@ -3,7 +3,7 @@
 #include "he_common.cuh"
 
 #define HE_MAX_DIGIT 8
-#define HE_MAX_ROT 8  // rotations one hoisted rotate-and-sum stage may take
+#define HE_MAX_ROT 16  // rotations one hoisted rotate-and-sum stage may take
 
 namespace he {
 
@@ -51,11 +51,10 @@ __global__ void k_inner_product(const uint64_t* ext, uint64_t ext_stride, const 
                                 const PrimeDev* primes);
 __global__ void k_inner_product_rot(const uint64_t* ext, uint64_t ext_stride, const uint64_t* d,
                                     uint64_t d_stride, RotSet rs, uint64_t* acc, uint64_t acc_stride,
-                                    uint64_t acc_rstride, uint32_t level, uint32_t alpha, uint32_t beta,
-                                    uint32_t L, uint32_t np, uint32_t count, int log_n, const PrimeDev* primes);
-__global__ void k_sum_acc(uint64_t* acc, uint64_t acc_stride, uint64_t acc_rstride, uint32_t nsum, uint32_t t0,
-                          uint32_t t1, uint32_t nt, uint32_t level, uint32_t L, uint32_t count, int log_n,
-                          const PrimeDev* primes);
+                                    uint32_t level, uint32_t alpha, uint32_t beta, uint32_t L, uint32_t np,
+                                    uint32_t count, int log_n, const PrimeDev* primes);
+__global__ void k_reduce_acc(uint64_t* acc, uint64_t acc_stride, uint32_t nt, uint32_t level, uint32_t L,
+                             uint32_t count, int log_n, const PrimeDev* primes);
 __global__ void k_add_automorphs(CtBatch A, CtBatch O, RotSet rs, uint32_t level, uint32_t count, int log_n,
                                  const PrimeDev* primes);
 __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_t* conv,

@@ -61,7 +61,7 @@ int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t le
 // decomposition and one ModDown; out must not overlap A.
 int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uint64_t* gals, uint32_t nrot,
                  CtBatch out, Arena& ar);
-size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count, uint32_t nrot);
+size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count);
 int mul_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int add_int_batch(he_ctx* c, CtBatch A, CtBatch O, int64_t k, uint32_t level, uint32_t count);
 int copy_batch(he_ctx* c, CtBatch A, CtBatch O, uint32_t level, uint32_t count);

@@ -76,15 +76,13 @@ bool ks_rot_fits(const he_ctx* c, uint32_t level) {
   return smem <= kRotSmemMax;
 }
 
-// ModUp -> NTT -> the inner products of every rotation of a hoisted
-// rotate-and-sum, fused; rotation r's accumulators at acc + r*acc_rstride,
-// or (*nacc = 1) all rotations summed in the first when each rotation maps
-// the kernel's row tiles onto themselves.
+// ModUp -> NTT -> the summed inner products of every rotation of a hoisted
+// rotate-and-sum, fused, into one accumulator; *unreduced when it holds sums
+// of rs.n residues (the rotations moved rows between CTAs).
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled,
-           uint32_t* nacc) {
+           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced) {
   *handled = false;
-  *nacc = rs.n;
+  *unreduced = false;
   if (!ks_rot_fits(c, level)) return HE_OK;
   KsRotArgs ra;
   ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
@@ -97,7 +95,6 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
   for (uint32_t u = 0; u < (uint32_t)c->alpha; ++u) bits = std::max(bits, (uint32_t)(64 - __builtin_clzll(c->q[c->L + u])));
   const uint32_t nprod = rs.n * ((level + (uint32_t)c->alpha - 1) / (uint32_t)c->alpha);
   ra.closed = 2 * bits + (32 - __builtin_clz(nprod)) <= 128 ? 1 : 0;
-  ra.acc_rstride = acc_rstride;
   for (uint32_t r = 0; r < rs.n; ++r) {
     ra.gal[r] = rs.gal[r];
     ra.gal_inv[r] = gal_inverse(rs.gal[r], c->log_n);
@@ -111,7 +108,7 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
     case 15: rc = ks_rot_n15(c, ra, count, handled, &closed); break;
     default: rc = ks_rot_n16(c, ra, count, handled, &closed); break;
   }
-  if (*handled && closed) *nacc = 1;
+  *unreduced = *handled && !closed;
   return rc;
 }
 
@@ -124,17 +121,14 @@ namespace he {
 // compiled shapes (the same ones as the NTT and ModUp).
 static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);
 
-int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t nsum, uint64_t sum_stride,
-                 uint64_t* conv, CtBatch add, int add_mode, const uint64_t* gals, uint32_t n_gal, CtBatch out,
-                 uint32_t level, uint32_t count, bool* handled) {
+int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
+                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
   *handled = false;
   if (!ks_fusable(c) || n_gal > HE_MAX_ROT) return HE_OK;
   const uint32_t nt = level + (uint32_t)c->alpha;
   MdArgs a;
   a.n_gal = n_gal;
   for (uint32_t g = 0; g < n_gal; ++g) a.gal[g] = gals[g];
-  a.nsum = nsum;
-  a.sum_stride = sum_stride;
   a.yP = acc + (size_t)level * c->n;
   a.yp_stride = acc_stride;
   a.yp_pstride = (uint64_t)nt * c->n;
@@ -155,8 +149,8 @@ int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t n
 
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
-  return md_fused_sum(c, acc, acc_stride, 1, 0, conv, add, add_mode, &add_gal, add_gal ? 1 : 0, out, level, count,
-                      handled);
+  return md_fused_gals(c, acc, acc_stride, conv, add, add_mode, &add_gal, add_gal ? 1 : 0, out, level, count,
+                       handled);
 }
 
 // Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
@@ -168,8 +162,6 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
   const uint32_t lt = level - 1;
   MdArgs a;
   a.n_gal = 0;
-  a.nsum = 1;
-  a.sum_stride = 0;
   a.yP = last;
   a.yp_stride = 2ull * c->n;
   a.yp_pstride = c->n;

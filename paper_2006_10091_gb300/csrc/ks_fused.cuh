@@ -318,12 +318,14 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(Ks
 // index modulo N/M, and X -> X^gal maps residue classes onto residue
 // classes.  So the CTA that holds input row c after the row pass can write
 // the whole of output row c' = src_{gal^-1}(c M) / M with coalesced stores and
-// key loads, reading its sources from shared memory.
+// key loads, reading its sources from shared memory.  When every rotation
+// maps each CTA's rows onto themselves, a thread sums all rotations for its
+// own positions; otherwise each rotation's row is added atomically to the
+// one accumulator (64-bit sums of at most 16 residues below 2^60).
 struct KsRotArgs {
-  KsFusedArgs k;           // k.acc: the accumulators of rotation 0
+  KsFusedArgs k;           // k.acc: the accumulator (summed over the rotations)
   uint32_t nrot, count;
-  int closed;              // every rotation maps each tile's rows onto themselves: one summed accumulator
-  uint64_t acc_rstride;    // words between the accumulators of consecutive rotations
+  int closed;              // every rotation maps each tile's rows onto themselves
   uint64_t gal[HE_MAX_ROT], gal_inv[HE_MAX_ROT];
   const uint64_t* evk[HE_MAX_ROT];
 };
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   }
   for (uint32_t r = 0; r < ra.nrot; ++r) {
     const uint64_t* ev = ra.evk[r];
-    uint64_t* o0 = a.acc + (size_t)r * ra.acc_rstride + ((size_t)i * 2 * a.nt + t) * N;
+    uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
     uint64_t* o1 = o0 + (size_t)a.nt * N;
 #pragma unroll 1
     for (int u0 = 0; u0 < PER; u0 += GRP) {
@@ -454,10 +456,14 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
           mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
         }
       }
+      // other CTAs add the other rotations' products to these rows: the
+      // accumulator (zeroed first) holds sums of nrot residues
 #pragma unroll
       for (int u = 0; u < GRP; ++u) {
-        o0[eo[u]] = reduce128_any(a0h[u], a0l[u], pr);
-        o1[eo[u]] = reduce128_any(a1h[u], a1l[u], pr);
+        atomicAdd(reinterpret_cast<unsigned long long*>(o0 + eo[u]),
+                  (unsigned long long)reduce128_any(a0h[u], a0l[u], pr));
+        atomicAdd(reinterpret_cast<unsigned long long*>(o1 + eo[u]),
+                  (unsigned long long)reduce128_any(a1h[u], a1l[u], pr));
       }
     }
   }
@@ -476,8 +482,6 @@ struct MdArgs {
   const uint64_t* yP;
   uint64_t yp_stride, yp_pstride;
   CtBatch accq;         // the Q part (evaluation form), limbs 0 .. level-1
-  uint32_t nsum;        // accq is the sum of nsum accumulators, sum_stride words apart
-  uint64_t sum_stride;
   uint64_t* conv;       // count x [2][level][N]: column-pass outputs
   CtBatch add, out;
   int has_add;          // 0 none, 1 part 0 only, 2 both parts, 3 permuted on part 0 plus plain on both
@@ -593,9 +597,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = threadIdx.x + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      uint64_t x = __ldg(accq + e);
-      for (uint32_t s = 1; s < a.nsum; ++s) x = add_mod(x, __ldg(accq + s * a.sum_stride + e), q);
-      av[u] = x;
+      av[u] = __ldg(accq + e);
       uint64_t d = add_plain ? __ldg(ad + e) : 0;
       if (add_perm)
         for (uint32_t g = 0; g < a.n_gal; ++g) d = add_mod(d, __ldg(ad + automorph_src(e, a.gal[g], LOG_N)), q);
@@ -792,6 +794,8 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits
     for (uint32_t r = 0; r < ra.nrot; ++r) rc.closed &= rot_closed<LOG_N, M2, K2 - 1>(ra.gal_inv[r]) ? 1 : 0;
     *closed_out = rc.closed;
+    if (!rc.closed)
+      HE_CUDA(cudaMemsetAsync(ra.k.acc, 0, sizeof(uint64_t) * count * 2 * a.nt * (1u << LOG_N), c->stream));
     ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(rc);
   }
   HE_CUDA(cudaGetLastError());

@@ -9,9 +9,8 @@
 // polynomial.  After the polynomial, the sum of the rotations by o < g
 // collects the per-feature sum on slots = 0 mod g, a 0/1 mask keeps those,
 // and the sum of the rotations by -o copies it back to all g slots.  Each
-// rotate-and-sum runs in hoisted stages of three rotations (rotsum_batch;
-// offsets s, 2s, 3s, then s <- 4s) and one of a single rotation when its
-// number of doublings is odd.
+// rotate-and-sum runs in hoisted stages (rotsum_batch) of up to fifteen
+// rotations (rotsum_stages).
 //
 // Op sequence and scale plan (doubles, same order as the CPU oracle; l0 the
 // input level, q[i] the limb primes):
@@ -142,9 +141,9 @@ static size_t lr_ct_words(const he_ctx* c, uint32_t l0) {
 // part over `chunk` ciphertexts and those of the finish over `ns` sums.
 static size_t lr_op_words(const he_ctx* c, uint32_t l0, uint32_t chunk, uint32_t ns) {
   size_t w = mul_words(c, l0, chunk, true);
-  w = std::max(w, rotsum_words(c, l0 - 1, chunk, 3));
+  w = std::max(w, rotsum_words(c, l0 - 1, chunk));
   w = std::max(w, rescale_words(c, l0 - 1, chunk));
-  w = std::max(w, rotsum_words(c, l0 - 4, ns, 3));
+  w = std::max(w, rotsum_words(c, l0 - 4, ns));
   w = std::max(w, ks_words(c, l0 - 3, ns) + (size_t)ns * 2 * (l0 - 3) * c->n + rescale_words(c, l0 - 3, ns) + 64);
   w = std::max(w, rescale_words(c, l0 - 4, ns) + (size_t)ns * 2 * (l0 - 4) * c->n);
   return w + 64;
@@ -156,17 +155,24 @@ struct LrGal {
 };
 
 // The stages of a rotate-and-sum over offsets 0, step, ..., (2^count - 1) step:
-// while two or more doublings remain, rotations by s, 2s, 3s in one hoisted
-// stage (then s <- 4s); a last stage with the rotation by s when count is odd.
+// stages of three doublings (rotations by s, 2s, ..., 7s in one hoisted
+// stage, then s <- 8s), the first of four when count = 1 mod 3 and a last
+// one of two when count = 2 mod 3 (every stage pays one ModUp and one
+// ModDown, each rotation one inner product).
 static void rotsum_stages(int log_n, int32_t step, uint32_t count, std::vector<std::vector<uint64_t>>* out) {
+  std::vector<uint32_t> sizes(count / 3, 3);
+  if (count % 3 == 1) {
+    if (sizes.empty()) sizes.push_back(1);
+    else sizes[0] = 4;
+  } else if (count % 3 == 2) {
+    sizes.push_back(2);
+  }
   int32_t s = step;
-  while (count > 0) {
-    const uint32_t ns = count >= 2 ? 3 : 1;
+  for (uint32_t k : sizes) {
     std::vector<uint64_t> st;
-    for (uint32_t m = 1; m <= ns; ++m) st.push_back(h_galois_elt(log_n, s * (int32_t)m));
+    for (int32_t m = 1; m < (1 << k); ++m) st.push_back(h_galois_elt(log_n, s * m));
     out->push_back(st);
-    s *= (int32_t)ns + 1;
-    count -= ns == 3 ? 2 : 1;
+    s *= 1 << k;
   }
 }
 

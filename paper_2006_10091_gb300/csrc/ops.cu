@@ -25,11 +25,9 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
              uint32_t count, bool* handled);
 bool ks_rot_fits(const he_ctx* c, uint32_t level);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           uint64_t acc_rstride, const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled,
-           uint32_t* nacc);
-int md_fused_sum(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint32_t nsum, uint64_t sum_stride,
-                 uint64_t* conv, CtBatch add, int add_mode, const uint64_t* gals, uint32_t n_gal, CtBatch out,
-                 uint32_t level, uint32_t count, bool* handled);
+           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced);
+int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
+                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -275,7 +273,7 @@ int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t 
 // out must not overlap A.
 int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uint64_t* gals, uint32_t nrot,
                  CtBatch out, Arena& ar) {
-  if (nrot < 1 || nrot > HE_MAX_ROT) return fail(HE_EINVAL, "rotate-and-sum: 1 to 8 rotations per stage");
+  if (nrot < 1 || nrot > HE_MAX_ROT) return fail(HE_EINVAL, "rotate-and-sum: 1 to 16 rotations per stage");
   RotSet rs;
   rs.n = nrot;
   for (uint32_t r = 0; r < nrot; ++r) {
@@ -291,10 +289,10 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
   const char* o_lo = (const char*)out.base;
   const char* o_hi = o_lo + sizeof(uint64_t) * ((size_t)(count - 1) * out.stride + (size_t)2 * out.cap * n);
   if (!(o_hi <= a_lo || a_hi <= o_lo)) return fail(HE_EINVAL, "rotate-and-sum: output overlaps the input");
-  const uint64_t acc_stride = (uint64_t)2 * nt * n, rstride = (uint64_t)count * acc_stride;
+  const uint64_t acc_stride = (uint64_t)2 * nt * n;
   uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
   uint64_t* ext = ar.take<uint64_t>((size_t)count * beta * nt * n);
-  uint64_t* acc = ar.take<uint64_t>((size_t)nrot * rstride);
+  uint64_t* acc = ar.take<uint64_t>((size_t)count * acc_stride);
   uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
   const uint64_t* d = A.base + (size_t)A.cap * n;
@@ -304,38 +302,32 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     const PolyBatch b = pb(d, d2c, A.stride, (size_t)level * n, count, level, 0, level);
     HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
   }
-  bool fused = false;
-  uint32_t nacc = nrot;  // accumulators to sum (1 when the fused kernel summed the rotations)
-  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rstride, rs, level, count, half, &fused, &nacc));
+  bool fused = false, unreduced = false;
+  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rs, level, count, half, &fused, &unreduced));
   if (!fused) {
     if (half) return fail(HE_ECUDA, "rotate-and-sum: fused kernels declined a half-transformed input");
     HE_TRY(modup_unfused(c, d2c, ext, level, count));
     {
       ProfScope prof(c, "inner_product", 2.0 * nrot * count * beta * nt * n,
-                     (double)n * 8 * ((double)count * beta * nt * (1 + 2.0 * nrot) + 2.0 * nrot * count * nt));
-      k_inner_product_rot<<<grid_for((size_t)nrot * count * nt * n), 256, 0, c->stream>>>(
-          ext, (size_t)beta * nt * n, d, A.stride, rs, acc, acc_stride, rstride, level, alpha, beta, L, np, count,
-          c->log_n, c->d_primes);
+                     (double)n * 8 * ((double)count * beta * nt * (1 + 2.0 * nrot) + 2.0 * count * nt));
+      k_inner_product_rot<<<grid_for((size_t)count * nt * n), 256, 0, c->stream>>>(
+          ext, (size_t)beta * nt * n, d, A.stride, rs, acc, acc_stride, level, alpha, beta, L, np, count, c->log_n,
+          c->d_primes);
     }
     HE_CUDA(cudaGetLastError());
   }
-  // the P limbs of all rotations' accumulators summed, to coefficient form
-  if (nacc > 1) {
-    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * alpha * n * 8 * (nacc + 1));
-    k_sum_acc<<<grid_for((size_t)count * 2 * alpha * n), 256, 0, c->stream>>>(
-        acc, acc_stride, rstride, nacc, level, nt, nt, level, L, count, c->log_n, c->d_primes);
-  }
-  HE_CUDA(cudaGetLastError());
-  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
-                           count * 2, alpha, level, level)));
-  bool md_done = false;  // the Q limbs are summed as the combine reads them
-  HE_TRY(md_fused_sum(c, acc, acc_stride, nacc, rstride, conv, A, 3, gals, nrot, out, level, count, &md_done));
-  if (md_done) return HE_OK;
-  if (nacc > 1) {
-    k_sum_acc<<<grid_for((size_t)count * 2 * level * n), 256, 0, c->stream>>>(
-        acc, acc_stride, rstride, nacc, 0, level, nt, level, L, count, c->log_n, c->d_primes);
+  if (unreduced) {  // sums of nrot residues from the rows the rotations moved between CTAs
+    ProfScope prof(c, "elementwise", 0.0, (double)count * 2 * nt * n * 16);
+    k_reduce_acc<<<grid_for((size_t)count * 2 * nt * n), 256, 0, c->stream>>>(acc, acc_stride, nt, level, L, count,
+                                                                              c->log_n, c->d_primes);
     HE_CUDA(cudaGetLastError());
   }
+  // ModDown of the summed inner products, plus A0 + sum_r kappa_r(A0) and A1
+  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
+                           count * 2, alpha, level, level)));
+  bool md_done = false;
+  HE_TRY(md_fused_gals(c, acc, acc_stride, conv, A, 3, gals, nrot, out, level, count, &md_done));
+  if (md_done) return HE_OK;
   uint64_t* sa = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!sa) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
   const CtBatch S{sa, (uint64_t)2 * level * n, level, 0};
@@ -345,9 +337,9 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
   return moddown_unfused(c, acc, conv, S, 2, out, level, count);
 }
 
-size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count, uint32_t nrot) {
+size_t rotsum_words(const he_ctx* c, uint32_t level, uint32_t count) {
   const size_t n = c->n, a = c->alpha, beta = (level + a - 1) / a, nt = level + a;
-  return count * n * (level + beta * nt + 2 * nt * nrot + 2 * level + 2 * level) + 6 * 32;
+  return count * n * (level + beta * nt + 2 * nt + 2 * level + 2 * level) + 6 * 32;
 }
 
 int addsub_batch(he_ctx* c, CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level, uint32_t count) {

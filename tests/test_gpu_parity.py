@@ -587,7 +587,7 @@ def test_rotate_sum_batch_and_errors(hoist, he):
     for i in range(count):
         want = hoist.o.rotate_sum(hoist.orc_enc(ms[i], level, cid=950 + i), [1, 2, 3])
         assert_same_residues(O[i], want, he, hoist.g)
-    for steps, code in (([7], he.HE_ENOKEY), ([1, 0], he.HE_EINVAL), ([1] * 9, he.HE_EINVAL)):
+    for steps, code in (([7], he.HE_ENOKEY), ([1, 0], he.HE_EINVAL), ([1] * 17, he.HE_EINVAL)):
         with pytest.raises(he.HeError) as e:
             he.he_rotate_sum(hoist.g, A[0], steps, O[0])
         assert e.value.code == code
