@@ -382,44 +382,54 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   const uint32_t row0 = (uint32_t)tile << LOG_K;
   constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
   if (ra.closed) {
-    // each thread sums every rotation's products for its own positions
+    // each thread sums every rotation's products for its own positions, two
+    // neighbouring positions at a time (16-byte key loads and stores)
     uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
     uint64_t* o1 = o0 + (size_t)a.nt * N;
+    constexpr int PAIRS = GRP / 2;
 #pragma unroll 1
-    for (int u0 = 0; u0 < PER; u0 += GRP) {
-      uint32_t eo[GRP];
+    for (int v0 = 0; v0 < PER / 2; v0 += PAIRS) {
+      uint32_t eo[PAIRS];  // first of the two positions (even)
       uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
 #pragma unroll
-      for (int u = 0; u < GRP; ++u) {
-        const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
-        eo[u] = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-        a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
+      for (int v = 0; v < PAIRS; ++v) {
+        const uint32_t idx = 2 * (threadIdx.x + (v0 + v) * S::T);
+        eo[v] = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       }
+#pragma unroll
+      for (int u = 0; u < GRP; ++u) a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
       for (uint32_t r = 0; r < ra.nrot; ++r) {
         uint32_t so[GRP];
 #pragma unroll
         for (int u = 0; u < GRP; ++u) {
-          const uint32_t p = automorph_src(eo[u], ra.gal[r], LOG_N);
+          const uint32_t p = automorph_src(eo[u >> 1] + (u & 1), ra.gal[r], LOG_N);
           const uint32_t sl = (((p >> LOG_M) - row0) << LOG_M) | (p & (S::M - 1));
           so[u] = sl + (sl >> 3);
         }
         const uint64_t* ev = ra.evk[r];
+#pragma unroll 2
         for (uint32_t j = 0; j < a.beta; ++j) {
           const uint64_t* sm = dig + (size_t)j * TW;
           const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
           const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
 #pragma unroll
-          for (int u = 0; u < GRP; ++u) {
-            const uint64_t x = sm[so[u]];
-            mac128(a0l[u], a0h[u], x, __ldg(kb + eo[u]));
-            mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
+          for (int v = 0; v < PAIRS; ++v) {
+            const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(kb + eo[v]));
+            const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(ka + eo[v]));
+            const uint64_t x0 = sm[so[2 * v]], x1 = sm[so[2 * v + 1]];
+            mac128(a0l[2 * v], a0h[2 * v], x0, wb.x);
+            mac128(a0l[2 * v + 1], a0h[2 * v + 1], x1, wb.y);
+            mac128(a1l[2 * v], a1h[2 * v], x0, wa.x);
+            mac128(a1l[2 * v + 1], a1h[2 * v + 1], x1, wa.y);
           }
         }
       }
 #pragma unroll
-      for (int u = 0; u < GRP; ++u) {
-        o0[eo[u]] = reduce128_any(a0h[u], a0l[u], pr);
-        o1[eo[u]] = reduce128_any(a1h[u], a1l[u], pr);
+      for (int v = 0; v < PAIRS; ++v) {
+        *reinterpret_cast<ulonglong2*>(o0 + eo[v]) =
+            make_ulonglong2(reduce128_any(a0h[2 * v], a0l[2 * v], pr), reduce128_any(a0h[2 * v + 1], a0l[2 * v + 1], pr));
+        *reinterpret_cast<ulonglong2*>(o1 + eo[v]) =
+            make_ulonglong2(reduce128_any(a1h[2 * v], a1l[2 * v], pr), reduce128_any(a1h[2 * v + 1], a1l[2 * v + 1], pr));
       }
     }
     return;
