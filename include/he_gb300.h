@@ -58,7 +58,7 @@ typedef struct he_params {
   uint32_t log_n;        /* N = 2^log_n, 4 <= log_n <= 16 */
   uint32_t n_limbs;      /* L: limb primes q_0..q_{L-1} */
   uint32_t limb_bits;
-  uint32_t n_special;    /* alpha: special primes (key-switching digit size) */
+  uint32_t n_special;    /* alpha: special primes (key-switching digit size), 1 .. 7 */
   uint32_t special_bits;
   uint32_t dnum;         /* 0, or must equal ceil(L / alpha) */
   double scale;

@@ -991,8 +991,11 @@ static void moddown_pair(orc_ctx* c, const uint64_t* acc, int level, uint64_t* k
  * out = round(acc / P): Conv(y) - h is the centered residue of acc mod P.  An
  * approximate conversion would add v P, 0 <= v < alpha, and so a one-sided
  * error of -v on every coefficient, the same drift as flooring. */
-static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key,
-                      uint64_t* k0, uint64_t* k1) {
+/* The inner products of a key switch before its ModDown: acc [2][level +
+ * alpha][N] (evaluation form over Q_level and P, zeroed by the caller) +=
+ * sum_j ModUp_j(d) * key_j.  Used by keyswitch below and, with the ModDown
+ * merged into the rescale, by the multiplication. */
+static void ks_inner(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key, uint64_t* acc) {
   uint32_t n = c->n;
   int nt = level + c->alpha; /* target primes: limbs 0..level-1, specials L..L+alpha-1 */
   int beta_l = (level + c->alpha - 1) / c->alpha;
@@ -1001,7 +1004,6 @@ static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* 
     memcpy(POLY(dc, t, n), POLY(d, t, n), sizeof(uint64_t) * n);
     intt_limb(c, t, POLY(dc, t, n));
   }
-  uint64_t* acc = calloc((size_t)2 * nt * n, sizeof(uint64_t)); /* [2][nt][N] */
   uint64_t* ext = malloc(sizeof(uint64_t) * n);
   for (int j = 0; j < beta_l; j++) {
     for (int ti = 0; ti < nt; ti++) {
@@ -1023,8 +1025,93 @@ static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* 
       }
     }
   }
+  free(dc); free(ext);
+}
+
+static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key,
+                      uint64_t* k0, uint64_t* k1) {
+  uint64_t* acc = calloc((size_t)2 * (level + c->alpha) * c->n, sizeof(uint64_t)); /* [2][nt][N] */
+  ks_inner(c, d, level, key, acc);
   moddown_pair(c, acc, level, k0, k1);
-  free(dc); free(acc); free(ext);
+  free(acc);
+}
+
+/* Exact conversion from k primes pr[0..k) to modulus m of coefficient
+ * residues y [k][N]: the integer Y in [0, prod pr) with Y = y_u mod pr[u]
+ * (Garner's mixed-radix digits), reduced mod m. */
+static void conv_exact(const uint64_t* y, const uint64_t* pr, int k, uint32_t n, uint64_t m, uint64_t* out) {
+  for (uint32_t i = 0; i < n; i++) {
+    uint64_t dg[ORC_MAX_PRIMES];
+    for (int u = 0; u < k; u++) {
+      uint64_t pu = pr[u], acc = 0, prod = 1 % pu;
+      for (int v = 0; v < u; v++) {
+        acc = addmod(acc, mulmod(dg[v] % pu, prod, pu), pu);
+        prod = mulmod(prod, pr[v] % pu, pu);
+      }
+      dg[u] = mulmod(submod(y[(size_t)u * n + i] % pu, acc, pu), invmod(prod, pu), pu);
+    }
+    bn Y;
+    memset(&Y, 0, sizeof Y);
+    for (int u = k - 1; u >= 0; u--) bn_mul_small_add(&Y, pr[u], dg[u]);
+    out[i] = bn_mod_small(&Y, m);
+  }
+}
+
+/* The ModDown of a relinearisation merged with the rescale that follows it
+ * [ext]: one division with rounding by P q_{level-1} of
+ *   V = P (d0, d1) + acc     over Q_level * P
+ * (acc [2][level + alpha][N] the key switch's inner products, d01
+ * [2][level][N] the tensor's first two parts, both evaluation form), instead
+ * of dividing acc by P, adding d and dividing by q_{level-1}.  V's residues
+ * on the dropped primes are acc's on p_k (P d vanishes there) and
+ * acc_{level-1} + P d_{level-1} on q_{level-1}; with Y their exact lift plus
+ * h = (P q_{level-1} - 1)/2 (coefficient form),
+ *   out_t = (V_t - NTT_t(Y mod q_t - h)) * (P q_{level-1})^-1   (t < level-1),
+ * i.e. out = round(V / (P q_{level-1})).  out [2][level-1][N]. */
+static void moddown_rescale_pair(orc_ctx* c, const uint64_t* acc, const uint64_t* d01, int level, uint64_t* out) {
+  uint32_t n = c->n;
+  int a = c->alpha, nt = level + a, l = level - 1, k = a + 1;
+  uint64_t pr[ORC_MAX_PRIMES];
+  pr[0] = c->q[l];
+  for (int u = 0; u < a; u++) pr[1 + u] = c->q[c->L + u];
+  uint64_t* y = malloc(sizeof(uint64_t) * (size_t)k * n);
+  uint64_t* conv = malloc(sizeof(uint64_t) * n);
+  uint64_t* res = malloc(sizeof(uint64_t) * 2 * (size_t)l * n);
+  for (int p = 0; p < 2; p++) {
+    const uint64_t* ap = acc + (size_t)p * nt * n;
+    const uint64_t* dp = d01 + (size_t)p * level * n;
+    for (int u = 0; u < k; u++) {
+      uint64_t m = pr[u];
+      uint64_t* yu = POLY(y, u, n);
+      if (u == 0) {
+        uint64_t Pm = P_mod(c, m);
+        for (uint32_t i = 0; i < n; i++) yu[i] = addmod(ap[(size_t)l * n + i], mulmod(Pm, dp[(size_t)l * n + i], m), m);
+        intt_limb(c, l, yu);
+      } else {
+        memcpy(yu, POLY(ap, level + u - 1, n), sizeof(uint64_t) * n);
+        intt_limb(c, c->L + u - 1, yu);
+      }
+      /* + h mod m, h = (P q_l - 1)/2 */
+      uint64_t h = mulmod(submod(mulmod(P_mod(c, m), pr[0] % m, m), 1, m), invmod(2, m), m);
+      for (uint32_t i = 0; i < n; i++) yu[i] = addmod(yu[i], h, m);
+    }
+    for (int t = 0; t < l; t++) {
+      uint64_t q = c->q[t];
+      uint64_t Pq = mulmod(P_mod(c, q), pr[0] % q, q);
+      uint64_t ht = mulmod(submod(Pq, 1, q), invmod(2, q), q);
+      conv_exact(y, pr, k, n, q, conv);
+      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
+      ntt_limb(c, t, conv);
+      uint64_t inv = invmod(Pq, q), Pm = P_mod(c, q);
+      uint64_t* o = POLY(res, p * l + t, n);
+      for (uint32_t i = 0; i < n; i++) {
+        uint64_t v = addmod(ap[(size_t)t * n + i], mulmod(Pm, dp[(size_t)t * n + i], q), q);
+        o[i] = mulmod(submod(v, conv[i], q), inv, q);
+      }
+    }
+  }
+  memcpy(out, res, sizeof(uint64_t) * 2 * (size_t)l * n);
+  free(y); free(conv); free(res);
 }
 
 /* key_id: -1 relinearisation key, i >= 0 Galois key i (in creation order). */
@@ -1069,28 +1156,21 @@ int orc_rescale(orc_ctx* c, const uint64_t* a, int level, uint64_t* out) {
   return 0;
 }
 
-/* Relinearise a three-part ciphertext d = (d0, d1, d2) [3][level][N]: switch
- * d2 with the s^2 key and add, (d0 + k0, d1 + k1); then rescale.  out has
- * level - 1 limbs. */
+/* Relinearise a three-part ciphertext d = (d0, d1, d2) [3][level][N] and
+ * rescale: the inner products of d2 with the s^2 key, then the division of
+ * P (d0, d1) + acc by P q_{level-1} with one rounding (moddown_rescale_pair).
+ * out has level - 1 limbs. */
 static void relin_rescale(orc_ctx* c, const uint64_t* d, int level, uint64_t* out) {
-  uint32_t n = c->n;
-  uint64_t* k0 = malloc(sizeof(uint64_t) * (size_t)level * n);
-  uint64_t* k1 = malloc(sizeof(uint64_t) * (size_t)level * n);
-  uint64_t* r = malloc(sizeof(uint64_t) * 2 * (size_t)level * n);
-  keyswitch(c, POLY(d, 2 * level, n), level, c->rlk, k0, k1);
-  for (int t = 0; t < level; t++) {
-    uint64_t q = c->q[t];
-    for (uint32_t i = 0; i < n; i++) {
-      r[(size_t)t * n + i] = addmod(d[(size_t)t * n + i], k0[(size_t)t * n + i], q);
-      r[((size_t)level + t) * n + i] = addmod(d[((size_t)level + t) * n + i], k1[(size_t)t * n + i], q);
-    }
-  }
-  orc_rescale(c, r, level, out);
-  free(k0); free(k1); free(r);
+  uint64_t* acc = calloc((size_t)2 * (level + c->alpha) * c->n, sizeof(uint64_t));
+  ks_inner(c, POLY(d, 2 * level, c->n), level, c->rlk, acc);
+  moddown_rescale_pair(c, acc, d, level, out);
+  free(acc);
 }
 
-/* HMult: tensor, relinearise d2 with the s^2 key, add, rescale.  out has
- * level - 1 limbs.  scale_out = scale_a * scale_b / q[level-1]. */
+/* HMult: tensor, relinearise d2 with the s^2 key and rescale, the key
+ * switch's division by P and the rescale's by q[level-1] taken as one
+ * rounding (relin_rescale).  out has level - 1 limbs.  scale_out = scale_a *
+ * scale_b / q[level-1]. */
 int orc_mul_relin_rescale(orc_ctx* c, const uint64_t* a, const uint64_t* b, int level, uint64_t* out) {
   if (level < 2 || level > c->L) return -1;
   uint32_t n = c->n;

@@ -119,6 +119,8 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->d_rescale = base->d_rescale;
   v->d_rescale_md = base->d_rescale_md;
   v->rescale_md_words = base->rescale_md_words;
+  v->d_mdrs = base->d_mdrs;
+  v->mdrs_words = base->mdrs_words;
   v->d_garner = base->d_garner;
   v->chunk_bytes = base->chunk_bytes;
   v->lr_chunk = base->lr_chunk;
@@ -159,6 +161,7 @@ static void destroy(he_ctx* c) {
   cudaFree(c->d_moddown);
   cudaFree(c->d_rescale);
   cudaFree(c->d_rescale_md);
+  cudaFree(c->d_mdrs);
   cudaFree(c->d_garner);
   cudaFree(c->d_s);
   cudaFree(c->d_pk);
@@ -212,7 +215,7 @@ int he_ctx_create(const he_params* p, const int32_t* rot_steps, size_t n_rot, vo
   if (!p || !out) return fail(HE_EINVAL, "he_ctx_create: null argument");
   *out = nullptr;
   if (p->log_n < 4 || p->log_n > 16) return fail(HE_EINVAL, "log_n must be in [4, 16]");
-  if (p->n_limbs < 1 || p->n_special < 1 || p->n_special > HE_MAX_DIGIT ||
+  if (p->n_limbs < 1 || p->n_special < 1 || p->n_special > HE_MAX_DIGIT - 1 ||
       p->n_limbs + p->n_special > HE_MAX_PRIMES)
     return fail(HE_EINVAL, "bad limb / special prime counts");
   if (p->limb_bits < 20 || p->limb_bits > 61 || p->special_bits < 20 || p->special_bits > 61)

@@ -190,12 +190,11 @@ __global__ void k_add_automorphs(CtBatch A, CtBatch O, RotSet rs, uint32_t level
 // conv[t] = sum_k [(y_k + h) * (P/p_k)^-1]_{p_k} * ((P/p_k) mod q_t) - h mod q_t:
 // subtracting this from the accumulator divides by P with rounding (for one
 // special prime it is the centered residue of the accumulator mod P).
-__global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_t* conv,
-                               uint64_t conv_stride, uint32_t level, uint32_t alpha, uint32_t L,
-                               uint32_t count, int log_n, const PrimeDev* primes,
-                               const uint64_t* md) {
+__global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint32_t nt, MdDrop dr, uint64_t* conv,
+                               uint64_t conv_stride, uint32_t level, uint32_t L, uint32_t count, int log_n,
+                               const PrimeDev* primes, const uint64_t* md) {
   const uint32_t n = 1u << log_n;
-  const uint32_t nt = level + alpha;
+  const uint32_t alpha = dr.n;
   const size_t total = (size_t)count * 2 * n;
   const uint64_t* mat = md + 2 * alpha;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
@@ -211,8 +210,8 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
     uint64_t fs = 0;
     uint32_t v = 0;
     for (uint32_t a = 0; a < alpha; ++a) {
-      const PrimeDev& pp = primes[L + a];
-      const uint64_t y = add_mod(acc[(size_t)i * acc_stride + ((size_t)p * nt + level + a) * n + k], hP[a], pp.q);
+      const PrimeDev& pp = primes[dr.pr[a]];
+      const uint64_t y = add_mod(acc[(size_t)i * acc_stride + ((size_t)p * nt + dr.first + a) * n + k], hP[a], pp.q);
       u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], pp.q);
       if (alpha > 1) frac_acc(u[a], pp.one_sh, wlo[a], &fs, &v);
     }
@@ -229,22 +228,20 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_
 }
 
 // ---- ModDown finish: out = add + (acc_Q - conv) * P^-1 ----------------------
-// has_add: 0 no addend, 1 addend on part 0 only, 2 on both parts.
-__global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, const uint64_t* conv,
-                             uint64_t conv_stride, CtBatch add, int has_add, CtBatch out,
-                             uint32_t out_part0, uint32_t nparts, uint32_t level, uint32_t alpha,
-                             uint32_t L_, uint32_t count, int log_n, const PrimeDev* primes,
+// has_add: 0 no addend, 1 addend on part 0 only, 2 on both parts; addw (if
+// set): the addend times these Shoup pairs per limb.  acc has nt limbs per part.
+__global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, uint32_t nt, const uint64_t* conv,
+                             uint64_t conv_stride, CtBatch add, int has_add, const uint64_t* addw, CtBatch out,
+                             uint32_t level, uint32_t count, int log_n, const PrimeDev* primes,
                              const uint64_t* pinv) {
   const uint32_t n = 1u << log_n, half = n >> 1;
-  const uint32_t nt = level + alpha;
-  const size_t total = (size_t)count * nparts * level * half;
+  const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const uint32_t k = (uint32_t)(g % half) * 2;
     size_t r = g / half;
     const uint32_t t = (uint32_t)(r % level);
     r /= level;
-    const uint32_t pp = (uint32_t)(r % nparts), i = (uint32_t)(r / nparts);
-    const uint32_t p = out_part0 + pp;
+    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
     const uint64_t q = primes[t].q;
     const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
     const ulonglong2 a = *(const ulonglong2*)(acc + (size_t)i * acc_stride + ((size_t)p * nt + t) * n + k);
@@ -253,11 +250,31 @@ __global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, const uin
     o.x = mul_shoup(sub_mod(a.x, c.x, q), w, wsh, q);
     o.y = mul_shoup(sub_mod(a.y, c.y, q), w, wsh, q);
     if (has_add == 2 || (has_add == 1 && p == 0)) {
-      const ulonglong2 d = *(const ulonglong2*)(cpoly(add, i, p, t, n) + k);
+      ulonglong2 d = *(const ulonglong2*)(cpoly(add, i, p, t, n) + k);
+      if (addw) {
+        d.x = mul_shoup(d.x, addw[2 * t], addw[2 * t + 1], q);
+        d.y = mul_shoup(d.y, addw[2 * t], addw[2 * t + 1], q);
+      }
       o.x = add_mod(o.x, d.x, q);
       o.y = add_mod(o.y, d.y, q);
     }
     *(ulonglong2*)(cpoly(out, i, p, t, n) + k) = o;
+  }
+}
+
+// acc limb l (both parts) += P_l * d_l: the merged ModDown's dropped limb
+// q_l holds V = acc + P d (P d vanishes on the special primes).
+__global__ void k_add_pd(uint64_t* acc, uint64_t acc_stride, uint32_t nt, CtBatch d, uint32_t l, uint64_t Pl,
+                         uint64_t Pl_sh, uint32_t count, int log_n, const PrimeDev* primes) {
+  const uint32_t n = 1u << log_n;
+  const size_t total = (size_t)count * 2 * n;
+  const uint64_t q = primes[l].q;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(g % n);
+    const size_t r = g / n;
+    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    uint64_t* a = acc + (size_t)i * acc_stride + ((size_t)p * nt + l) * n + k;
+    *a = add_mod(*a, mul_shoup(cpoly(d, i, p, l, n)[k], Pl, Pl_sh, q), q);
   }
 }
 

@@ -87,6 +87,8 @@ struct he_ctx {
   uint64_t* d_rescale = nullptr;
   uint64_t* d_rescale_md = nullptr;  // per dropped limb l: the ModDown tables with q_l as the one special prime
   size_t rescale_md_words = 0;       // words per l
+  uint64_t* d_mdrs = nullptr;        // per level l: the ModDown tables dividing by P q_{l-1} (ModDown + rescale)
+  size_t mdrs_words = 0;             // words per l
   // Garner (decryption CRT): [L] Shoup pairs of (q_0..q_{i-1})^-1 mod q_i, then
   // [L][L] prefix products (q_0..q_{i'-1}) mod q_i
   uint64_t* d_garner = nullptr;

@@ -57,15 +57,21 @@ __global__ void k_reduce_acc(uint64_t* acc, uint64_t acc_stride, uint32_t nt, ui
                              uint32_t count, int log_n, const PrimeDev* primes);
 __global__ void k_add_automorphs(CtBatch A, CtBatch O, RotSet rs, uint32_t level, uint32_t count, int log_n,
                                  const PrimeDev* primes);
-__global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint64_t* conv,
-                               uint64_t conv_stride, uint32_t level, uint32_t alpha, uint32_t L,
-                               uint32_t count, int log_n, const PrimeDev* primes,
-                               const uint64_t* md);
-__global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, const uint64_t* conv,
-                             uint64_t conv_stride, CtBatch add, int has_add, CtBatch out,
-                             uint32_t out_part0, uint32_t nparts, uint32_t level, uint32_t alpha,
-                             uint32_t L_, uint32_t count, int log_n, const PrimeDev* primes,
+// The dropped limbs of a ModDown: n limbs of acc starting at limb `first`,
+// over the primes pr[0 .. n).
+struct MdDrop {
+  uint32_t n, first;
+  uint32_t pr[HE_MAX_DIGIT];
+};
+__global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint32_t nt, MdDrop dr, uint64_t* conv,
+                               uint64_t conv_stride, uint32_t level, uint32_t L, uint32_t count, int log_n,
+                               const PrimeDev* primes, const uint64_t* md);
+__global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, uint32_t nt, const uint64_t* conv,
+                             uint64_t conv_stride, CtBatch add, int has_add, const uint64_t* addw, CtBatch out,
+                             uint32_t level, uint32_t count, int log_n, const PrimeDev* primes,
                              const uint64_t* pinv);
+__global__ void k_add_pd(uint64_t* acc, uint64_t acc_stride, uint32_t nt, CtBatch d, uint32_t l, uint64_t Pl,
+                         uint64_t Pl_sh, uint32_t count, int log_n, const PrimeDev* primes);
 __global__ void k_rescale_corr(const uint64_t* last, uint64_t* corr, uint32_t level, uint32_t count,
                                int log_n, const PrimeDev* primes);
 __global__ void k_rescale_final(CtBatch in, const uint64_t* corr, CtBatch out, uint32_t level,

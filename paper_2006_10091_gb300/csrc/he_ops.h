@@ -47,8 +47,12 @@ size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count);
 // (out = add + rotate(add) for a rotation of add).  gal != 0:
 // d and the addend are read through the automorphism X -> X^gal (fused
 // kernels only; the output must not overlap them).
+// merged: divide P * add + (the inner products) by P q_{level-1} with one
+// rounding (the ModDown and the rescale of a multiplication; add_mode 2, add
+// = (d0, d1), out has level - 1 limbs).
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
-                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal = 0);
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal = 0,
+                    bool merged = false);
 // Whether N has compiled shapes for the fused key-switching kernels.
 inline bool ks_fusable(const he_ctx* c) { return !c->ntt_generic && c->log_n >= 12 && c->log_n <= 16; }
 int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch out, Arena& ar);

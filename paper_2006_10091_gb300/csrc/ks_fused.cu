@@ -62,8 +62,13 @@ static uint64_t gal_inverse(uint64_t gal, int log_n) {
   return x & ((2ull << log_n) - 1);
 }
 
-bool ks_rot_fits(const he_ctx* c, uint32_t level) {
+bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot) {
   if (!ks_fusable(c)) return false;
+  // rows moved between CTAs are summed as nrot unreduced residues in 64 bits
+  uint64_t qmax = 0;
+  for (uint32_t t = 0; t < level; ++t) qmax = std::max(qmax, c->q[t]);
+  for (uint32_t u = 0; u < (uint32_t)c->alpha; ++u) qmax = std::max(qmax, c->q[c->L + u]);
+  if (qmax > ~0ull / nrot) return false;
   const uint32_t beta = (level + (uint32_t)c->alpha - 1) / (uint32_t)c->alpha;
   size_t smem = 0;
   switch (c->log_n) {
@@ -83,7 +88,7 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
            const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced) {
   *handled = false;
   *unreduced = false;
-  if (!ks_rot_fits(c, level)) return HE_OK;
+  if (!ks_rot_fits(c, level, rs.n)) return HE_OK;
   KsRotArgs ra;
   ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
   ra.nrot = rs.n;
@@ -133,7 +138,9 @@ int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t*
   a.yp_stride = acc_stride;
   a.yp_pstride = (uint64_t)nt * c->n;
   a.accq = CtBatch{const_cast<uint64_t*>(acc), acc_stride, nt, 0};
-  a.sp0 = (uint32_t)c->L;
+  for (uint32_t u = 0; u < (uint32_t)c->alpha; ++u) a.spr[u] = (uint32_t)c->L + u;
+  a.kind = 0;
+  a.addw = nullptr;
   a.conv = conv;
   a.add = add;
   a.out = out;
@@ -153,6 +160,39 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
                        handled);
 }
 
+// The ModDown of a multiplication's relinearisation merged with its rescale:
+// acc's limbs level-1 .. level+alpha-1 (q_{level-1}, then the special primes;
+// q_{level-1}'s already holds acc + P d) in coefficient form are converted
+// to the level-1 remaining limbs, and out_t = (acc_t - NTT(conv_t)) (P q_{level-1})^-1
+// + d_t q_{level-1}^-1 (the addend d on both parts).
+int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, CtBatch out,
+                     uint32_t level, uint32_t count, bool* handled) {
+  *handled = false;
+  if (!ks_fusable(c) || !c->d_mdrs || level < 2) return HE_OK;
+  const uint32_t nt = level + (uint32_t)c->alpha, lo = level - 1;
+  MdArgs a;
+  a.n_gal = 0;
+  a.yP = acc + (size_t)lo * c->n;
+  a.yp_stride = acc_stride;
+  a.yp_pstride = (uint64_t)nt * c->n;
+  a.accq = CtBatch{const_cast<uint64_t*>(acc), acc_stride, nt, 0};
+  a.spr[0] = lo;
+  for (uint32_t u = 0; u < (uint32_t)c->alpha; ++u) a.spr[1 + u] = (uint32_t)c->L + u;
+  a.kind = 2;
+  a.addw = c->d_rescale + (size_t)lo * c->L * 2;
+  a.conv = conv;
+  a.add = add;
+  a.out = out;
+  a.has_add = 2;
+  a.level = lo;
+  a.alpha = (uint32_t)c->alpha + 1;
+  a.L = (uint32_t)c->L;
+  a.primes = c->d_primes;
+  a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.md = c->d_mdrs + (size_t)level * c->mdrs_words;
+  return md_dispatch(c, a, count, handled);
+}
+
 // Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
 // last: the dropped limb of both parts in coefficient form, count x [2][N].
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
@@ -166,7 +206,9 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
   a.yp_stride = 2ull * c->n;
   a.yp_pstride = c->n;
   a.accq = in;
-  a.sp0 = lt;
+  a.spr[0] = lt;
+  a.kind = 1;
+  a.addw = nullptr;
   a.conv = conv;
   a.add = out;
   a.out = out;

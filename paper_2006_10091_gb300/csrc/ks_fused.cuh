@@ -498,7 +498,10 @@ struct MdArgs {
   uint32_t n_gal;       // part 0 of the addend is added through each automorphism X -> X^gal[g]
   uint64_t gal[HE_MAX_ROT];
   uint32_t level, alpha, L;
-  uint32_t sp0;         // prime index of the first special prime (L; l for a rescale by q_l)
+  uint32_t spr[HE_MAX_DIGIT];  // prime indices of the alpha dropped limbs (the special primes; q_l for a
+                               // rescale by q_l; q_{l-1} and the special primes for a ModDown merged with it)
+  int kind;                    // 0 ModDown, 1 rescale, 2 ModDown merged with the rescale (profile names)
+  const uint64_t* addw;        // the addend is multiplied by these Shoup pairs per target limb (nullptr: not)
   const PrimeDev* primes;
   const ulonglong2* tw;
   const uint64_t* md;   // ModDown tables (params.cu)
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     uint64_t fs = 0;
     uint32_t v = 0;
     for (uint32_t u = 0; u < a.alpha; ++u) {
-      const PrimeDev& pp = a.primes[a.sp0 + u];
+      const PrimeDev& pp = a.primes[a.spr[u]];
       const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pp.q);
       const uint64_t w = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
       wv[(size_t)u * S::TILE + idx] = w;
@@ -586,6 +589,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
   const bool lazy = q < (1ull << 58);
   const uint64_t* pinv = a.md + 2 * a.alpha + (size_t)a.alpha * a.L;
   const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
+  const uint64_t dw = a.addw ? a.addw[2 * t] : 1, dwsh = a.addw ? a.addw[2 * t + 1] : 0;
   stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)t * N, tile);
   constexpr int PER = S::TILE / S::T;
   for (uint32_t p = 0; p < 2; ++p) {
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
       const uint64_t v = sm[idx + (idx >> 3)];
       const uint64_t cv = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
       uint64_t r = mul_shoup(sub_mod(av[u], cv, q), w, wsh, q);
-      if (add) r = add_mod(r, dv[u], q);
+      if (add) r = add_mod(r, a.addw ? mul_shoup(dv[u], dw, dwsh, q) : dv[u], q);
       o[e] = r;
     }
   }
@@ -651,10 +655,12 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   }
   const double n = (double)(1u << LOG_N);
   const double polys = 2.0 * count * a.level;  // transformed limbs
-  const bool rescale = a.sp0 != a.L;
+  const char* nm_col = a.kind == 1 ? "rescale_ntt" : a.kind == 2 ? "moddown_rescale_ntt" : "moddown_ntt";
+  const char* nm_row = a.kind == 1 ? "rescale_ntt_final" : a.kind == 2 ? "moddown_rescale_ntt_combine"
+                                                                       : "moddown_ntt_combine";
   {
     const size_t blocks = (size_t)count * 2 * SC::TILES;
-    ProfScope prof(c, rescale ? "rescale_ntt" : "moddown_ntt", polys * (n / 2 * M1 + n * a.alpha),
+    ProfScope prof(c, nm_col, polys * (n / 2 * M1 + n * a.alpha),
                    n * 8 * (2.0 * count * a.alpha + polys));
     md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
@@ -662,7 +668,7 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   {
     const size_t blocks = (size_t)count * a.level * SR::TILES;
     const double addw = a.has_add == 3 ? 1.5 * polys : a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
-    ProfScope prof(c, rescale ? "rescale_ntt_final" : "moddown_ntt_combine", polys * (n / 2 * M2 + 2 * n),
+    ProfScope prof(c, nm_row, polys * (n / 2 * M2 + 2 * n),
                    n * 8 * (3.0 * polys + addw));
     md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
   }

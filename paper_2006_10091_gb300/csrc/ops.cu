@@ -23,11 +23,13 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
              uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
              uint32_t count, bool* handled);
-bool ks_rot_fits(const he_ctx* c, uint32_t level);
+bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
            const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced);
 int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
                   const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
+int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, CtBatch out,
+                     uint32_t level, uint32_t count, bool* handled);
 }
 
 namespace he {
@@ -125,34 +127,45 @@ static int ks_unfused_middle(he_ctx* c, const uint64_t* d, uint64_t d_stride, co
   return HE_OK;
 }
 
-// The ModDown of a key switch as separate kernels: conversion of the P limbs
-// (already in coefficient form), NTT, combine (add_mode 0 none, 1 part 0,
-// 2 both parts).
+// The ModDown of a key switch as separate kernels: conversion of the dropped
+// limbs (already in coefficient form), NTT, combine (add_mode 0 none, 1 part
+// 0, 2 both parts; addw scales the addend).  `merged`: the dropped limbs are
+// q_{level-1} and the special primes (the ModDown merged with the rescale;
+// out has level - 1 limbs), else the special primes.
 static int moddown_unfused(he_ctx* c, const uint64_t* acc, uint64_t* conv, CtBatch add, int add_mode, CtBatch out,
-                           uint32_t level, uint32_t count) {
+                           uint32_t level, uint32_t count, bool merged = false) {
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, nt = level + alpha;
+  const uint32_t lt = merged ? level - 1 : level;  // target limbs
+  MdDrop dr;
+  dr.n = merged ? alpha + 1 : alpha;
+  dr.first = lt;
+  for (uint32_t u = 0; u < dr.n; ++u) dr.pr[u] = merged ? (u == 0 ? level - 1 : L + u - 1) : L + u;
+  const uint64_t* md = merged ? c->d_mdrs + (size_t)level * c->mdrs_words : c->d_moddown;
+  const uint64_t* addw = merged ? c->d_rescale + (size_t)(level - 1) * L * 2 : nullptr;
   {
-    ProfScope prof(c, "moddown_conv", 2.0 * count * n * alpha * (level + 1), (double)count * 2 * n * 8 * (alpha + level));
+    ProfScope prof(c, "moddown_conv", 2.0 * count * n * dr.n * (lt + 1), (double)count * 2 * n * 8 * (dr.n + lt));
     k_moddown_conv<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, level, alpha, L, count, c->log_n,
-        c->d_primes, c->d_moddown);
+        acc, (size_t)2 * nt * n, nt, dr, conv, (size_t)2 * lt * n, lt, L, count, c->log_n, c->d_primes, md);
   }
   HE_CUDA(cudaGetLastError());
-  HE_TRY(ntt_forward(c, pb(conv, conv, (size_t)level * n, (size_t)level * n, count * 2, level, 0, level)));
-  const uint64_t* pinv = c->d_moddown + 2 * alpha + (size_t)alpha * L;
+  HE_TRY(ntt_forward(c, pb(conv, conv, (size_t)lt * n, (size_t)lt * n, count * 2, lt, 0, lt)));
+  const uint64_t* pinv = md + 2 * dr.n + (size_t)dr.n * L;
   {
-    ProfScope prof(c, "ks_combine", 2.0 * count * level * n, (double)count * 2 * level * n * 8 * (add_mode ? 4 : 3));
-    k_ks_combine<<<grid_for((size_t)count * 2 * level * n / 2), 256, 0, c->stream>>>(
-        acc, (size_t)2 * nt * n, conv, (size_t)2 * level * n, add, add_mode, out, 0, 2, level, alpha, L,
-        count, c->log_n, c->d_primes, pinv);
+    ProfScope prof(c, "ks_combine", 2.0 * count * lt * n, (double)count * 2 * lt * n * 8 * (add_mode ? 4 : 3));
+    k_ks_combine<<<grid_for((size_t)count * 2 * lt * n / 2), 256, 0, c->stream>>>(
+        acc, (size_t)2 * nt * n, nt, conv, (size_t)2 * lt * n, add, add_mode, addw, out, lt, count, c->log_n,
+        c->d_primes, pinv);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
 }
 
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
-                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal) {
+                    const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal,
+                    bool merged) {
   if (gal && !ks_fusable(c)) return fail(HE_EINVAL, "keyswitch_batch: automorphism needs the fused kernels");
+  if (merged && (gal || add_mode != 2 || level < 2 || !c->d_mdrs))
+    return fail(HE_EINVAL, "keyswitch_batch: the merged rescale takes (d0, d1) as addend, level >= 2");
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
   const uint32_t nt = level + alpha, beta = (level + alpha - 1) / alpha;
   uint64_t* d2c = ar.take<uint64_t>((size_t)count * level * n);
@@ -173,6 +186,22 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, gal, half, &fused));
   if (!fused) HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
   // 4. ModDown
+  if (merged) {  // divide P (d0, d1) + acc by P q_{level-1}: its dropped limbs are acc's last alpha + 1
+    const uint32_t lo = level - 1;
+    {
+      ProfScope prof(c, "elementwise", (double)count * 2 * n, (double)count * 2 * n * 24);
+      k_add_pd<<<grid_for((size_t)count * 2 * n), 256, 0, c->stream>>>(
+          acc, (size_t)2 * nt * n, nt, add, lo, c->P_mod_q[lo], h_shoup(c->P_mod_q[lo], c->q[lo]), count, c->log_n,
+          c->d_primes);
+    }
+    HE_CUDA(cudaGetLastError());
+    HE_TRY(ntt_inverse(c, pb(acc + (size_t)lo * n, acc + (size_t)lo * n, (size_t)nt * n, (size_t)nt * n, count * 2,
+                             alpha + 1, lo, level)));
+    bool done = false;
+    HE_TRY(md_fused_rescale(c, acc, (size_t)2 * nt * n, conv, add, out, level, count, &done));
+    if (done) return HE_OK;
+    return moddown_unfused(c, acc, conv, add, 2, out, level, count, true);
+  }
   HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
                            (size_t)nt * n, count * 2, alpha, level, level)));
   bool md_done = false;
@@ -226,8 +255,7 @@ int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t co
   const uint32_t n = c->n;
   uint64_t* d01 = ar.take<uint64_t>((size_t)count * 2 * level * n);
   uint64_t* d2 = ar.take<uint64_t>((size_t)count * level * n);
-  uint64_t* r = rescale ? ar.take<uint64_t>((size_t)count * 2 * level * n) : nullptr;
-  if (!d01 || !d2 || (rescale && !r)) return fail(HE_ENOMEM, "multiplication scratch too small");
+  if (!d01 || !d2) return fail(HE_ENOMEM, "multiplication scratch too small");
   CtBatch D{d01, (size_t)2 * level * n, level, 0};
   {
     ProfScope prof(c, "tensor", 4.0 * count * level * n, (double)count * level * n * 8 * 7);
@@ -235,10 +263,8 @@ int mul_relin_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t level, uint32_t co
         A, B, D, d2, (size_t)level * n, level, count, c->log_n, c->d_primes);
   }
   HE_CUDA(cudaGetLastError());
-  CtBatch R = rescale ? CtBatch{r, (size_t)2 * level * n, level, 0} : out;
-  HE_TRY(keyswitch_batch(c, d2, (size_t)level * n, level, count, c->d_rlk, D, 2, R, ar));
-  if (rescale) HE_TRY(rescale_batch(c, R, level, count, out, ar));
-  return HE_OK;
+  // with the rescale: the key switch's ModDown and the rescale as one division by P q_{level-1}
+  return keyswitch_batch(c, d2, (size_t)level * n, level, count, c->d_rlk, D, 2, out, ar, 0, rescale);
 }
 
 int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t gal, CtBatch out,
@@ -296,7 +322,7 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
   uint64_t* conv = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
   const uint64_t* d = A.base + (size_t)A.cap * n;
-  const bool fits = ks_rot_fits(c, level);
+  const bool fits = ks_rot_fits(c, level, nrot);
   const bool half = fits && ks_converts_per_digit(c, level);
   {
     const PolyBatch b = pb(d, d2c, A.stride, (size_t)level * n, count, level, 0, level);
@@ -459,15 +485,13 @@ int tensor_acc_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t count, uint64_t* 
 }
 
 // Relinearise three-part ciphertexts D (count x [3][level][N] at d_stride)
-// and rescale: out (level - 1 limbs) = rescale((d0, d1) + KS(d2)).
+// and rescale, as one division by P q_{level-1} of P (d0, d1) + the inner
+// products of d2 (out: level - 1 limbs).
 int relin_rescale_batch(he_ctx* c, uint64_t* D, uint64_t d_stride, uint32_t level, uint32_t count, CtBatch out,
                         Arena& ar) {
-  const uint32_t n = c->n;
-  uint64_t* r = ar.take<uint64_t>((size_t)count * 2 * level * n);
-  if (!r) return fail(HE_ENOMEM, "relinearisation scratch too small");
-  const CtBatch D01{D, d_stride, level, 0}, R{r, (uint64_t)2 * level * n, level, 0};
-  HE_TRY(keyswitch_batch(c, D + (size_t)2 * level * n, d_stride, level, count, c->d_rlk, D01, 2, R, ar));
-  return rescale_batch(c, R, level, count, out, ar);
+  const CtBatch D01{D, d_stride, level, 0};
+  return keyswitch_batch(c, D + (size_t)2 * level * c->n, d_stride, level, count, c->d_rlk, D01, 2, out, ar, 0,
+                         true);
 }
 
 }  // namespace he

@@ -243,59 +243,78 @@ int build_tables(he_ctx* c) {
     HE_CUDA(cudaMemcpy(c->d_modup, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }
 
-  // ModDown constants: [alpha] Shoup pairs of (P/p_k)^-1 mod p_k; [alpha][L] values
-  // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2 reduced:
-  // [alpha] h mod p_k and [L] h mod q_t (the division by P rounds); then the
-  // [alpha][L] Shoup companions of the (P/p_k) mod q_t values; [alpha] low
-  // words of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t;
-  // [L][8] v P mod q_t.
-  // The last two make the conversion exact: v = floor(sum_k u_k / p_k) is
-  // evaluated in 64.64 fixed point and v P subtracted.
-  {
+  // ModDown constants for dividing by the product P of the dropped primes
+  // drop[0 .. a) (the special primes; with q_{l-1} first, the ModDown merged
+  // with a rescale): [a] Shoup pairs of (P/p_k)^-1 mod p_k; [a][L] values
+  // (P/p_k) mod q_t; [L] Shoup pairs of P^-1 mod q_t; then h = (P-1)/2
+  // reduced: [a] h mod p_k and [L] h mod q_t (the division by P rounds); then
+  // the [a][L] Shoup companions of the (P/p_k) mod q_t values; [a] low words
+  // of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t;
+  // [L][8] v P mod q_t.  The last two make the conversion exact: v =
+  // floor(sum_k u_k / p_k) is evaluated in 64.64 fixed point and v P
+  // subtracted.  4a + 2aL + 12L words.
+  auto md_words = [&](const std::vector<int>& drop) {
+    const int a = (int)drop.size();
     std::vector<uint64_t> words;
-    for (int k = 0; k < alpha; ++k) {
-      const uint64_t pk = c->q[L + k];
-      uint64_t prod = 1 % pk;
-      for (int k2 = 0; k2 < alpha; ++k2)
-        if (k2 != k) prod = h_mulmod(prod, c->q[L + k2] % pk, pk);
-      const uint64_t inv = h_invmod(prod, pk);
+    auto prod_mod = [&](uint64_t m, int skip) {  // prod of drop[] except drop[skip], mod m
+      uint64_t r = 1 % m;
+      for (int k2 = 0; k2 < a; ++k2)
+        if (k2 != skip) r = h_mulmod(r, c->q[drop[k2]] % m, m);
+      return r;
+    };
+    for (int k = 0; k < a; ++k) {
+      const uint64_t pk = c->q[drop[k]];
+      const uint64_t inv = h_invmod(prod_mod(pk, k), pk);
       words.push_back(inv);
       words.push_back(h_shoup(inv, pk));
     }
-    for (int k = 0; k < alpha; ++k) {
-      for (int t = 0; t < L; ++t) {
-        const uint64_t qt = c->q[t];
-        uint64_t prod = 1 % qt;
-        for (int k2 = 0; k2 < alpha; ++k2)
-          if (k2 != k) prod = h_mulmod(prod, c->q[L + k2] % qt, qt);
-        words.push_back(prod);
-      }
-    }
-    c->P_mod_q.assign(L, 0);
+    for (int k = 0; k < a; ++k)
+      for (int t = 0; t < L; ++t) words.push_back(prod_mod(c->q[t], k));
+    std::vector<uint64_t> Pq(L);
     for (int t = 0; t < L; ++t) {
       const uint64_t qt = c->q[t];
-      uint64_t P = 1 % qt;
-      for (int k = 0; k < alpha; ++k) P = h_mulmod(P, c->q[L + k] % qt, qt);
-      c->P_mod_q[t] = P;
-      const uint64_t inv = h_invmod(P, qt);
+      Pq[t] = prod_mod(qt, -1);
+      const uint64_t inv = Pq[t] ? h_invmod(Pq[t], qt) : 0;  // P = 0 mod q_t only for a dropped q_t (not a target)
       words.push_back(inv);
       words.push_back(h_shoup(inv, qt));
     }
     auto half_P = [&](uint64_t m) {  // (P - 1)/2 mod m = (P mod m - 1) * 2^-1 mod m
-      uint64_t P = 1 % m;
-      for (int k = 0; k < alpha; ++k) P = h_mulmod(P, c->q[L + k] % m, m);
-      return h_mulmod((P + m - 1) % m, h_invmod(2, m), m);
+      return h_mulmod((prod_mod(m, -1) + m - 1) % m, h_invmod(2, m), m);
     };
-    for (int k = 0; k < alpha; ++k) words.push_back(half_P(c->q[L + k]));
+    for (int k = 0; k < a; ++k) words.push_back(half_P(c->q[drop[k]]));
     for (int t = 0; t < L; ++t) words.push_back(half_P(c->q[t]));
-    for (int k = 0; k < alpha; ++k)
-      for (int t = 0; t < L; ++t) words.push_back(h_shoup(words[2 * alpha + (size_t)k * L + t], c->q[t]));
-    for (int k = 0; k < alpha; ++k) words.push_back((uint64_t)(~(unsigned __int128)0 / c->q[L + k]));
-    for (int t = 0; t < L; ++t) words.push_back(c->P_mod_q[t]);
-    for (int t = 0; t < L; ++t)  // [L][8]: v P mod q_t for v = 0 .. 7 (v < alpha <= 8)
-      for (uint64_t v = 0; v < 8; ++v) words.push_back(h_mulmod(v % c->q[t], c->P_mod_q[t], c->q[t]));
+    for (int k = 0; k < a; ++k)
+      for (int t = 0; t < L; ++t) words.push_back(h_shoup(words[2 * a + (size_t)k * L + t], c->q[t]));
+    for (int k = 0; k < a; ++k) words.push_back((uint64_t)(~(unsigned __int128)0 / c->q[drop[k]]));
+    for (int t = 0; t < L; ++t) words.push_back(Pq[t]);
+    for (int t = 0; t < L; ++t)  // [L][8]: v P mod q_t for v = 0 .. 7 (v < a <= 8)
+      for (uint64_t v = 0; v < 8; ++v) words.push_back(h_mulmod(v % c->q[t], Pq[t], c->q[t]));
+    return words;
+  };
+  {
+    std::vector<int> sp;
+    for (int k = 0; k < alpha; ++k) sp.push_back(L + k);
+    const std::vector<uint64_t> words = md_words(sp);
+    c->P_mod_q.assign(L, 0);
+    for (int t = 0; t < L; ++t) c->P_mod_q[t] = words[words.size() - 9 * (size_t)L + t];
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
+  }
+  // The same for dividing by P q_{l-1} (ModDown merged with the rescale of a
+  // multiplication at level l, 2 <= l <= L): dropped primes q_{l-1}, then the
+  // special primes; one table of 4(alpha+1) + 2(alpha+1)L + 12L words per l.
+  if (alpha + 1 <= 8) {
+    const size_t W = 4 * (size_t)(alpha + 1) + 2 * (size_t)(alpha + 1) * L + 12 * (size_t)L;
+    std::vector<uint64_t> all(W * (L + 1), 0);
+    for (int l = 2; l <= L; ++l) {
+      std::vector<int> drop{l - 1};
+      for (int k = 0; k < alpha; ++k) drop.push_back(L + k);
+      const std::vector<uint64_t> words = md_words(drop);
+      std::copy(words.begin(), words.end(), all.begin() + W * l);
+    }
+    c->mdrs_words = W;
+    HE_CUDA(cudaMalloc(&c->d_mdrs, sizeof(uint64_t) * all.size()));
+    HE_CUDA(cudaMemcpy(c->d_mdrs, all.data(), sizeof(uint64_t) * all.size(), cudaMemcpyHostToDevice));
   }
 
   // Rescale constants: for dropping limb l (1 <= l < L), q_l^-1 mod q_t for t < l.

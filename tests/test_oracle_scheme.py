@@ -420,6 +420,56 @@ def test_keyswitch_equals_big_integer_definition(tiny):
                 assert int(gotc[t][c]) == out % q[t], (p, c, t)
 
 
+def test_mul_relin_rescale_equals_big_integer_definition(tiny):
+    """Multiplication recomputed with Python integers: the tensor's parts
+    (d0, d1, d2) residue by residue, the integer ModUp of d2 and its products
+    with the relinearisation key over Q_level P (as in the key-switch pin),
+    V = P (d0, d1) + those products, and one division with rounding by
+    P q_{level-1}: out = floor((V + h) / (P q_{level-1})), h = (P q_{level-1}
+    - 1)/2.  Must equal the oracle's residues."""
+    o = tiny
+    level, n, L, alpha = 5, o.n, o.L, o.alpha
+    q = o.primes
+    P = math.prod(q[L:L + alpha])
+    D = P * q[level - 1]
+    h = (D - 1) // 2
+    a = workloads.residues(97, q[:level], n, parts=2)
+    b = workloads.residues(98, q[:level], n, parts=2)
+    out = o.mul_relin_rescale(oracle.Ciphertext(a, level, o.scale), oracle.Ciphertext(b, level, o.scale))
+    d0 = np.stack([(a[0][t].astype(object) * b[0][t].astype(object)) % q[t] for t in range(level)])
+    d1 = np.stack([(a[0][t].astype(object) * b[1][t].astype(object) + a[1][t].astype(object) * b[0][t].astype(object))
+                   % q[t] for t in range(level)])
+    d2 = np.stack([(a[1][t].astype(object) * b[1][t].astype(object)) % q[t] for t in range(level)])
+    as_u64 = lambda x: np.array(x, dtype=np.uint64)
+    d2c = to_coef(o, as_u64(d2), level)
+    targets = list(range(level)) + list(range(L, L + alpha))
+    mod = math.prod(q[t] for t in targets)
+    key = o.key(1)
+    acc = [[0] * n, [0] * n]
+    for j in range((level + alpha - 1) // alpha):
+        digit = list(range(j * alpha, min((j + 1) * alpha, level)))
+        Qj = math.prod(q[i] for i in digit)
+        y = [0] * n
+        for i in digit:
+            qhat = Qj // q[i]
+            inv = pow(qhat, -1, q[i])
+            for c in range(n):
+                y[c] += (int(d2c[i][c]) * inv % q[i]) * qhat
+        for p in range(2):
+            kc = [oracle.intt_def(key[j, p, t], o.log_n, q[t], o.roots[t]) for t in targets]
+            kint = [crt([kc[ti][c] for ti in range(len(targets))], [q[t] for t in targets]) for c in range(n)]
+            acc[p] = [(x + v) % mod for x, v in zip(acc[p], negacyclic(y, kint))]
+    for p, dp in enumerate((d0, d1)):
+        dc = to_coef(o, as_u64(dp), level)
+        dint = [crt([dc[t][c] for t in range(level)], q[:level]) for c in range(n)]
+        gotc = to_coef(o, out.data[p], level - 1)
+        for c in range(n):
+            V = (P * dint[c] + acc[p][c]) % mod
+            want = (V + h) // D
+            for t in range(level - 1):
+                assert int(gotc[t][c]) == want % q[t], (p, c, t)
+
+
 def _kappa_int(y, k, n):
     """X -> X^k on integer coefficients, X^N = -1."""
     z = [0] * n
