@@ -156,9 +156,14 @@ ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "ks_ntt_ro
                "moddown_ntt_combine", "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes (read + write) per modular product of the fused key-switch row
 # pass, from an ncu capture of one launch over 64 ciphertexts at level 7 of
-# these parameters (479.1 MB for 212.3 M products); the roofline scales it to
+# these parameters (478.5 MB for 212.3 M products); the roofline scales it to
 # the step's average launch, whose traffic grows in proportion to its work.
-KS_ROW_TRAFFIC_PER_MODMUL = 479.085056e6 / 212336640
+KS_ROW_TRAFFIC_PER_MODMUL = 478.5e6 / 212336640
+# DRAM bytes per algorithmic byte of the hoisted stage's row kernel, from an
+# ncu capture of one 7-rotation stage over 64 ciphertexts at level 7 (498.2 MB
+# against 453.0 MB): its traffic grows with the ciphertexts, not with the
+# rotations, so the roofline scales the launch's algorithmic bytes.
+KS_ROT_TRAFFIC_PER_ALG_BYTE = 498.2 / 453.0
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
@@ -178,6 +183,8 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
         traffic = None
         if name == "ks_ntt_inner_product":
             traffic = KS_ROW_TRAFFIC_PER_MODMUL * p["work"] / max(1, p["launches"])
+        elif name == "ks_ntt_rot_products":
+            traffic = KS_ROT_TRAFFIC_PER_ALG_BYTE * p["bytes"] / max(1, p["launches"])
         if frac_alu >= frac_hbm:
             return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_PEAK["per_second"] / 1e9,
                     "unit": "G modmul/s", "frac": frac_alu, "traffic": traffic,

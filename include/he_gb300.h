@@ -223,9 +223,11 @@ int he_rescale(he_ctx* ctx, const he_ct* a, he_ct* out);
 int he_rescale_noalloc(he_ctx* ctx, const he_ct* a, he_ct* out);
 
 /* Homomorphic multiplication (Sec. 3; the cost the paper names in Sec. 6):
- * tensor product, relinearisation by hybrid key switching, rescale.  Both
- * operands at the same level l >= 2 (else the lower is used); out at l-1
- * with scale a.scale*b.scale/q_{l-1}. */
+ * tensor product (d0, d1, d2), relinearisation by hybrid key switching, and
+ * rescale, the key switch's division by P and the rescale's by q_{l-1} taken
+ * as one rounding: out = round((P (d0, d1) + <ModUp(d2), rlk>) / (P q_{l-1})).
+ * Both operands at the same level l >= 2 (else the lower is used); out at
+ * l-1 with scale a.scale*b.scale/q_{l-1}. */
 int he_mul_relin_rescale(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
 
 /* Same, without the rescale (out at level l, scale a.scale*b.scale). */
