@@ -98,9 +98,7 @@ int he_sync(he_ctx* ctx);
  * of one batched operation (default 2^34), "lr_chunk" = data ciphertexts per
  * chunk of the logistic-regression step (0 = from the budget), "ntt_generic"
  * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
- * one for N = 2^12 .. 2^16, "ks_row_ctas" = 2 or 3 (default) CTAs per SM for the
- * fused key-switch row pass (register budget 128 or 80 per thread),
- * "ntt_shape" = 0 (default), 1 or 2 for the three NTT tile-shape pairs compiled
+ * one for N = 2^12 .. 2^16, "ntt_shape" = 0 (default), 1 or 2 for the three NTT tile-shape pairs compiled
  * per ring size (also used by the fused key switch), "ntt_pb_max" = at most this
  * many polynomials of one limb per NTT CTA (default 8).  HE_EINVAL for an
  * unknown key or a value out of range. */
@@ -123,15 +121,14 @@ int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second);
  * degree <= 16, n > degree.  HE_EINVAL for null pointers, a non-finite sample,
  * too few samples or samples that do not determine the polynomial (fewer
  * than degree + 1 distinct abscissas).  Table 2's binomial row is the fit of
- * the negated logistic-loss derivative 1/(1+e^x) on samples uniform in
- * [-16, 16], to its printed digits. */
+ * the negated logistic-loss derivative 1/(1+e^x) on [-16, 16] (evenly spaced
+ * samples), to its printed digits. */
 int he_fit_poly(const double* x, const double* y, size_t n, uint32_t degree, double* coeffs);
 
 /* Autotuner (no counterpart in the paper; it serves the batched workers of
  * Sec. 4): times the relinearisation key switch (iNTT, ModUp + NTT, inner
  * product, ModDown) of `count` polynomials of uniform residues at `level`
- * under every setting of "ntt_shape", "ks_row_ctas" and "ntt_pb_max" in
- * {1, 4, 8}, keeps the fastest in the context and writes its time per key
+ * under every setting of "ntt_shape" and "ntt_pb_max" in {1, 4, 8}, keeps the fastest in the context and writes its time per key
  * switch (ms) to *best_ms (may be NULL).  Synchronises the context's stream;
  * results never depend on these knobs.  HE_EINVAL for level outside [1, L] or
  * count outside [1, 4096]; on an error the knobs keep their previous values. */

@@ -299,7 +299,7 @@ def he_autotune(ctx: Context, level: int, count: int) -> dict:
     and keep the fastest; returns the chosen knobs and the time (ms)."""
     ms = ctypes.c_double()
     _check(load().he_autotune(ctx.ptr, level, count, ctypes.byref(ms)))
-    out = {k: he_get_tuning(ctx, k) for k in ("ntt_shape", "ks_row_ctas", "ntt_pb_max")}
+    out = {k: he_get_tuning(ctx, k) for k in ("ntt_shape", "ntt_pb_max")}
     out["ms_per_keyswitch"] = ms.value
     return out
 

@@ -125,7 +125,6 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->chunk_bytes = base->chunk_bytes;
   v->lr_chunk = base->lr_chunk;
   v->ntt_generic = base->ntt_generic;
-  v->ks_row_ctas = base->ks_row_ctas;
   v->ntt_shape = base->ntt_shape;
   v->ntt_pb_max = base->ntt_pb_max;
   v->P_mod_q = base->P_mod_q;
@@ -277,9 +276,6 @@ int he_set_tuning(he_ctx* c, const char* key, double value) {
   } else if (k == "lr_chunk") {
     if (!(value >= 0 && value <= 1 << 20)) return fail(HE_EINVAL, "lr_chunk out of range");
     c->lr_chunk = (uint32_t)value;
-  } else if (k == "ks_row_ctas") {
-    if (value != 2.0 && value != 3.0) return fail(HE_EINVAL, "ks_row_ctas is 2 or 3");
-    c->ks_row_ctas = (int)value;
   } else if (k == "ntt_shape") {
     if (value != 0.0 && value != 1.0 && value != 2.0) return fail(HE_EINVAL, "ntt_shape is 0, 1 or 2");
     c->ntt_shape = (int)value;

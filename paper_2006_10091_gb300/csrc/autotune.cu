@@ -2,9 +2,8 @@
 //
 // The knobs never change a residue, only how the work is cut: the NTT tile
 // shapes (three per ring size, shared by the plain transforms and the fused
-// key-switching kernels), how many CTAs per SM the fused row pass is compiled
-// for, and how many polynomials of one limb an NTT CTA transforms with one
-// staging of its twiddles.  The timed operation is the relinearisation key
+// key-switching kernels) and how many polynomials of one limb an NTT CTA
+// transforms with one staging of its twiddles.  The timed operation is the relinearisation key
 // switch (iNTT, ModUp + NTT, inner product, ModDown), which carries most of
 // the work of every multiplication and rotation, on `count` polynomials of
 // uniform residues at `level`; each candidate runs once untimed and then
@@ -26,7 +25,7 @@ __global__ void k_fill_uniform(uint64_t* out, size_t total, uint32_t level, int 
 }
 
 struct Knobs {
-  int shape, ctas;
+  int shape;
   uint32_t pb;
 };
 
@@ -55,9 +54,8 @@ extern "C" int he_autotune(he_ctx* c, uint32_t level, uint32_t count, double* be
   std::vector<Knobs> cand;
   const bool shaped = c->log_n >= 12 && c->log_n <= 16 && !c->ntt_generic;
   for (int shape = 0; shape < (shaped ? 3 : 1); ++shape)
-    for (int ctas = 2; ctas <= 3; ++ctas)
-      for (uint32_t pb : {1u, 4u, 8u}) cand.push_back(Knobs{shape, ctas, pb});
-  const Knobs saved{c->ntt_shape, c->ks_row_ctas, c->ntt_pb_max};
+    for (uint32_t pb : {1u, 4u, 8u}) cand.push_back(Knobs{shape, pb});
+  const Knobs saved{c->ntt_shape, c->ntt_pb_max};
   cudaEvent_t e0, e1;
   HE_CUDA(cudaEventCreate(&e0));
   HE_CUDA(cudaEventCreate(&e1));
@@ -67,7 +65,6 @@ extern "C" int he_autotune(he_ctx* c, uint32_t level, uint32_t count, double* be
   int rc = HE_OK;
   for (const Knobs& k : cand) {
     c->ntt_shape = k.shape;
-    c->ks_row_ctas = k.ctas;
     c->ntt_pb_max = k.pb;
     Arena a = scratch;
     rc = keyswitch_batch(c, d, (uint64_t)level * n, level, count, c->d_rlk, O, 0, O, a);  // warm-up
@@ -93,7 +90,6 @@ extern "C" int he_autotune(he_ctx* c, uint32_t level, uint32_t count, double* be
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->ntt_shape = rc == HE_OK ? win.shape : saved.shape;
-  c->ks_row_ctas = rc == HE_OK ? win.ctas : saved.ctas;
   c->ntt_pb_max = rc == HE_OK ? win.pb : saved.pb;
   if (rc == HE_OK && best_ms) *best_ms = best;
   return rc;
@@ -105,7 +101,6 @@ extern "C" int he_get_tuning(he_ctx* c, const char* key, double* value) {
   if (k == "chunk_bytes") *value = (double)c->chunk_bytes;
   else if (k == "ntt_generic") *value = c->ntt_generic ? 1.0 : 0.0;
   else if (k == "lr_chunk") *value = c->lr_chunk;
-  else if (k == "ks_row_ctas") *value = c->ks_row_ctas;
   else if (k == "ntt_shape") *value = c->ntt_shape;
   else if (k == "ntt_pb_max") *value = c->ntt_pb_max;
   else return fail(HE_EINVAL, "unknown tuning key " + k);

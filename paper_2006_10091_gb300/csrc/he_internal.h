@@ -95,7 +95,6 @@ struct he_ctx {
   size_t chunk_bytes = (size_t)1 << 34;  // scratch budget of one batched operation (16 GiB)
   uint32_t lr_chunk = 0;                 // data ciphertexts per chunk of the LR step (0: from the budget)
   bool ntt_generic = false;              // force the runtime-shaped NTT kernel (tuning)
-  int ks_row_ctas = 3;                   // CTAs per SM the key-switch row pass is compiled for (2 or 3)
   int ntt_shape = 0;                     // NTT tile shapes: 0, 1 or 2 (ntt2.cu)
   uint32_t ntt_pb_max = 8;               // polynomials of one limb per NTT CTA, at most
   std::map<std::string, cudaGraphExec_t> graphs;  // captured multi-worker steps

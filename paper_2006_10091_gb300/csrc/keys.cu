@@ -97,15 +97,6 @@ __global__ void k_evk_combine(uint64_t* key, const uint64_t* e, const uint64_t* 
 // Shoup companions floor(k 2^64 / q_t) of every key word, written after the
 // key ([beta][2][np][N] values, then the same layout of companions), so the
 // key inner product multiplies by a key word with one Shoup product.
-__global__ void k_key_companions(const uint64_t* key, uint64_t* sh, uint32_t np, size_t total, int log_n,
-                                 const PrimeDev* primes) {
-  const uint32_t n = 1u << log_n;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)((g / n) % np);
-    sh[g] = shoup_companion_dev(key[g], primes[t].q);
-  }
-}
-
 // Encryption body.  pk: out0 = v b + em, out1 = v a + e1; sk: out0 = em - a s
 // (a already in out1).  em = NTT(e0 + m), v, e1 in evaluation form.
 __global__ void k_enc_combine(CtBatch out, const uint64_t* v, const uint64_t* em, const uint64_t* e1,
@@ -183,9 +174,6 @@ static int gen_switch_key(he_ctx* c, const uint64_t* sp, uint32_t tag, uint64_t*
                                                         (uint32_t)c->alpha, (uint32_t)c->L, np, pm,
                                                         c->log_n, c->d_primes);
   HE_CUDA(cudaGetLastError());
-  const size_t kw = c->key_words();
-  k_key_companions<<<grid_for(kw), 256, 0, c->stream>>>(key, key + kw, np, kw, c->log_n, c->d_primes);
-  HE_CUDA(cudaGetLastError());
   return HE_OK;
 }
 
@@ -193,7 +181,7 @@ int keygen(he_ctx* c, const std::vector<int32_t>& rots) {
   const uint32_t n = c->n, np = c->np, L = c->L;
   HE_CUDA(cudaMalloc(&c->d_s, sizeof(uint64_t) * np * n));
   HE_CUDA(cudaMalloc(&c->d_pk, sizeof(uint64_t) * 2 * L * n));
-  HE_CUDA(cudaMalloc(&c->d_rlk, sizeof(uint64_t) * 2 * c->key_words()));
+  HE_CUDA(cudaMalloc(&c->d_rlk, sizeof(uint64_t) * c->key_words()));
   // secret: ternary coefficients on every prime, to evaluation form
   HE_TRY(sample(c, c->d_s, 0, 0, np, 0, np, 0, DOM_S, 1, 0));
   HE_TRY(ntt_forward(c, one_batch(c->d_s, c->d_s, 0, 1, np, np)));
@@ -223,7 +211,7 @@ int keygen(he_ctx* c, const std::vector<int32_t>& rots) {
     k_automorph<<<grid_for((size_t)np * n), 256, 0, c->stream>>>(in, out, 1, np, g, 1, c->log_n);
     HE_CUDA(cudaGetLastError());
     uint64_t* key = nullptr;
-    if (cudaMalloc(&key, sizeof(uint64_t) * 2 * c->key_words()) != cudaSuccess) {
+    if (cudaMalloc(&key, sizeof(uint64_t) * c->key_words()) != cudaSuccess) {
       cudaFree(sg);
       return fail(HE_ENOMEM, "Galois key allocation failed");
     }

@@ -6,8 +6,7 @@
 
 namespace he {
 
-// ModUp -> NTT -> inner product of keyswitch_batch, fused.  Returns HE_OK and
-// sets *handled when N has a compiled shape.
+// The arguments shared by the fused ModUp and row kernels.
 static KsFusedArgs ks_args(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext,
                            uint64_t* acc, const uint64_t* evk, uint32_t level, uint64_t gal, bool half) {
   KsFusedArgs a;
@@ -19,7 +18,6 @@ static KsFusedArgs ks_args(he_ctx* c, const uint64_t* d, uint64_t d_stride, cons
   a.ext = ext;
   a.acc = acc;
   a.evk = evk;
-  a.evk_sh = evk ? evk + c->key_words() : nullptr;
   a.d_stride = d_stride;
   a.level = level;
   a.alpha = (uint32_t)c->alpha;
@@ -37,21 +35,6 @@ static KsFusedArgs ks_args(he_ctx* c, const uint64_t* d, uint64_t d_stride, cons
     a.off[j] = mc.off;
   }
   return a;
-}
-
-int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled) {
-  *handled = false;
-  if (!ks_fusable(c)) return HE_OK;
-  const KsFusedArgs a = ks_args(c, d, d_stride, d2c, ext, acc, evk, level, gal, half);
-  *handled = true;
-  switch (c->log_n) {  // the tile shapes of ntt2.cu
-    case 12: return ks_fused_n12(c, a, count);
-    case 13: return ks_fused_n13(c, a, count);
-    case 14: return ks_fused_n14(c, a, count);
-    case 15: return ks_fused_n15(c, a, count);
-    default: return ks_fused_n16(c, a, count);
-  }
 }
 
 // Inverse of an odd Galois element modulo 2N (Newton's iteration for the
@@ -85,12 +68,13 @@ bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot) {
 // rotate-and-sum, fused, into one accumulator; *unreduced when it holds sums
 // of rs.n residues (the rotations moved rows between CTAs).
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced) {
+           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced,
+           uint64_t in_gal) {
   *handled = false;
   *unreduced = false;
   if (!ks_rot_fits(c, level, rs.n)) return HE_OK;
   KsRotArgs ra;
-  ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, 0, half);
+  ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, in_gal, half);
   ra.nrot = rs.n;
   ra.count = count;
   // the summed path adds nrot * beta products below q^2 in 128 bits (the

@@ -7,11 +7,11 @@
 //    straight from the coefficient-form input (the digit's limbs, converted
 //    to prime t as in k_modup) and runs the column pass; the ModUp output is
 //    never written;
-//  * ks_row_ip: a CTA of target limb t and one row tile keeps two
-//    accumulators per residue in registers, and for every digit finishes the
-//    row pass of that digit's tile (or, on the digit's own limb, reads the
-//    input as it is) and adds its products with the two key polynomials; the
-//    transformed digits are never written.
+//  * ks_row_rot: a CTA of target limb t and two rows finishes the row pass of
+//    every digit's tile (or, on the digit's own limb, reads the input as it
+//    is), keeps the tiles in shared memory and adds their products with the
+//    key polynomials of each rotation (a plain key switch is one rotation by
+//    the identity); the transformed digits are never written.
 #include <algorithm>
 
 #pragma once
@@ -31,7 +31,6 @@ struct KsFusedArgs {
   uint64_t* ext;         // column-pass outputs: count x [beta][nt][N]
   uint64_t* acc;         // accumulators: count x [2][nt][N]
   const uint64_t* evk;   // [beta_top][2][np][N]
-  const uint64_t* evk_sh;  // Shoup companions of evk, same layout
   uint64_t d_stride;
   uint64_t gal;            // d is read through the automorphism X -> X^gal (0: none)
   uint32_t level, alpha, beta, L, np, nt;
@@ -188,126 +187,6 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
   }
 }
 
-// Row pass of every digit's tile fused with the key inner product.
-// Grid: count * nt * TILES.  Each thread owns residues idx = tid + u*T.
-// MINB: CTAs per SM the register allocation must allow (2: 128 registers,
-// with the next digit's tile prefetched into registers; 3: 80 registers with
-// a few spilled words, no prefetch), chosen at run time.
-template <int LOG_N, int LOG_M, int LOG_K, int MINB>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, MINB) ks_row_ip(KsFusedArgs a) {
-  using S = Shape<LOG_N, LOG_M, LOG_K, false>;
-  constexpr uint32_t N = 1u << LOG_N;
-  constexpr int PER = S::TILE / S::T;  // 8
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw + sizeof(ulonglong2) * S::NTW);
-  uint32_t b = blockIdx.x;
-  const uint32_t tile = b % S::TILES;
-  b /= S::TILES;
-  const uint32_t t = b % a.nt, i = b / a.nt;
-  const uint32_t prime = ks_prime(t, a.level, a.L);
-  const PrimeDev pr = a.primes[prime];
-  const uint64_t q = pr.q, q2 = q + q;
-  const bool lazy = q < (1ull << 58);
-  // Products by key words are Shoup products in [0, 2q); they are summed
-  // without reduction while beta of them stay below 2^64, else kept in [0, 2q).
-  const bool acc_lazy = q < ~0ull / (2ull * a.beta);
-  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
-  uint64_t acc0[PER], acc1[PER];
-#pragma unroll
-  for (int u = 0; u < PER; ++u) acc0[u] = acc1[u] = 0;
-  auto mac = [&](uint64_t& acc, uint64_t x, uint64_t k, uint64_t ksh) {
-    acc += mul_shoup_lazy(x, k, ksh, q);
-    if (!acc_lazy) acc = acc >= q2 ? acc - q2 : acc;
-  };
-  // With room for the registers (MINB 2) the next converted digit's tile is
-  // loaded while the current one is transformed, so its memory latency
-  // overlaps the rounds and the products.
-  constexpr bool PIPE = MINB <= 2;
-  auto own_of = [&](uint32_t j) { return t >= a.lo[j] && t < a.lo[j] + a.cnt[j]; };
-  auto next_conv = [&](uint32_t j) {  // first digit >= j whose limb t was converted
-    while (j < a.beta && own_of(j)) ++j;
-    return j;
-  };
-  auto tile_src = [&](uint32_t j) { return a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N; };
-  uint64_t nxt[PER];
-  if (PIPE) {
-    const uint32_t j0 = next_conv(0);
-    if (j0 < a.beta) {
-      const uint64_t* src = tile_src(j0);
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const uint32_t idx = threadIdx.x + u * S::T;
-        nxt[u] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
-      }
-    }
-  }
-  for (uint32_t j = 0; j < a.beta; ++j) {
-    const bool own = own_of(j);
-    const size_t kb_off = (((size_t)j * 2 + 0) * a.np + prime) * N;
-    const size_t ka_off = (((size_t)j * 2 + 1) * a.np + prime) * N;
-    const uint64_t *kb = a.evk + kb_off, *ka = a.evk + ka_off;
-    const uint64_t *kbs = a.evk_sh + kb_off, *kas = a.evk_sh + ka_off;
-    if (own) {
-      const uint64_t* dd = a.d + (size_t)i * a.d_stride + (size_t)t * N;
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const uint32_t idx = threadIdx.x + u * S::T;
-        const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-        const uint64_t x = __ldg(dd + (a.gal ? automorph_src(e, a.gal, LOG_N) : e));
-        mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
-        mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
-      }
-      continue;
-    }
-    if (PIPE) {
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const uint32_t idx = threadIdx.x + u * S::T;
-        sm[idx + (idx >> 3)] = nxt[u];
-      }
-      const uint32_t jn = next_conv(j + 1);
-      if (jn < a.beta) {
-        const uint64_t* src = tile_src(jn);
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-          const uint32_t idx = threadIdx.x + u * S::T;
-          nxt[u] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
-        }
-      }
-    } else {
-      const uint64_t* src = tile_src(j);
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const uint32_t idx = threadIdx.x + u * S::T;
-        sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
-      }
-    }
-    __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, pr.q);
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
-      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      const uint64_t v = sm[idx + (idx >> 3)];
-      const uint64_t x = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
-      mac(acc0[u], x, __ldg(kb + e), __ldg(kbs + e));
-      mac(acc1[u], x, __ldg(ka + e), __ldg(kas + e));
-    }
-    __syncthreads();  // the tile buffer is reused by the next digit
-  }
-  uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
-  uint64_t* o1 = a.acc + ((size_t)i * 2 * a.nt + a.nt + t) * N;
-#pragma unroll
-  for (int u = 0; u < PER; ++u) {
-    const uint32_t idx = threadIdx.x + u * S::T;
-    const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-    o0[e] = reduce64(acc0[u], pr);
-    o1[e] = reduce64(acc1[u], pr);
-  }
-}
-
 // ---- hoisted rotate-and-sum ------------------------------------------------
 // The rotations of one rotate-and-sum stage share the decomposition of the
 // input: the column pass (ks_modup_col[_all], run once) and the row pass of
@@ -360,10 +239,14 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
     const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
     const uint64_t* src = own ? a.d + (size_t)i * a.d_stride + (size_t)t * N
                               : a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
+    // the own limb is read through the input's automorphism (a single
+    // rotation's key switch: the converted tiles already are)
+    const uint64_t in_gal = own ? a.gal : 0;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = threadIdx.x + u * S::T;
-      sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+      const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+      sm[idx + (idx >> 3)] = __ldg(src + (in_gal ? automorph_src(e, in_gal, LOG_N) : e));
     }
     if (own) continue;
     __syncthreads();
@@ -727,32 +610,6 @@ int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   return HE_OK;
 }
 
-template <int LOG_N, int M1, int K1, int M2, int K2>
-int ks_fused_run(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  using SR = Shape<LOG_N, M2, K2, false>;
-  const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    HE_CUDA(cudaFuncSetAttribute(ks_row_ip<LOG_N, M2, K2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    attr_set |= 1ull << c->device;
-  }
-  const double n = (double)(1u << LOG_N);
-  double own = 0;  // limbs each ciphertext takes as they are
-  for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
-  const double conv = (double)a.beta * a.nt - own;  // converted limbs per ciphertext
-  HE_TRY((ks_modup_launch<LOG_N, M1, K1>(c, a, count)));
-  {
-    const size_t blocks = (size_t)count * a.nt * SR::TILES;
-    ProfScope prof(c, "ks_ntt_inner_product", count * (conv * n / 2 * M2 + 2.0 * a.beta * a.nt * n),
-                   count * n * 8 * (conv + own + 2.0 * a.beta * a.nt + 2.0 * a.nt));
-    if (c->ks_row_ctas == 3) ks_row_ip<LOG_N, M2, K2, 3><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
-    else ks_row_ip<LOG_N, M2, K2, 2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
-  }
-  HE_CUDA(cudaGetLastError());
-  return HE_OK;
-}
-
 // Dynamic shared memory of ks_row_rot (row tiles of half the row pass's
 // tile: M2 x 2^(K2-1)) for beta digits.
 template <int LOG_N, int M2, int K2>
@@ -822,7 +679,6 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
 // each, so that the template instances compile in parallel): the launches
 // for the tile shape c->ntt_shape.
 #define HE_KS_FUSED_DECL(NN)                                                         \
-  int ks_fused_n##NN(he_ctx* c, const KsFusedArgs& a, uint32_t count);               \
   int ks_rot_n##NN(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed); \
   size_t ks_rot_smem_n##NN(const he_ctx* c, uint32_t beta);                          \
   int md_fused_n##NN(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);     \

@@ -4,12 +4,6 @@
 
 namespace he {
 
-int ks_fused_n12(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  const int sh = c->ntt_shape;
-  return sh == 1 ? ks_fused_run<12, 5, 6, 7, 4>(c, a, count)
-       : sh == 2 ? ks_fused_run<12, 3, 8, 9, 2>(c, a, count) : ks_fused_run<12, 6, 5, 6, 5>(c, a, count);
-}
-
 int ks_rot_n12(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
   return sh == 1 ? ks_rot_run<12, 5, 6, 7, 4>(c, a, count, handled, closed)

@@ -4,12 +4,6 @@
 
 namespace he {
 
-int ks_fused_n13(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  const int sh = c->ntt_shape;
-  return sh == 1 ? ks_fused_run<13, 6, 5, 7, 4>(c, a, count)
-       : sh == 2 ? ks_fused_run<13, 4, 7, 9, 2>(c, a, count) : ks_fused_run<13, 7, 4, 6, 5>(c, a, count);
-}
-
 int ks_rot_n13(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
   return sh == 1 ? ks_rot_run<13, 6, 5, 7, 4>(c, a, count, handled, closed)

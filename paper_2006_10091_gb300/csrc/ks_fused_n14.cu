@@ -4,12 +4,6 @@
 
 namespace he {
 
-int ks_fused_n14(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  const int sh = c->ntt_shape;
-  return sh == 1 ? ks_fused_run<14, 8, 3, 6, 5>(c, a, count)
-       : sh == 2 ? ks_fused_run<14, 5, 6, 9, 2>(c, a, count) : ks_fused_run<14, 7, 4, 7, 4>(c, a, count);
-}
-
 int ks_rot_n14(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
   return sh == 1 ? ks_rot_run<14, 8, 3, 6, 5>(c, a, count, handled, closed)

@@ -4,12 +4,6 @@
 
 namespace he {
 
-int ks_fused_n16(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
-  const int sh = c->ntt_shape;
-  return sh == 1 ? ks_fused_run<16, 7, 4, 9, 2>(c, a, count)
-       : sh == 2 ? ks_fused_run<16, 6, 5, 10, 1>(c, a, count) : ks_fused_run<16, 8, 4, 8, 3>(c, a, count);
-}
-
 int ks_rot_n16(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed) {
   const int sh = c->ntt_shape;
   return sh == 1 ? ks_rot_run<16, 7, 4, 9, 2>(c, a, count, handled, closed)

@@ -15,8 +15,6 @@
 #include "he_ops.h"
 
 namespace he {
-int ks_fused(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-             const uint64_t* evk, uint32_t level, uint32_t count, uint64_t gal, bool half, bool* handled);
 bool ks_converts_per_digit(const he_ctx* c, uint32_t level);
 int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b);
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
@@ -25,7 +23,8 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
              uint32_t count, bool* handled);
 bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
-           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced);
+           const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced,
+           uint64_t in_gal = 0);
 int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
                   const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
 int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, CtBatch out,
@@ -163,7 +162,6 @@ static int moddown_unfused(he_ctx* c, const uint64_t* acc, uint64_t* conv, CtBat
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
                     const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal,
                     bool merged) {
-  if (gal && !ks_fusable(c)) return fail(HE_EINVAL, "keyswitch_batch: automorphism needs the fused kernels");
   if (merged && (gal || add_mode != 2 || level < 2 || !c->d_mdrs))
     return fail(HE_EINVAL, "keyswitch_batch: the merged rescale takes (d0, d1) as addend, level >= 2");
   const uint32_t n = c->n, alpha = c->alpha, L = c->L, np = c->np;
@@ -175,16 +173,30 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   if (!d2c || !ext || !acc || !conv) return fail(HE_ENOMEM, "key switch scratch too small");
   // 1. coefficient form (when each digit is converted in one CTA, only the
   //    inverse transform's row pass here; the conversion kernel finishes it)
-  const bool half = ks_converts_per_digit(c, level);
+  const bool fits = ks_rot_fits(c, level, 1);
+  if (gal && !fits) return fail(HE_EINVAL, "keyswitch_batch: automorphism needs the fused kernels");
+  const bool half = fits && ks_converts_per_digit(c, level);
   {
     PolyBatch b = pb(d, d2c, d_stride, (size_t)level * n, count, level, 0, level);
     b.gal = gal;
     HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
   }
-  // 2-3. fused ModUp + NTT + inner product where N has compiled shapes
+  // 2-3. ModUp + NTT + inner product, fused where N has compiled shapes and
+  //      the digits' tiles fit in shared memory (the hoisted row kernel with
+  //      one rotation by the identity; d read through X -> X^gal)
   bool fused = false;
-  HE_TRY(ks_fused(c, d, d_stride, d2c, ext, acc, evk, level, count, gal, half, &fused));
-  if (!fused) HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
+  if (fits) {
+    RotSet rs;
+    rs.n = 1;
+    rs.gal[0] = 1;
+    rs.evk[0] = evk;
+    bool unreduced = false;
+    HE_TRY(ks_rot(c, d, d_stride, d2c, ext, acc, rs, level, count, half, &fused, &unreduced, gal));
+  }
+  if (!fused) {
+    if (half || gal) return fail(HE_ECUDA, "keyswitch_batch: fused kernels declined");
+    HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
+  }
   // 4. ModDown
   if (merged) {  // divide P (d0, d1) + acc by P q_{level-1}: its dropped limbs are acc's last alpha + 1
     const uint32_t lo = level - 1;
@@ -278,7 +290,7 @@ int rotate_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, uint64_t 
   const char* a_hi = a_lo + sizeof(uint64_t) * ((size_t)(count - 1) * A.stride + (size_t)2 * A.cap * n);
   const char* o_lo = (const char*)out.base;
   const char* o_hi = o_lo + sizeof(uint64_t) * ((size_t)(count - 1) * out.stride + (size_t)2 * out.cap * n);
-  if (ks_fusable(c) && (o_hi <= a_lo || a_hi <= o_lo))
+  if (ks_rot_fits(c, level, 1) && (o_hi <= a_lo || a_hi <= o_lo))
     return keyswitch_batch(c, A.base + (size_t)A.cap * n, A.stride, level, count, key, A, 1, out, ar, gal);
   uint64_t* t = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!t) return fail(HE_ENOMEM, "rotation scratch too small");

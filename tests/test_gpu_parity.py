@@ -409,27 +409,23 @@ def test_fused_keyswitch_bit_exact(wide, he, level):
     d = workloads.residues(500 + level, wide.o.primes[:level], wide.n)[0]
     k0, k1 = wide.o.keyswitch(d, level, -1)
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
-    # fused kernels (every tile shape, row pass compiled for 2 and for 3 CTAs
-    # per SM), then the unfused sequence
-    for generic, shape, ctas in ((False, 0, 2), (False, 0, 3), (False, 1, 2), (False, 1, 3), (False, 2, 2),
-                                 (False, 2, 3), (True, 0, 2)):
+    # fused kernels (every tile shape), then the unfused sequence
+    for generic, shape in ((False, 0), (False, 1), (False, 2), (True, 0)):
         he.he_set_tuning(wide.g, "ntt_generic", generic)
         he.he_set_tuning(wide.g, "ntt_shape", shape)
-        he.he_set_tuning(wide.g, "ks_row_ctas", ctas)
         o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
         he.he_keyswitch(wide.g, dt, level, 0, o0, o1)
         assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
         assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
     he.he_set_tuning(wide.g, "ntt_generic", False)
     he.he_set_tuning(wide.g, "ntt_shape", 0)
-    he.he_set_tuning(wide.g, "ks_row_ctas", 3)
 
 
 def test_autotune_keeps_results(wide, he):
     """The autotuner picks knobs among its candidates; a rotation and a
     multiplication after it still match the oracle bit for bit."""
     res = he.he_autotune(wide.g, 6, 8)
-    assert res["ntt_shape"] in (0, 1, 2) and res["ks_row_ctas"] in (2, 3) and res["ntt_pb_max"] in (1, 4, 8)
+    assert res["ntt_shape"] in (0, 1, 2) and res["ntt_pb_max"] in (1, 4, 8)
     assert res["ms_per_keyswitch"] > 0
     m1, m2 = workloads.int_poly(81, wide.n, 1 << 36), workloads.int_poly(82, wide.n, 1 << 36)
     ga, oa = wide.gpu_enc(m1, 6, 81), wide.orc_enc(m1, 6, 81)
@@ -439,27 +435,25 @@ def test_autotune_keeps_results(wide, he):
     assert_same_residues(out, wide.o.rotate(oa, 5), he, wide.g)
     he.he_mul_relin_rescale(wide.g, ga, gb, out)
     assert_same_residues(out, wide.o.mul_relin_rescale(oa, ob), he, wide.g)
-    for k, v in (("ntt_shape", 0), ("ks_row_ctas", 3), ("ntt_pb_max", 8)):
+    for k, v in (("ntt_shape", 0), ("ntt_pb_max", 8)):
         he.he_set_tuning(wide.g, k, v)
     with pytest.raises(he.HeError):
         he.he_autotune(wide.g, 0, 8)
 
 
-def test_fused_keyswitch_reduced_accumulation(he):
-    """Nine digits and a 60-bit special prime: 2 * 9 * q exceeds 2^64 there,
-    so that limb's inner product reduces after every product while the
-    40-bit limbs accumulate unreduced."""
+def test_fused_keyswitch_many_digits(he):
+    """Nine one-limb digits and a 60-bit special prime: the fused inner
+    product sums nine full products below 2^120 in 128 bits per residue
+    before its one reduction."""
     import torch
     p = Pair(12, 9, 40, 1, 60, 2.0 ** 40, seed=12)
     d = workloads.residues(900, p.o.primes[:9], p.n)[0]
     k0, k1 = p.o.keyswitch(d, 9, -1)
     dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
-    for ctas in (2, 3):
-        he.he_set_tuning(p.g, "ks_row_ctas", ctas)
-        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
-        he.he_keyswitch(p.g, dt, 9, 0, o0, o1)
-        assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
-        assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
+    o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+    he.he_keyswitch(p.g, dt, 9, 0, o0, o1)
+    assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0)
+    assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
 
 
 def test_fused_rotation_and_mul_bit_exact(wide, he):
