@@ -152,13 +152,8 @@ def measure_alu_peak(he) -> None:
                         f"({r['per_clock_per_sm']:.2f} per clock per SM)")
 
 
-ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_inner_product", "ks_ntt_rot_products", "moddown_ntt",
-               "moddown_ntt_combine", "rescale_ntt", "rescale_ntt_final")
-# DRAM bytes (read + write) per modular product of the fused key-switch row
-# pass, from an ncu capture of one launch over 64 ciphertexts at level 7 of
-# these parameters (478.5 MB for 212.3 M products); the roofline scales it to
-# the step's average launch, whose traffic grows in proportion to its work.
-KS_ROW_TRAFFIC_PER_MODMUL = 478.5e6 / 212336640
+ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_rot_products", "moddown_ntt", "moddown_ntt_combine",
+               "moddown_rescale_ntt", "moddown_rescale_ntt_combine", "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes per algorithmic byte of the hoisted stage's row kernel, from an
 # ncu capture of one 7-rotation stage over 64 ciphertexts at level 7 (498.2 MB
 # against 453.0 MB): its traffic grows with the ciphertexts, not with the
@@ -181,9 +176,7 @@ def roofline(prof: dict, hbm_peak: float, peak_kind: str):
         rate = p["work"] / (p["ms"] * 1e-3)
         frac_alu = rate / ALU_PEAK["per_second"]
         traffic = None
-        if name == "ks_ntt_inner_product":
-            traffic = KS_ROW_TRAFFIC_PER_MODMUL * p["work"] / max(1, p["launches"])
-        elif name == "ks_ntt_rot_products":
+        if name == "ks_ntt_rot_products":
             traffic = KS_ROT_TRAFFIC_PER_ALG_BYTE * p["bytes"] / max(1, p["launches"])
         if frac_alu >= frac_hbm:
             return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_PEAK["per_second"] / 1e9,
@@ -658,7 +651,9 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
         stats = srv.stats()
         bad = [x for x in res if x["status"] != 0]
         if bad or len(res) != len(timed):
-            raise RuntimeError(f"serving: {len(bad)} failed requests, {len(res)} of {len(timed)} returned")
+            codes = sorted({x["status"] for x in bad})
+            raise RuntimeError(f"serving: {len(bad)} failed requests (codes {codes}: {srv.last_error()}), "
+                               f"{len(res)} of {len(timed)} returned")
         lat = np.array([x["latency_ms"] for x in res])
         return {"requests": len(timed), "offered_per_s": len(timed) / float(arr[len(timed) - 1]),
                 "requests_per_s": len(timed) / span, "p50_ms": float(np.percentile(lat, 50)),

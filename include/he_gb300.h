@@ -424,6 +424,9 @@ int he_server_drain(he_server* s, double timeout_s);
 /* Device bytes held now and at most so far (request buffers and slot
  * workspaces), waves launched, and the most waves running at once. */
 int he_server_stats(he_server* s, size_t* used, size_t* peak_used, size_t* waves, size_t* peak_running);
+/* The message of the most recent failed wave (empty if none), copied to buf
+ * (cap bytes including the terminating zero). */
+int he_server_last_error(he_server* s, char* buf, size_t cap);
 int he_server_destroy(he_server* s);
 
 /* The key holder's refresh (Algorithm 1, Algorithm 2),

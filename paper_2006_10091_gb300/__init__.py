@@ -147,6 +147,7 @@ def load():
         "he_server_poll": [VP, VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
         "he_server_drain": [VP, ctypes.c_double],
         "he_server_stats": [VP, VP, VP, VP, VP],
+        "he_server_last_error": [VP, ctypes.c_char_p, ctypes.c_size_t],
         "he_server_destroy": [VP],
     }
     for name, args in sig.items():
@@ -704,6 +705,11 @@ class Server:
 
     def drain(self, timeout_s: float = 600.0):
         _check(load().he_server_drain(self.ptr, float(timeout_s)))
+
+    def last_error(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        _check(load().he_server_last_error(self.ptr, buf, 512))
+        return buf.value.decode()
 
     def stats(self) -> dict:
         v = [ctypes.c_size_t() for _ in range(4)]

@@ -103,7 +103,7 @@ struct he_ctx {
   // keys (evaluation form)
   uint64_t* d_s = nullptr;    // [np][N]
   uint64_t* d_pk = nullptr;   // [2][L][N] (b, a)
-  uint64_t* d_rlk = nullptr;  // [beta][2][np][N], then the Shoup companions in the same layout
+  uint64_t* d_rlk = nullptr;  // [beta][2][np][N]
   std::map<uint64_t, uint64_t*> gal;  // Galois element -> [beta][2][np][N]
   // encoded 0/1 masks of the logistic-regression step, per (g, scale)
   std::map<std::pair<uint32_t, double>, int64_t*> lr_masks;

@@ -94,9 +94,6 @@ __global__ void k_evk_combine(uint64_t* key, const uint64_t* e, const uint64_t* 
   }
 }
 
-// Shoup companions floor(k 2^64 / q_t) of every key word, written after the
-// key ([beta][2][np][N] values, then the same layout of companions), so the
-// key inner product multiplies by a key word with one Shoup product.
 // Encryption body.  pk: out0 = v b + em, out1 = v a + e1; sk: out0 = em - a s
 // (a already in out1).  em = NTT(e0 + m), v, e1 in evaluation form.
 __global__ void k_enc_combine(CtBatch out, const uint64_t* v, const uint64_t* em, const uint64_t* e1,

@@ -68,8 +68,10 @@ static int lr_mask(he_ctx* c, uint32_t g, double ms, const int64_t** out) {
   int* ovf = (int*)(z + nh);
   std::vector<double> host(nh, 0.0);
   for (size_t j = 0; j < nh; j += g) host[j] = 1.0;
-  HE_CUDA(cudaMemcpy(z, host.data(), sizeof(double) * nh, cudaMemcpyHostToDevice));
-  HE_CUDA(cudaMemset(ovf, 0, sizeof(int)));
+  // stream-ordered: the context's stream may be a non-blocking one, which
+  // the legacy default stream's copies do not order against
+  HE_CUDA(cudaMemcpyAsync(z, host.data(), sizeof(double) * nh, cudaMemcpyHostToDevice, c->stream));
+  HE_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), c->stream));
   HE_TRY(encode_dev(c, z, nh, ms, d, fft, ovf));
   int flag = 0;
   HE_CUDA(cudaMemcpyAsync(&flag, ovf, sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -381,6 +381,9 @@ int build_tables(he_ctx* c) {
     HE_CUDA(cudaMalloc(&c->d_garner, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_garner, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }
+  // copies from pageable memory may still be in flight when cudaMemcpy
+  // returns; kernels on a non-blocking stream would not wait for them
+  HE_CUDA(cudaDeviceSynchronize());
   return HE_OK;
 }
 

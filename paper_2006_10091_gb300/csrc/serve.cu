@@ -170,6 +170,10 @@ static int enqueue_wave(Slot& sl, std::vector<ServeReq*>& wave) {
 static int launch_wave(he_server* s, Slot& sl, std::vector<ServeReq*>& wave) {
   const size_t ws_before = sl.view->ws.size;
   const int rc = enqueue_wave(sl, wave);
+  if (rc != HE_OK) {  // the scheduler thread's message, for he_server_last_error
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->error = he_last_error();
+  }
   for (ServeReq* q : wave) {
     q->status = rc;
     if (q->dev) cudaFreeAsync(q->dev, sl.stream);
@@ -388,6 +392,15 @@ extern "C" int he_server_stats(he_server* s, size_t* used, size_t* peak_used, si
   if (peak_used) *peak_used = s->peak_used;
   if (waves) *waves = s->waves;
   if (peak_running) *peak_running = s->peak_running;
+  return HE_OK;
+}
+
+extern "C" int he_server_last_error(he_server* s, char* buf, size_t cap) {
+  if (!s || !buf || cap == 0) return fail(HE_EINVAL, "he_server_last_error: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  const size_t k = std::min(cap - 1, s->error.size());
+  memcpy(buf, s->error.data(), k);
+  buf[k] = 0;
   return HE_OK;
 }
 
