@@ -42,9 +42,7 @@ size_t mul_words(const he_ctx* c, uint32_t level, uint32_t count, bool rescale);
 size_t rot_words(const he_ctx* c, uint32_t level, uint32_t count);
 size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count);
 
-// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts, 3 (with gal)
-// add the addend permuted to part 0 and the addend itself to both parts
-// (out = add + rotate(add) for a rotation of add).  gal != 0:
+// add_mode: 0 none, 1 add to part 0 only, 2 add to both parts.  gal != 0:
 // d and the addend are read through the automorphism X -> X^gal (fused
 // kernels only; the output must not overlap them).
 // merged: divide P * add + (the inner products) by P q_{level-1} with one

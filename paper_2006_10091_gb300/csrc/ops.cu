@@ -219,7 +219,6 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
   bool md_done = false;
   HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, &md_done));
   if (md_done) return HE_OK;
-  const CtBatch add_in = add;
   if (gal && add_mode) {  // the unfused combine reads its addend as it is: permute part 0 first
     uint64_t* pa = ar.take<uint64_t>((size_t)count * level * n);
     if (!pa) return fail(HE_ENOMEM, "key switch scratch too small");
@@ -228,10 +227,7 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
     HE_CUDA(cudaGetLastError());
     add = P;
   }
-  const int combine_mode = add_mode == 3 ? 1 : add_mode;  // mode 3 adds the unpermuted input afterwards
-  HE_TRY(moddown_unfused(c, acc, conv, add, combine_mode, out, level, count));
-  if (add_mode == 3) return addsub_batch(c, out, add_in, out, 0, level, count);
-  return HE_OK;
+  return moddown_unfused(c, acc, conv, add, add_mode, out, level, count);
 }
 
 int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch out, Arena& ar) {
