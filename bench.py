@@ -340,6 +340,7 @@ def run_ours(args, rank: int, world: int):
                    "scale_log2": 40, "samples": N_SAMPLES, "features": N_FEATURES,
                    "samples_per_ciphertext": G, "data_ciphertexts": nZ,
                    "l2": "inputs larger than L2 (1.07 GB of ciphertexts per step)",
+                   "scratch_budget_bytes": int(args.chunk_bytes) if args.chunk_bytes else None,
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "accuracy": {"max_rel_err_vs_fp64": rel_err, "gate": 2.0 ** -20, "ok": rel_err < 2.0 ** -20},
         "e2e": {"value": weak_scaling_value(1.0, world, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
@@ -1000,7 +1001,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the extra multiplication-rate lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--chunk-bytes", type=float, default=0, help="scratch budget of one batched operation")
+    ap.add_argument("--chunk-bytes", type=float, default=float(1 << 35),
+                    help="scratch budget of one batched operation (default 32 GiB: the step's 512 data "
+                         "ciphertexts in one batch)")
     ap.add_argument("--graph", action="store_true", help="replay the step as a captured CUDA graph")
     ap.add_argument("--alpha", type=int, default=None, help="special primes of the step's parameters")
     ap.add_argument("--special-bits", type=int, default=None)
