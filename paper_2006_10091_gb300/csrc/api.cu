@@ -180,9 +180,12 @@ int mul_plain_dev(he_ctx* c, CtBatch A, const int64_t* d_coeffs, CtBatch O, uint
   const size_t n = c->n;
   uint64_t* pt = ar.take<uint64_t>((size_t)level * n);
   if (!pt) return fail(HE_ENOMEM, "plaintext scratch too small");
-  k_signed_to_residues<<<grid_for((size_t)level * n), 256, 0, c->stream>>>(d_coeffs, pt, level, c->log_n,
-                                                                           c->d_primes);
-  HE_CUDA(cudaGetLastError());
+  {
+    ProfScope prof(c, "elementwise", 0.0, (double)level * n * 16);
+    k_signed_to_residues<<<grid_for((size_t)level * n), 256, 0, c->stream>>>(d_coeffs, pt, level, c->log_n,
+                                                                             c->d_primes);
+    HE_CUDA(cudaGetLastError());
+  }
   PolyBatch b;
   b.src = pt;
   b.dst = pt;
@@ -194,6 +197,7 @@ int mul_plain_dev(he_ctx* c, CtBatch A, const int64_t* d_coeffs, CtBatch O, uint
   b.skip_alpha = 0;
   b.skip_beta = 1;
   HE_TRY(ntt_forward(c, b));
+  ProfScope prof(c, "elementwise", 0.0, (double)(4 * count + 1) * level * n * 8);
   k_mul_plain<<<grid_for((size_t)count * level * n), 256, 0, c->stream>>>(A, pt, O, level, count, c->log_n,
                                                                           c->d_primes);
   HE_CUDA(cudaGetLastError());

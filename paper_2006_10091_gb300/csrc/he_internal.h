@@ -119,6 +119,7 @@ struct he_ctx {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> io_events;
   size_t io_piece = 0;             // data ciphertexts per copied piece (0: no pipelined input)
+  size_t io_first_chunk = 0;       // data ciphertexts of the step's first chunk (0: a full chunk)
   size_t io_pieces_waited = 0;     // pieces the step's stream already waits for
 
   size_t key_words() const { return (size_t)beta * 2 * np * n; }

@@ -345,15 +345,17 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
       return fail(HE_ENOMEM, "step scratch too small");
     if (!D3) return fail(HE_ENOMEM, "step scratch too small");
     HE_CUDA(cudaMemsetAsync(D3, 0, sizeof(uint64_t) * d3_stride * ns, c->stream));
-    // walk the group's data ciphertexts chunk by chunk
+    // walk the group's data ciphertexts chunk by chunk (a pipelined host
+    // input may ask for a shorter first chunk: only its copy is not overlapped)
     size_t gi = 0, idx = 0;  // shard position in grp, ciphertext index in that shard
+    size_t lim = c->io_first_chunk ? std::min(c->io_first_chunk, chunk) : chunk;
     while (gi < grp.size()) {
       // segments of this chunk: (group position, first ciphertext, count)
       std::vector<std::pair<size_t, std::pair<size_t, size_t>>> seg;
       size_t m = 0;
-      while (m < chunk && gi < grp.size()) {
+      while (m < lim && gi < grp.size()) {
         const Shard& s = sh[grp[gi]];
-        const size_t take = std::min(chunk - m, s.nZ - idx);
+        const size_t take = std::min(lim - m, s.nZ - idx);
         seg.push_back({gi, {idx, take}});
         m += take;
         idx += take;
@@ -400,6 +402,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
         }
       }
       HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops, infer));
+      lim = chunk;
       size_t off = 0;
       if (infer) {  // copy S_k of each segment's ciphertexts to their outputs
         for (auto& sg : seg) {
@@ -622,8 +625,9 @@ extern "C" int he_lr_gradient_step(he_ctx* c, const he_ct* Z, size_t nZ, const h
 
 // The step with its inputs and output in host memory: the weights, then the
 // data ciphertexts in pieces, are copied on a second stream while the circuit
-// runs chunk by chunk on the context's stream, each chunk waiting only for the
-// pieces it reads; the new weights are copied back at the end.
+// runs chunk by chunk on the context's stream (a short first chunk, then
+// chunks of the scratch budget), each chunk waiting only for the pieces it
+// reads; the new weights are copied back at the end.
 extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ, uint32_t z_level, double z_scale,
                                         const uint64_t* W, uint32_t w_level, double w_scale,
                                         const he_lr_config* cfg, uint64_t* out, size_t out_words,
@@ -676,12 +680,12 @@ extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ,
   HE_CUDA(cudaStreamWaitEvent(c->stream, c->io_events[0], 0));
   c->io_piece = piece;
   c->io_pieces_waited = 1;
-  // unless the caller chose a chunk, run the data in two chunks so that the
-  // second half's copy overlaps the first half's arithmetic
-  const uint32_t saved_chunk = c->lr_chunk;
-  if (!saved_chunk && nZ > 2 * piece) c->lr_chunk = (uint32_t)(((nZ + 1) / 2 + piece - 1) / piece * piece);
+  // unless the caller chose a chunk, the first chunk is an eighth of the data
+  // (whole pieces): only its copy is exposed, the rest's copy overlaps its
+  // arithmetic; the later chunks follow the scratch budget
+  if (!c->lr_chunk && nZ > 2 * piece) c->io_first_chunk = std::max(piece, nZ / 8 / piece * piece);
   const int rc = lr_entry(c, &sh, 1, cfg, 0, 0, false);
-  c->lr_chunk = saved_chunk;
+  c->io_first_chunk = 0;
   c->io_piece = 0;
   if (rc != HE_OK) {
     cudaStreamSynchronize(c->copy_stream);

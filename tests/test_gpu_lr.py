@@ -241,9 +241,10 @@ def test_extreme_packings_bit_exact(g):
 
 
 def test_host_input_step_matches_device_step():
-    """The step on host buffers (copies overlapped with the circuit, here in
-    many chunks) gives the residues of the step on device buffers, at a ring
-    size with the fused kernels and a ragged number of data ciphertexts."""
+    """The step on host buffers (copies overlapped with the circuit, in chunks
+    of 5 and in the library's own short first chunk and budget-sized rest)
+    gives the residues of the step on device buffers, at a ring size with the
+    fused kernels and a ragged number of data ciphertexts."""
     import torch
     log_n, g = 12, 8
     n_slots = (1 << log_n) // 2
@@ -264,10 +265,15 @@ def test_host_input_step_matches_device_step():
     he.he_ct_export_batch(ctx, Z, zh)
     wh = he.he_ct_export(ctx, W)
     oh = np.zeros((2, 2, ctx.n), dtype=np.uint64)
-    for _ in range(2):  # the second call reuses the device buffers and events
-        level, scale = he.he_lr_gradient_step_host(ctx, zh, 7, 2.0 ** 40, wh, 7, 2.0 ** 40, cfg, oh)
-        assert level == 2 and scale == out.scale
-        assert np.array_equal(oh, want)
+    # chunks of 5; then the library's own: a first chunk of one 16-ciphertext
+    # piece, the rest in one chunk of the budget
+    for chunk in (5, 0):
+        he.he_set_tuning(ctx, "lr_chunk", chunk)
+        for _ in range(2):  # the second call reuses the device buffers and events
+            oh[:] = 0
+            level, scale = he.he_lr_gradient_step_host(ctx, zh, 7, 2.0 ** 40, wh, 7, 2.0 ** 40, cfg, oh)
+            assert level == 2 and scale == out.scale
+            assert np.array_equal(oh, want), chunk
     with pytest.raises(he.HeError) as e:
         he.he_lr_gradient_step_host(ctx, zh, 7, 2.0 ** 40, wh[:, :5].copy(), 5, 2.0 ** 40, cfg, oh)
     assert e.value.code == he.HE_ELEVEL

@@ -456,6 +456,62 @@ def test_fused_keyswitch_many_digits(he):
     assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1)
 
 
+@pytest.mark.parametrize("log_n", [14, 16])
+def test_ntt_largest_primes(he, log_n):
+    """Limb primes just below 2^58 (the largest whose forward butterflies skip
+    the correction: values reach 33q) and special primes just below 2^61 (the
+    largest allowed: corrected butterflies reach 4q), on inputs all q - 1 and
+    on uniform ones: bit-exact against the oracle's radix-2 transform, and the
+    inverse restores the input, for every compiled tile shape."""
+    import torch
+    ctx = he.Context(log_n, 2, 58, 1, 61, 2.0 ** 40, seed=5)
+    n = 1 << log_n
+    data = workloads.residues(300 + log_n, ctx.primes, n, parts=2)
+    for k, q in enumerate(ctx.primes):
+        data[0, k, :] = q - 1
+    assert ctx.primes[0] > 2 ** 57 and ctx.primes[2] > 2 ** 60
+    want = [[oracle.ntt_r2(data[p, k], log_n, q, oracle.min_root(q, log_n)) for k, q in enumerate(ctx.primes)]
+            for p in range(2)]
+    for shape in (0, 1, 2):
+        he.he_set_tuning(ctx, "ntt_shape", shape)
+        t = torch.from_numpy(data.view(np.int64).copy()).cuda()
+        he.he_ntt(ctx, t, 2, 3 * n, 3, 0, False)
+        got = t.cpu().numpy().view(np.uint64)
+        for p in range(2):
+            for k in range(3):
+                assert np.array_equal(got[p, k], want[p][k]), (shape, p, k)
+        he.he_ntt(ctx, t, 2, 3 * n, 3, 0, True)
+        assert np.array_equal(t.cpu().numpy().view(np.uint64), data), shape
+    he.he_set_tuning(ctx, "ntt_shape", 0)
+
+
+def test_keyswitch_largest_primes(he):
+    """Key switching, rotation and multiplication with 58-bit limbs and a
+    61-bit special prime (fused conversions and transforms at the largest
+    prime of each butterfly kind), on a digit input of all q - 1 as well."""
+    import torch
+    p = Pair(14, 3, 58, 1, 61, 2.0 ** 40, seed=21, rots=[1])
+    for fill in (False, True):
+        d = workloads.residues(910, p.o.primes[:3], p.n)[0]
+        if fill:
+            for k in range(3):
+                d[k, :] = p.o.primes[k] - 1
+        k0, k1 = p.o.keyswitch(d, 3, -1)
+        dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+        he.he_keyswitch(p.g, dt, 3, 0, o0, o1)
+        assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0), fill
+        assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1), fill
+    m1, m2 = workloads.int_poly(71, p.n, 1 << 36), workloads.int_poly(72, p.n, 1 << 36)
+    ga, oa = p.gpu_enc(m1, 3, 71), p.orc_enc(m1, 3, 71)
+    gb, ob = p.gpu_enc(m2, 3, 72), p.orc_enc(m2, 3, 72)
+    out = p.g.new_ct(3)
+    he.he_rotate(p.g, ga, 1, out)
+    assert_same_residues(out, p.o.rotate(oa, 1), he, p.g)
+    he.he_mul_relin_rescale(p.g, ga, gb, out)
+    assert_same_residues(out, p.o.mul_relin_rescale(oa, ob), he, p.g)
+
+
 def test_fused_rotation_and_mul_bit_exact(wide, he):
     m1, m2 = workloads.int_poly(61, wide.n, 1 << 36), workloads.int_poly(62, wide.n, 1 << 36)
     ga, oa = wide.gpu_enc(m1, 5, 61), wide.orc_enc(m1, 5, 61)
