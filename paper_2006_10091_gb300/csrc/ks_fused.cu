@@ -111,9 +111,13 @@ namespace he {
 static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);
 
 int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
+                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool half,
+                  bool* handled) {
   *handled = false;
-  if (!ks_fusable(c) || n_gal > HE_MAX_ROT) return HE_OK;
+  if (!ks_fusable(c) || n_gal > HE_MAX_ROT) {
+    if (half) return fail(HE_EINVAL, "md_fused: half-transformed input needs the fused kernels");
+    return HE_OK;
+  }
   const uint32_t nt = level + (uint32_t)c->alpha;
   MdArgs a;
   a.n_gal = n_gal;
@@ -134,13 +138,15 @@ int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t*
   a.L = (uint32_t)c->L;
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.itw = reinterpret_cast<const ulonglong2*>(c->d_itw);
+  a.half = half;
   a.md = c->d_moddown;
   return md_dispatch(c, a, count, handled);
 }
 
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled) {
-  return md_fused_gals(c, acc, acc_stride, conv, add, add_mode, &add_gal, add_gal ? 1 : 0, out, level, count,
+             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool half, bool* handled) {
+  return md_fused_gals(c, acc, acc_stride, conv, add, add_mode, &add_gal, add_gal ? 1 : 0, out, level, count, half,
                        handled);
 }
 
@@ -150,9 +156,12 @@ int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv
 // to the level-1 remaining limbs, and out_t = (acc_t - NTT(conv_t)) (P q_{level-1})^-1
 // + d_t q_{level-1}^-1 (the addend d on both parts).
 int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, CtBatch out,
-                     uint32_t level, uint32_t count, bool* handled) {
+                     uint32_t level, uint32_t count, bool half, bool* handled) {
   *handled = false;
-  if (!ks_fusable(c) || !c->d_mdrs || level < 2) return HE_OK;
+  if (!ks_fusable(c) || !c->d_mdrs || level < 2) {
+    if (half) return fail(HE_EINVAL, "md_fused: half-transformed input needs the fused kernels");
+    return HE_OK;
+  }
   const uint32_t nt = level + (uint32_t)c->alpha, lo = level - 1;
   MdArgs a;
   a.n_gal = 0;
@@ -173,6 +182,8 @@ int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64
   a.L = (uint32_t)c->L;
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.itw = reinterpret_cast<const ulonglong2*>(c->d_itw);
+  a.half = half;
   a.md = c->d_mdrs + (size_t)level * c->mdrs_words;
   return md_dispatch(c, a, count, handled);
 }
@@ -180,9 +191,12 @@ int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64
 // Rescale by q_{l-1} as a ModDown by that one prime, fused the same way.
 // last: the dropped limb of both parts in coefficient form, count x [2][N].
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
-             uint32_t count, bool* handled) {
+             uint32_t count, bool half, bool* handled) {
   *handled = false;
-  if (!ks_fusable(c) || level < 2) return HE_OK;
+  if (!ks_fusable(c) || level < 2) {
+    if (half) return fail(HE_EINVAL, "md_fused: half-transformed input needs the fused kernels");
+    return HE_OK;
+  }
   const uint32_t lt = level - 1;
   MdArgs a;
   a.n_gal = 0;
@@ -202,6 +216,8 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
   a.L = (uint32_t)c->L;
   a.primes = c->d_primes;
   a.tw = reinterpret_cast<const ulonglong2*>(c->d_tw);
+  a.itw = reinterpret_cast<const ulonglong2*>(c->d_itw);
+  a.half = half;
   a.md = c->d_rescale_md + (size_t)lt * c->rescale_md_words;
   return md_dispatch(c, a, count, handled);
 }
@@ -219,6 +235,22 @@ static int md_dispatch(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled
 }  // namespace he
 
 namespace he {
+
+// Whether the fused ModDown (or rescale) with nd dropped limbs runs, so that
+// its conversion kernel can finish the dropped limbs' inverse transform
+// (the caller then runs only its row pass).
+bool md_half_ok(const he_ctx* c, uint32_t nd) {
+  if (!ks_fusable(c)) return false;
+  size_t smem = 0;
+  switch (c->log_n) {
+    case 12: smem = md_col_smem_n12(c, nd); break;
+    case 13: smem = md_col_smem_n13(c, nd); break;
+    case 14: smem = md_col_smem_n14(c, nd); break;
+    case 15: smem = md_col_smem_n15(c, nd); break;
+    default: smem = md_col_smem_n16(c, nd); break;
+  }
+  return smem <= kModupAllSmem;
+}
 
 // Whether the fused key switch at this level converts each digit in one CTA
 // (then it can finish the inverse transform of its input itself).

@@ -387,6 +387,8 @@ struct MdArgs {
   const uint64_t* addw;        // the addend is multiplied by these Shoup pairs per target limb (nullptr: not)
   const PrimeDev* primes;
   const ulonglong2* tw;
+  const ulonglong2* itw;  // inverse twiddles (half)
+  int half;               // yP holds only the inverse transform's row pass: md_conv_col finishes it
   const uint64_t* md;   // ModDown tables (params.cu)
 };
 
@@ -413,18 +415,35 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   const uint64_t* yP = a.yP + (size_t)i * a.yp_stride + (size_t)p * a.yp_pstride;
   // exact conversion: sum_u w_u (P/p_u) - v P, w_u = [y_u (P/p_u)^-1]_{p_u},
   // v = floor(sum_u w_u / p_u)
+  for (uint32_t u = 0; u < a.alpha; ++u) {
+    const PrimeDev pp = a.primes[a.spr[u]];
+    const uint64_t* src = yP + (size_t)u * N;
+    if (a.half) {
+      // the inverse transform's column pass on this tile, then the scaling by N^-1
+      stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.itw + (size_t)a.spr[u] * N, tile);
+#pragma unroll 4
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T)
+        sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx & (S::K - 1), idx >> LOG_K));
+      __syncthreads();
+      run_rounds<true, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pp.q);
+    }
+#pragma unroll 2
+    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+      const uint64_t y0 = a.half ? mul_shoup(sm[idx + (idx >> 3)], pp.n_inv, pp.n_inv_sh, pp.q)
+                                 : __ldg(src + S::gidx(tile, idx & (S::K - 1), idx >> LOG_K));
+      const uint64_t y = add_mod(y0, hP[u], pp.q);
+      wv[(size_t)u * S::TILE + idx] = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
+    }
+    // the next limb's staging overwrites stw and sm: wait for every thread
+    if (a.half) __syncthreads();
+  }
 #pragma unroll 2
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-    const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
     uint64_t fs = 0;
     uint32_t v = 0;
-    for (uint32_t u = 0; u < a.alpha; ++u) {
-      const PrimeDev& pp = a.primes[a.spr[u]];
-      const uint64_t y = add_mod(__ldg(yP + (size_t)u * N + e), hP[u], pp.q);
-      const uint64_t w = mul_shoup(y, a.md[2 * u], a.md[2 * u + 1], pp.q);
-      wv[(size_t)u * S::TILE + idx] = w;
-      if (a.alpha > 1) frac_acc(w, pp.one_sh, wlo[u], &fs, &v);
-    }
+    if (a.alpha > 1)
+      for (uint32_t u = 0; u < a.alpha; ++u)
+        frac_acc(wv[(size_t)u * S::TILE + idx], a.primes[a.spr[u]].one_sh, wlo[u], &fs, &v);
     vv[idx] = v;
   }
   for (uint32_t t = 0; t < a.level; ++t) {
@@ -517,15 +536,23 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
   }
 }
 
+// Shared memory of md_conv_col with nd dropped limbs.
+template <int LOG_N, int M1, int K1>
+size_t md_col_smem(uint32_t nd) {
+  using SC = Shape<LOG_N, M1, K1, true>;
+  return sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
+         (sizeof(uint64_t) * nd + sizeof(uint32_t)) * SC::TILE;
+}
+
 template <int LOG_N, int M1, int K1, int M2, int K2>
 int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   using SC = Shape<LOG_N, M1, K1, true>;
   using SR = Shape<LOG_N, M2, K2, false>;
-  const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8) +
-                     (sizeof(uint64_t) * a.alpha + sizeof(uint32_t)) * SC::TILE;
+  const size_t smc = md_col_smem<LOG_N, M1, K1>(a.alpha);
   const size_t smr = sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8);
   if (smc > kModupAllSmem) {  // too many special primes for this tile: the caller runs the unfused sequence
     *handled = false;
+    if (a.half) return fail(HE_EINVAL, "md_fused: half-transformed input needs the fused kernels");
     return HE_OK;
   }
   *handled = true;
@@ -543,7 +570,8 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
                                                                        : "moddown_ntt_combine";
   {
     const size_t blocks = (size_t)count * 2 * SC::TILES;
-    ProfScope prof(c, nm_col, polys * (n / 2 * M1 + n * a.alpha),
+    // with a half-transformed input, also the dropped limbs' inverse column pass
+    ProfScope prof(c, nm_col, polys * (n / 2 * M1 + n * a.alpha) + (a.half ? 2.0 * count * a.alpha * n / 2 * M1 : 0.0),
                    n * 8 * (2.0 * count * a.alpha + polys));
     md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
@@ -682,6 +710,7 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
   int ks_rot_n##NN(he_ctx* c, const KsRotArgs& a, uint32_t count, bool* handled, int* closed); \
   size_t ks_rot_smem_n##NN(const he_ctx* c, uint32_t beta);                          \
   int md_fused_n##NN(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled);     \
+  size_t md_col_smem_n##NN(const he_ctx* c, uint32_t nd);                            \
   size_t ks_all_smem_n##NN(const he_ctx* c, uint32_t beta, const uint32_t* cnt);
 HE_KS_FUSED_DECL(12)
 HE_KS_FUSED_DECL(13)

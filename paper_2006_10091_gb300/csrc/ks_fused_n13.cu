@@ -21,6 +21,12 @@ int md_fused_n13(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
        : sh == 2 ? md_fused_run<13, 4, 7, 9, 2>(c, a, count, handled) : md_fused_run<13, 7, 4, 6, 5>(c, a, count, handled);
 }
 
+size_t md_col_smem_n13(const he_ctx* c, uint32_t nd) {
+  const int sh = c->ntt_shape;
+  return sh == 1 ? md_col_smem<13, 6, 5>(nd)
+       : sh == 2 ? md_col_smem<13, 4, 7>(nd) : md_col_smem<13, 7, 4>(nd);
+}
+
 size_t ks_all_smem_n13(const he_ctx* c, uint32_t beta, const uint32_t* cnt) {
   const int sh = c->ntt_shape;
   return sh == 1 ? ks_all_smem<13, 6, 5>(c, beta, cnt)

@@ -16,19 +16,21 @@
 
 namespace he {
 bool ks_converts_per_digit(const he_ctx* c, uint32_t level);
+bool md_half_ok(const he_ctx* c, uint32_t nd);
 int ntt2_inverse_rows(he_ctx* c, const PolyBatch& b);
 int md_fused(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
+             uint64_t add_gal, CtBatch out, uint32_t level, uint32_t count, bool half, bool* handled);
 int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatch out, uint32_t level,
-             uint32_t count, bool* handled);
+             uint32_t count, bool half, bool* handled);
 bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
            const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced,
            uint64_t in_gal = 0);
 int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
-                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool* handled);
+                  const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool half,
+                  bool* handled);
 int md_fused_rescale(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, CtBatch out,
-                     uint32_t level, uint32_t count, bool* handled);
+                     uint32_t level, uint32_t count, bool half, bool* handled);
 }
 
 namespace he {
@@ -207,17 +209,25 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
           c->d_primes);
     }
     HE_CUDA(cudaGetLastError());
-    HE_TRY(ntt_inverse(c, pb(acc + (size_t)lo * n, acc + (size_t)lo * n, (size_t)nt * n, (size_t)nt * n, count * 2,
-                             alpha + 1, lo, level)));
+    // the dropped limbs to coefficient form (only the row pass when the
+    // fused conversion kernel finishes the transform)
+    const bool mh = md_half_ok(c, alpha + 1);
+    const PolyBatch bd = pb(acc + (size_t)lo * n, acc + (size_t)lo * n, (size_t)nt * n, (size_t)nt * n, count * 2,
+                            alpha + 1, lo, level);
+    HE_TRY(mh ? ntt2_inverse_rows(c, bd) : ntt_inverse(c, bd));
     bool done = false;
-    HE_TRY(md_fused_rescale(c, acc, (size_t)2 * nt * n, conv, add, out, level, count, &done));
+    HE_TRY(md_fused_rescale(c, acc, (size_t)2 * nt * n, conv, add, out, level, count, mh, &done));
     if (done) return HE_OK;
     return moddown_unfused(c, acc, conv, add, 2, out, level, count, true);
   }
-  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n,
-                           (size_t)nt * n, count * 2, alpha, level, level)));
+  const bool mh = md_half_ok(c, alpha);
+  {
+    const PolyBatch bd = pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
+                            count * 2, alpha, level, level);
+    HE_TRY(mh ? ntt2_inverse_rows(c, bd) : ntt_inverse(c, bd));
+  }
   bool md_done = false;
-  HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, &md_done));
+  HE_TRY(md_fused(c, acc, (size_t)2 * nt * n, conv, add, add_mode, gal, out, level, count, mh, &md_done));
   if (md_done) return HE_OK;
   if (gal && add_mode) {  // the unfused combine reads its addend as it is: permute part 0 first
     uint64_t* pa = ar.take<uint64_t>((size_t)count * level * n);
@@ -236,11 +246,14 @@ int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch
   uint64_t* last = ar.take<uint64_t>((size_t)count * 2 * n);
   uint64_t* corr = ar.take<uint64_t>((size_t)count * 2 * lt * n);
   if (!last || !corr) return fail(HE_ENOMEM, "rescale scratch too small");
-  for (uint32_t p = 0; p < 2; ++p)
-    HE_TRY(ntt_inverse(c, pb(in.base + ((size_t)p * in.cap + lt) * n, last + (size_t)p * n, in.stride,
-                             2ull * n, count, 1, lt, c->L)));
+  const bool mh = md_half_ok(c, 1);  // the fused kernel finishes the inverse transform
+  for (uint32_t p = 0; p < 2; ++p) {
+    const PolyBatch bd = pb(in.base + ((size_t)p * in.cap + lt) * n, last + (size_t)p * n, in.stride, 2ull * n,
+                            count, 1, lt, c->L);
+    HE_TRY(mh ? ntt2_inverse_rows(c, bd) : ntt_inverse(c, bd));
+  }
   bool fused = false;  // correction, NTT and division fused like ModDown's
-  HE_TRY(rs_fused(c, in, last, corr, out, level, count, &fused));
+  HE_TRY(rs_fused(c, in, last, corr, out, level, count, mh, &fused));
   if (fused) return HE_OK;
   {
     ProfScope prof(c, "rescale", (double)count * 2 * n * lt, (double)count * 2 * n * 8 * (1 + lt));
@@ -357,10 +370,14 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     HE_CUDA(cudaGetLastError());
   }
   // ModDown of the summed inner products, plus A0 + sum_r kappa_r(A0) and A1
-  HE_TRY(ntt_inverse(c, pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
-                           count * 2, alpha, level, level)));
+  const bool mh = md_half_ok(c, alpha);
+  {
+    const PolyBatch bd = pb(acc + (size_t)level * n, acc + (size_t)level * n, (size_t)nt * n, (size_t)nt * n,
+                            count * 2, alpha, level, level);
+    HE_TRY(mh ? ntt2_inverse_rows(c, bd) : ntt_inverse(c, bd));
+  }
   bool md_done = false;
-  HE_TRY(md_fused_gals(c, acc, acc_stride, conv, A, 3, gals, nrot, out, level, count, &md_done));
+  HE_TRY(md_fused_gals(c, acc, acc_stride, conv, A, 3, gals, nrot, out, level, count, mh, &md_done));
   if (md_done) return HE_OK;
   uint64_t* sa = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!sa) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
