@@ -9,9 +9,11 @@
 //      basis conversion, coefficient form), then forward NTT of the converted
 //      limbs (the digit's own limbs are taken from d as they are);
 //   3. inner product with the switching key, two accumulators over l + alpha limbs;
-//   4. ModDown: inverse NTT of the special limbs, conversion of (y + h) to
-//      each q_t minus h (h = (P-1)/2, so that the division by P rounds),
-//      forward NTT, out_t = (acc_t - conv_t) * P^-1 (+ an optional addend).
+//   4. ModDown: inverse NTT of the special limbs (the fused path runs only
+//      its row pass here; the conversion kernel does the column pass),
+//      conversion of (y + h) to each q_t minus h (h = (P-1)/2, so that the
+//      division by P rounds), forward NTT, out_t = (acc_t - conv_t) * P^-1
+//      (+ an optional addend).
 #include "he_ops.h"
 
 namespace he {
