@@ -363,9 +363,10 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
 }
 
 // ---- ModDown, fused the same way ------------------------------------------
-// The P-part of the accumulators (coefficient form after its inverse NTT) is
-// converted to each target limb inside the load of the forward NTT's column
-// pass (as k_moddown_conv: conv = BConv(y + h) - h), and the row pass ends
+// The P-part of the accumulators (coefficient form after its inverse NTT,
+// whose column pass md_conv_col runs itself when only the row pass was run
+// before it) is converted to each target limb inside the load of the forward
+// NTT's column pass (as k_moddown_conv: conv = BConv(y + h) - h), and the row pass ends
 // with the combine of k_ks_combine: out = add + (acc_Q - NTT(conv)) * P^-1.
 // A CTA handles both parts of one ciphertext for one limb and tile, so the
 // staged twiddles serve two transforms.
