@@ -512,6 +512,44 @@ def test_keyswitch_largest_primes(he):
     assert_same_residues(out, p.o.mul_relin_rescale(oa, ob), he, p.g)
 
 
+def test_moddown_fused_and_unfused_after_fused_keyswitch(he):
+    """N = 2^15 with four special primes: in the (8, 4) column shape the
+    conversion kernel would need more shared memory than it may take, so a
+    fused decomposition and row kernel are followed by the unfused ModDown
+    (full inverse transform first); in the other shapes the conversion kernel
+    finishes the dropped limbs' inverse transform itself.  Key switching, the
+    multiplication (ModDown merged with the rescale), a rescale, a rotation
+    and a hoisted rotate-and-sum, bit-exact in every shape."""
+    import torch
+    p = Pair(15, 3, 40, 4, 50, 2.0 ** 40, seed=31, rots=[1, 2, 3])
+    d = workloads.residues(930, p.o.primes[:3], p.n)[0]
+    k0, k1 = p.o.keyswitch(d, 3, -1)
+    m1, m2 = workloads.int_poly(931, p.n, 1 << 36), workloads.int_poly(932, p.n, 1 << 36)
+    ga, oa = p.gpu_enc(m1, 3, 931), p.orc_enc(m1, 3, 931)
+    gb, ob = p.gpu_enc(m2, 3, 932), p.orc_enc(m2, 3, 932)
+    want_mul = p.o.mul_relin_rescale(oa, ob)
+    want_rs = p.o.rescale(oa)
+    want_rot = p.o.rotate(oa, 2)
+    want_sum = p.o.rotate_sum(oa, [1, 2, 3])
+    dt = torch.from_numpy(d.view(np.int64).copy()).cuda()
+    for shape in (0, 1, 2):
+        he.he_set_tuning(p.g, "ntt_shape", shape)
+        o0, o1 = torch.empty_like(dt), torch.empty_like(dt)
+        he.he_keyswitch(p.g, dt, 3, 0, o0, o1)
+        assert np.array_equal(o0.cpu().numpy().view(np.uint64), k0), shape
+        assert np.array_equal(o1.cpu().numpy().view(np.uint64), k1), shape
+        out = p.g.new_ct(3)
+        he.he_mul_relin_rescale(p.g, ga, gb, out)
+        assert_same_residues(out, want_mul, he, p.g)
+        he.he_rescale(p.g, ga, out)
+        assert_same_residues(out, want_rs, he, p.g)
+        he.he_rotate(p.g, ga, 2, out)
+        assert_same_residues(out, want_rot, he, p.g)
+        he.he_rotate_sum(p.g, ga, [1, 2, 3], out)
+        assert_same_residues(out, want_sum, he, p.g)
+    he.he_set_tuning(p.g, "ntt_shape", 0)
+
+
 def test_fused_rotation_and_mul_bit_exact(wide, he):
     m1, m2 = workloads.int_poly(61, wide.n, 1 << 36), workloads.int_poly(62, wide.n, 1 << 36)
     ga, oa = wide.gpu_enc(m1, 5, 61), wide.orc_enc(m1, 5, 61)
