@@ -310,7 +310,7 @@ def run_ours(args, rank: int, world: int):
     host_step = lambda: he.he_lr_gradient_step_host(ctx, host_in, L, SCALE, host_w[0], L, SCALE, cfg,  # noqa: E731
                                                     host_out)
     host_step()  # grows the device input buffer
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
