@@ -804,12 +804,16 @@ def run_reference(args, rank: int):
 
 def run_micro(args):
     """One kernel class alone: forward/inverse NTT over `--polys` polynomials
-    of 8 limbs at N = 2^log_n (more than L2), timed with CUDA events."""
+    of 8 limbs at N = 2^log_n (more than L2), timed with CUDA events.  Each
+    rate is also given as a fraction of the register-resident radix-8 lazy
+    butterfly chain (he_probe_alu kind 2: the same butterflies with no memory
+    traffic), beside the fraction of the Shoup-product roof."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2006_10091_gb300 as he
     measure_alu_peak(he)
+    bfly_roof = he.he_probe_alu(2)["per_second"]
     from paper_2006_10091_gb300 import workloads
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -841,9 +845,11 @@ def run_micro(args):
         bfly = limbs * (n / 2) * log_n
         out[("intt" if inverse else "ntt") + ("_runtime_shaped" if generic else f"_shape{shape}" if shape else "")] = {
             "ms": ms, "Gbutterfly_s": bfly / ms / 1e6, "alu_frac": bfly / (ms * 1e-3) / ALU_PEAK["per_second"],
+            "butterfly_chain_frac": bfly / (ms * 1e-3) / bfly_roof,
             "algorithmic_GBs_2pass": limbs * n * 32 / ms / 1e6 if log_n > 11 else limbs * n * 16 / ms / 1e6}
     he.he_set_tuning(ctx, "ntt_generic", False)
-    print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps, **out}))
+    print(json.dumps({"micro": "ntt", "N": n, "limbs": args.polys * nl, "steps": args.steps,
+                      "butterfly_chain_per_s": bfly_roof, **out}))
 
 
 def run_micro_keyswitch(args):
