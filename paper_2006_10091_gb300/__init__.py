@@ -269,6 +269,12 @@ def _batch(cts):
     return arr
 
 
+def _same_len(name: str, first: list, *others: list) -> None:
+    # the C entry points take one count for all their arrays
+    if any(len(o) != len(first) for o in others):
+        raise ValueError(f"{name}: the batches must have the same length")
+
+
 # ---------------------------------------------------------------------------
 # Entry points (names of the C ABI)
 # ---------------------------------------------------------------------------
@@ -423,6 +429,7 @@ def he_rotate_sum(ctx, a, steps, out):
 
 
 def he_rotate_sum_batch(ctx, a: list, steps, out: list):
+    _same_len("he_rotate_sum_batch", a, out)
     st = (ctypes.c_int32 * len(steps))(*steps)
     A, O = _batch(a), _batch(out)
     _check(load().he_rotate_sum_batch(ctx.ptr, A, st, len(steps), O, len(a)))
@@ -432,6 +439,7 @@ def he_rotate_sum_batch(ctx, a: list, steps, out: list):
 
 
 def he_mul_relin_rescale_batch(ctx, a: list, b: list, out: list):
+    _same_len("he_mul_relin_rescale_batch", a, b, out)
     A, B, O = _batch(a), _batch(b), _batch(out)
     _check(load().he_mul_relin_rescale_batch(ctx.ptr, A, B, O, len(a)))
     for o, s in zip(out, O):
@@ -440,6 +448,7 @@ def he_mul_relin_rescale_batch(ctx, a: list, b: list, out: list):
 
 
 def he_rotate_batch(ctx, a: list, steps: int, out: list):
+    _same_len("he_rotate_batch", a, out)
     A, O = _batch(a), _batch(out)
     _check(load().he_rotate_batch(ctx.ptr, A, steps, O, len(a)))
     for o, s in zip(out, O):
@@ -535,6 +544,7 @@ def _shards(shards, infer):
         cid = sh[3] if len(sh) > 3 else 0x40000000 + k
         zs, w = _batch(Z), W.c()
         if infer:
+            _same_len("inference shard", Z, out)
             so = _batch(out)
             keep.append((zs, w, so))
             arr[k] = he_lr_shard(ctypes.cast(zs, ctypes.c_void_p), len(Z), ctypes.addressof(w), None,
@@ -565,6 +575,8 @@ def he_lr_gradient_step_host(ctx, Z_host, z_level: int, z_scale: float, W_host, 
     """The step on host buffers (numpy uint64 arrays or pinned CPU torch tensors):
     Z_host [nZ][2][z_level][N], W_host [2][w_level][N], out_host >= [2][w_level-5][N].
     Returns (level, scale) of the result."""
+    if (_nwords(Z_host) < Z_host.shape[0] * 2 * z_level * ctx.n or _nwords(W_host) < 2 * w_level * ctx.n):
+        raise ValueError("he_lr_gradient_step_host: host arrays smaller than their ciphertexts")
     lv, sc = ctypes.c_uint32(), ctypes.c_double()
     _check(load().he_lr_gradient_step_host(ctx.ptr, ctypes.c_void_p(_addr(Z_host)), Z_host.shape[0], z_level,
                                            float(z_scale), ctypes.c_void_p(_addr(W_host)), w_level, float(w_scale),
@@ -616,6 +628,8 @@ def he_keyswitch(ctx, d, level: int, galois: int, out0, out1):
 
 def he_ct_import_batch(ctx, host, level: int, scale: float, out: list):
     """host: uint64 array [count][2][level][N] (pinned memory copies fastest)."""
+    if _nwords(host) < len(out) * 2 * level * ctx.n:
+        raise ValueError("he_ct_import_batch: host array smaller than the ciphertexts")
     O = _batch(out)
     _check(load().he_ct_import_batch(ctx.ptr, ctypes.c_void_p(_addr(host)), level, float(scale), O, len(out)))
     for o, s in zip(out, O):
