@@ -140,6 +140,8 @@ static void destroy(he_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (cudaEvent_t e : c->io_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->io_time)
+    if (e) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   cudaFree(c->io.ptr);
   if (c->view) {  // only the view's own state

@@ -120,6 +120,10 @@ struct he_ctx {
   std::vector<cudaEvent_t> io_events;
   size_t io_piece = 0;             // data ciphertexts per copied piece (0: no pipelined input)
   size_t io_first_chunk = 0;       // data ciphertexts of the step's first chunk (0: a full chunk)
+  // timing of the last host-input step: its copies (copy stream) and its
+  // first chunk's arithmetic (step stream); sizes the next first chunk
+  cudaEvent_t io_time[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t io_timed_nZ = 0, io_timed_first = 0;  // ciphertexts the events cover (0: none)
   size_t io_pieces_waited = 0;     // pieces the step's stream already waits for
 
   size_t key_words() const { return (size_t)beta * 2 * np * n; }

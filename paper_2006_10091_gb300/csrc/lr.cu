@@ -349,6 +349,7 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
     // input may ask for a shorter first chunk: only its copy is not overlapped)
     size_t gi = 0, idx = 0;  // shard position in grp, ciphertext index in that shard
     size_t lim = c->io_first_chunk ? std::min(c->io_first_chunk, chunk) : chunk;
+    bool time_first = c->io_first_chunk && c->io_time[2];  // the first chunk's arithmetic, timed
     while (gi < grp.size()) {
       // segments of this chunk: (group position, first ciphertext, count)
       std::vector<std::pair<size_t, std::pair<size_t, size_t>>> seg;
@@ -401,7 +402,13 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
           c->io_pieces_waited = need;
         }
       }
+      if (time_first) HE_CUDA(cudaEventRecord(c->io_time[2], c->stream));
       HE_TRY(lr_chunk(c, P, gl, Zc, Wc, (uint32_t)m, b, ops, infer));
+      if (time_first) {
+        HE_CUDA(cudaEventRecord(c->io_time[3], c->stream));
+        c->io_timed_first = m;
+        time_first = false;
+      }
       lim = chunk;
       size_t off = 0;
       if (infer) {  // copy S_k of each segment's ciphertexts to their outputs
@@ -662,9 +669,29 @@ extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ,
   uint64_t* dZ = (uint64_t*)c->io.ptr;
   uint64_t* dW = dZ + zw * nZ;
   uint64_t* dO = dW + ww;
+  for (cudaEvent_t& e : c->io_time)
+    if (!e) HE_CUDA(cudaEventCreate(&e));
+  // the first chunk (whole pieces): only its copy is exposed, the rest's copy
+  // overlaps its arithmetic.  From the previous call's timings, the smallest
+  // f with (nZ - f) * copy <= f * arithmetic per ciphertext; else an eighth.
+  size_t first_chunk = std::max(piece, nZ / 8 / piece * piece);
+  if (c->io_timed_nZ && c->io_timed_first) {
+    float copy_ms = 0.f, arith_ms = 0.f;
+    if (cudaEventElapsedTime(&copy_ms, c->io_time[0], c->io_time[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&arith_ms, c->io_time[2], c->io_time[3]) == cudaSuccess && copy_ms > 0.f &&
+        arith_ms > 0.f) {
+      const double cp = copy_ms / (double)c->io_timed_nZ, ar = arith_ms / (double)c->io_timed_first;
+      const size_t f = (size_t)ceil((double)nZ * cp / (cp + ar) / (double)piece) * piece;
+      first_chunk = std::min(std::max(f, piece), std::max(piece, nZ / 2 / piece * piece));
+    } else {
+      cudaGetLastError();  // events of a call that failed: keep the default
+    }
+  }
+  c->io_timed_nZ = c->io_timed_first = 0;
   // the copy stream may overwrite the buffers only after the previous step on c->stream is done with them
   HE_CUDA(cudaEventRecord(c->io_events[pieces], c->stream));
   HE_CUDA(cudaStreamWaitEvent(c->copy_stream, c->io_events[pieces], 0));
+  HE_CUDA(cudaEventRecord(c->io_time[0], c->copy_stream));
   HE_CUDA(cudaMemcpyAsync(dW, W, sizeof(uint64_t) * ww, cudaMemcpyHostToDevice, c->copy_stream));
   for (size_t k = 0; k < pieces; ++k) {
     const size_t first = k * piece, cnt = std::min(piece, nZ - first);
@@ -672,6 +699,7 @@ extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ,
                             c->copy_stream));
     HE_CUDA(cudaEventRecord(c->io_events[k], c->copy_stream));
   }
+  HE_CUDA(cudaEventRecord(c->io_time[1], c->copy_stream));
   std::vector<he_ct> zc(nZ);
   for (size_t i = 0; i < nZ; ++i) zc[i] = he_ct{dZ + i * zw, z_level, z_level, z_scale};
   he_ct wc{dW, w_level, w_level, w_scale}, oc{dO, 0, lo, 0.0};
@@ -680,13 +708,13 @@ extern "C" int he_lr_gradient_step_host(he_ctx* c, const uint64_t* Z, size_t nZ,
   HE_CUDA(cudaStreamWaitEvent(c->stream, c->io_events[0], 0));
   c->io_piece = piece;
   c->io_pieces_waited = 1;
-  // unless the caller chose a chunk, the first chunk is an eighth of the data
-  // (whole pieces): only its copy is exposed, the rest's copy overlaps its
-  // arithmetic; the later chunks follow the scratch budget
-  if (!c->lr_chunk && nZ > 2 * piece) c->io_first_chunk = std::max(piece, nZ / 8 / piece * piece);
+  // unless the caller chose a chunk: the short first chunk, then chunks of
+  // the scratch budget
+  if (!c->lr_chunk && nZ > 2 * piece) c->io_first_chunk = first_chunk;
   const int rc = lr_entry(c, &sh, 1, cfg, 0, 0, false);
   c->io_first_chunk = 0;
   c->io_piece = 0;
+  if (rc == HE_OK && c->io_timed_first) c->io_timed_nZ = nZ;
   if (rc != HE_OK) {
     cudaStreamSynchronize(c->copy_stream);
     return rc;

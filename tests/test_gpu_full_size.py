@@ -48,8 +48,10 @@ def test_full_size_step_accuracy_and_entry_points_agree():
     zh = torch.empty((512, 2, L, ctx.n), dtype=torch.int64, pin_memory=True)
     he.he_ct_export_batch(ctx, Z, zh)
     oh = np.zeros((2, L - 5, ctx.n), dtype=np.uint64)
-    he.he_lr_gradient_step_host(ctx, zh, L, 2.0 ** 40, he.he_ct_export(ctx, W), L, 2.0 ** 40, cfg, oh)
-    assert np.array_equal(oh, ref)
+    for _ in range(3):  # later calls size the first chunk from the previous call's timings
+        oh[:] = 0
+        he.he_lr_gradient_step_host(ctx, zh, L, 2.0 ** 40, he.he_ct_export(ctx, W), L, 2.0 ** 40, cfg, oh)
+        assert np.array_equal(oh, ref)
     # the same shard as one of several workers, graph-captured
     other = ctx.new_ct(L, 8)
     for k in range(8):
