@@ -290,7 +290,9 @@ int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
  * size), its level and scale to *out_level / *out_scale (may be NULL).  The
  * weights and then pieces of 16 data ciphertexts are copied on a second
  * stream while the circuit runs chunk by chunk on the context's stream, so
- * the copies overlap the arithmetic; pinned host memory is needed for that
+ * the copies overlap the arithmetic (unless lr_chunk is set, a short first
+ * chunk, sized from the copy and arithmetic times of the previous call, then
+ * chunks of the scratch budget); pinned host memory is needed for that
  * overlap (pageable memory is copied synchronously).  Returns after the
  * result is in `out`.  The device copy of the inputs is a context-owned
  * buffer, grown on demand.  HE_ELEVEL if w_level < 6. */
