@@ -95,7 +95,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFus
   uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
   if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
   else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-#pragma unroll 4
+#pragma unroll 8
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
     const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
     out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
     if (a.half) {
       // the inverse transform's column pass on this tile, then the scaling by N^-1
       stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.itw + (size_t)(lo + u) * N, tile);
-#pragma unroll 4
+#pragma unroll 8
       for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
         const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
         sm[idx + (idx >> 3)] = __ldg(x + (size_t)(lo + u) * N + e);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
       __syncthreads();
       run_rounds<true, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pa.q);
     }
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
       uint64_t xv;
       if (a.half) {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
     uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
     if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
     else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
       const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
       out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     if (a.half) {
       // the inverse transform's column pass on this tile, then the scaling by N^-1
       stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.itw + (size_t)a.spr[u] * N, tile);
-#pragma unroll 4
+#pragma unroll 8
       for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T)
         sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, idx & (S::K - 1), idx >> LOG_K));
       __syncthreads();
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
     else run_rounds<false, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
     uint64_t* out = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
       const uint32_t xx = idx >> LOG_K, k = idx & (S::K - 1);
       out[S::gidx(tile, k, xx)] = sm[idx + (idx >> 3)];
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
   constexpr int PER = S::TILE / S::T;
   for (uint32_t p = 0; p < 2; ++p) {
     const uint64_t* src = a.conv + (((size_t)i * 2 + p) * a.level + t) * N;
-#pragma unroll 4
+#pragma unroll 8
     for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
       const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
       sm[idx + (idx >> 3)] = __ldg(src + S::gidx(tile, k, x));
