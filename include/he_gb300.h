@@ -448,6 +448,17 @@ int he_ntt(he_ctx* ctx, uint64_t* data, uint32_t npolys, uint64_t poly_stride, u
  * out0 + out1*s ~ d*s'.  out0/out1: device, level limbs each. */
 int he_keyswitch(he_ctx* ctx, const uint64_t* d, uint32_t level, uint64_t galois, uint64_t* out0,
                  uint64_t* out1);
+/* The key switch's last step alone (the ModDown of hybrid key switching
+ * behind Sec. 3's multiplication and rotation), on accumulators the caller
+ * chooses: acc (device, [2][level + alpha][N] evaluation form, limbs q_0 ..
+ * q_{level-1} then the special primes p_0 .. p_{alpha-1}; not modified).
+ * d01 == NULL: out = round(acc / P) at `level` (the exact lift of acc's
+ * P-part, so every coefficient is rounded, whatever that lift is).
+ * d01 != NULL (a ciphertext at `level` >= 2): out = round((P d01 + acc) /
+ * (P q_{level-1})) at level - 1 with d01's scale, the multiplication's
+ * merged ModDown and rescale.  out must not overlap d01.  HE_EINVAL for a
+ * null or misaligned pointer or a bad level. */
+int he_moddown(he_ctx* ctx, const uint64_t* acc, uint32_t level, const he_ct* d01, he_ct* out);
 
 /* Kernel timing for measurement (not part of the paper's method).  While
  * enabled, every launch of an instrumented kernel class ("ntt", "intt",

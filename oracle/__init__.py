@@ -89,6 +89,8 @@ def _load():
             lib.orc_modup_coef.argtypes = [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, VP]
             lib.orc_moddown_conv.argtypes = [VP, VP, ctypes.c_int, VP]
             lib.orc_keyswitch.argtypes = [VP, VP, ctypes.c_int, ctypes.c_int, VP, VP]
+            lib.orc_moddown.argtypes = [VP, VP, ctypes.c_int, VP, VP]
+            lib.orc_moddown_rescale.argtypes = [VP, VP, VP, ctypes.c_int, VP]
             lib.orc_rescale.argtypes = [VP, VP, ctypes.c_int, VP]
             lib.orc_mul_relin_rescale.argtypes = [VP, VP, VP, ctypes.c_int, VP]
             lib.orc_mul_relin.argtypes = [VP, VP, VP, ctypes.c_int, VP]
@@ -395,6 +397,25 @@ class Oracle:
         if rc:
             raise KeyError(key_id)
         return k0, k1
+
+    def moddown(self, acc, level: int):
+        """round(acc / P) of an accumulator [2][level + alpha][N] (evaluation
+        form): the key switch's last step (orc_moddown)."""
+        a = _u64(acc)
+        k0 = np.zeros((level, self.n), dtype=np.uint64)
+        k1 = np.zeros((level, self.n), dtype=np.uint64)
+        if self._lib.orc_moddown(self.ptr, _p(a), level, _p(k0), _p(k1)):
+            raise ValueError("moddown: level")
+        return k0, k1
+
+    def moddown_rescale(self, acc, d01, level: int) -> np.ndarray:
+        """round((P d01 + acc) / (P q_{level-1})), the multiplication's merged
+        ModDown and rescale (orc_moddown_rescale): [2][level-1][N]."""
+        a, d = _u64(acc), _u64(d01)
+        out = np.zeros((2, level - 1, self.n), dtype=np.uint64)
+        if self._lib.orc_moddown_rescale(self.ptr, _p(a), _p(d), level, _p(out)):
+            raise ValueError("moddown_rescale: level")
+        return out
 
     def rescale(self, a: Ciphertext) -> Ciphertext:
         out = self._new(a.level - 1)

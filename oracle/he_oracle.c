@@ -1114,6 +1114,21 @@ static void moddown_rescale_pair(orc_ctx* c, const uint64_t* acc, const uint64_t
   free(y); free(conv); free(res);
 }
 
+/* The two ModDown forms above on accumulators the caller gives (boundary
+ * tests feed P-parts whose lift lies next to 0 or P): acc [2][level +
+ * alpha][N], d01 [2][level][N], evaluation form. */
+int orc_moddown(orc_ctx* c, const uint64_t* acc, int level, uint64_t* k0, uint64_t* k1) {
+  if (level < 1 || level > c->L) return -1;
+  moddown_pair(c, acc, level, k0, k1);
+  return 0;
+}
+
+int orc_moddown_rescale(orc_ctx* c, const uint64_t* acc, const uint64_t* d01, int level, uint64_t* out) {
+  if (level < 2 || level > c->L) return -1;
+  moddown_rescale_pair(c, acc, d01, level, out);
+  return 0;
+}
+
 /* key_id: -1 relinearisation key, i >= 0 Galois key i (in creation order). */
 int orc_keyswitch(orc_ctx* c, const uint64_t* d, int level, int key_id, uint64_t* k0, uint64_t* k1) {
   const uint64_t* key = find_key(c, key_id);

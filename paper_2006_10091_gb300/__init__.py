@@ -122,6 +122,7 @@ def load():
         "he_refresh": [VP, CTP, ctypes.c_uint32, ctypes.c_double, ctypes.c_uint32, CTP],
         "he_ntt": [VP, VP, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int],
         "he_keyswitch": [VP, VP, ctypes.c_uint32, ctypes.c_uint64, VP, VP],
+        "he_moddown": [VP, VP, ctypes.c_uint32, CTP, CTP],
         "he_ct_import_batch": [VP, VP, ctypes.c_uint32, ctypes.c_double, CTP, ctypes.c_size_t],
         "he_ct_export_batch": [VP, CTP, ctypes.c_size_t, VP, ctypes.c_size_t],
         "he_profile_enable": [VP, ctypes.c_int],
@@ -624,6 +625,19 @@ def he_keyswitch(ctx, d, level: int, galois: int, out0, out1):
     _check(load().he_keyswitch(ctx.ptr, ctypes.c_void_p(d.data_ptr()), level, galois,
                                ctypes.c_void_p(out0.data_ptr()), ctypes.c_void_p(out1.data_ptr())))
     return out0, out1
+
+
+def he_moddown(ctx, acc, level: int, out, d01=None):
+    """ModDown of a device accumulator acc ([2][level + alpha][N] residues in
+    an int64 tensor): round(acc / P) into out at `level`, or with d01 the
+    merged form round((P d01 + acc) / (P q_{level-1})) at level - 1."""
+    if acc.numel() < 2 * (level + ctx.alpha) * ctx.n:
+        raise ValueError("he_moddown: accumulator smaller than [2][level + alpha][N]")
+    if d01 is None:
+        _run(load().he_moddown, ctx, [out], ctypes.c_void_p(acc.data_ptr()), level, None, out)
+    else:
+        _run(load().he_moddown, ctx, [out], ctypes.c_void_p(acc.data_ptr()), level, d01, out)
+    return out
 
 
 def he_ct_import_batch(ctx, host, level: int, scale: float, out: list):

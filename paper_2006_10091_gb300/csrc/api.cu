@@ -858,4 +858,31 @@ int he_keyswitch(he_ctx* c, const uint64_t* d, uint32_t level, uint64_t galois, 
   return HE_OK;
 }
 
+int he_moddown(he_ctx* c, const uint64_t* acc, uint32_t level, const he_ct* d01, he_ct* out) {
+  if (!c || !acc) return fail(HE_EINVAL, "he_moddown: null argument");
+  if (!aligned16(acc)) return fail(HE_EINVAL, "he_moddown: pointers must be 16-byte aligned");
+  if (level < 1 || level > (uint32_t)c->L) return fail(HE_EINVAL, "he_moddown: bad level");
+  const bool merged = d01 != nullptr;
+  if (merged) {
+    if (level < 2) return fail(HE_ELEVEL, "he_moddown: the merged rescale needs two limbs");
+    if (!c->d_mdrs) return fail(HE_EINVAL, "he_moddown: no merged tables (more than 7 special primes)");
+    HE_TRY(check_ct(c, d01, "he_moddown"));
+    if (d01->level != level) return fail(HE_EINVAL, "he_moddown: d01 must be at the accumulator's level");
+  }
+  const uint32_t lt = merged ? level - 1 : level;
+  HE_TRY(check_out(c, out, lt, "he_moddown"));
+  const size_t n = c->n, nt = level + (size_t)c->alpha;
+  HE_TRY(ws_reserve(c, sizeof(uint64_t) * (2 * nt * n + 4 * level * n) + 8192));
+  Arena ar = arena(c);
+  uint64_t* a = ar.take<uint64_t>(2 * nt * n);
+  uint64_t* conv = ar.take<uint64_t>(2 * (size_t)level * n);
+  if (!a || !conv) return fail(HE_ENOMEM, "he_moddown: scratch too small");
+  HE_CUDA(cudaMemcpyAsync(a, acc, sizeof(uint64_t) * 2 * nt * n, cudaMemcpyDeviceToDevice, c->stream));
+  const CtBatch add = merged ? one(d01) : CtBatch{nullptr, 0, 0, 0};
+  HE_TRY(moddown_batch(c, a, conv, level, 1, add, merged ? 2 : 0, one(out), ar, 0, merged));
+  out->level = lt;
+  if (merged) out->scale = d01->scale;
+  return HE_OK;
+}
+
 }  // extern "C"

@@ -215,6 +215,10 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint32_
       u[a] = mul_shoup(y, md[2 * a], md[2 * a + 1], pp.q);
       if (alpha > 1) frac_acc(u[a], pp.one_sh, wlo[a], &fs, &v);
     }
+    if (alpha > 1 && frac_in_window(fs, alpha)) {
+      const uint64_t* phat = wlo + alpha + 9 * (size_t)L;  // [alpha][8] words of P/p_a, then [8] of P
+      v = exact_lift_multiple(u, 1, alpha, phat, phat + 8 * (size_t)alpha, v);
+    }
     uint64_t* out = conv + (size_t)i * conv_stride + (size_t)p * level * n;
     for (uint32_t t = 0; t < level; ++t) {
       const PrimeDev pr = primes[t];

@@ -86,6 +86,46 @@ __device__ __forceinline__ void frac_acc(uint64_t u, uint64_t one_sh, uint64_t w
   *v += *s < t;
 }
 
+// The fixed-point sum of frac_acc over a terms is at most 2a units of 2^-64
+// below sum_k u_k / p_k = v + x/P (x in [0, P) the exact lift), so its integer
+// part is v - 1 only when its fractional part fs lies within 2a units of the
+// next integer.  Such an element (about 2a 2^-64 of uniform inputs) takes the
+// exact test below.
+__device__ __forceinline__ bool frac_in_window(uint64_t fs, uint32_t a) { return fs >= 0ull - 2ull * a; }
+
+// Exact v for an element in that window: v = vc + 1 iff
+// sum_k u_k (P/p_k) >= (vc + 1) P, compared as 8-word integers.  u_k at
+// u[k * ustride]; phat = [a][8] words of P/p_k, pw = [8] words of P.
+static __device__ __noinline__ uint32_t exact_lift_multiple(const uint64_t* u, size_t ustride, uint32_t a,
+                                                            const uint64_t* phat, const uint64_t* pw, uint32_t vc) {
+  uint64_t s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (uint32_t k = 0; k < a; ++k) {
+    const uint64_t x = u[(size_t)k * ustride];
+    uint64_t carry = 0;
+    for (int w = 0; w < 8; ++w) {
+      const uint64_t ph = phat[(size_t)k * 8 + w];
+      uint64_t lo = x * ph, hi = __umul64hi(x, ph);
+      lo += carry;
+      hi += lo < carry;
+      s[w] += lo;
+      hi += s[w] < lo;
+      carry = hi;
+    }
+  }
+  const uint64_t m = (uint64_t)vc + 1;
+  uint64_t t[8], carry = 0;
+  for (int w = 0; w < 8; ++w) {
+    uint64_t lo = m * pw[w], hi = __umul64hi(m, pw[w]);
+    lo += carry;
+    hi += lo < carry;
+    t[w] = lo;
+    carry = hi;
+  }
+  for (int w = 7; w >= 0; --w)
+    if (s[w] != t[w]) return s[w] > t[w] ? vc + 1 : vc;
+  return vc + 1;
+}
+
 // Signed integer to residue.
 __device__ __forceinline__ uint64_t from_signed(int64_t x, const PrimeDev& p) {
   if (x >= 0) return reduce64((uint64_t)x, p);

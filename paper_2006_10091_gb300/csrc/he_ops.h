@@ -51,6 +51,12 @@ size_t rescale_words(const he_ctx* c, uint32_t level, uint32_t count);
 int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t level, uint32_t count,
                     const uint64_t* evk, CtBatch add, int add_mode, CtBatch out, Arena& ar, uint64_t gal = 0,
                     bool merged = false);
+// The key switch's ModDown alone: acc (count x [2][level + alpha][N],
+// evaluation form over Q_level and P; its dropped limbs are overwritten)
+// divided by P with rounding (merged: P add + acc divided by P q_{level-1}),
+// conv (count x [2][level][N]) as scratch; add_mode and gal as above.
+int moddown_batch(he_ctx* c, uint64_t* acc, uint64_t* conv, uint32_t level, uint32_t count, CtBatch add,
+                  int add_mode, CtBatch out, Arena& ar, uint64_t gal, bool merged);
 // Whether N has compiled shapes for the fused key-switching kernels.
 inline bool ks_fusable(const he_ctx* c) { return !c->ntt_generic && c->log_n >= 12 && c->log_n <= 16; }
 int rescale_batch(he_ctx* c, CtBatch in, uint32_t level, uint32_t count, CtBatch out, Arena& ar);

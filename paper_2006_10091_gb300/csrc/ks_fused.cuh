@@ -415,7 +415,8 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   const uint64_t* wlo = mat_sh + (size_t)a.alpha * a.L;
   const uint64_t* yP = a.yP + (size_t)i * a.yp_stride + (size_t)p * a.yp_pstride;
   // exact conversion: sum_u w_u (P/p_u) - v P, w_u = [y_u (P/p_u)^-1]_{p_u},
-  // v = floor(sum_u w_u / p_u)
+  // v = floor(sum_u w_u / p_u) (64.64 fixed point, resolved exactly near an
+  // integer)
   for (uint32_t u = 0; u < a.alpha; ++u) {
     const PrimeDev pp = a.primes[a.spr[u]];
     const uint64_t* src = yP + (size_t)u * N;
@@ -442,9 +443,14 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
   for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
     uint64_t fs = 0;
     uint32_t v = 0;
-    if (a.alpha > 1)
+    if (a.alpha > 1) {
       for (uint32_t u = 0; u < a.alpha; ++u)
         frac_acc(wv[(size_t)u * S::TILE + idx], a.primes[a.spr[u]].one_sh, wlo[u], &fs, &v);
+      if (frac_in_window(fs, a.alpha)) {
+        const uint64_t* phat = wlo + a.alpha + 9 * (size_t)a.L;  // [alpha][8] words of P/p_u, then [8] of P
+        v = exact_lift_multiple(wv + idx, S::TILE, a.alpha, phat, phat + 8 * (size_t)a.alpha, v);
+      }
+    }
     vv[idx] = v;
   }
   for (uint32_t t = 0; t < a.level; ++t) {

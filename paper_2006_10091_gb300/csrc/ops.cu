@@ -202,6 +202,15 @@ int keyswitch_batch(he_ctx* c, const uint64_t* d, uint64_t d_stride, uint32_t le
     HE_TRY(ks_unfused_middle(c, d, d_stride, d2c, ext, acc, evk, level, count));
   }
   // 4. ModDown
+  return moddown_batch(c, acc, conv, level, count, add, add_mode, out, ar, gal, merged);
+}
+
+// Step 4 of the key switch on acc (count x [2][level + alpha][N], evaluation
+// form; its dropped limbs are overwritten), with conv (count x [2][level][N])
+// as scratch.
+int moddown_batch(he_ctx* c, uint64_t* acc, uint64_t* conv, uint32_t level, uint32_t count, CtBatch add,
+                  int add_mode, CtBatch out, Arena& ar, uint64_t gal, bool merged) {
+  const uint32_t n = c->n, alpha = c->alpha, nt = level + alpha;
   if (merged) {  // divide P (d0, d1) + acc by P q_{level-1}: its dropped limbs are acc's last alpha + 1
     const uint32_t lo = level - 1;
     {

@@ -252,7 +252,11 @@ int build_tables(he_ctx* c) {
   // of floor(2^128 / p_k) (the high word is floor(2^64 / p_k)); [L] P mod q_t;
   // [L][8] v P mod q_t.  The last two make the conversion exact: v =
   // floor(sum_k u_k / p_k) is evaluated in 64.64 fixed point and v P
-  // subtracted.  4a + 2aL + 12L words.
+  // subtracted.  Then, for the rare elements whose fixed-point sum lies
+  // within its error of an integer, the integers themselves: [a][8] words of
+  // P/p_k and [8] words of P (little-endian 64-bit words; a <= 8 primes below
+  // 2^61 keep sum_k u_k P/p_k and 8 P below 2^512).  4a + 2aL + 12L + 8a + 8
+  // words.
   auto md_words = [&](const std::vector<int>& drop) {
     const int a = (int)drop.size();
     std::vector<uint64_t> words;
@@ -289,6 +293,23 @@ int build_tables(he_ctx* c) {
     for (int t = 0; t < L; ++t) words.push_back(Pq[t]);
     for (int t = 0; t < L; ++t)  // [L][8]: v P mod q_t for v = 0 .. 7 (v < a <= 8)
       for (uint64_t v = 0; v < 8; ++v) words.push_back(h_mulmod(v % c->q[t], Pq[t], c->q[t]));
+    auto prod_words = [&](int skip) {  // prod of drop[] except drop[skip], as 8 words
+      std::vector<uint64_t> x(8, 0);
+      x[0] = 1;
+      for (int k2 = 0; k2 < a; ++k2) {
+        if (k2 == skip) continue;
+        u128 carry = 0;
+        for (int w = 0; w < 8; ++w) {
+          const u128 t = (u128)x[w] * c->q[drop[k2]] + carry;
+          x[w] = (uint64_t)t;
+          carry = t >> 64;
+        }
+      }
+      return x;
+    };
+    for (int k = 0; k < a; ++k)
+      for (uint64_t w : prod_words(k)) words.push_back(w);
+    for (uint64_t w : prod_words(-1)) words.push_back(w);
     return words;
   };
   {
@@ -296,15 +317,16 @@ int build_tables(he_ctx* c) {
     for (int k = 0; k < alpha; ++k) sp.push_back(L + k);
     const std::vector<uint64_t> words = md_words(sp);
     c->P_mod_q.assign(L, 0);
-    for (int t = 0; t < L; ++t) c->P_mod_q[t] = words[words.size() - 9 * (size_t)L + t];
+    const size_t pq_off = 4 * (size_t)alpha + 2 * (size_t)alpha * L + 3 * (size_t)L;  // the [L] P mod q_t
+    for (int t = 0; t < L; ++t) c->P_mod_q[t] = words[pq_off + t];
     HE_CUDA(cudaMalloc(&c->d_moddown, sizeof(uint64_t) * words.size()));
     HE_CUDA(cudaMemcpy(c->d_moddown, words.data(), sizeof(uint64_t) * words.size(), cudaMemcpyHostToDevice));
   }
   // The same for dividing by P q_{l-1} (ModDown merged with the rescale of a
   // multiplication at level l, 2 <= l <= L): dropped primes q_{l-1}, then the
-  // special primes; one table of 4(alpha+1) + 2(alpha+1)L + 12L words per l.
+  // special primes; one table of 12(alpha+1) + 2(alpha+1)L + 12L + 8 words per l.
   if (alpha + 1 <= 8) {
-    const size_t W = 4 * (size_t)(alpha + 1) + 2 * (size_t)(alpha + 1) * L + 12 * (size_t)L;
+    const size_t W = 12 * (size_t)(alpha + 1) + 2 * (size_t)(alpha + 1) * L + 12 * (size_t)L + 8;
     std::vector<uint64_t> all(W * (L + 1), 0);
     for (int l = 2; l <= L; ++l) {
       std::vector<int> drop{l - 1};

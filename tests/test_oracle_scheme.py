@@ -192,6 +192,28 @@ def test_moddown_conversion_is_exact(tiny):
             assert int(conv[k]) == ints[k] % o.primes[t]
 
 
+@pytest.mark.parametrize("merged", [False, True])
+def test_moddown_rounds_boundary_lifts(tiny, merged):
+    """ModDown on accumulators chosen as integers X whose (X + h) mod D lifts
+    to 0, 1, 2, D - 2 or D - 1 (D = P, or P q_{l-1} merged with the rescale):
+    every output coefficient is floor((X + h) / D), the rounded quotient,
+    residue by residue (Python integers)."""
+    from tests import moddown_inputs as mi
+    o = tiny
+    level = 5
+    acc, d01, X, D = mi.accumulator(o, level, seed=17, merged=merged)
+    lt = level - 1 if merged else level
+    want = mi.expected_coef(X, D, o.primes[:lt])
+    if merged:
+        got = o.moddown_rescale(acc, d01, level)
+    else:
+        got = np.stack(o.moddown(acc, level))
+    for p in range(2):
+        gotc = to_coef(o, got[p], lt)
+        for t in range(lt):
+            assert [int(v) for v in gotc[t]] == want[p][t], (p, t)
+
+
 # ------------------------------------------------------------------ rescale
 
 
