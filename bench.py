@@ -138,57 +138,88 @@ def measured_peaks():
 # basis-conversion and inner-product products.
 ALU_MODMUL_PEAK = 152 * 2.070e9 * 64 / 17.3
 ALU_PEAK = {"per_second": ALU_MODMUL_PEAK, "note": "fallback: 152 SMs x 2070 MHz x 64 IMAD/clk / 17.3 IMAD slots "
-                                                  "per 64-bit Shoup product"}
+                                                  "per 64-bit Shoup product",
+            # 64 x 64 -> 128-bit multiply-accumulates (he_probe_alu kind 3); fallback: the Shoup rate
+            "mac_per_second": ALU_MODMUL_PEAK, "mac_note": "fallback: the Shoup-product rate",
+            # radix-8 rounds of the lazy butterfly in registers (kind 2): the practical ceiling of a transform
+            "butterfly_per_second": None}
 
 
 def measure_alu_peak(he) -> None:
-    """Replace the fallback integer roof by this GPU's measured Shoup-product rate."""
+    """Replace the fallback integer roofs by this GPU's measured rates."""
     try:
         r = he.he_probe_alu(1)
-    except Exception:  # keep the fallback
+        ALU_PEAK["per_second"] = r["per_second"]
+        ALU_PEAK["note"] = (f"measured: register-resident 64-bit Shoup product chain on this GPU "
+                            f"({r['per_clock_per_sm']:.2f} per clock per SM)")
+        m = he.he_probe_alu(3)
+        ALU_PEAK["mac_per_second"] = m["per_second"]
+        ALU_PEAK["mac_note"] = (f"measured: register-resident 64x64->128-bit multiply-accumulate chain "
+                                f"({m['per_clock_per_sm']:.2f} per clock per SM)")
+        ALU_PEAK["butterfly_per_second"] = he.he_probe_alu(2)["per_second"]
+    except Exception:  # keep the fallbacks
         return
-    ALU_PEAK["per_second"] = r["per_second"]
-    ALU_PEAK["note"] = (f"measured: register-resident 64-bit Shoup product chain on this GPU "
-                        f"({r['per_clock_per_sm']:.2f} per clock per SM)")
 
 
 ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_rot_products", "moddown_ntt", "moddown_ntt_combine",
                "moddown_rescale_ntt", "moddown_rescale_ntt_combine", "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes per algorithmic byte of the hoisted stage's row kernel, from an
-# ncu capture of one 7-rotation stage over 64 ciphertexts at level 7 (498.2 MB
-# against 453.0 MB): its traffic grows with the ciphertexts, not with the
-# rotations, so the roofline scales the launch's algorithmic bytes.
-KS_ROT_TRAFFIC_PER_ALG_BYTE = 498.2 / 453.0
+# ncu capture of one 7-rotation stage over 64 ciphertexts at level 7: 498.2 MB
+# of DRAM traffic against 519.1 MB of algorithmic bytes (453.0 MB of
+# ciphertext limbs read and accumulators written, 66.1 MB of the seven keys
+# read once); its traffic grows with the ciphertexts, so the roofline scales
+# the launch's algorithmic bytes by it.
+KS_ROT_TRAFFIC_PER_ALG_BYTE = 498.2 / 519.1
+
+
+def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: bool | None = None) -> dict:
+    """Roofline of one kernel class (or of several summed): the launch time
+    against max(integer-pipe time, HBM time).  The integer-pipe time weighs
+    the class's modular products and butterflies at the measured Shoup-product
+    rate and its unreduced 128-bit key products at the measured
+    multiply-accumulate rate; `frac_shoup_only` is the older single-rate
+    figure (every unit of work at the Shoup rate)."""
+    t = p["ms"] * 1e-3
+    work, mac, by = p["work"], p.get("mac", 0.0), p["bytes"]
+    t_alu = (work - mac) / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
+    t_hbm = by / (hbm_peak * 1e9)
+    gbs = by / t / 1e9 if t > 0 else 0.0
+    base = {"kernel": name, "per_launch_ms": p["ms"] / max(1, p["launches"]), "launches": p["launches"],
+            "algorithmic_gbs": gbs, "hbm_frac": gbs / hbm_peak, "traffic": None}
+    if integer is None:
+        integer = name in ALU_CLASSES
+    if integer and work > 0:
+        if t_alu >= t_hbm:
+            rate = work / t if t > 0 else 0.0
+            peak = work / t_alu if t_alu > 0 else ALU_PEAK["per_second"]
+            base.update({"bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "G modmul/s",
+                         "frac": t_alu / t if t > 0 else 0.0,
+                         "frac_shoup_only": rate / ALU_PEAK["per_second"],
+                         "mac_share_of_work": mac / work if work else 0.0,
+                         "peak_note": (f"weighted integer roof: {work - mac:.3g} products and butterflies at "
+                                       f"{ALU_PEAK['note']}; {mac:.3g} 128-bit key multiply-accumulates at "
+                                       f"{ALU_PEAK['mac_note']}")})
+            if ALU_PEAK["butterfly_per_second"] and name in ("ntt", "intt"):
+                base["butterfly_chain_frac"] = rate / ALU_PEAK["butterfly_per_second"]
+            return base
+    base.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                 "peak_note": f"{peak_kind} HBM copy bandwidth"})
+    return base
 
 
 def roofline(prof: dict, hbm_peak: float, peak_kind: str):
-    """Dominant kernel class by device time -> achieved vs its roof: the
-    integer pipe for the transform kernels (modular products per second),
-    HBM for the rest (algorithmic bytes per second), whichever is closer."""
+    """Dominant kernel class by device time -> achieved vs its roof (the
+    integer pipe, weighted, for the transform and key-switching kernels; HBM
+    for the rest, whichever bounds it)."""
     if not prof:
         return None
     name = max(prof, key=lambda k: prof[k]["ms"])
-    p = prof[name]
-    per_launch_ms = p["ms"] / max(1, p["launches"])
-    gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else 0.0
-    frac_hbm = gbs / hbm_peak
-    if name in ALU_CLASSES:
-        rate = p["work"] / (p["ms"] * 1e-3)
-        frac_alu = rate / ALU_PEAK["per_second"]
-        traffic = None
-        if name == "ks_ntt_rot_products":
-            traffic = KS_ROT_TRAFFIC_PER_ALG_BYTE * p["bytes"] / max(1, p["launches"])
-        if frac_alu >= frac_hbm:
-            return {"kernel": name, "bound": "alu", "achieved": rate / 1e9, "peak": ALU_PEAK["per_second"] / 1e9,
-                    "unit": "G modmul/s", "frac": frac_alu, "traffic": traffic,
-                    "traffic_note": "bytes per launch, scaled from an ncu capture of a smaller launch" if traffic
-                    else None,
-                    "per_launch_ms": per_launch_ms, "launches": p["launches"],
-                    "algorithmic_gbs": gbs, "hbm_frac": frac_hbm,
-                    "peak_note": ALU_PEAK["note"]}
-    return {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-            "frac": frac_hbm, "traffic": None, "per_launch_ms": per_launch_ms,
-            "launches": p["launches"], "peak_note": f"{peak_kind} HBM copy bandwidth"}
+    r = class_roof(prof[name], hbm_peak, peak_kind, name)
+    if name == "ks_ntt_rot_products":
+        r["traffic"] = KS_ROT_TRAFFIC_PER_ALG_BYTE * prof[name]["bytes"] / max(1, prof[name]["launches"])
+        r["traffic_note"] = ("DRAM bytes per launch: the launch's algorithmic bytes times the DRAM/algorithmic "
+                             "ratio of an ncu capture of a smaller launch of the same kernel")
+    return r
 
 
 # ----------------------------------------------------------------------------- ranks
@@ -369,6 +400,7 @@ def hmult_rates(he, torch, stream):
             rots = [1 << t for t in range(10)]
             rots += [r for st in he.rotsum_stages(1, 10) for r in st if r not in rots]
         ctx = he.Context(log_n, nl, bits, alpha, sbits, scale, seed=0, stream=stream.cuda_stream, rot_steps=rots)
+        tuned = he.he_autotune(ctx, nl, 16) if name == "hmult_large" else None
         n = 1 << log_n
         A, B, O = ctx.new_ct(nl, count), ctx.new_ct(nl, count), ctx.new_ct(nl, count)
         for i in range(count):
@@ -422,9 +454,57 @@ def hmult_rates(he, torch, stream):
                 torch.cuda.synchronize()
                 out[name][key] = count * 1000.0 / e0.elapsed_time(e1)
             out[name]["rotate_and_sum_stages"] = [list(st) for st in stages]
+            out[name]["autotune"] = tuned
+            out[name]["roofline"] = large_rooflines(he, torch, stream, ctx, A, B, O, T)
         ctx.close()
         del A, B, O
         torch.cuda.empty_cache()
+    return out
+
+
+def large_rooflines(he, torch, stream, ctx, A, B, O, T):
+    """Roofline objects at N = 2^16 (24 limbs, four special primes, the
+    batch of 64 ciphertexts): the key switch of a rotation by one slot (all its
+    kernel classes together and its row kernel alone), of a multiplication,
+    and the forward and inverse NTT over the batch's 3072 limbs (1.6 GB, more
+    than L2), each from kernel-class timing of one profiled batch."""
+    hbm_peak, peak_kind = measured_peaks()
+    ks_classes = ("ks_modup_ntt", "ks_ntt_rot_products", "intt", "moddown_ntt", "moddown_ntt_combine",
+                  "moddown_rescale_ntt", "moddown_rescale_ntt_combine", "tensor")
+    out = {}
+
+    def profiled(fn):
+        fn()
+        torch.cuda.synchronize()
+        he.he_profile_enable(ctx, True)
+        fn()
+        prof = {k: he.he_profile_read(ctx, k) for k in he.he_profile_names(ctx)}
+        he.he_profile_enable(ctx, False)
+        return prof
+
+    def summed(prof, names):
+        keys = [k for k in names if k in prof]
+        return {"ms": sum(prof[k]["ms"] for k in keys), "work": sum(prof[k]["work"] for k in keys),
+                "mac": sum(prof[k]["mac"] for k in keys), "bytes": sum(prof[k]["bytes"] for k in keys),
+                "launches": sum(prof[k]["launches"] for k in keys)}
+
+    for key, fn in (("keyswitch_rotation", lambda: he.he_rotate_batch(ctx, A, 1, O)),
+                    ("mul_relin_rescale", lambda: he.he_mul_relin_rescale_batch(ctx, A, B, O))):
+        prof = profiled(fn)
+        out[key] = class_roof(summed(prof, ks_classes), hbm_peak, peak_kind, key, integer=True)
+        out[key]["classes"] = [k for k in ks_classes if k in prof]
+        if key == "keyswitch_rotation":
+            out["ks_ntt_rot_products"] = class_roof(prof["ks_ntt_rot_products"], hbm_peak, peak_kind,
+                                                    "ks_ntt_rot_products")
+            out["moddown_ntt_combine"] = class_roof(prof["moddown_ntt_combine"], hbm_peak, peak_kind,
+                                                    "moddown_ntt_combine")
+    buf = torch.cat([a.tensor.reshape(-1) for a in A]).reshape(len(A) * 2, -1)  # 128 polynomials of 24 limbs
+    nl = A[0].level
+    for inverse in (False, True):
+        fn = lambda: he.he_ntt(ctx, buf, buf.shape[0], nl * ctx.n, nl, 0, inverse)  # noqa: E731
+        prof = profiled(fn)
+        k = "intt" if inverse else "ntt"
+        out[k] = class_roof(prof[k], hbm_peak, peak_kind, k)
     return out
 
 

@@ -109,9 +109,10 @@ int he_get_tuning(he_ctx* ctx, const char* key, double* value);
 /* Measurement utility (no counterpart in the paper): register-resident
  * throughput on the current device of kind 0 = 32-bit multiply-adds, 1 =
  * 64-bit Shoup modular products (the integer roof of the transforms), 2 =
- * radix-8 rounds of the lazy forward butterfly; per clock per SM (at the
- * device's maximum clock) and per second.  Runs two short kernels on the
- * default stream and synchronises. */
+ * radix-8 rounds of the lazy forward butterfly, 3 = 64 x 64 -> 128-bit
+ * multiply-accumulates (the key switch's unreduced key products); per clock
+ * per SM (at the device's maximum clock) and per second.  Runs two short
+ * kernels on the default stream and synchronises. */
 int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second);
 
 /* Least-squares polynomial fit of a nonlinearity from samples (Sec. 3,
@@ -133,6 +134,12 @@ int he_fit_poly(const double* x, const double* y, size_t n, uint32_t degree, dou
  * results never depend on these knobs.  HE_EINVAL for level outside [1, L] or
  * count outside [1, 4096]; on an error the knobs keep their previous values. */
 int he_autotune(he_ctx* ctx, uint32_t level, uint32_t count, double* best_ms);
+
+/* The context's workspace: the device bytes it holds now (scratch that the
+ * entry points needing it grow on demand, key generation included) and how
+ * many times an entry point has asked it for scratch, whether or not it grew.
+ * Either output may be NULL. */
+int he_ctx_workspace(const he_ctx* ctx, size_t* bytes, uint64_t* requests);
 
 /* Context facts: N, L, alpha, beta (digits at the top level), and the
  * L + alpha primes (limbs first) into primes_out (may be NULL). */
@@ -213,7 +220,11 @@ int he_rescale(he_ctx* ctx, const he_ct* a, he_ct* out);
  * library until exit.  Limit: 2*level*N + 64 words <= 2^19 (level <= 15 at
  * N = 2^14), else HE_EINVAL with the sizes in the message.  The first call on
  * a device looks up the array's device address with that device current;
- * make that first call before any stream capture.  All calls share the
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process, which assumes the device's primary context is
+ * never reset: after cudaDeviceReset do not call this entry point again.
+ * The context's workspace (he_ctx_workspace) is neither used nor grown, and
+ * kernel timing (he_profile_*) is skipped for this call.  All calls share the
  * array: calls that overlap on the GPU race, so serialise them; nothing in
  * it needs clearing, each call writes every word it reads.  Same results,
  * errors and aliasing rules as he_rescale; kernel timing is not recorded. */
@@ -262,7 +273,8 @@ int he_rotate_sum_batch(he_ctx* ctx, const he_ct* a, const int32_t* steps, uint3
  * polynomial; Algorithm 1).  Z[k] hold g samples each, slot g*f + s =
  * y_s*x_{s,f}; W holds w_f in slots g*f + s for every s.  Computes
  * w' = w + lr * sum_k sum_s p(y_s w.x_s) y_s x_s with p(x) = c0 + c1 x +
- * c2 x^2 + c3 x^3, replicated over the g slots of each feature.  Consumes 5
+ * c2 x^2 + c3 x^3, replicated over the g slots of each feature (minus
+ * lr * l2 * w with the L2 regulariser below).  Consumes 5
  * levels: Z and W at the same level l >= 6; W_out at l - 5 with W's scale.
  * Each of its three rotate-and-sums (over F = N/(2g) feature positions of
  * step g, and over the g samples with steps 1 and -1) runs as he_rotate_sum
@@ -278,6 +290,10 @@ typedef struct he_lr_config {
   uint32_t g;           /* samples per ciphertext, a power of two */
   uint32_t pad;
   double mask_scale;    /* scale of the 0/1 slot mask plaintext */
+  double l2;            /* >= 0: weight of the regulariser R(w) = (l2/2) |w|^2 of Eq. 4, whose
+                           gradient l2 w joins the sum (Eq. 6, 8): w' = w + lr (sum ... - l2 w);
+                           taken as round(-lr l2 q_{l-6}) times w at level l - 4, rescaled to
+                           l - 5 and W's scale, and added last (0: no regulariser) */
 } he_lr_config;
 
 int he_lr_gradient_step(he_ctx* ctx, const he_ct* Z, size_t nZ, const he_ct* W,
@@ -417,7 +433,9 @@ typedef struct he_result {
 
 int he_server_create(const he_server_config* cfg, he_server** out);
 /* Queue a request (the descriptor is copied; host buffers must stay valid
- * until its result is polled).  Returns its id. */
+ * until its result is polled).  Returns its id.  HE_ENOMEM (nothing queued)
+ * for a request whose own device memory -- its buffers and the workspace of
+ * its circuit -- exceeds the whole budget: it could never be admitted. */
 int he_server_submit(he_server* s, const he_request* req, uint64_t* id);
 /* Results completed since the last poll (up to cap). */
 int he_server_poll(he_server* s, he_result* results, size_t cap, size_t* n);
@@ -474,6 +492,11 @@ int he_profile_enable(he_ctx* ctx, int enable);
 int he_profile_read(he_ctx* ctx, const char* kernel_class, uint64_t* launches, double* total_ms,
                     double* work, double* bytes);
 int he_profile_names(he_ctx* ctx, char* buf, size_t cap);
+/* The part of a class's work (as counted by he_profile_read) that is 64 x 64
+ * -> 128-bit multiply-accumulates summed without reduction (the key products
+ * of the fused key switch), the rest being Shoup or Barrett products and
+ * butterflies: lets a roofline weigh the two at their own measured rates. */
+int he_profile_read_mac(he_ctx* ctx, const char* kernel_class, double* mac_work);
 
 #ifdef __cplusplus
 }

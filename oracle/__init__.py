@@ -108,8 +108,8 @@ def _load():
                 VP, ctypes.c_double, ctypes.c_int, VP, VP]
             lib.orc_lr_gradient_step.argtypes = [
                 VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int,
-                ctypes.c_double, VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, VP,
-                VP, VP]
+                ctypes.c_double, VP, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                VP, VP, VP]
             _lib = lib
     return _lib
 
@@ -466,7 +466,8 @@ class Oracle:
         return out
 
     def lr_gradient_step(self, Z: list, W: Ciphertext, coeffs, lr: float, g: int,
-                         mask_scale: float) -> Ciphertext:
+                         mask_scale: float, l2: float = 0.0) -> Ciphertext:
+        """w' = w + lr (sum_i p(y_i w.x_i) y_i x_i - l2 w) (orc_lr_gradient_step)."""
         arrs = [_u64(z.data) for z in Z]
         ptrs = np.array([a.ctypes.data for a in arrs], dtype=np.uint64)
         co = np.ascontiguousarray(coeffs, dtype=np.float64)
@@ -475,7 +476,7 @@ class Oracle:
         sc = ctypes.c_double(0.0)
         rc = self._lib.orc_lr_gradient_step(
             self.ptr, _p(ptrs), len(Z), Z[0].level, float(Z[0].scale), _p(_u64(W.data)),
-            W.level, float(W.scale), _p(co), float(lr), g, float(mask_scale), _p(out),
+            W.level, float(W.scale), _p(co), float(lr), g, float(mask_scale), float(l2), _p(out),
             ctypes.byref(lvl), ctypes.byref(sc))
         if rc:
             raise ValueError(f"lr_gradient_step failed ({rc})")

@@ -1419,9 +1419,17 @@ int orc_lr_mask(orc_ctx* c, int g, double ms, int64_t* out) {
   return rc;
 }
 
+/* The worker's update of Eq. 5-8 with a Table 2 polynomial p and, for
+ * l2 > 0, the gradient of the smooth regulariser R(w) = (l2/2) |w|^2 of
+ * Eq. 4 (Eq. 6 and 8: grad f = sum_i y_i grad L x_i + grad R, grad R = l2 w):
+ *   w' = w + lr * (sum_i p(y_i w.x_i) y_i x_i - l2 w)
+ * (the sign reading of the Table 2 polynomials and lr = eta/n as above).
+ * The regulariser's term is the constant product of w taken at level l0-4,
+ * by round(-lr l2 q_{l0-5}) at scale q_{l0-5}, rescaled to level l0-5 and W's
+ * scale, and added last. */
 int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int levelZ, double sZ,
                          const uint64_t* Wd, int levelW, double sW, const double coeffs[4],
-                         double lr, int g, double mask_scale, uint64_t* Wout, int* level_out,
+                         double lr, int g, double mask_scale, double l2, uint64_t* Wout, int* level_out,
                          double* scale_out) {
   uint32_t n = c->n;
   int l0 = levelZ;
@@ -1517,6 +1525,20 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
     orc_add(c, tmp, R.d, l0 - 5, Wout);
     *level_out = l0 - 5;
     *scale_out = sW;
+  }
+  if (rc == 0 && l2 != 0.0) {
+    /* - lr l2 w: w at level l0-4 times round(-lr l2 q_{l0-5}), rescaled */
+    if (!(l2 > 0.0)) {
+      rc = -1;
+    } else {
+      uint64_t* wr = malloc(sizeof(uint64_t) * 2 * (size_t)(l0 - 4) * n);
+      orc_drop(c, Wd, l0, l0 - 4, wr);
+      orc_mul_int(c, wr, l0 - 4, round_const(-lr * l2 * (double)q[l0 - 5]), tmp);
+      orc_rescale(c, tmp, l0 - 4, wr);
+      if (!scales_match((sW * (double)q[l0 - 5]) / (double)q[l0 - 5], sW)) rc = -3;
+      else orc_add(c, Wout, wr, l0 - 5, Wout);
+      free(wr);
+    }
   }
   free(tmp);
   free(G.d); free(U.d); free(T.d); free(A.d); free(Cc.d); free(B.d); free(Qq.d);

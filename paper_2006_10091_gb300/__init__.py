@@ -52,7 +52,8 @@ HE_REQ_GRADIENT, HE_REQ_INFERENCE = 0, 1
 
 class he_lr_config(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_double * 4), ("lr", ctypes.c_double),
-                ("g", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mask_scale", ctypes.c_double)]
+                ("g", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mask_scale", ctypes.c_double),
+                ("l2", ctypes.c_double)]
 
 
 class he_server_config(ctypes.Structure):
@@ -128,6 +129,7 @@ def load():
         "he_profile_enable": [VP, ctypes.c_int],
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
+        "he_profile_read_mac": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
         "he_lr_train": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config), ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_uint32, ctypes.c_uint32, CTP],
@@ -139,6 +141,7 @@ def load():
         "he_fit_poly": [VP, VP, ctypes.c_size_t, ctypes.c_uint32, VP],
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
+        "he_ctx_workspace": [VP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
         "he_lr_inference_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
@@ -296,7 +299,8 @@ def he_get_tuning(ctx: Context, key: str) -> float:
 
 
 def he_probe_alu(kind: int) -> dict:
-    """Register-resident integer throughput: kind 0 IMAD, 1 Shoup product, 2 lazy butterfly."""
+    """Register-resident integer throughput: kind 0 IMAD, 1 Shoup product, 2 lazy butterfly,
+    3 64 x 64 -> 128-bit multiply-accumulate."""
     pc, ps = ctypes.c_double(), ctypes.c_double()
     _check(load().he_probe_alu(kind, ctypes.byref(pc), ctypes.byref(ps)))
     return {"per_clock_per_sm": pc.value, "per_second": ps.value}
@@ -397,6 +401,13 @@ def he_mul_plain(ctx, a, coeffs, pt_scale: float, out):
 def he_rescale(ctx, a, out):
     _run(load().he_rescale, ctx, [out], a, out)
     return out
+
+
+def he_ctx_workspace(ctx) -> dict:
+    """The context's workspace: bytes held now and scratch requests so far."""
+    b, r = ctypes.c_size_t(), ctypes.c_uint64()
+    _check(load().he_ctx_workspace(ctx.ptr, ctypes.byref(b), ctypes.byref(r)))
+    return {"bytes": b.value, "requests": r.value}
 
 
 def he_rescale_noalloc(ctx, a, out):
@@ -525,8 +536,9 @@ def lr_rot_steps(n_slots: int, g: int) -> list:
     return steps
 
 
-def lr_config(coeffs, lr: float, g: int, mask_scale: float) -> he_lr_config:
-    return he_lr_config((ctypes.c_double * 4)(*coeffs), float(lr), g, 0, float(mask_scale))
+def lr_config(coeffs, lr: float, g: int, mask_scale: float, l2: float = 0.0) -> he_lr_config:
+    """Step configuration; l2 > 0 adds the L2 regulariser's gradient l2 * w (Eq. 4, 6)."""
+    return he_lr_config((ctypes.c_double * 4)(*coeffs), float(lr), g, 0, float(mask_scale), float(l2))
 
 
 def he_lr_gradient_step(ctx, Z: list, W: Ciphertext, cfg: he_lr_config, W_out: Ciphertext):
@@ -678,7 +690,9 @@ def he_profile_read(ctx, kernel_class: str) -> dict:
     ms, work, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().he_profile_read(ctx.ptr, kernel_class.encode(), ctypes.byref(n), ctypes.byref(ms),
                                   ctypes.byref(work), ctypes.byref(by)))
-    return {"launches": n.value, "ms": ms.value, "work": work.value, "bytes": by.value}
+    mac = ctypes.c_double()
+    _check(load().he_profile_read_mac(ctx.ptr, kernel_class.encode(), ctypes.byref(mac)))
+    return {"launches": n.value, "ms": ms.value, "work": work.value, "bytes": by.value, "mac": mac.value}
 
 
 def he_profile_names(ctx) -> list:

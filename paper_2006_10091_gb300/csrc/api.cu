@@ -24,6 +24,7 @@ int fail(int code, const std::string& msg) {
 size_t ws_alloc_bytes(size_t bytes) { return bytes + bytes / 8 + (1 << 20); }
 
 int ws_reserve(he_ctx* c, size_t bytes) {
+  c->ws_requests += 1;
   if (c->ws.size >= bytes) return HE_OK;
   HE_CUDA(cudaStreamSynchronize(c->stream));
   if (c->ws.ptr) cudaFree(c->ws.ptr);
@@ -302,6 +303,13 @@ int he_ctx_info(const he_ctx* c, uint32_t* n, uint32_t* L, uint32_t* alpha, uint
   if (alpha) *alpha = (uint32_t)c->alpha;
   if (beta) *beta = (uint32_t)c->beta;
   if (primes) memcpy(primes, c->q.data(), sizeof(uint64_t) * c->np);
+  return HE_OK;
+}
+
+int he_ctx_workspace(const he_ctx* c, size_t* bytes, uint64_t* requests) {
+  if (!c) return fail(HE_EINVAL, "he_ctx_workspace: null context");
+  if (bytes) *bytes = c->ws.size;
+  if (requests) *requests = c->ws_requests;
   return HE_OK;
 }
 

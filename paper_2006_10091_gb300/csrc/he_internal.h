@@ -56,6 +56,7 @@ struct Workspace {
 struct ProfClass {
   uint64_t launches = 0;
   double work = 0.0, bytes = 0.0;
+  double mac = 0.0;  // the part of work that is unreduced 128-bit multiply-accumulates
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
 };
 
@@ -109,6 +110,7 @@ struct he_ctx {
   std::map<std::pair<uint32_t, double>, int64_t*> lr_masks;
 
   he::Workspace ws;
+  uint64_t ws_requests = 0;  // calls of ws_reserve on this context (he_ctx_workspace)
   bool prof_on = false;
   std::map<std::string, he::ProfClass> prof;
   uint64_t* h_stage = nullptr;  // pinned staging (host <-> device)
@@ -136,7 +138,7 @@ namespace he {
 // (algorithmic DRAM bytes) to kernel class `name` when timing is enabled.
 class ProfScope {
  public:
-  ProfScope(he_ctx* c, const char* name, double work, double bytes);
+  ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac = 0.0);
   ~ProfScope();
 
  private:
@@ -144,6 +146,17 @@ class ProfScope {
   cudaEvent_t stop_ = nullptr;
 };
 void prof_clear(he_ctx* c);
+// While one of these lives, launches on this host thread are not timed
+// (ProfScope records nothing), whatever the context's setting: for entry
+// points that must create no CUDA objects, without touching shared state.
+class ProfSuppress {
+ public:
+  ProfSuppress();
+  ~ProfSuppress();
+
+ private:
+  bool prev_;
+};
 
 // ---- workspace ----------------------------------------------------------------
 int ws_reserve(he_ctx* c, size_t bytes);  // may reallocate (synchronises first)

@@ -695,8 +695,13 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
   const double conv = (double)a.beta * a.nt - own;
   {
     const size_t blocks = (size_t)count * a.nt * SR::TILES;
-    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * ra.nrot * a.beta * a.nt * n),
-                   count * n * 8 * (conv + own + 2.0 * ra.nrot * a.nt));
+    // work: the converted limbs' row-pass butterflies, one reduction per
+    // accumulator residue, and the key products (128-bit multiply-accumulates);
+    // bytes: the limbs read once, one accumulator written (the rotations'
+    // products are summed into it), each rotation's key read once per launch
+    const double macs = count * 2.0 * ra.nrot * a.beta * a.nt * n;
+    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs,
+                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs);
     KsRotArgs rc = ra;
     rc.count = count;
     rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits

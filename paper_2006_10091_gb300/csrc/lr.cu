@@ -26,11 +26,13 @@
 //   D  = sum_k tensor(S_k, drop(Z_k)) ;  G = rescale(relinearise(D))   (one key switch per shard)
 //   H  = sum over o < g of rot(G, o) ;  R = rescale(H (x) mask) ;  R <- sum over o < g of rot(R, -o)
 //   W' = drop(W) + R                        (scale sW, level l0-5)
+//   W' += rescale(drop(W, l0-4) * round(-lr l2 q[l0-5]))   with the L2 regulariser (Eq. 4, 6)
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <vector>
@@ -91,6 +93,7 @@ struct LrPlan {
   uint32_t l0, g, logF, logg;
   double sZ, sW, sU, sT, sS, sigA, sigB, sigQ, sA_out, sC, sB, sQ, sG, sR;
   int64_t kA, kB, kQ, k0;
+  int64_t kR;  // round(-lr l2 q_{l0-5}): the regulariser's constant (0: none)
   bool has_c2;
 };
 
@@ -125,10 +128,15 @@ static int lr_plan(const he_ctx* c, uint32_t l0, double sZ, double sW, const he_
   p->sQ = (p->sT * p->sigQ) / (double)q[l0 - 3];
   if (p->has_c2 && !scales_eq(p->sC, p->sQ)) return fail(HE_ESCALE, "quadratic term scale mismatch");
   if (!to_int(cfg->coeffs[0] * lr * p->sC, &p->k0)) return fail(HE_EINVAL, "constant beyond int64");
+  p->kR = 0;
   if (infer) return HE_OK;
   p->sG = p->sC * sZ / (double)q[l0 - 4];
   p->sR = (p->sG * ms) / (double)q[l0 - 5];
   if (!scales_eq(p->sR, sW)) return fail(HE_ESCALE, "output scale mismatch");
+  if (cfg->l2 != 0.0) {  // - lr l2 w at W's scale: w times round(-lr l2 q_{l0-5}), rescaled by q_{l0-5}
+    if (!to_int(-lr * cfg->l2 * (double)q[l0 - 5], &p->kR)) return fail(HE_EINVAL, "l2 constant beyond int64");
+    if (!scales_eq((sW * (double)q[l0 - 5]) / (double)q[l0 - 5], sW)) return fail(HE_ESCALE, "l2 term scale");
+  }
   return HE_OK;
 }
 
@@ -445,6 +453,16 @@ static int lr_run(he_ctx* c, std::vector<Shard>& sh, const he_lr_config* cfg, ui
       r.base += (size_t)i * R.stride;
       HE_TRY(addsub_batch(c, CtBatch{s.W.data, 0, s.W.cap, 0}, r, CtBatch{s.W_out->data, 0, s.W_out->cap, 0}, 0,
                           l0 - 5, 1));
+      if (P.kR) {  // the regulariser's gradient (Eq. 6, 8): W_out += rescale(drop(W, l0-4) * kR)
+        ops.off = 0;
+        uint64_t* wt = ops.take<uint64_t>((size_t)2 * (l0 - 4) * c->n);
+        uint64_t* wr = ops.take<uint64_t>((size_t)2 * (l0 - 5) * c->n);
+        if (!wt || !wr) return fail(HE_ENOMEM, "regulariser scratch too small");
+        const CtBatch Wt{wt, 0, l0 - 4, 0}, Wr{wr, 0, l0 - 5, 0}, Wo{s.W_out->data, 0, s.W_out->cap, 0};
+        HE_TRY(mul_int_batch(c, CtBatch{s.W.data, 0, s.W.cap, 0}, Wt, P.kR, l0 - 4, 1));
+        HE_TRY(rescale_batch(c, Wt, l0 - 4, 1, Wr, ops));
+        HE_TRY(addsub_batch(c, Wo, Wr, Wo, 0, l0 - 5, 1));
+      }
     }
   }
   return HE_OK;
@@ -524,6 +542,7 @@ static int validate_shard(he_ctx* c, const he_lr_shard& in, const he_lr_config* 
   const uint32_t g = cfg->g;
   if (g < 1 || (g & (g - 1)) || g > (uint32_t)c->n / 2) return fail(HE_EINVAL, "g must be a power of two <= N/2");
   if (!(cfg->mask_scale > 0.0)) return fail(HE_EINVAL, "mask_scale must be positive");
+  if (!(cfg->l2 >= 0.0) || !std::isfinite(cfg->l2)) return fail(HE_EINVAL, "l2 must be finite and >= 0");
   return HE_OK;
 }
 
@@ -563,8 +582,8 @@ int lr_entry(he_ctx* c, const he_lr_shard* shards, size_t count, const he_lr_con
     // one CUDA graph per distinct call (pointers, sizes, configuration)
     std::string key;
     char buf[160];
-    snprintf(buf, sizeof buf, "%d|%u|%a|%a|%a|%a|%a|%a|%u|", (int)infer, refresh_level, cfg->coeffs[0],
-             cfg->coeffs[1], cfg->coeffs[2], cfg->coeffs[3], cfg->lr, cfg->mask_scale, cfg->g);
+    snprintf(buf, sizeof buf, "%d|%u|%a|%a|%a|%a|%a|%a|%u|%a|", (int)infer, refresh_level, cfg->coeffs[0],
+             cfg->coeffs[1], cfg->coeffs[2], cfg->coeffs[3], cfg->lr, cfg->mask_scale, cfg->g, cfg->l2);
     key += buf;
     for (auto& s : sh) {
       snprintf(buf, sizeof buf, "%p,%zu,%p,%u,%a,%p,%p,%u;", (const void*)s.Z, s.nZ, (const void*)s.W_in->data,

@@ -34,6 +34,9 @@ static uint64_t* g_noalloc_addr[HE_NOALLOC_DEVICES];
 
 // Device address of the static array on `dev`, looked up once per device
 // with that device current (the host-side symbol is not a device address).
+// The cache assumes the device's primary context lives as long as the
+// process: after cudaDeviceReset the cached address is stale, and this entry
+// point must not be called again in that process.
 static int noalloc_scratch(int dev, uint64_t** out) {
   if (dev < 0 || dev >= HE_NOALLOC_DEVICES) return fail(HE_EINVAL, "he_rescale_noalloc: device index out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -75,12 +78,10 @@ extern "C" int he_rescale_noalloc(he_ctx* c, const he_ct* a, he_ct* out) {
   ar.size = sizeof(uint64_t) * HE_NOALLOC_WORDS;
   ar.off = 0;
   const double scale = a->scale / (double)c->q[level - 1];
-  // kernel timing creates CUDA events; it is not recorded for this call
-  const bool prof = c->prof_on;
-  c->prof_on = false;
-  const int rc = rescale_batch(c, CtBatch{a->data, 0, a->cap, 0}, level, 1, CtBatch{out->data, 0, out->cap, 0}, ar);
-  c->prof_on = prof;
-  HE_TRY(rc);
+  // kernel timing creates CUDA events: it is suppressed for this call on this
+  // thread only (the context's own setting is left alone)
+  ProfSuppress quiet;
+  HE_TRY(rescale_batch(c, CtBatch{a->data, 0, a->cap, 0}, level, 1, CtBatch{out->data, 0, out->cap, 0}, ar));
   out->level = level - 1;
   out->scale = scale;
   return HE_OK;

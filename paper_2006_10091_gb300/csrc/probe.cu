@@ -1,7 +1,7 @@
 // probe.cu -- register-resident integer throughput probes behind the integer
 // roof the benchmark reports: chains of 32-bit multiply-adds, chains of 64-bit
-// Shoup products (w known: a*w - umulhi(a, w')*q), and radix-8 rounds of the
-// lazy forward butterfly.  No memory traffic inside the timed loops; every
+// Shoup products (w known: a*w - umulhi(a, w')*q), radix-8 rounds of the
+// lazy forward butterfly, and 64 x 64 -> 128-bit multiply-accumulates.  No memory traffic inside the timed loops; every
 // thread writes one word at the end (the output buffer holds exactly one word
 // per thread).
 #include <cuda_runtime.h>
@@ -68,12 +68,30 @@ __global__ void probe_bfly(uint64_t* out, int iters, uint64_t q, const uint64_t*
   out[blockIdx.x * blockDim.x + threadIdx.x] = r;
 }
 
+// 64 x 64 -> 128-bit multiply-accumulates (the key products of the fused
+// key switch, summed unreduced), four independent 128-bit sums per thread
+// over eight register-resident operand pairs; one reduction at the end.
+__global__ void probe_mac(uint64_t* out, int iters, uint64_t q) {
+  uint64_t x[8], y[8], lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 8; ++k) {
+    x[k] = (0x9E3779B97F4A7C15ull * (threadIdx.x + 8u * k + 1)) % q;
+    y[k] = (0xC2B2AE3D27D4EB4Full * (blockIdx.x + 8u * k + 3)) % q;
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mac128(lo[k], hi[k], x[(u + k) & 7], y[u]);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (lo[0] ^ lo[1] ^ lo[2] ^ lo[3]) + (hi[0] ^ hi[1] ^ hi[2] ^ hi[3]) % q;
+}
+
 }  // namespace he
 
 using namespace he;
 
 extern "C" int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second) {
-  if (kind < 0 || kind > 2 || !per_clock_per_sm || !per_second) return fail(HE_EINVAL, "he_probe_alu: bad argument");
+  if (kind < 0 || kind > 3 || !per_clock_per_sm || !per_second) return fail(HE_EINVAL, "he_probe_alu: bad argument");
   int dev = 0, sms = 0, khz = 0;
   HE_CUDA(cudaGetDevice(&dev));
   HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -106,9 +124,12 @@ extern "C" int he_probe_alu(int kind, double* per_clock_per_sm, double* per_seco
     } else if (kind == 1) {
       probe_shoup<<<blocks, threads>>>((uint64_t*)out, 1024, q, htw[0], htw[1]);
       ops = (double)blocks * threads * 1024 * 8 * 4;
-    } else {
+    } else if (kind == 2) {
       probe_bfly<<<blocks, threads>>>((uint64_t*)out, 2000, q, tw);
       ops = (double)blocks * threads * 2000 * 12;
+    } else {
+      probe_mac<<<blocks, threads>>>((uint64_t*)out, 2048, q);
+      ops = (double)blocks * threads * 2048 * 8 * 4;
     }
     cudaEventRecord(e1);
   }

@@ -8,14 +8,20 @@
 
 namespace he {
 
-ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes) : c_(c) {
-  if (!c->prof_on) {
+static thread_local bool tl_prof_suppressed = false;
+
+ProfSuppress::ProfSuppress() : prev_(tl_prof_suppressed) { tl_prof_suppressed = true; }
+ProfSuppress::~ProfSuppress() { tl_prof_suppressed = prev_; }
+
+ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac) : c_(c) {
+  if (!c->prof_on || tl_prof_suppressed) {
     c_ = nullptr;
     return;
   }
   ProfClass& k = c->prof[name];
   k.work += work;
   k.bytes += bytes;
+  k.mac += mac;
   k.launches += 1;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -84,5 +90,12 @@ extern "C" int he_profile_names(he_ctx* c, char* buf, size_t cap) {
   }
   if (s.size() + 1 > cap) return fail(HE_EINVAL, "buffer too small");
   memcpy(buf, s.c_str(), s.size() + 1);
+  return HE_OK;
+}
+
+extern "C" int he_profile_read_mac(he_ctx* c, const char* name, double* mac_work) {
+  if (!c || !name || !mac_work) return fail(HE_EINVAL, "null argument");
+  auto it = c->prof.find(name);
+  *mac_work = it == c->prof.end() ? 0.0 : it->second.mac;
   return HE_OK;
 }

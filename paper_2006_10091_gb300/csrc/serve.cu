@@ -262,8 +262,17 @@ static void scheduler(he_server* s) {
           ServeReq* q = s->pending[k];
           if (!same_wave(q->r, head->r)) { ++k; continue; }
           shapes.push_back(req_shape(q->r));
-          const size_t g = ws_growth(free_slot->view, shapes, head->r.z_level);
-          if (s->used + bytes + q->dev_bytes + g > s->budget && !(wave.empty() && s->inflight == 0)) {
+          size_t g = ws_growth(free_slot->view, shapes, head->r.z_level);
+          if (s->used + bytes + q->dev_bytes + g > s->budget && wave.empty() && s->inflight == 0 &&
+              free_slot->view->ws.ptr) {
+            // nothing runs and the other idle slots gave their workspaces back
+            // above: the slot's own goes too, so that only this request is
+            // counted (submit refused any request that alone exceeds the budget)
+            s->used -= free_slot->view->ws.size;
+            ws_release(free_slot->view);
+            g = ws_growth(free_slot->view, shapes, head->r.z_level);
+          }
+          if (s->used + bytes + q->dev_bytes + g > s->budget) {
             shapes.pop_back();
             break;
           }
@@ -346,6 +355,15 @@ extern "C" int he_server_submit(he_server* s, const he_request* r, uint64_t* id)
     return fail(HE_EINVAL, "he_server_submit: output buffer too small");
   }
   q->dev_bytes = sizeof(uint64_t) * req_words(*r, c->n);
+  {  // the request alone: its buffers and a slot's workspace for it
+    const LrShape sh = req_shape(*r);
+    he_ctx* v = s->slots[r->ctx].empty() ? c : s->slots[r->ctx][0].view;
+    const size_t alone = q->dev_bytes + ws_alloc_bytes(lr_ws_bytes(v, &sh, 1, r->z_level));
+    if (alone > s->budget) {
+      delete q;
+      return fail(HE_ENOMEM, "he_server_submit: the request alone needs more device memory than the budget");
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     q->id = s->next_id++;

@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 
+import oracle
 from paper_2006_10091_gb300 import workloads
 from tests.gpu_util import Pair, assert_same_residues, gpu_lib
 from tests.lr_reference import lr_step_fp64, table2
@@ -43,6 +44,45 @@ def test_lr_step_bit_exact(lr_pair, loss):
     want = pair.o.lr_gradient_step(Zo, Wo, coeffs, lr, g, 2.0 ** 40)
     assert out.level == level - 5
     assert_same_residues(out, want, he, pair.g)
+
+
+@pytest.mark.parametrize("l2", [0.5, 3.0])
+def test_lr_step_with_l2_regulariser_bit_exact(lr_pair, l2):
+    """The step with the L2 regulariser's gradient (Eq. 4, 6: grad R = l2 w)
+    equals the oracle's residues, and decrypts to w + lr (sum p y x - l2 w)."""
+    pair, g = lr_pair
+    he = pair.he
+    n_slots = pair.n // 2
+    data = workloads.LRData(seed=3, n_samples=16, n_features=100)
+    coeffs = table2()["binomial"]
+    lr = 1.0 / data.n
+    zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+    ms = [pair.o.encode(v, scale=2.0 ** 40) for v in zs]
+    mw = pair.o.encode(workloads.pack_weights(data.w0, n_slots, g), scale=2.0 ** 40)
+    Zg = pair.g.new_ct(7, len(ms))
+    for k, m in enumerate(ms):
+        he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 7, Zg[k], cid=100 + k)
+    Wg = pair.gpu_enc(mw, 7, 99, scale=2.0 ** 40)
+    out = pair.g.new_ct(7)
+    he.he_lr_gradient_step(pair.g, Zg, Wg, he.lr_config(coeffs, lr, g, 2.0 ** 40, l2=l2), out)
+    Zo = [pair.orc_enc(m, 7, 100 + k, scale=2.0 ** 40) for k, m in enumerate(ms)]
+    want = pair.o.lr_gradient_step(Zo, pair.orc_enc(mw, 7, 99, scale=2.0 ** 40), coeffs, lr, g, 2.0 ** 40, l2=l2)
+    assert_same_residues(out, want, he, pair.g)
+    got = he.he_decrypt_decode(pair.g, out)
+    ref = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, lr, l2=l2), n_slots, g)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 2.0 ** -20
+
+
+def test_lr_step_refuses_negative_l2(lr_pair):
+    pair, g = lr_pair
+    he = pair.he
+    Z = pair.g.new_ct(7, 1)
+    he.he_encrypt_poly(pair.g, workloads.int_poly(1, pair.n, 100), 2.0 ** 40, 7, Z[0], cid=1)
+    W = pair.gpu_enc(workloads.int_poly(2, pair.n, 100), 7, 2, scale=2.0 ** 40)
+    out = pair.g.new_ct(7)
+    with pytest.raises(he.HeError) as e:
+        he.he_lr_gradient_step(pair.g, Z, W, he.lr_config(table2()["binomial"], 0.1, g, 2.0 ** 40, l2=-1.0), out)
+    assert e.value.code == he.HE_EINVAL
 
 
 def test_lr_step_non_uniform_inputs(lr_pair):
@@ -142,6 +182,44 @@ def test_workers_match_separate_calls(lr_pair, graph):
         he.he_lr_gradient_step(pair.g, Zv, W, cfg, single)
         assert W_out.level == W.level - 5
         assert np.array_equal(he.he_ct_export(pair.g, W_out), he.he_ct_export(pair.g, single))
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_workers_match_oracle(lr_pair, graph):
+    """Three workers of 1, 3 and 2 data ciphertexts, weights at levels 7, 7
+    and 6 (no refresh), in one batched call (eager, and captured then
+    replayed as a CUDA graph): each worker's new weights equal the oracle's
+    step on that worker's data, residue for residue."""
+    pair, g = lr_pair
+    he = pair.he
+    coeffs, lr, ms = table2()["huber"], 0.05, 2.0 ** 40
+    sizes, wlevels = [1, 3, 2], [7, 7, 6]
+    shards, wants = [], []
+    for k, (nz, wl) in enumerate(zip(sizes, wlevels)):
+        mz = [workloads.int_poly(9000 + 100 * k + i, pair.n, 1 << 28) for i in range(nz)]
+        mw = workloads.int_poly(9000 + 100 * k + 99, pair.n, 1 << 28)
+        Z = pair.g.new_ct(7, nz)
+        for i, m in enumerate(mz):
+            he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 7, Z[i], cid=9000 + 100 * k + i)
+        W = pair.gpu_enc(mw, wl, 9000 + 100 * k + 99, scale=2.0 ** 40, cap=7)
+        shards.append((Z, W, pair.g.new_ct(7)))
+        Zo = [pair.orc_enc(m, 7, 9000 + 100 * k + i, scale=2.0 ** 40) for i, m in enumerate(mz)]
+        Zo = [oracle.Ciphertext(np.ascontiguousarray(z.data[:, :wl]), wl, z.scale) for z in Zo]
+        Wo = pair.orc_enc(mw, wl, 9000 + 100 * k + 99, scale=2.0 ** 40)
+        wants.append(pair.o.lr_gradient_step(Zo, Wo, coeffs, lr, g, ms))
+    cfg = he.lr_config(coeffs, lr, g, ms)
+    import torch
+    side = torch.cuda.Stream()  # graph capture needs a non-default stream
+    torch.cuda.synchronize()
+    he.he_set_stream(pair.g, side.cuda_stream)
+    try:
+        for _ in range(2 if graph else 1):  # a graph call captures, the next one replays
+            he.he_lr_gradient_step_workers(pair.g, shards, cfg, graph=graph)
+        he.he_sync(pair.g)
+    finally:
+        he.he_set_stream(pair.g, torch.cuda.current_stream().cuda_stream)
+    for (Z, W, W_out), want in zip(shards, wants):
+        assert_same_residues(W_out, want, he, pair.g)
 
 
 def test_workers_refresh_low_levels(lr_pair):
@@ -363,3 +441,4 @@ def test_training_loop_matches_fp64_algorithm(refresh_every, top, iterations):
     with pytest.raises(he.HeError) as e:  # the limbs hold fewer steps than that between refreshes
         he.he_lr_train(ctx, workers, cfg, iterations, (top - 1) // 5 + 1, top, out)
     assert e.value.code == he.HE_ELEVEL
+

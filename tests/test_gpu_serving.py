@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2006_10091_gb300 import workloads
-from tests.gpu_util import gpu_lib
+from tests.gpu_util import Pair, gpu_lib
 from tests.lr_reference import lr_step_fp64, table2
 
 pytestmark = pytest.mark.gpu
@@ -122,3 +122,60 @@ def test_budget_bounds_device_memory(setup):
     _, stats = serve(he, ctxs, reqs[:6], budget, 3, 4, False)
     assert stats["used"] == 0 or stats["used"] <= stats["peak_used"]
     assert stats["peak_used"] <= budget
+
+
+def test_served_results_equal_the_oracle():
+    """A gradient request and an inference request (N = 2^12, two special
+    primes, weights at the data's level: no refresh), served together and
+    each alone: the result residues equal the oracle's step and inference on
+    the same ciphertexts."""
+    he = gpu_lib()
+    g, n_slots = 16, 1 << 11
+    pair = Pair(12, 7, 40, 2, 50, 2.0 ** 40, seed=32, rots=rots(he, n_slots, g))
+    coeffs = table2()["binomial"]
+    data = workloads.LRData(seed=400, n_samples=2 * g, n_features=125)
+    zs = workloads.pack_samples(data.X, data.y, n_slots, g)
+    Zo = [pair.orc_enc(pair.o.encode(v, scale=2.0 ** 40), 7, 500 + k, scale=2.0 ** 40) for k, v in enumerate(zs)]
+    Wo = pair.orc_enc(pair.o.encode(workloads.pack_weights(data.w0, n_slots, g), scale=2.0 ** 40), 7, 499,
+                      scale=2.0 ** 40)
+    Zh = np.ascontiguousarray(np.stack([z.data for z in Zo]))
+    Wh = np.ascontiguousarray(Wo.data)
+    grad_cfg = he.lr_config(coeffs, 1.0 / 64, g, 2.0 ** 27)
+    inf_cfg = he.lr_config(coeffs, 1.0, g, 2.0 ** 40)
+    want_grad = pair.o.lr_gradient_step(Zo, Wo, coeffs, 1.0 / 64, g, 2.0 ** 27)
+    want_inf = pair.o.lr_inference(Zo, Wo, coeffs, 1.0, g)
+    for together in (True, False):
+        srv = he.Server([pair.g], 1 << 34, max_inflight=2, max_wave=4)
+        try:
+            out_g = np.zeros((2, 2, pair.n), dtype=np.uint64)
+            out_i = np.zeros((len(zs), 2, 4, pair.n), dtype=np.uint64)
+            srv.submit(0, he.HE_REQ_GRADIENT, Zh, 7, 2.0 ** 40, Wh, 7, 2.0 ** 40, grad_cfg, out_g)
+            if not together:
+                srv.drain()
+            srv.submit(0, he.HE_REQ_INFERENCE, Zh, 7, 2.0 ** 40, Wh, 7, 2.0 ** 40, inf_cfg, out_i)
+            srv.drain()
+            res = srv.poll()
+        finally:
+            srv.close()
+        assert [r["status"] for r in res] == [0, 0]
+        assert np.array_equal(out_g, want_grad.data)
+        for k in range(len(zs)):
+            assert np.array_equal(out_i[k], want_inf[k].data), k
+
+
+def test_request_larger_than_the_budget_is_refused(setup):
+    """A request whose own buffers and workspace exceed the whole budget is
+    refused at submit with HE_ENOMEM instead of being admitted alone."""
+    he, ctxs, reqs, _ = setup
+    srv = he.Server(ctxs, 1 << 20, max_inflight=1, max_wave=1)
+    try:
+        r = reqs[1]
+        out = np.zeros(r["shape"], dtype=np.uint64)
+        with pytest.raises(he.HeError) as e:
+            srv.submit(r["ci"], r["kind"], r["Zh"], 7, 2.0 ** 40, r["Wh"], r["w_level"], 2.0 ** 40, r["cfg"], out,
+                       refresh_cid=r["cid"], min_w_level=r["min_w"])
+        assert e.value.code == he.HE_ENOMEM
+        srv.drain()
+        assert srv.stats()["peak_used"] == 0
+    finally:
+        srv.close()

@@ -401,6 +401,31 @@ def test_lr_step_matches_fp64_update(loss):
     assert rel < 2.0 ** -20, rel
 
 
+@pytest.mark.parametrize("l2", [0.5, 3.0])
+def test_lr_step_with_l2_regulariser_matches_fp64_update(l2):
+    """The step with the regulariser of Eq. 4 (R = (l2/2) |w|^2, so the
+    gradient of Eq. 6/8 gains l2 w) decrypts to the FP64 update
+    w + lr (sum p(.) y x - l2 w), and differs from the unregularised step by
+    -lr l2 w slot by slot (a dropped or sign-flipped term fails both)."""
+    log_n, g = 10, 4
+    n_slots = (1 << log_n) // 2
+    data = workloads.LRData(seed=3, n_samples=16, n_features=100)
+    o = oracle.Oracle(log_n, 7, 40, 1, 60, 2.0 ** 40, seed=1, rot_steps=he.lr_rot_steps(n_slots, g))
+    coeffs = table2()["binomial"]
+    lr = 1.0 / data.n
+    Z = [_enc(o, v, 7, 100 + k) for k, v in enumerate(workloads.pack_samples(data.X, data.y, n_slots, g))]
+    W = _enc(o, workloads.pack_weights(data.w0, n_slots, g), 7, 99)
+    out = o.lr_gradient_step(Z, W, coeffs, lr, g, 2.0 ** 40, l2=l2)
+    assert out.level == 2 and out.scale == W.scale
+    re, _ = o.decrypt(out)
+    want = workloads.pack_weights(lr_step_fp64(data.X, data.y, data.w0, coeffs, lr, l2=l2), n_slots, g)
+    assert np.max(np.abs(re - want)) / np.max(np.abs(want)) < 2.0 ** -20
+    re0, _ = o.decrypt(o.lr_gradient_step(Z, W, coeffs, lr, g, 2.0 ** 40))
+    delta = -lr * l2 * workloads.pack_weights(data.w0, n_slots, g)
+    assert np.max(np.abs((re - re0) - delta)) < 2.0 ** -20 * np.max(np.abs(want))
+    assert np.max(np.abs(delta)) > 1e-3  # the term is far above the tolerance
+
+
 def test_keyswitch_equals_big_integer_definition(tiny):
     """Hybrid key switching recomputed with Python integers from its
     definition: per digit the approximate ModUp y_j = sum_i [x_i (Q_j/q_i)^-1]_{q_i}

@@ -27,6 +27,48 @@ def test_rescale_noalloc_matches_rescale_on_consecutive_calls():
         assert np.array_equal(he.he_ct_export(ctx, out), he.he_ct_export(ctx, ref))
 
 
+def test_rescale_noalloc_never_asks_the_workspace():
+    """On a fresh context (no rescale run yet) the entry point neither grows
+    the context's workspace nor asks it for scratch at all (a fallback to the
+    workspace would count a request), and its result equals he_rescale's,
+    which does ask."""
+    he = gpu_lib()
+    ctx = he.Context(13, 6, 45, 1, 60, 2.0 ** 45, seed=23)
+    host = workloads.residues(5, ctx.primes[:6], ctx.n, parts=2)
+    a = ctx.new_ct(6)
+    he.he_ct_import(ctx, host, 6, 2.0 ** 45, a)
+    before = he.he_ctx_workspace(ctx)
+    out = ctx.new_ct(6)
+    he.he_rescale_noalloc(ctx, a, out)
+    he.he_sync(ctx)
+    assert he.he_ctx_workspace(ctx) == before
+    ref = ctx.new_ct(6)
+    he.he_rescale(ctx, a, ref)
+    assert he.he_ctx_workspace(ctx)["requests"] == before["requests"] + 1
+    assert np.array_equal(he.he_ct_export(ctx, out), he.he_ct_export(ctx, ref))
+
+
+def test_rescale_noalloc_at_the_size_limit():
+    """N = 2^14: level 15 needs 2*15*N + 64 words, within the 2^19 of the
+    array, and matches he_rescale; level 16 needs 2^19 + 64 and is refused."""
+    he = gpu_lib()
+    ctx = he.Context(14, 16, 40, 1, 60, 2.0 ** 40, seed=24)
+    for level, ok in ((15, True), (16, False)):
+        host = workloads.residues(60 + level, ctx.primes[:level], ctx.n, parts=2)
+        a = ctx.new_ct(level)
+        he.he_ct_import(ctx, host, level, 2.0 ** 40, a)
+        out = ctx.new_ct(level)
+        if not ok:
+            with pytest.raises(he.HeError) as e:
+                he.he_rescale_noalloc(ctx, a, out)
+            assert e.value.code == he.HE_EINVAL
+            continue
+        he.he_rescale_noalloc(ctx, a, out)
+        ref = ctx.new_ct(level)
+        he.he_rescale(ctx, a, ref)
+        assert np.array_equal(he.he_ct_export(ctx, out), he.he_ct_export(ctx, ref))
+
+
 def test_rescale_noalloc_rejects_sizes_beyond_the_static_array():
     he = gpu_lib()
     ctx = he.Context(16, 4, 50, 1, 60, 2.0 ** 50, seed=22)  # 2 * 4 * 2^16 words > 2^19
