@@ -812,34 +812,87 @@ def serving(he, torch, stream, n_requests=400, n_warm=100, rate=2000.0, seed=0, 
                       "not 128-bit secure at N<=2^15 (benchmark parameters)"}
 
 
-def cpu_baseline(data, coeffs, lr):
-    """The oracle as it stands on a bounded sample: the step over 1 and over 2
-    data ciphertexts, extrapolated linearly to the 512 ciphertexts of a step."""
-    import oracle
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_step_inputs(o, data, n_ct):
     from paper_2006_10091_gb300 import workloads
     n_slots = (1 << LOG_N) // 2
-    o = oracle.Oracle(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0,
-                      rot_steps=rot_steps(n_slots, G))
-    zs = workloads.pack_samples(data.X[:2 * G], data.y[:2 * G], n_slots, G)
+    zs = workloads.pack_samples(data.X[:n_ct * G], data.y[:n_ct * G], n_slots, G)
     Z = [o.encrypt(o.encode(v), L, cid=1000 + k) for k, v in enumerate(zs)]
     W = o.encrypt(o.encode(workloads.pack_weights(data.w0, n_slots, G)), L, cid=999)
+    return Z, W
+
+
+def _oracle_rate(o, Z, W, coeffs, lr, m):
+    """Seconds of the oracle's step over m and over 2m data ciphertexts ->
+    (per-ciphertext seconds at this thread count, fixed seconds of the final
+    stage); the step over the 512 ciphertexts is extrapolated linearly."""
     t = []
-    for k in (1, 2):
+    for k in (m, 2 * m):
         t0 = time.perf_counter()
         o.lr_gradient_step(Z[:k], W, coeffs, lr, G, MASK_SCALE)
         t.append(time.perf_counter() - t0)
-    per_ct = max(t[1] - t[0], 1e-9)
-    fixed = max(t[0] - per_ct, 0.0)
+    per = max((t[1] - t[0]) / m, 1e-9)
+    return per, max(t[0] - m * per, 0.0), t
+
+
+def cpu_baseline(data, coeffs, lr):
+    """The oracle as it stands on a bounded sample of the step, on all host
+    cores (OpenMP over the data ciphertexts and over limbs) and on one core:
+    the step over m and 2m of the 512 data ciphertexts (m = 1 on one core,
+    m = the thread count on all), extrapolated linearly to the 512."""
+    import oracle
+    nproc = os.cpu_count() or 1
+    threads0 = oracle.get_threads()
+    o = oracle.Oracle(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0,
+                      rot_steps=rot_steps((1 << LOG_N) // 2, G))
     n_ct = N_SAMPLES // G
-    step_s = fixed + n_ct * per_ct
-    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"the step over 1 and 2 of the {n_ct} data ciphertexts ({t[0]:.1f} s, {t[1]:.1f} s), "
-                      f"extrapolated linearly; single-threaded C, exact __int128 residue arithmetic"}
+    out = {}
+    try:
+        for label, nt in (("all", max(1, threads0)), ("one", 1)):
+            oracle.set_threads(nt)
+            m = 1 if nt == 1 else min(nt, n_ct // 2)
+            Z, W = _oracle_step_inputs(o, data, 2 * m)
+            per, fixed, t = _oracle_rate(o, Z, W, coeffs, lr, m)
+            step_s = fixed + n_ct * per
+            out[label] = {"value": 1.0 / step_s, "cores": nt, "sample_s": t, "m": m}
+    finally:
+        oracle.set_threads(threads0)
+    a, one = out["all"], out["one"]
+    return {"value": a["value"], "unit": "steps/s", "cores": a["cores"], "kind": "oracle",
+            "nproc": nproc, "cpu_model": cpu_model(),
+            "sample": (f"the oracle's step over {a['m']} and {2 * a['m']} of the {n_ct} data ciphertexts on "
+                       f"{a['cores']} threads ({a['sample_s'][0]:.1f} s, {a['sample_s'][1]:.1f} s), extrapolated "
+                       f"linearly; exact __int128 residue arithmetic, OpenMP over ciphertexts and limbs"),
+            "one_core": {"value": one["value"], "unit": "steps/s", "cores": 1,
+                         "sample": f"the step over 1 and 2 data ciphertexts ({one['sample_s'][0]:.1f} s, "
+                                   f"{one['sample_s'][1]:.1f} s), extrapolated linearly"}}
 
 
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank: int):
+    """The oracle as it stands, on the host's cores, on the step this bench
+    times: each timed step runs the oracle's step over m data ciphertexts (m =
+    the thread count) and extrapolates to the 512 with the fixed final-stage
+    cost measured during warm-up (a run over 2m)."""
     if rank != 0:
         return
     import oracle
@@ -847,37 +900,31 @@ def run_reference(args, rank: int):
     data = workloads.LRData(seed=0, n_samples=N_SAMPLES, n_features=N_FEATURES)
     coeffs = table2_binomial()
     lr = 1.0 / N_SAMPLES
-    n_slots = (1 << LOG_N) // 2
     o = oracle.Oracle(LOG_N, L, LIMB_BITS, ALPHA, SPECIAL_BITS, SCALE, seed=0,
-                      rot_steps=rot_steps(n_slots, G))
-    zs = workloads.pack_samples(data.X[:2 * G], data.y[:2 * G], n_slots, G)
-    Z = [o.encrypt(o.encode(v), L, cid=1000 + k) for k, v in enumerate(zs)]
-    W = o.encrypt(o.encode(workloads.pack_weights(data.w0, n_slots, G)), L, cid=999)
+                      rot_steps=rot_steps((1 << LOG_N) // 2, G))
+    threads = oracle.get_threads()
     n_ct = N_SAMPLES // G
-    # warm-up: the fixed (final-stage) cost from the 1- and 2-ciphertext samples
-    t = []
-    for k in (1, 2):
-        t0 = time.perf_counter()
-        o.lr_gradient_step(Z[:k], W, coeffs, lr, G, MASK_SCALE)
-        t.append(time.perf_counter() - t0)
-    fixed = max(t[0] - (t[1] - t[0]), 0.0)
+    m = min(max(1, threads), n_ct // 2)
+    Z, W = _oracle_step_inputs(o, data, 2 * m)
+    per, fixed, _ = _oracle_rate(o, Z, W, coeffs, lr, m)  # warm-up: the fixed final-stage cost
     for _ in range(max(0, args.warmup - 2)):
-        o.lr_gradient_step(Z[:1], W, coeffs, lr, G, MASK_SCALE)
+        o.lr_gradient_step(Z[:m], W, coeffs, lr, G, MASK_SCALE)
     step_s = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.lr_gradient_step(Z[:1], W, coeffs, lr, G, MASK_SCALE)
-        one = time.perf_counter() - t0
-        step_s.append(fixed + n_ct * (one - fixed))
+        o.lr_gradient_step(Z[:m], W, coeffs, lr, G, MASK_SCALE)
+        t = time.perf_counter() - t0
+        step_s.append(fixed + (n_ct / m) * max(t - fixed, 1e-9))
     mean = sum(step_s) / len(step_s)
     value = 1.0 / mean
-    sample = (f"each step times the oracle's step over 1 of the {n_ct} data ciphertexts and "
-              f"extrapolates linearly (fixed final-stage cost {fixed:.2f} s from a 2-ciphertext run)")
+    sample = (f"each step times the oracle's step over {m} of the {n_ct} data ciphertexts on {threads} threads "
+              f"and extrapolates linearly (fixed final-stage cost {fixed:.2f} s from a {2 * m}-ciphertext run)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1000.0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

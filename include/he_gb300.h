@@ -100,8 +100,10 @@ int he_sync(he_ctx* ctx);
  * = 1 to run the runtime-shaped NTT kernel instead of the compile-time-shaped
  * one for N = 2^12 .. 2^16, "ntt_shape" = 0 (default), 1 or 2 for the three NTT tile-shape pairs compiled
  * per ring size (also used by the fused key switch), "ntt_pb_max" = at most this
- * many polynomials of one limb per NTT CTA (default 8).  HE_EINVAL for an
- * unknown key or a value out of range. */
+ * many polynomials of one limb per NTT CTA (default 8), "ks_ct" = 1, 2 or 4
+ * ciphertexts per CTA of the key switch's product kernel in stages whose
+ * rotations keep each CTA's rows (0, the default: 2 when their tiles fit in
+ * shared memory).  HE_EINVAL for an unknown key or a value out of range. */
 int he_set_tuning(he_ctx* ctx, const char* key, double value);
 /* Current value of a tuning knob (the keys above). */
 int he_get_tuning(he_ctx* ctx, const char* key, double* value);
@@ -190,6 +192,13 @@ int he_ct_export_batch(he_ctx* ctx, const he_ct* cts, size_t count, uint64_t* ho
  * differ.  out may alias a or b. */
 int he_add(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
 int he_sub(he_ctx* ctx, const he_ct* a, const he_ct* b, he_ct* out);
+
+/* out = a[0] + ... + a[count-1] (Eq. 1 applied count - 1 times): residues
+ * added modulo each limb's prime, in one kernel when a[1..count) sit at a
+ * constant stride in one allocation.  The sum is taken at the lowest level
+ * of the inputs, all at one scale (else HE_ESCALE); out may alias a[0] only.
+ * The aggregation of several workers' encrypted weights (Algorithm 2). */
+int he_sum(he_ctx* ctx, const he_ct* a, size_t count, he_ct* out);
 
 /* Keep the first `level` limbs (modulus reduction without division). */
 int he_drop_level(he_ctx* ctx, const he_ct* a, uint32_t level, he_ct* out);

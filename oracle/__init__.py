@@ -34,14 +34,24 @@ VP = ctypes.c_void_p
 
 def build(force: bool = False) -> str:
     """Compile he_oracle.c into liboracle.so (gcc, no FMA contraction so
-    that double scale bookkeeping is the same on every host)."""
+    that double scale bookkeeping is the same on every host), with OpenMP
+    when the compiler has it (results do not depend on the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-             "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base + ["-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (OpenMP; 1 without it)."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _load():
@@ -55,6 +65,8 @@ def _load():
                                        ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_uint64, VP, ctypes.c_int]
             lib.orc_destroy.argtypes = [VP]
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_get_threads.restype = ctypes.c_int
             lib.orc_is_prime.argtypes = [ctypes.c_uint64]
             lib.orc_min_root.restype = ctypes.c_uint64
             lib.orc_min_root.argtypes = [ctypes.c_uint64, ctypes.c_int]

@@ -21,14 +21,42 @@
  * switching (Han-Ki 2020).  Every such reading is marked [ext] and every
  * free convention (prime order, root choice, random streams, samplers) is
  * spelled out where it is implemented.
+ *
+ * Threads: when built with OpenMP, independent limbs (key generation, the
+ * key switch's targets, ModDown's targets) and, in the gradient step,
+ * independent data ciphertexts run in parallel.  Every parallel loop writes
+ * disjoint outputs, and the one shared sum (the step's gradient over the data
+ * ciphertexts) is exact modular addition, so results do not depend on the
+ * thread count.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 typedef unsigned __int128 u128;
 typedef __int128 i128;
+
+/* Threads of the parallel loops (1 without OpenMP). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 #define ORC_MAX_PRIMES 64
 
@@ -437,12 +465,13 @@ static uint64_t P_mod(orc_ctx* c, uint64_t m) {
  * evaluation form; e_j discrete Gaussian.  Stream id = tag * 256 + j. */
 static void gen_evk(orc_ctx* c, const uint64_t* sprime, uint32_t tag, uint64_t* key) {
   uint32_t n = c->n;
-  uint64_t* e = malloc(sizeof(uint64_t) * n);
   int64_t* ec = malloc(sizeof(int64_t) * n);
   for (int j = 0; j < c->beta; j++) {
     uint32_t sid = tag * 256u + (uint32_t)j;
     for (uint32_t i = 0; i < n; i++) ec[i] = sample_gauss(c->seed, i, sid, DOM_EVK_E, c->gT, c->gK);
+#pragma omp parallel for schedule(dynamic)
     for (int t = 0; t < c->np; t++) {
+      uint64_t* e = malloc(sizeof(uint64_t) * n);
       uint64_t q = c->q[t];
       uint64_t* b = key + ((size_t)(j * 2 + 0) * c->np + t) * n;
       uint64_t* a = key + ((size_t)(j * 2 + 1) * c->np + t) * n;
@@ -458,9 +487,9 @@ static void gen_evk(orc_ctx* c, const uint64_t* sprime, uint32_t tag, uint64_t* 
         if (in_digit) v = addmod(v, mulmod(pm, sp[i], q), q);
         b[i] = v;
       }
+      free(e);
     }
   }
-  free(e);
   free(ec);
 }
 
@@ -963,16 +992,19 @@ static void moddown_pair(orc_ctx* c, const uint64_t* acc, int level, uint64_t* k
       for (uint32_t i = 0; i < n; i++) yP[(size_t)k * n + i] = addmod(yP[(size_t)k * n + i], hk, pk);
     }
     uint64_t* dst = p == 0 ? k0 : k1;
+#pragma omp parallel for schedule(dynamic)
     for (int t = 0; t < level; t++) {
+      uint64_t* cv = malloc(sizeof(uint64_t) * n);
       uint64_t q = c->q[t];
       uint64_t ht = half_P_mod(c, q);
-      moddown_conv(c, yP, t, conv);
-      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
-      ntt_limb(c, t, conv);
+      moddown_conv(c, yP, t, cv);
+      for (uint32_t i = 0; i < n; i++) cv[i] = submod(cv[i], ht, q);
+      ntt_limb(c, t, cv);
       uint64_t pinv = invmod(P_mod(c, q), q);
       const uint64_t* at = POLY(ap, t, n);
       uint64_t* o = POLY(dst, t, n);
-      for (uint32_t i = 0; i < n; i++) o[i] = mulmod(submod(at[i], conv[i], q), pinv, q);
+      for (uint32_t i = 0; i < n; i++) o[i] = mulmod(submod(at[i], cv[i], q), pinv, q);
+      free(cv);
     }
   }
   free(yP); free(conv);
@@ -1004,9 +1036,10 @@ static void ks_inner(orc_ctx* c, const uint64_t* d, int level, const uint64_t* k
     memcpy(POLY(dc, t, n), POLY(d, t, n), sizeof(uint64_t) * n);
     intt_limb(c, t, POLY(dc, t, n));
   }
-  uint64_t* ext = malloc(sizeof(uint64_t) * n);
   for (int j = 0; j < beta_l; j++) {
+#pragma omp parallel for schedule(dynamic)
     for (int ti = 0; ti < nt; ti++) {
+      uint64_t* ext = malloc(sizeof(uint64_t) * n);
       int tp = ti < level ? ti : c->L + (ti - level); /* prime index */
       uint64_t q = c->q[tp];
       if (tp < level && tp >= digit_lo(c, j) && tp < digit_hi(c, j, level)) {
@@ -1023,9 +1056,10 @@ static void ks_inner(orc_ctx* c, const uint64_t* d, int level, const uint64_t* k
         a0[i] = addmod(a0[i], mulmod(ext[i], kb[i], q), q);
         a1[i] = addmod(a1[i], mulmod(ext[i], ka[i], q), q);
       }
+      free(ext);
     }
   }
-  free(dc); free(ext);
+  free(dc);
 }
 
 static void keyswitch(orc_ctx* c, const uint64_t* d, int level, const uint64_t* key,
@@ -1095,19 +1129,22 @@ static void moddown_rescale_pair(orc_ctx* c, const uint64_t* acc, const uint64_t
       uint64_t h = mulmod(submod(mulmod(P_mod(c, m), pr[0] % m, m), 1, m), invmod(2, m), m);
       for (uint32_t i = 0; i < n; i++) yu[i] = addmod(yu[i], h, m);
     }
+#pragma omp parallel for schedule(dynamic)
     for (int t = 0; t < l; t++) {
+      uint64_t* cv = malloc(sizeof(uint64_t) * n);
       uint64_t q = c->q[t];
       uint64_t Pq = mulmod(P_mod(c, q), pr[0] % q, q);
       uint64_t ht = mulmod(submod(Pq, 1, q), invmod(2, q), q);
-      conv_exact(y, pr, k, n, q, conv);
-      for (uint32_t i = 0; i < n; i++) conv[i] = submod(conv[i], ht, q);
-      ntt_limb(c, t, conv);
+      conv_exact(y, pr, k, n, q, cv);
+      for (uint32_t i = 0; i < n; i++) cv[i] = submod(cv[i], ht, q);
+      ntt_limb(c, t, cv);
       uint64_t inv = invmod(Pq, q), Pm = P_mod(c, q);
       uint64_t* o = POLY(res, p * l + t, n);
       for (uint32_t i = 0; i < n; i++) {
         uint64_t v = addmod(ap[(size_t)t * n + i], mulmod(Pm, dp[(size_t)t * n + i], q), q);
-        o[i] = mulmod(submod(v, conv[i], q), inv, q);
+        o[i] = mulmod(submod(v, cv[i], q), inv, q);
       }
+      free(cv);
     }
   }
   memcpy(out, res, sizeof(uint64_t) * 2 * (size_t)l * n);
@@ -1286,10 +1323,11 @@ int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* step
     intt_limb(c, t, POLY(dc, t, n));
   }
   uint64_t* acc = calloc((size_t)2 * nt * n, sizeof(uint64_t)); /* [2][nt][N], summed over rotations */
-  uint64_t* y = malloc(sizeof(uint64_t) * n);
-  uint64_t* z = malloc(sizeof(uint64_t) * n);
   for (int j = 0; j < beta_l; j++) {
+#pragma omp parallel for schedule(dynamic)
     for (int ti = 0; ti < nt; ti++) {
+      uint64_t* y = malloc(sizeof(uint64_t) * n);
+      uint64_t* z = malloc(sizeof(uint64_t) * n);
       int tp = ti < level ? ti : c->L + (ti - level);
       uint64_t q = c->q[tp];
       if (tp < level && tp >= digit_lo(c, j) && tp < digit_hi(c, j, level))
@@ -1308,8 +1346,10 @@ int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* step
           s1[i] = addmod(s1[i], mulmod(z[i], ka[i], q), q);
         }
       }
+      free(y); free(z);
     }
   }
+  uint64_t* z = malloc(sizeof(uint64_t) * n);
   uint64_t* k0 = malloc(sizeof(uint64_t) * (size_t)level * n);
   uint64_t* k1 = malloc(sizeof(uint64_t) * (size_t)level * n);
   moddown_pair(c, acc, level, k0, k1);
@@ -1328,7 +1368,7 @@ int orc_rotate_sum(orc_ctx* c, const uint64_t* a, int level, const int32_t* step
     }
   }
   memcpy(out, res, sizeof(uint64_t) * 2 * (size_t)level * n);
-  free(dc); free(acc); free(y); free(z); free(k0); free(k1); free(res);
+  free(dc); free(acc); free(z); free(k0); free(k1); free(res);
   return 0;
 }
 
@@ -1451,54 +1491,82 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
   int rc = 0;
   orc_ct G = ct_new(c, l0 - 4, 0.0);
   memset(G.d, 0, sizeof(uint64_t) * 2 * (size_t)G.level * n);
-  orc_ct U = ct_new(c, l0 - 1, sU), T = ct_new(c, l0 - 2, sT), A = ct_new(c, l0 - 2, 0.0);
-  orc_ct Cc = ct_new(c, l0 - 3, 0.0), B = ct_new(c, l0 - 2, 0.0), Qq = ct_new(c, l0 - 3, 0.0);
-  orc_ct Zd = ct_new(c, l0 - 3, sZ);
   uint64_t* tmp = malloc(sizeof(uint64_t) * 2 * (size_t)l0 * n);
   const size_t w3 = 3 * (size_t)(l0 - 3) * n;
   uint64_t* D = calloc(w3, sizeof(uint64_t));  /* sum_k tensor(S_k, Z_k) */
-  uint64_t* Dk = malloc(sizeof(uint64_t) * w3);
   double sD = 0.0;
-  for (int k = 0; k < nZ && rc == 0; k++) {
-    /* U = HMult(Z_k, W); M = rotate-and-sum over the F features */
-    orc_mul_relin_rescale(c, Z[k], Wd, l0, U.d);
-    rc = rotsum(c, &U, g, logF);
-    if (rc) break;
-    /* T = M^2 */
-    orc_mul_relin_rescale(c, U.d, U.d, l0 - 1, T.d);
-    /* A = c3 * M */
-    orc_mul_int(c, U.d, l0 - 1, kA, tmp);
-    orc_rescale(c, tmp, l0 - 1, A.d);
-    A.scale = (sU * sigA) / (double)q[l0 - 2];
-    /* C = T * A */
-    orc_mul_relin_rescale(c, T.d, A.d, l0 - 2, Cc.d);
-    Cc.scale = sT * A.scale / (double)q[l0 - 3];
-    /* B = c1 * M, dropped to level l0-3 */
-    orc_mul_int(c, U.d, l0 - 1, kB, tmp);
-    orc_rescale(c, tmp, l0 - 1, B.d);
-    B.scale = (sU * sigB) / (double)q[l0 - 2];
-    orc_drop(c, B.d, l0 - 2, l0 - 3, B.d);
-    if (!scales_match(Cc.scale, B.scale)) { rc = -3; break; }
-    orc_add(c, Cc.d, B.d, l0 - 3, Cc.d);
-    if (coeffs[2] != 0.0) {
-      orc_mul_int(c, T.d, l0 - 2, kQ, tmp);
-      orc_rescale(c, tmp, l0 - 2, Qq.d);
-      Qq.scale = (sT * sigQ) / (double)q[l0 - 3];
-      if (!scales_match(Cc.scale, Qq.scale)) { rc = -3; break; }
-      orc_add(c, Cc.d, Qq.d, l0 - 3, Cc.d);
-    }
-    orc_add_int(c, Cc.d, l0 - 3, round_const(coeffs[0] * lr * Cc.scale), Cc.d);
-    /* D += tensor(S_k, Z_k) */
-    orc_drop(c, Z[k], l0, l0 - 3, Zd.d);
-    orc_tensor(c, Cc.d, Zd.d, l0 - 3, Dk);
-    if (k == 0) sD = Cc.scale * sZ;
-    else if (!scales_match(sD, Cc.scale * sZ)) { rc = -3; break; }
-    for (int p = 0; p < 3; p++)
-      for (int t = 0; t < l0 - 3; t++) {
-        uint64_t* dst = POLY(D, p * (l0 - 3) + t, n);
-        const uint64_t* src = POLY(Dk, p * (l0 - 3) + t, n);
-        for (uint32_t i = 0; i < n; i++) dst[i] = addmod(dst[i], src[i], q[t]);
+  int have_sD = 0;
+  /* the data ciphertexts' circuits are independent up to the sum D (exact
+     modular addition, so its order does not matter) */
+#pragma omp parallel if (nZ >= 4)
+  {
+    orc_ct U = ct_new(c, l0 - 1, sU), T = ct_new(c, l0 - 2, sT), A = ct_new(c, l0 - 2, 0.0);
+    orc_ct Cc = ct_new(c, l0 - 3, 0.0), B = ct_new(c, l0 - 2, 0.0), Qq = ct_new(c, l0 - 3, 0.0);
+    orc_ct Zd = ct_new(c, l0 - 3, sZ);
+    uint64_t* tk = malloc(sizeof(uint64_t) * 2 * (size_t)l0 * n);
+    uint64_t* Dk = malloc(sizeof(uint64_t) * w3);
+#pragma omp for schedule(dynamic)
+    for (int k = 0; k < nZ; k++) {
+      int lrc = 0;
+      /* U = HMult(Z_k, W); M = rotate-and-sum over the F features */
+      orc_mul_relin_rescale(c, Z[k], Wd, l0, U.d);
+      U.scale = sU;
+      lrc = rotsum(c, &U, g, logF);
+      if (lrc == 0) {
+        /* T = M^2 */
+        orc_mul_relin_rescale(c, U.d, U.d, l0 - 1, T.d);
+        /* A = c3 * M */
+        orc_mul_int(c, U.d, l0 - 1, kA, tk);
+        orc_rescale(c, tk, l0 - 1, A.d);
+        A.scale = (sU * sigA) / (double)q[l0 - 2];
+        /* C = T * A */
+        orc_mul_relin_rescale(c, T.d, A.d, l0 - 2, Cc.d);
+        Cc.scale = sT * A.scale / (double)q[l0 - 3];
+        /* B = c1 * M, dropped to level l0-3 */
+        orc_mul_int(c, U.d, l0 - 1, kB, tk);
+        orc_rescale(c, tk, l0 - 1, B.d);
+        B.scale = (sU * sigB) / (double)q[l0 - 2];
+        orc_drop(c, B.d, l0 - 2, l0 - 3, B.d);
+        if (!scales_match(Cc.scale, B.scale)) lrc = -3;
       }
+      if (lrc == 0) {
+        orc_add(c, Cc.d, B.d, l0 - 3, Cc.d);
+        if (coeffs[2] != 0.0) {
+          orc_mul_int(c, T.d, l0 - 2, kQ, tk);
+          orc_rescale(c, tk, l0 - 2, Qq.d);
+          Qq.scale = (sT * sigQ) / (double)q[l0 - 3];
+          if (!scales_match(Cc.scale, Qq.scale)) lrc = -3;
+          else orc_add(c, Cc.d, Qq.d, l0 - 3, Cc.d);
+        }
+      }
+      if (lrc == 0) {
+        orc_add_int(c, Cc.d, l0 - 3, round_const(coeffs[0] * lr * Cc.scale), Cc.d);
+        /* D += tensor(S_k, Z_k) */
+        orc_drop(c, Z[k], l0, l0 - 3, Zd.d);
+        orc_tensor(c, Cc.d, Zd.d, l0 - 3, Dk);
+      }
+#pragma omp critical(orc_lr_gradient_sum)
+      {
+        if (lrc) {
+          rc = lrc;
+        } else {
+          if (!have_sD) {
+            sD = Cc.scale * sZ;
+            have_sD = 1;
+          } else if (!scales_match(sD, Cc.scale * sZ)) {
+            rc = -3;
+          }
+          for (int pt = 0; pt < 3; pt++)
+            for (int t = 0; t < l0 - 3; t++) {
+              uint64_t* dst = POLY(D, pt * (l0 - 3) + t, n);
+              const uint64_t* src = POLY(Dk, pt * (l0 - 3) + t, n);
+              for (uint32_t i = 0; i < n; i++) dst[i] = addmod(dst[i], src[i], q[t]);
+            }
+        }
+      }
+    }
+    free(U.d); free(T.d); free(A.d); free(Cc.d); free(B.d); free(Qq.d); free(Zd.d);
+    free(tk); free(Dk);
   }
   if (rc == 0) {
     /* G = rescale(relinearise(D)) */
@@ -1541,8 +1609,7 @@ int orc_lr_gradient_step(orc_ctx* c, const uint64_t* const* Z, int nZ, int level
     }
   }
   free(tmp);
-  free(G.d); free(U.d); free(T.d); free(A.d); free(Cc.d); free(B.d); free(Qq.d);
-  free(Zd.d); free(D); free(Dk); free(R.d);
+  free(G.d); free(D); free(R.d);
   return rc;
 }
 

@@ -141,6 +141,7 @@ def load():
         "he_fit_poly": [VP, VP, ctypes.c_size_t, ctypes.c_uint32, VP],
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
+        "he_sum": [VP, VP, ctypes.c_size_t, CTP],
         "he_ctx_workspace": [VP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
@@ -400,6 +401,15 @@ def he_mul_plain(ctx, a, coeffs, pt_scale: float, out):
 
 def he_rescale(ctx, a, out):
     _run(load().he_rescale, ctx, [out], a, out)
+    return out
+
+
+def he_sum(ctx, cts: list, out):
+    """out = sum of the ciphertexts (modular addition of residues, one scale)."""
+    arr = _batch(cts)
+    s = out.c()
+    _check(load().he_sum(ctx.ptr, arr, len(cts), ctypes.byref(s)))
+    out.update(s)
     return out
 
 

@@ -128,6 +128,7 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->ntt_generic = base->ntt_generic;
   v->ntt_shape = base->ntt_shape;
   v->ntt_pb_max = base->ntt_pb_max;
+  v->ks_ct = base->ks_ct;
   v->P_mod_q = base->P_mod_q;
   v->d_s = base->d_s;
   v->d_pk = base->d_pk;
@@ -290,6 +291,9 @@ int he_set_tuning(he_ctx* c, const char* key, double value) {
     if (!(value >= 1 && value <= 64) || value != (double)(uint32_t)value)
       return fail(HE_EINVAL, "ntt_pb_max is an integer in [1, 64]");
     c->ntt_pb_max = (uint32_t)value;
+  } else if (k == "ks_ct") {
+    if (value != 0.0 && value != 1.0 && value != 2.0 && value != 4.0) return fail(HE_EINVAL, "ks_ct is 0, 1, 2 or 4");
+    c->ks_ct = (uint32_t)value;
   } else {
     return fail(HE_EINVAL, "unknown tuning key " + k);
   }
@@ -536,6 +540,32 @@ static int addsub(he_ctx* c, const he_ct* a, const he_ct* b, he_ct* out, int op)
 
 int he_add(he_ctx* c, const he_ct* a, const he_ct* b, he_ct* out) { return addsub(c, a, b, out, 0); }
 int he_sub(he_ctx* c, const he_ct* a, const he_ct* b, he_ct* out) { return addsub(c, a, b, out, 1); }
+
+int he_sum(he_ctx* c, const he_ct* a, size_t count, he_ct* out) {
+  if (!c || !a || count == 0) return fail(HE_EINVAL, "he_sum: null argument or no ciphertext");
+  uint32_t level = (uint32_t)c->L;
+  for (size_t i = 0; i < count; ++i) {
+    HE_TRY(check_ct(c, &a[i], "he_sum"));
+    if (!scales_match(a[i].scale, a[0].scale)) return fail(HE_ESCALE, "he_sum: scales differ");
+    level = std::min(level, a[i].level);
+  }
+  HE_TRY(check_out(c, out, level, "he_sum"));
+  for (size_t i = 1; i < count; ++i)
+    if (a[i].data == out->data) return fail(HE_EINVAL, "he_sum: out may alias only the first input");
+  const double scale = a[0].scale;
+  if (a[0].data != out->data) HE_TRY(copy_batch(c, one(&a[0]), one(out), level, 1));
+  if (count > 1) {
+    CtBatch rest;
+    if (uniform_view(a + 1, count - 1, &rest)) {
+      HE_TRY(accumulate_batch(c, rest, (uint32_t)(count - 1), one(out), level));
+    } else {
+      for (size_t i = 1; i < count; ++i) HE_TRY(addsub_batch(c, one(out), one(&a[i]), one(out), 0, level, 1));
+    }
+  }
+  out->level = level;
+  out->scale = scale;
+  return HE_OK;
+}
 
 int he_drop_level(he_ctx* c, const he_ct* a, uint32_t level, he_ct* out) {
   if (!c) return fail(HE_EINVAL, "null context");

@@ -103,6 +103,7 @@ extern "C" int he_get_tuning(he_ctx* c, const char* key, double* value) {
   else if (k == "lr_chunk") *value = c->lr_chunk;
   else if (k == "ntt_shape") *value = c->ntt_shape;
   else if (k == "ntt_pb_max") *value = c->ntt_pb_max;
+  else if (k == "ks_ct") *value = c->ks_ct;
   else return fail(HE_EINVAL, "unknown tuning key " + k);
   return HE_OK;
 }

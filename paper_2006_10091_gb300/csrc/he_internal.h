@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -28,6 +29,19 @@ int fail(int code, const std::string& msg);
     int rc_ = (call);                 \
     if (rc_ != HE_OK) return rc_;     \
   } while (0)
+
+// cudaFuncSetAttribute (the dynamic shared memory a kernel may take) once per
+// device for each kernel instance: `bits` is that instance's set of devices
+// done, an atomic so that host threads first using a ring size at the same
+// time do not race on it (a repeated call is harmless).
+inline int set_smem_attr_once(std::atomic<unsigned long long>& bits, int device, const void* fn, size_t bytes) {
+  if (device < 0 || device >= 64) return HE_OK;
+  const unsigned long long m = 1ull << device;
+  if (bits.load(std::memory_order_acquire) & m) return HE_OK;
+  HE_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  bits.fetch_or(m, std::memory_order_acq_rel);
+  return HE_OK;
+}
 
 // ---- host number theory (params.cpp) ---------------------------------------
 uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t q);
@@ -98,6 +112,7 @@ struct he_ctx {
   bool ntt_generic = false;              // force the runtime-shaped NTT kernel (tuning)
   int ntt_shape = 0;                     // NTT tile shapes: 0, 1 or 2 (ntt2.cu)
   uint32_t ntt_pb_max = 8;               // polynomials of one limb per NTT CTA, at most
+  uint32_t ks_ct = 0;                    // ciphertexts per key-product CTA in closed stages (0: most that fit)
   std::map<std::string, cudaGraphExec_t> graphs;  // captured multi-worker steps
   std::vector<uint64_t> P_mod_q;  // [L] P mod q_t (host)
 

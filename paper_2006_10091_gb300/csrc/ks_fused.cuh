@@ -12,9 +12,9 @@
 //    is), keeps the tiles in shared memory and adds their products with the
 //    key polynomials of each rotation (a plain key switch is one rotation by
 //    the identity); the transformed digits are never written.
-#include <algorithm>
-
 #pragma once
+#include <algorithm>
+#include <atomic>
 #include "he_ops.h"
 #include "ntt2.cuh"
 
@@ -209,17 +209,24 @@ struct KsRotArgs {
   const uint64_t* evk[HE_MAX_ROT];
 };
 
-// Grid: nt * count * TILES, target limb slowest and row tile fastest, so
-// that the CTAs resident at one time share their keys (one limb of each
-// rotation's key) in L2 and finish each ciphertext's limb together.  Shared
-// memory: the tile's twiddles and every digit's transformed tile
-// ([beta][TILE + TILE/8] words).
-template <int LOG_N, int LOG_M, int LOG_K>
-__global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRotArgs ra) {
+// Grid: nt * ceil(count / CT) * TILES, target limb slowest and row tile
+// fastest, so that the CTAs resident at one time share their keys (one limb
+// of each rotation's key) in L2 and finish each ciphertext's limb together.
+// A CTA holds CT ciphertexts of one limb and tile: group g of T threads runs
+// the row passes of ciphertext i0 + g, and in a closed stage every thread
+// then sums the products for its positions of all CT ciphertexts, so each
+// key word it loads serves CT ciphertexts (8/CT bytes of key per 128-bit
+// multiply-accumulate).  CT > 1 only for closed stages; a tail CTA repeats its
+// last ciphertext in the groups beyond the count and stores nothing for them.
+// Shared memory: the tile's twiddles and every digit's transformed tile of
+// each ciphertext ([CT][beta][TILE + TILE/8] words).
+template <int LOG_N, int LOG_M, int LOG_K, int CT>
+__global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_row_rot(KsRotArgs ra) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
   constexpr uint32_t N = 1u << LOG_N;
   constexpr int PER = S::TILE / S::T;  // 8
   constexpr uint32_t TW = S::TILE + S::TILE / 8;
+  static_assert(CT == 1 || CT == 2 || CT == 4, "ciphertexts per CTA");
   const KsFusedArgs& a = ra.k;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* stw = reinterpret_cast<ulonglong2*>(smem_raw);
@@ -227,15 +234,19 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   uint32_t b = blockIdx.x;
   const uint32_t tile = b % S::TILES;
   b /= S::TILES;
-  const uint32_t i = b % ra.count, t = b / ra.count;
+  const uint32_t ngrp = (ra.count + CT - 1) / CT;
+  const uint32_t i0 = (b % ngrp) * CT, t = b / ngrp;
+  const uint32_t grp = CT == 1 ? 0u : threadIdx.x / S::T;  // warp-uniform: T is a multiple of 32
+  const uint32_t ltid = CT == 1 ? threadIdx.x : threadIdx.x % S::T;
+  const uint32_t i = min(i0 + grp, ra.count - 1);
   const uint32_t prime = ks_prime(t, a.level, a.L);
   const PrimeDev pr = a.primes[prime];
   const uint64_t q = pr.q;
   const bool lazy = q < (1ull << 58);
-  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile);
+  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile, threadIdx.x, CT * S::T);
   // 1. every digit's tile in evaluation form, canonical residues
   for (uint32_t j = 0; j < a.beta; ++j) {
-    uint64_t* sm = dig + (size_t)j * TW;
+    uint64_t* sm = dig + ((size_t)grp * a.beta + j) * TW;
     const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
     const uint64_t* src = own ? a.d + (size_t)i * a.d_stride + (size_t)t * N
                               : a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
@@ -244,17 +255,17 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
     const uint64_t in_gal = own ? a.gal : 0;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint32_t idx = ltid + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       sm[idx + (idx >> 3)] = __ldg(src + (in_gal ? automorph_src(e, in_gal, LOG_N) : e));
     }
     if (own) continue;
     __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-      const uint32_t idx = threadIdx.x + u * S::T;
+      const uint32_t idx = ltid + u * S::T;
       const uint64_t v = sm[idx + (idx >> 3)];
       sm[idx + (idx >> 3)] = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
     }
@@ -263,28 +274,30 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
   // 2. the products of the permuted digits with each rotation's key, summed
   // as full 128-bit products and reduced once per residue
   const uint32_t row0 = (uint32_t)tile << LOG_K;
-  constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
   if (ra.closed) {
     // each thread sums every rotation's products for its own positions, two
-    // neighbouring positions at a time (16-byte key loads and stores)
-    uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
-    uint64_t* o1 = o0 + (size_t)a.nt * N;
-    constexpr int PAIRS = GRP / 2;
+    // neighbouring positions at a time (16-byte key loads and stores), for
+    // all CT ciphertexts with each key load
+    constexpr int PPT = PER / 2 / CT;          // position pairs per thread
+    constexpr int PAIRS = PPT < 2 ? PPT : 2;   // pairs per pass (bounds the registers)
+    constexpr int NP = 2 * PAIRS;              // positions per pass
 #pragma unroll 1
-    for (int v0 = 0; v0 < PER / 2; v0 += PAIRS) {
+    for (int v0 = 0; v0 < PPT; v0 += PAIRS) {
       uint32_t eo[PAIRS];  // first of the two positions (even)
-      uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
+      uint64_t a0l[CT][NP], a0h[CT][NP], a1l[CT][NP], a1h[CT][NP];  // 128-bit sums of full products
 #pragma unroll
       for (int v = 0; v < PAIRS; ++v) {
-        const uint32_t idx = 2 * (threadIdx.x + (v0 + v) * S::T);
+        const uint32_t idx = 2 * (threadIdx.x + (v0 + v) * CT * S::T);
         eo[v] = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       }
 #pragma unroll
-      for (int u = 0; u < GRP; ++u) a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
-      for (uint32_t r = 0; r < ra.nrot; ++r) {
-        uint32_t so[GRP];
+      for (int c = 0; c < CT; ++c)
 #pragma unroll
-        for (int u = 0; u < GRP; ++u) {
+        for (int u = 0; u < NP; ++u) a0l[c][u] = a0h[c][u] = a1l[c][u] = a1h[c][u] = 0;
+      for (uint32_t r = 0; r < ra.nrot; ++r) {
+        uint32_t so[NP];
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
           const uint32_t p = automorph_src(eo[u >> 1] + (u & 1), ra.gal[r], LOG_N);
           const uint32_t sl = (((p >> LOG_M) - row0) << LOG_M) | (p & (S::M - 1));
           so[u] = sl + (sl >> 3);
@@ -292,71 +305,85 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 4) ks_row_rot(KsRo
         const uint64_t* ev = ra.evk[r];
 #pragma unroll 2
         for (uint32_t j = 0; j < a.beta; ++j) {
-          const uint64_t* sm = dig + (size_t)j * TW;
           const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
           const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
 #pragma unroll
           for (int v = 0; v < PAIRS; ++v) {
             const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(kb + eo[v]));
             const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(ka + eo[v]));
-            const uint64_t x0 = sm[so[2 * v]], x1 = sm[so[2 * v + 1]];
-            mac128(a0l[2 * v], a0h[2 * v], x0, wb.x);
-            mac128(a0l[2 * v + 1], a0h[2 * v + 1], x1, wb.y);
-            mac128(a1l[2 * v], a1h[2 * v], x0, wa.x);
-            mac128(a1l[2 * v + 1], a1h[2 * v + 1], x1, wa.y);
+#pragma unroll
+            for (int c = 0; c < CT; ++c) {
+              const uint64_t* sm = dig + ((size_t)c * a.beta + j) * TW;
+              const uint64_t x0 = sm[so[2 * v]], x1 = sm[so[2 * v + 1]];
+              mac128(a0l[c][2 * v], a0h[c][2 * v], x0, wb.x);
+              mac128(a0l[c][2 * v + 1], a0h[c][2 * v + 1], x1, wb.y);
+              mac128(a1l[c][2 * v], a1h[c][2 * v], x0, wa.x);
+              mac128(a1l[c][2 * v + 1], a1h[c][2 * v + 1], x1, wa.y);
+            }
           }
         }
       }
 #pragma unroll
-      for (int v = 0; v < PAIRS; ++v) {
-        *reinterpret_cast<ulonglong2*>(o0 + eo[v]) =
-            make_ulonglong2(reduce128_any(a0h[2 * v], a0l[2 * v], pr), reduce128_any(a0h[2 * v + 1], a0l[2 * v + 1], pr));
-        *reinterpret_cast<ulonglong2*>(o1 + eo[v]) =
-            make_ulonglong2(reduce128_any(a1h[2 * v], a1l[2 * v], pr), reduce128_any(a1h[2 * v + 1], a1l[2 * v + 1], pr));
+      for (int c = 0; c < CT; ++c) {
+        if (i0 + c >= ra.count) break;
+        uint64_t* o0 = a.acc + ((size_t)(i0 + c) * 2 * a.nt + t) * N;
+        uint64_t* o1 = o0 + (size_t)a.nt * N;
+#pragma unroll
+        for (int v = 0; v < PAIRS; ++v) {
+          *reinterpret_cast<ulonglong2*>(o0 + eo[v]) =
+              make_ulonglong2(reduce128_any(a0h[c][2 * v], a0l[c][2 * v], pr),
+                              reduce128_any(a0h[c][2 * v + 1], a0l[c][2 * v + 1], pr));
+          *reinterpret_cast<ulonglong2*>(o1 + eo[v]) =
+              make_ulonglong2(reduce128_any(a1h[c][2 * v], a1l[c][2 * v], pr),
+                              reduce128_any(a1h[c][2 * v + 1], a1l[c][2 * v + 1], pr));
+        }
       }
     }
     return;
   }
-  for (uint32_t r = 0; r < ra.nrot; ++r) {
-    const uint64_t* ev = ra.evk[r];
-    uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
-    uint64_t* o1 = o0 + (size_t)a.nt * N;
+  if constexpr (CT == 1) {  // rotations that move rows between CTAs (launched with one ciphertext per CTA)
+    constexpr int GRP = PER / 2;  // residues per thread and pass (bounds the registers)
+    for (uint32_t r = 0; r < ra.nrot; ++r) {
+      const uint64_t* ev = ra.evk[r];
+      uint64_t* o0 = a.acc + ((size_t)i * 2 * a.nt + t) * N;
+      uint64_t* o1 = o0 + (size_t)a.nt * N;
 #pragma unroll 1
-    for (int u0 = 0; u0 < PER; u0 += GRP) {
-      uint32_t so[GRP], eo[GRP];
-#pragma unroll
-      for (int u = 0; u < GRP; ++u) {
-        const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
-        const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
-        const uint32_t row = row0 + k;
-        const uint32_t orow = automorph_src(row << LOG_M, ra.gal_inv[r], LOG_N) >> LOG_M;
-        const uint32_t e = (orow << LOG_M) | x;
-        const uint32_t sl = (k << LOG_M) | (automorph_src(e, ra.gal[r], LOG_N) & (S::M - 1));
-        so[u] = sl + (sl >> 3);
-        eo[u] = e;
-      }
-      uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
-#pragma unroll
-      for (int u = 0; u < GRP; ++u) a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
-      for (uint32_t j = 0; j < a.beta; ++j) {
-        const uint64_t* sm = dig + (size_t)j * TW;
-        const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
-        const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
+      for (int u0 = 0; u0 < PER; u0 += GRP) {
+        uint32_t so[GRP], eo[GRP];
 #pragma unroll
         for (int u = 0; u < GRP; ++u) {
-          const uint64_t x = sm[so[u]];
-          mac128(a0l[u], a0h[u], x, __ldg(kb + eo[u]));
-          mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
+          const uint32_t idx = threadIdx.x + (u0 + u) * S::T;
+          const uint32_t k = idx >> LOG_M, x = idx & (S::M - 1);
+          const uint32_t row = row0 + k;
+          const uint32_t orow = automorph_src(row << LOG_M, ra.gal_inv[r], LOG_N) >> LOG_M;
+          const uint32_t e = (orow << LOG_M) | x;
+          const uint32_t sl = (k << LOG_M) | (automorph_src(e, ra.gal[r], LOG_N) & (S::M - 1));
+          so[u] = sl + (sl >> 3);
+          eo[u] = e;
         }
-      }
-      // other CTAs add the other rotations' products to these rows: the
-      // accumulator (zeroed first) holds sums of nrot residues
+        uint64_t a0l[GRP], a0h[GRP], a1l[GRP], a1h[GRP];  // 128-bit sums of full products
 #pragma unroll
-      for (int u = 0; u < GRP; ++u) {
-        atomicAdd(reinterpret_cast<unsigned long long*>(o0 + eo[u]),
-                  (unsigned long long)reduce128_any(a0h[u], a0l[u], pr));
-        atomicAdd(reinterpret_cast<unsigned long long*>(o1 + eo[u]),
-                  (unsigned long long)reduce128_any(a1h[u], a1l[u], pr));
+        for (int u = 0; u < GRP; ++u) a0l[u] = a0h[u] = a1l[u] = a1h[u] = 0;
+        for (uint32_t j = 0; j < a.beta; ++j) {
+          const uint64_t* sm = dig + (size_t)j * TW;
+          const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
+          const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
+#pragma unroll
+          for (int u = 0; u < GRP; ++u) {
+            const uint64_t x = sm[so[u]];
+            mac128(a0l[u], a0h[u], x, __ldg(kb + eo[u]));
+            mac128(a1l[u], a1h[u], x, __ldg(ka + eo[u]));
+          }
+        }
+        // other CTAs add the other rotations' products to these rows: the
+        // accumulator (zeroed first) holds sums of nrot residues
+#pragma unroll
+        for (int u = 0; u < GRP; ++u) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(o0 + eo[u]),
+                    (unsigned long long)reduce128_any(a0h[u], a0l[u], pr));
+          atomicAdd(reinterpret_cast<unsigned long long*>(o1 + eo[u]),
+                    (unsigned long long)reduce128_any(a1h[u], a1l[u], pr));
+        }
       }
     }
   }
@@ -563,13 +590,9 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
     return HE_OK;
   }
   *handled = true;
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(md_conv_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kModupAllSmem));
-    HE_CUDA(cudaFuncSetAttribute(md_row_combine<LOG_N, M2, K2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
-    attr_set |= 1ull << c->device;
-  }
+  static std::atomic<unsigned long long> attr_col{0}, attr_row{0};
+  HE_TRY(set_smem_attr_once(attr_col, c->device, (const void*)md_conv_col<LOG_N, M1, K1>, kModupAllSmem));
+  HE_TRY(set_smem_attr_once(attr_row, c->device, (const void*)md_row_combine<LOG_N, M2, K2>, smr));
   const double n = (double)(1u << LOG_N);
   const double polys = 2.0 * count * a.level;  // transformed limbs
   const char* nm_col = a.kind == 1 ? "rescale_ntt" : a.kind == 2 ? "moddown_rescale_ntt" : "moddown_ntt";
@@ -611,13 +634,9 @@ template <int LOG_N, int M1, int K1>
 int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   using SC = Shape<LOG_N, M1, K1, true>;
   const size_t smc = sizeof(ulonglong2) * SC::NTW + sizeof(uint64_t) * (SC::TILE + SC::TILE / 8);
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ks_modup_col<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-    HE_CUDA(cudaFuncSetAttribute(ks_modup_col_all<LOG_N, M1, K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kModupAllSmem));
-    attr_set |= 1ull << c->device;
-  }
+  static std::atomic<unsigned long long> attr_one{0}, attr_all{0};
+  HE_TRY(set_smem_attr_once(attr_one, c->device, (const void*)ks_modup_col<LOG_N, M1, K1>, smc));
+  HE_TRY(set_smem_attr_once(attr_all, c->device, (const void*)ks_modup_col_all<LOG_N, M1, K1>, kModupAllSmem));
   const double n = (double)(1u << LOG_N);
   double own = 0;  // limbs each ciphertext takes as they are
   for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
@@ -646,12 +665,14 @@ int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
 }
 
 // Dynamic shared memory of ks_row_rot (row tiles of half the row pass's
-// tile: M2 x 2^(K2-1)) for beta digits.
+// tile: M2 x 2^(K2-1)) for beta digits of ct ciphertexts.
 template <int LOG_N, int M2, int K2>
-size_t ks_rot_smem(uint32_t beta) {
+size_t ks_rot_smem(uint32_t beta, uint32_t ct = 1) {
   using SR = Shape<LOG_N, M2, K2 - 1, false>;
-  return sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8) * beta;
+  return sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8) * beta * ct;
 }
+
+
 
 // The hoisted rotate-and-sum's ModUp, column pass and row pass with the
 // inner products of every rotation.  *handled = false (nothing launched)
@@ -682,19 +703,16 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
   const size_t smr = ks_rot_smem<LOG_N, M2, K2>(a.beta);
   *handled = smr <= kRotSmemMax;
   if (!*handled) return HE_OK;
-  static unsigned long long attr_set = 0;
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ks_row_rot<LOG_N, M2, K2 - 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kRotSmemMax));
-    attr_set |= 1ull << c->device;
-  }
+  static std::atomic<unsigned long long> attr1{0}, attr2{0}, attr4{0};
+  HE_TRY(set_smem_attr_once(attr1, c->device, (const void*)ks_row_rot<LOG_N, M2, K2 - 1, 1>, kRotSmemMax));
+  HE_TRY(set_smem_attr_once(attr2, c->device, (const void*)ks_row_rot<LOG_N, M2, K2 - 1, 2>, kRotSmemMax));
+  HE_TRY(set_smem_attr_once(attr4, c->device, (const void*)ks_row_rot<LOG_N, M2, K2 - 1, 4>, kRotSmemMax));
   HE_TRY((ks_modup_launch<LOG_N, M1, K1>(c, a, count)));
   const double n = (double)(1u << LOG_N);
   double own = 0;
   for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
   const double conv = (double)a.beta * a.nt - own;
   {
-    const size_t blocks = (size_t)count * a.nt * SR::TILES;
     // work: the converted limbs' row-pass butterflies, one reduction per
     // accumulator residue, and the key products (128-bit multiply-accumulates);
     // bytes: the limbs read once, one accumulator written (the rotations'
@@ -709,7 +727,21 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     *closed_out = rc.closed;
     if (!rc.closed)
       HE_CUDA(cudaMemsetAsync(ra.k.acc, 0, sizeof(uint64_t) * count * 2 * a.nt * (1u << LOG_N), c->stream));
-    ks_row_rot<LOG_N, M2, K2 - 1><<<(unsigned)blocks, SR::T, smr, c->stream>>>(rc);
+    // ciphertexts per CTA (closed stages only): the knob, else 2 when the
+    // tiles fit (a 15-rotation stage of 512 ciphertexts at N = 2^14: 9.3 ms
+    // against 10.1 ms for 1 and 10.0 ms for 4)
+    uint32_t ct = 1;
+    if (rc.closed) {
+      const uint32_t want = c->ks_ct ? (uint32_t)c->ks_ct : 2u;
+      for (uint32_t cand : {4u, 2u})
+        if (ct == 1 && cand <= want && cand <= count && ks_rot_smem<LOG_N, M2, K2>(a.beta, cand) <= kRotSmemMax)
+          ct = cand;
+    }
+    const size_t blocks = (size_t)a.nt * ((count + ct - 1) / ct) * SR::TILES;
+    const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, ct);
+    if (ct == 4) ks_row_rot<LOG_N, M2, K2 - 1, 4><<<(unsigned)blocks, 4 * SR::T, sm, c->stream>>>(rc);
+    else if (ct == 2) ks_row_rot<LOG_N, M2, K2 - 1, 2><<<(unsigned)blocks, 2 * SR::T, sm, c->stream>>>(rc);
+    else ks_row_rot<LOG_N, M2, K2 - 1, 1><<<(unsigned)blocks, SR::T, sm, c->stream>>>(rc);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;

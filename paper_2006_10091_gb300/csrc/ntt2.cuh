@@ -38,8 +38,10 @@ struct Shape {
 // unevenly), so only the first offset is computed.  At stage st the group
 // needs 2^st distinct twiddles, one per value of the top st bits of j; each
 // is loaded once.
+// `tid` is the thread's index among the T threads that share the tile (a CTA
+// may hold several tiles, one per group of T threads).
 template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R, int LOG_V = 3>
-__device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int sig0, uint64_t q) {
+__device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int sig0, uint64_t q, uint32_t tid) {
   using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   constexpr int G = 1 << R, GPT = (1 << LOG_V) >> R;
   const uint64_t q2 = q + q;
@@ -48,7 +50,7 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
   const uint32_t s = COL ? (1u << (lo_bits + LOG_K)) : (1u << lo_bits);
 #pragma unroll
   for (int u = 0; u < GPT; ++u) {
-    const uint32_t g = threadIdx.x + u * S::T;
+    const uint32_t g = tid + u * S::T;
     uint32_t k, xhi, xlo;
     if (COL) {
       k = g & (S::K - 1);
@@ -101,11 +103,13 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
 // Stage the twiddle pairs of one pass into shared memory: a column pass
 // needs tw[0 .. M), a row pass for rows f0 .. f0+K-1 needs, per local stage
 // sigma, the K*2^sigma entries from 2^(S0+sigma) + f0*2^sigma on.
+// (Threads tid = 0 .. nthreads-1 share the copy; by default the tile's T.)
 template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
-__device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile) {
+__device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile,
+                                               uint32_t tid, uint32_t nthreads) {
   using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
   if (COL) {
-    for (uint32_t e = threadIdx.x; e < (uint32_t)S::M; e += S::T) stw[e] = __ldg(tw + e);
+    for (uint32_t e = tid; e < (uint32_t)S::M; e += nthreads) stw[e] = __ldg(tw + e);
   } else {
     const uint32_t f0 = tile << LOG_K;
 #pragma unroll
@@ -113,26 +117,37 @@ __device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2
       const uint32_t cnt = (uint32_t)S::K << sig;
       const uint32_t off = (uint32_t)(S::K * ((1 << sig) - 1));
       const ulonglong2* g = tw + (1u << (S::S0 + sig)) + (f0 << sig);
-      for (uint32_t e = threadIdx.x; e < cnt; e += S::T) stw[off + e] = __ldg(g + e);
+      for (uint32_t e = tid; e < cnt; e += nthreads) stw[off + e] = __ldg(g + e);
     }
   }
 }
 
+template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
+__device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile) {
+  stage_twiddles<LOG_N, LOG_M, LOG_K, COL, LOG_V>(stw, tw, tile, threadIdx.x,
+                                                  (uint32_t)Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>::T);
+}
+
 // All rounds of one pass on the tile in shared memory (ends with a barrier).
 template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
-__device__ __forceinline__ void run_rounds(uint64_t* sm, const ulonglong2* stw, uint64_t q) {
+__device__ __forceinline__ void run_rounds(uint64_t* sm, const ulonglong2* stw, uint64_t q, uint32_t tid) {
   constexpr int NR = (LOG_M + LOG_V - 1) / LOG_V;
 #pragma unroll
   for (int rr = 0; rr < NR; ++rr) {
     const int r = INV ? NR - 1 - rr : rr;
     const int sig0 = LOG_V * r;
     const int R = LOG_M - sig0 < LOG_V ? LOG_M - sig0 : LOG_V;
-    if (R == 4) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, (LOG_V >= 4 ? 4 : 1), LOG_V>(sm, stw, sig0, q);
-    else if (R == 3) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3, LOG_V>(sm, stw, sig0, q);
-    else if (R == 2) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2, LOG_V>(sm, stw, sig0, q);
-    else round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1, LOG_V>(sm, stw, sig0, q);
+    if (R == 4) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, (LOG_V >= 4 ? 4 : 1), LOG_V>(sm, stw, sig0, q, tid);
+    else if (R == 3) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3, LOG_V>(sm, stw, sig0, q, tid);
+    else if (R == 2) round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2, LOG_V>(sm, stw, sig0, q, tid);
+    else round2<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1, LOG_V>(sm, stw, sig0, q, tid);
     __syncthreads();
   }
+}
+
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
+__device__ __forceinline__ void run_rounds(uint64_t* sm, const ulonglong2* stw, uint64_t q) {
+  run_rounds<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, LOG_V>(sm, stw, q, threadIdx.x);
 }
 
 // Canonical residue of a forward-pass output: lazy values (< 33q) by one

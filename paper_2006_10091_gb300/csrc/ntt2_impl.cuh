@@ -119,12 +119,8 @@ int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t* dst, u
   a.primes = c->d_primes;
   a.last = last ? 1 : 0;
   const size_t smem = sizeof(ulonglong2) * S::NTW + sizeof(uint64_t) * (S::TILE + S::TILE / 8);
-  static unsigned long long attr_set = 0;  // per instantiation: one bit per device
-  if (c->device < 64 && !(attr_set & (1ull << c->device))) {
-    HE_CUDA(cudaFuncSetAttribute(ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL, LOG_V>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set |= 1ull << c->device;
-  }
+  static std::atomic<unsigned long long> attr{0};  // per instantiation: one bit per device
+  HE_TRY(set_smem_attr_once(attr, c->device, (const void*)ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL, LOG_V>, smem));
   // several polynomials of one limb per CTA share its staged twiddles, as
   // long as the grid keeps about four waves of CTAs
   const size_t tiles = (size_t)b.npolys * b.nl * S::TILES;

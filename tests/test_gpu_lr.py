@@ -442,3 +442,61 @@ def test_training_loop_matches_fp64_algorithm(refresh_every, top, iterations):
         he.he_lr_train(ctx, workers, cfg, iterations, (top - 1) // 5 + 1, top, out)
     assert e.value.code == he.HE_ELEVEL
 
+
+def test_sum_of_weights_equals_oracle_additions(lr_pair):
+    """he_sum (the aggregation of Algorithm 2) of four ciphertexts, uniform and
+    not, equals the oracle's chained additions residue for residue."""
+    pair, g = lr_pair
+    he = pair.he
+    ms = [workloads.int_poly(300 + k, pair.n, 1 << 30) for k in range(4)]
+    want = pair.orc_enc(ms[0], 6, 300)
+    for k in range(1, 4):
+        want = pair.o.add(want, pair.orc_enc(ms[k], 6, 300 + k))
+    uni = pair.g.new_ct(7, 4)
+    for k, m in enumerate(ms):
+        he.he_encrypt_poly(pair.g, m, 2.0 ** 40, 6, uni[k], cid=300 + k)
+    loose = [pair.gpu_enc(m, 6, 300 + k) for k, m in enumerate(ms)]
+    for cts in (uni, loose):
+        out = pair.g.new_ct(7)
+        he.he_sum(pair.g, cts, out)
+        assert_same_residues(out, want, he, pair.g)
+    he.he_sum(pair.g, loose, loose[0])  # in place on the first
+    assert_same_residues(loose[0], want, he, pair.g)
+
+
+def test_sharded_training_loop_one_rank_matches_fp64():
+    """The sharded Algorithms 1-2 loop on one process (three workers, the
+    key holder's average taken as the decrypted modular sum of their
+    weights): within 2^-20 of the FP64 procedure."""
+    from paper_2006_10091_gb300 import sharding
+    he = gpu_lib()
+    log_n, g, top = 12, 8, 11
+    n_slots = (1 << log_n) // 2
+    ctx = he.Context(log_n, top, 40, 2, 55, 2.0 ** 40, seed=17, rot_steps=rot_steps(n_slots, g))
+    coeffs = table2()["binomial"]
+    lr = 1.0 / 16
+    w0 = workloads.LRData(seed=40, n_samples=16, n_features=200).w0
+    datas = [workloads.LRData(seed=51 + k, n_samples=8 * (k + 1), n_features=200) for k in range(3)]
+    parts = sharding.partition_shards([len(d.y) // g for d in datas], 1)
+    assert parts == [[0, 1, 2]]
+    workers = []
+    for k, d in enumerate(datas):
+        zs = workloads.pack_samples(d.X, d.y, n_slots, g)
+        Z = ctx.new_ct(top, len(zs))
+        for i, v in enumerate(zs):
+            he.he_encode_encrypt(ctx, v, 2.0 ** 40, top, Z[i], cid=100 * k + i)
+        W = ctx.new_ct(top)
+        he.he_encode_encrypt(ctx, workloads.pack_weights(w0, n_slots, g), 2.0 ** 40, top, W, cid=100 * k + 99)
+        workers.append((Z, W))
+    cfg = he.lr_config(coeffs, lr, g, 2.0 ** 27)
+    out = sharding.train_sharded(ctx, workers, cfg, 3, 2, top, 5000, len(workers))
+    assert out.level == top
+    ws = [w0.copy() for _ in datas]
+    for it in range(1, 4):
+        ws = [lr_step_fp64(d.X, d.y, w, coeffs, lr) for d, w in zip(datas, ws)]
+        if it % 2 == 0 or it == 3:
+            avg = sum(ws) / len(ws)
+            ws = [avg.copy() for _ in ws]
+    want = workloads.pack_weights(ws[0], n_slots, g)
+    got = he.he_decrypt_decode(ctx, out)
+    assert np.max(np.abs(got - want)) / np.max(np.abs(want)) < 2.0 ** -20

@@ -684,6 +684,41 @@ def test_rotate_sum_batch_and_errors(hoist, he):
     assert e.value.code == he.HE_EINVAL
 
 
+@pytest.mark.parametrize("ks_ct", [1, 2, 4])
+def test_key_products_per_cta_bit_exact(hoist, he, ks_ct):
+    """The product kernel with 1, 2 or 4 ciphertexts per CTA (each key word
+    serving that many): a ragged batch of 7 (a tail CTA with fewer) through a
+    closed hoisted stage (steps 8, 16, 24), a relinearising multiplication and
+    a single rotation, in every tile shape, equal to the oracle."""
+    count, level = 7, 5
+    ms = [workloads.int_poly(1700 + i, hoist.n, 1 << 30) for i in range(count)]
+    A = hoist.g.new_ct(level, count)
+    for i in range(count):
+        he.he_encrypt_poly(hoist.g, ms[i], hoist.g.scale, level, A[i], cid=1700 + i)
+    orc = [hoist.orc_enc(ms[i], level, cid=1700 + i) for i in range(count)]
+    want_sum = [hoist.o.rotate_sum(o, [8, 16, 24]) for o in orc]
+    want_mul = [hoist.o.mul_relin_rescale(o, orc[(i + 1) % count]) for i, o in enumerate(orc)]
+    want_rot = [hoist.o.rotate(o, 8) for o in orc]
+    B = [A[(i + 1) % count] for i in range(count)]
+    he.he_set_tuning(hoist.g, "ks_ct", ks_ct)
+    try:
+        for shape in (0, 1, 2):
+            he.he_set_tuning(hoist.g, "ntt_shape", shape)
+            O = hoist.g.new_ct(level, count)
+            he.he_rotate_sum_batch(hoist.g, A, [8, 16, 24], O)
+            for i in range(count):
+                assert_same_residues(O[i], want_sum[i], he, hoist.g)
+            he.he_mul_relin_rescale_batch(hoist.g, A, B, O)
+            for i in range(count):
+                assert_same_residues(O[i], want_mul[i], he, hoist.g)
+            he.he_rotate_batch(hoist.g, A, 8, O)
+            for i in range(count):
+                assert_same_residues(O[i], want_rot[i], he, hoist.g)
+    finally:
+        he.he_set_tuning(hoist.g, "ks_ct", 0)
+        he.he_set_tuning(hoist.g, "ntt_shape", 0)
+
+
 def test_rotate_sum_accuracy(hoist, he):
     z = workloads.uniform_slots(96, hoist.n // 2)
     a = hoist.g.new_ct(4)

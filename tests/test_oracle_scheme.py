@@ -614,3 +614,28 @@ def test_lr_inference_matches_fp64_polynomial():
         for s in range(g):
             i = k * g + s
             assert np.max(np.abs(re[s::g] - p[i])) < 2.0 ** -20
+
+
+def test_results_do_not_depend_on_thread_count():
+    """Keys, key switching and the gradient step over five data ciphertexts
+    (the step's parallel loop) give the same residues on one thread and on
+    every thread."""
+    log_n, g = 9, 4
+    n_slots = (1 << log_n) // 2
+    rots = he.lr_rot_steps(n_slots, g)
+    data = workloads.LRData(seed=8, n_samples=5 * g, n_features=60)
+    outs = []
+    threads = oracle.get_threads()
+    try:
+        for nt in (1, max(2, threads)):
+            oracle.set_threads(nt)
+            o = oracle.Oracle(log_n, 7, 40, 2, 50, 2.0 ** 40, seed=4, rot_steps=rots)
+            Z = [_enc(o, v, 7, 10 + k) for k, v in enumerate(workloads.pack_samples(data.X, data.y, n_slots, g))]
+            W = _enc(o, workloads.pack_weights(data.w0, n_slots, g), 7, 9)
+            assert len(Z) == 5
+            step = o.lr_gradient_step(Z, W, table2()["binomial"], 1.0 / 20, g, 2.0 ** 30, l2=0.25)
+            outs.append((o.key(1), o.key(2), step.data))
+    finally:
+        oracle.set_threads(threads)
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
