@@ -108,6 +108,7 @@ he_ctx* ctx_view(he_ctx* base, cudaStream_t stream) {
   v->psi = base->psi;
   v->stream = stream;
   v->device = base->device;
+  v->smem_per_sm = base->smem_per_sm;
   v->d_primes = base->d_primes;
   v->d_tw = base->d_tw;
   v->d_itw = base->d_itw;
@@ -241,6 +242,11 @@ int he_ctx_create(const he_params* p, const int32_t* rot_steps, size_t n_rot, vo
   c->beta = (int)beta;
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
+  {
+    int smem = 0;
+    if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device) == cudaSuccess && smem > 0)
+      c->smem_per_sm = (size_t)smem;
+  }
   int rc = build_tables(c);
   if (rc == HE_OK) {
     std::vector<int32_t> rots(rot_steps, rot_steps + n_rot);

@@ -84,6 +84,7 @@ struct he_ctx {
   std::vector<uint64_t> psi;  // [np]
   cudaStream_t stream = nullptr;
   int device = 0;
+  size_t smem_per_sm = 228 * 1024;  // shared memory of one SM (queried at creation)
 
   // device tables
   PrimeDev* d_primes = nullptr;  // [np]

@@ -727,14 +727,22 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     *closed_out = rc.closed;
     if (!rc.closed)
       HE_CUDA(cudaMemsetAsync(ra.k.acc, 0, sizeof(uint64_t) * count * 2 * a.nt * (1u << LOG_N), c->stream));
-    // ciphertexts per CTA (closed stages only): the knob, else 2 when the
-    // tiles fit (a 15-rotation stage of 512 ciphertexts at N = 2^14: 9.3 ms
-    // against 10.1 ms for 1 and 10.0 ms for 4)
+    // ciphertexts per CTA (closed stages only): the knob, else 2 when that
+    // keeps as many warps resident per SM as 1 does (a 15-rotation stage of
+    // 512 ciphertexts at N = 2^14, 16 warps either way: 9.3 ms against 10.1 ms
+    // for 1 and 10.0 ms for 4; six digits at N = 2^16 would fall from 12 to 8
+    // warps, slower)
     uint32_t ct = 1;
     if (rc.closed) {
+      auto warps = [&](uint32_t k) {  // resident warps per SM with k ciphertexts per CTA
+        const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, k) + 1024;  // + the runtime's reserve per CTA
+        const size_t by_smem = c->smem_per_sm / sm, by_regs = 4 / k;
+        return std::min(by_smem, by_regs) * k * (size_t)SR::T / 32;
+      };
       const uint32_t want = c->ks_ct ? (uint32_t)c->ks_ct : 2u;
       for (uint32_t cand : {4u, 2u})
-        if (ct == 1 && cand <= want && cand <= count && ks_rot_smem<LOG_N, M2, K2>(a.beta, cand) <= kRotSmemMax)
+        if (ct == 1 && cand <= want && cand <= count && ks_rot_smem<LOG_N, M2, K2>(a.beta, cand) <= kRotSmemMax &&
+            (c->ks_ct || warps(cand) >= warps(1)))
           ct = cand;
     }
     const size_t blocks = (size_t)a.nt * ((count + ct - 1) / ct) * SR::TILES;
