@@ -178,13 +178,17 @@ KS_ROT_TRAFFIC_PER_ALG_BYTE = 498.2 / 519.1
 def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: bool | None = None) -> dict:
     """Roofline of one kernel class (or of several summed): the launch time
     against max(integer-pipe time, HBM time).  The integer-pipe time weighs
-    the class's modular products and butterflies at the measured Shoup-product
-    rate and its unreduced 128-bit key products at the measured
-    multiply-accumulate rate; `frac_shoup_only` is the older single-rate
+    each kind of work at its own measured register-resident rate: NTT
+    butterflies at the radix-8 lazy butterfly chain (he_probe_alu kind 2),
+    Shoup/Barrett products (conversions, scalings, reductions) at the Shoup
+    product chain (kind 1), and the unreduced 128-bit key products at the
+    multiply-accumulate chain (kind 3).  `frac_shoup_only` is the single-rate
     figure (every unit of work at the Shoup rate)."""
     t = p["ms"] * 1e-3
-    work, mac, by = p["work"], p.get("mac", 0.0), p["bytes"]
-    t_alu = (work - mac) / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
+    work, mac, bfly, by = p["work"], p.get("mac", 0.0), p.get("bfly", 0.0), p["bytes"]
+    r_bfly = ALU_PEAK["butterfly_per_second"] or ALU_PEAK["per_second"]
+    other = max(work - mac - bfly, 0.0)
+    t_alu = bfly / r_bfly + other / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
     t_hbm = by / (hbm_peak * 1e9)
     gbs = by / t / 1e9 if t > 0 else 0.0
     base = {"kernel": name, "per_launch_ms": p["ms"] / max(1, p["launches"]), "launches": p["launches"],
@@ -198,12 +202,14 @@ def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: boo
             base.update({"bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "G modmul/s",
                          "frac": t_alu / t if t > 0 else 0.0,
                          "frac_shoup_only": rate / ALU_PEAK["per_second"],
-                         "mac_share_of_work": mac / work if work else 0.0,
-                         "peak_note": (f"weighted integer roof: {work - mac:.3g} products and butterflies at "
-                                       f"{ALU_PEAK['note']}; {mac:.3g} 128-bit key multiply-accumulates at "
-                                       f"{ALU_PEAK['mac_note']}")})
-            if ALU_PEAK["butterfly_per_second"] and name in ("ntt", "intt"):
-                base["butterfly_chain_frac"] = rate / ALU_PEAK["butterfly_per_second"]
+                         "work_mix": {"butterflies": bfly, "shoup_products": other, "macs": mac},
+                         "peak_note": (f"weighted integer roof: {bfly:.3g} butterflies at the measured radix-8 "
+                                       f"lazy butterfly chain ({r_bfly / 1e9:.0f} G/s), {other:.3g} Shoup/Barrett "
+                                       f"products at {ALU_PEAK['note']} ({ALU_PEAK['per_second'] / 1e9:.0f} G/s), "
+                                       f"{mac:.3g} 128-bit key multiply-accumulates at {ALU_PEAK['mac_note']} "
+                                       f"({ALU_PEAK['mac_per_second'] / 1e9:.0f} G/s)")})
+            if name in ("ntt", "intt"):
+                base["butterfly_chain_frac"] = rate / r_bfly
             return base
     base.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                  "peak_note": f"{peak_kind} HBM copy bandwidth"})
@@ -504,9 +510,7 @@ def large_rooflines(he, torch, stream, ctx, A, B, O, T):
 
     def summed(prof, names):
         keys = [k for k in names if k in prof]
-        return {"ms": sum(prof[k]["ms"] for k in keys), "work": sum(prof[k]["work"] for k in keys),
-                "mac": sum(prof[k]["mac"] for k in keys), "bytes": sum(prof[k]["bytes"] for k in keys),
-                "launches": sum(prof[k]["launches"] for k in keys)}
+        return {f: sum(prof[k][f] for k in keys) for f in ("ms", "work", "mac", "bfly", "bytes", "launches")}
 
     for key, fn in (("keyswitch_rotation", lambda: he.he_rotate_batch(ctx, A, 1, O)),
                     ("mul_relin_rescale", lambda: he.he_mul_relin_rescale_batch(ctx, A, B, O))):
@@ -1186,7 +1190,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         import paper_2006_10091_gb300 as he
-        names = ("imad_32", "shoup_product_64", "lazy_butterfly_radix8")
+        names = ("imad_32", "shoup_product_64", "lazy_butterfly_radix8", "mac_128")
         print(json.dumps({"micro": "alu", **{n: he.he_probe_alu(k) for k, n in enumerate(names)},
                           "fallback_roof": {"per_second": ALU_MODMUL_PEAK,
                                             "note": "152 SMs x 2070 MHz x 64 / 17.3 (Shoup product)"}}))

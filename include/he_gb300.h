@@ -501,11 +501,13 @@ int he_profile_enable(he_ctx* ctx, int enable);
 int he_profile_read(he_ctx* ctx, const char* kernel_class, uint64_t* launches, double* total_ms,
                     double* work, double* bytes);
 int he_profile_names(he_ctx* ctx, char* buf, size_t cap);
-/* The part of a class's work (as counted by he_profile_read) that is 64 x 64
- * -> 128-bit multiply-accumulates summed without reduction (the key products
- * of the fused key switch), the rest being Shoup or Barrett products and
- * butterflies: lets a roofline weigh the two at their own measured rates. */
-int he_profile_read_mac(he_ctx* ctx, const char* kernel_class, double* mac_work);
+/* How a class's work (as counted by he_profile_read) splits by kind: NTT
+ * butterflies, and 64 x 64 -> 128-bit multiply-accumulates summed without
+ * reduction (the key products of the fused key switch); the rest is Shoup or
+ * Barrett products (basis conversion, scaling, reductions).  Lets a roofline
+ * weigh each kind at its own measured rate (he_probe_alu kinds 2, 3, 1).
+ * Either output may be NULL. */
+int he_profile_read_kinds(he_ctx* ctx, const char* kernel_class, double* butterflies, double* macs);
 
 #ifdef __cplusplus
 }

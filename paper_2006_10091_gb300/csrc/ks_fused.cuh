@@ -601,16 +601,15 @@ int md_fused_run(he_ctx* c, const MdArgs& a, uint32_t count, bool* handled) {
   {
     const size_t blocks = (size_t)count * 2 * SC::TILES;
     // with a half-transformed input, also the dropped limbs' inverse column pass
-    ProfScope prof(c, nm_col, polys * (n / 2 * M1 + n * a.alpha) + (a.half ? 2.0 * count * a.alpha * n / 2 * M1 : 0.0),
-                   n * 8 * (2.0 * count * a.alpha + polys));
+    const double bfly = polys * n / 2 * M1 + (a.half ? 2.0 * count * a.alpha * n / 2 * M1 : 0.0);
+    ProfScope prof(c, nm_col, bfly + polys * n * a.alpha, n * 8 * (2.0 * count * a.alpha + polys), 0.0, bfly);
     md_conv_col<LOG_N, M1, K1><<<(unsigned)blocks, SC::T, smc, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
   {
     const size_t blocks = (size_t)count * a.level * SR::TILES;
     const double addw = a.has_add == 3 ? 1.5 * polys : a.has_add == 2 ? polys : a.has_add == 1 ? polys / 2 : 0.0;
-    ProfScope prof(c, nm_row, polys * (n / 2 * M2 + 2 * n),
-                   n * 8 * (3.0 * polys + addw));
+    ProfScope prof(c, nm_row, polys * (n / 2 * M2 + 2 * n), n * 8 * (3.0 * polys + addw), 0.0, polys * n / 2 * M2);
     md_row_combine<LOG_N, M2, K2><<<(unsigned)blocks, SR::T, smr, c->stream>>>(a);
   }
   HE_CUDA(cudaGetLastError());
@@ -648,8 +647,9 @@ int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
   {
     // with a half-transformed input the kernel also runs the inverse column pass of the level input limbs
     const double inv_bfly = a.half ? (double)a.level * n / 2 * M1 + (double)a.level * n : 0.0;
+    const double bfly = count * (conv * n / 2 * M1 + (a.half ? (double)a.level * n / 2 * M1 : 0.0));
     ProfScope prof(c, "ks_modup_ntt", count * (conv * n / 2 * M1 + conv_products * n + inv_bfly),
-                   count * n * 8 * (a.level + conv));
+                   count * n * 8 * (a.level + conv), 0.0, bfly);
     const size_t sma = ks_all_smem<LOG_N, M1, K1>(c, a.beta, a.cnt);
     if (a.half && sma > kModupAllSmem) return fail(HE_EINVAL, "ks_fused: half-transformed input needs the all-targets kernel");
     if (sma <= kModupAllSmem) {  // one CTA per digit and tile, all targets
@@ -719,7 +719,8 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     // products are summed into it), each rotation's key read once per launch
     const double macs = count * 2.0 * ra.nrot * a.beta * a.nt * n;
     ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs,
-                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs);
+                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs,
+                   count * conv * n / 2 * M2);
     KsRotArgs rc = ra;
     rc.count = count;
     rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits

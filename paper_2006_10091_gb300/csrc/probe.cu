@@ -69,19 +69,21 @@ __global__ void probe_bfly(uint64_t* out, int iters, uint64_t q, const uint64_t*
 }
 
 // 64 x 64 -> 128-bit multiply-accumulates (the key products of the fused
-// key switch, summed unreduced), four independent 128-bit sums per thread
-// over eight register-resident operand pairs; one reduction at the end.
+// key switch, summed unreduced): four independent 128-bit sums per thread,
+// 32 products per iteration; the eight first operands are perturbed by the
+// sums after every iteration, so that no product is the same from one
+// iteration to the next (a loop-invariant product could be computed once).
 __global__ void probe_mac(uint64_t* out, int iters, uint64_t q) {
-  uint64_t x[8], y[8], lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
-  for (int k = 0; k < 8; ++k) {
-    x[k] = (0x9E3779B97F4A7C15ull * (threadIdx.x + 8u * k + 1)) % q;
-    y[k] = (0xC2B2AE3D27D4EB4Full * (blockIdx.x + 8u * k + 3)) % q;
-  }
+  uint64_t x[8], y[4], lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 8; ++k) x[k] = (0x9E3779B97F4A7C15ull * (threadIdx.x + 8u * k + 1)) % q;
+  for (int k = 0; k < 4; ++k) y[k] = (0xC2B2AE3D27D4EB4Full * (blockIdx.x + 8u * k + 3)) % q;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 8; ++u)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) mac128(lo[k], hi[k], x[(u + k) & 7], y[u]);
+      for (int k = 0; k < 4; ++k) mac128(lo[k], hi[k], x[u], y[k]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] += lo[u & 3] & 0xFF;
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = (lo[0] ^ lo[1] ^ lo[2] ^ lo[3]) + (hi[0] ^ hi[1] ^ hi[2] ^ hi[3]) % q;
 }
@@ -128,8 +130,8 @@ extern "C" int he_probe_alu(int kind, double* per_clock_per_sm, double* per_seco
       probe_bfly<<<blocks, threads>>>((uint64_t*)out, 2000, q, tw);
       ops = (double)blocks * threads * 2000 * 12;
     } else {
-      probe_mac<<<blocks, threads>>>((uint64_t*)out, 2048, q);
-      ops = (double)blocks * threads * 2048 * 8 * 4;
+      probe_mac<<<blocks, threads>>>((uint64_t*)out, 1024, q);
+      ops = (double)blocks * threads * 1024 * 8 * 4;
     }
     cudaEventRecord(e1);
   }

@@ -13,7 +13,7 @@ static thread_local bool tl_prof_suppressed = false;
 ProfSuppress::ProfSuppress() : prev_(tl_prof_suppressed) { tl_prof_suppressed = true; }
 ProfSuppress::~ProfSuppress() { tl_prof_suppressed = prev_; }
 
-ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac) : c_(c) {
+ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac, double bfly) : c_(c) {
   if (!c->prof_on || tl_prof_suppressed) {
     c_ = nullptr;
     return;
@@ -22,6 +22,7 @@ ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, dou
   k.work += work;
   k.bytes += bytes;
   k.mac += mac;
+  k.bfly += bfly;
   k.launches += 1;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
@@ -93,9 +94,10 @@ extern "C" int he_profile_names(he_ctx* c, char* buf, size_t cap) {
   return HE_OK;
 }
 
-extern "C" int he_profile_read_mac(he_ctx* c, const char* name, double* mac_work) {
-  if (!c || !name || !mac_work) return fail(HE_EINVAL, "null argument");
+extern "C" int he_profile_read_kinds(he_ctx* c, const char* name, double* butterflies, double* macs) {
+  if (!c || !name) return fail(HE_EINVAL, "null argument");
   auto it = c->prof.find(name);
-  *mac_work = it == c->prof.end() ? 0.0 : it->second.mac;
+  if (butterflies) *butterflies = it == c->prof.end() ? 0.0 : it->second.bfly;
+  if (macs) *macs = it == c->prof.end() ? 0.0 : it->second.mac;
   return HE_OK;
 }
