@@ -175,6 +175,17 @@ int he_decrypt_poly(he_ctx* ctx, const he_ct* ct, double* coeffs_out);
  * divided by the ciphertext's scale (host).  Synchronous. */
 int he_decrypt_decode(he_ctx* ctx, const he_ct* ct, double* slots_out, size_t n_slots);
 
+/* Library-owned ciphertexts (the handle form of the conventions above): a
+ * device buffer of 2*cap*N words allocated by the library (cap limbs per
+ * part, 1 <= cap <= L), level 0 until an entry point writes it; pass the
+ * handle wherever an he_ct* is taken.  he_ct_free synchronises the device
+ * (work queued on any stream may still use the buffer), then frees the buffer
+ * and the handle; NULL is ignored.  HE_EINVAL for a bad capacity, HE_ENOMEM
+ * when device memory is exhausted.  Caller-owned buffers (an he_ct the caller
+ * fills in) remain accepted everywhere. */
+int he_ct_alloc(he_ctx* ctx, uint32_t cap, he_ct** out);
+int he_ct_free(he_ct* ct);
+
 /* Residues to and from host memory, packed [2][level][N] (uint64).  Export is
  * synchronous; cap_words is the capacity of `host` in words. */
 int he_ct_export(he_ctx* ctx, const he_ct* ct, uint64_t* host, size_t cap_words);

@@ -142,6 +142,8 @@ def load():
         "he_autotune": [VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double)],
         "he_rescale_noalloc": [VP, CTP, CTP],
         "he_sum": [VP, VP, ctypes.c_size_t, CTP],
+        "he_ct_alloc": [VP, ctypes.c_uint32, ctypes.POINTER(CTP)],
+        "he_ct_free": [CTP],
         "he_ctx_workspace": [VP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64)],
         "he_lr_gradient_step_workers": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config),
                                         ctypes.c_uint32, ctypes.c_int],
@@ -261,12 +263,15 @@ def _run(fn, ctx, outs, *args):
             s = a.c()
             structs[id(a)] = (a, s)
             cargs.append(ctypes.byref(s))
+        elif isinstance(a, Handle):  # the library's own he_ct: level and scale live in it
+            cargs.append(a.ptr)
         else:
             cargs.append(a)
     _check(fn(ctx.ptr, *cargs))
     for o in outs:
-        a, s = structs[id(o)]
-        a.update(s)
+        if id(o) in structs:
+            a, s = structs[id(o)]
+            a.update(s)
 
 
 def _batch(cts):
@@ -411,6 +416,39 @@ def he_sum(ctx, cts: list, out):
     _check(load().he_sum(ctx.ptr, arr, len(cts), ctypes.byref(s)))
     out.update(s)
     return out
+
+
+class Handle:
+    """A library-owned ciphertext (he_ct_alloc): .ptr is the he_ct*; freed by
+    close() or on collection."""
+
+    def __init__(self, ctx, cap: int):
+        p = CTP()
+        _check(load().he_ct_alloc(ctx.ptr, cap, ctypes.byref(p)))
+        self.ptr = p
+
+    @property
+    def level(self) -> int:
+        return self.ptr.contents.level
+
+    @property
+    def scale(self) -> float:
+        return self.ptr.contents.scale
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _check(load().he_ct_free(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def he_ct_alloc(ctx, cap: int) -> Handle:
+    return Handle(ctx, cap)
 
 
 def he_ctx_workspace(ctx) -> dict:

@@ -437,6 +437,33 @@ int he_decrypt_decode(he_ctx* c, const he_ct* ct, double* slots_out, size_t n_sl
   return HE_OK;
 }
 
+int he_ct_alloc(he_ctx* c, uint32_t cap, he_ct** out) {
+  if (!c || !out) return fail(HE_EINVAL, "he_ct_alloc: null argument");
+  *out = nullptr;
+  if (cap < 1 || cap > (uint32_t)c->L) return fail(HE_EINVAL, "he_ct_alloc: capacity outside [1, L]");
+  he_ct* h = new he_ct();
+  const size_t bytes = sizeof(uint64_t) * 2 * (size_t)cap * c->n;
+  if (cudaMalloc(&h->data, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(HE_ENOMEM, "he_ct_alloc: device memory");
+  }
+  h->level = 0;
+  h->cap = cap;
+  h->scale = 0.0;
+  *out = h;
+  return HE_OK;
+}
+
+int he_ct_free(he_ct* ct) {
+  if (!ct) return HE_OK;
+  // the buffer may still be in use by work queued on any stream
+  cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(ct->data);
+  delete ct;
+  return e == cudaSuccess ? HE_OK : fail(HE_ECUDA, std::string("he_ct_free: ") + cudaGetErrorString(e));
+}
+
 int he_ct_export(he_ctx* c, const he_ct* ct, uint64_t* host, size_t cap_words) {
   if (!c || !host) return fail(HE_EINVAL, "he_ct_export: null argument");
   HE_TRY(check_ct(c, ct, "he_ct_export"));

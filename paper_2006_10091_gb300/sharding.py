@@ -15,12 +15,53 @@ continues from them.
 The partition gives each rank a set of workers with about the same number of
 data ciphertexts (largest first, to the least loaded rank), which is what a
 step costs.
+
+Failure detection is on the host: before each aggregation every rank checks in
+through a key-value store (refresh_check_in) and waits, bounded, for all the
+others.  A rank that dropped out or stalled past the limit, or one that
+arrives with a stale or duplicated refresh (another iteration, level or
+scale), raises an error on every rank before any collective starts, so no rank
+is left waiting in all_gather.
 """
 from __future__ import annotations
 
+import datetime
+
 import torch
 
-from . import (Ciphertext, he_lr_gradient_step_workers, he_refresh, he_sum)
+from . import (HE_ETIMEOUT, HE_ESCALE, Ciphertext, he_lr_gradient_step_workers, he_refresh, he_sum)
+
+
+class RefreshError(RuntimeError):
+    """A rank's refresh could not proceed; `code` is HE_ETIMEOUT (a rank did not
+    check in within the limit) or HE_ESCALE (ranks disagree on the iteration,
+    level or scale of the weights they bring)."""
+
+    def __init__(self, code: int, msg: str):
+        super().__init__(msg)
+        self.code = code
+
+
+def refresh_check_in(store, iteration: int, rank: int, world: int, level: int, scale: float,
+                     timeout_s: float = 60.0, prefix: str = "he_refresh") -> None:
+    """Publish this rank's (iteration, level, scale) under
+    prefix/iteration/rank in `store` (a torch.distributed Store) and wait at
+    most timeout_s for every rank's entry; then check that all agree.  Raises
+    RefreshError(HE_ETIMEOUT) naming the ranks missing after the limit, or
+    RefreshError(HE_ESCALE) when the entries differ."""
+    mine = f"{iteration}:{level}:{float(scale).hex()}"
+    keys = [f"{prefix}/{iteration}/{r}" for r in range(world)]
+    store.set(keys[rank], mine)
+    try:
+        store.wait(keys, datetime.timedelta(seconds=timeout_s))
+    except Exception as e:  # the store's own timeout error
+        missing = [r for r in range(world) if not store.check([keys[r]])]
+        raise RefreshError(HE_ETIMEOUT, f"refresh {iteration}: ranks {missing} did not check in within "
+                                        f"{timeout_s} s ({type(e).__name__})") from None
+    vals = [store.get(k).decode() for k in keys]
+    if any(v != mine for v in vals):
+        raise RefreshError(HE_ESCALE, f"refresh {iteration}: ranks bring different weights "
+                                      f"(iteration:level:scale) {vals}")
 
 
 def partition_shards(sizes, world: int) -> list[list[int]]:
@@ -94,14 +135,16 @@ def key_holder_refresh(ctx, total: Ciphertext, n_workers: int, top_level: int, s
 
 
 def train_sharded(ctx, shards: list, cfg, iterations: int, refresh_every: int, top_level: int, cid0: int,
-                  n_workers: int, group=None) -> Ciphertext:
+                  n_workers: int, group=None, store=None, timeout_s: float = 60.0) -> Ciphertext:
     """Algorithms 1 and 2 over ranks: `shards` = this rank's workers as
     (Z list, W) with W at top_level (all workers start from the same
     weights); `n_workers` = the workers of all ranks.  Every worker runs
     `iterations` gradient steps (Eq. 7-8) on its own data; after every
     `refresh_every` steps and after the last, the weights of all workers are
     summed across ranks and the key holder replaces them by the re-encrypted
-    average (random stream cid0 + iteration).  Returns the final average (at
+    average (random stream cid0 + iteration).  With a `store` (the ranks'
+    torch.distributed Store) every rank checks in before each aggregation
+    (refresh_check_in, bounded by timeout_s).  Returns the final average (at
     top_level), identical on every rank."""
     if top_level < 5 * refresh_every + 1:
         raise ValueError("the weights run out of limbs before the refresh")
@@ -120,6 +163,11 @@ def train_sharded(ctx, shards: list, cfg, iterations: int, refresh_every: int, t
         cur, nxt = nxt, cur
         if it % refresh_every == 0 or it == iterations:
             he_sum(ctx, cur, local_sum)
+            if store is not None:
+                dist = _dist()
+                rank = dist.get_rank(group) if dist else 0
+                world = dist.get_world_size(group) if dist else 1
+                refresh_check_in(store, it, rank, world, local_sum.level, local_sum.scale, timeout_s)
             allreduce_ciphertext(ctx, local_sum, total, group)
             key_holder_refresh(ctx, total, n_workers, top_level, scale, cid0 + it, fresh, group)
             for c in cur:

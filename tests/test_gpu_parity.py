@@ -750,3 +750,24 @@ def test_alu_probes_run(he):
     assert r[0]["per_clock_per_sm"] > 4 * r[1]["per_clock_per_sm"]
     with pytest.raises(he.HeError):
         he.he_probe_alu(7)
+
+
+def test_library_owned_ciphertexts(small, he):
+    """Handles from he_ct_alloc serve every entry point like caller-owned
+    buffers: encrypt into two, multiply into a third, equal to the oracle;
+    he_ct_free releases them; a capacity outside [1, L] is refused."""
+    ma, mb = workloads.int_poly(61, small.n, 1 << 30), workloads.int_poly(62, small.n, 1 << 30)
+    a, b, out = he.he_ct_alloc(small.g, 5), he.he_ct_alloc(small.g, 5), he.he_ct_alloc(small.g, 4)
+    assert a.level == 0
+    he.he_encrypt_poly(small.g, ma, small.g.scale, 5, a, cid=61)
+    he.he_encrypt_poly(small.g, mb, small.g.scale, 5, b, cid=62)
+    he.he_mul_relin_rescale(small.g, a, b, out)
+    want = small.o.mul_relin_rescale(small.orc_enc(ma, 5, 61), small.orc_enc(mb, 5, 62))
+    assert (out.level, out.scale) == (want.level, pytest.approx(want.scale, rel=1e-15))
+    assert np.array_equal(he.he_ct_export(small.g, out), want.data)
+    for h in (a, b, out):
+        h.close()
+    for cap in (0, small.L + 1):
+        with pytest.raises(he.HeError) as e:
+            he.he_ct_alloc(small.g, cap)
+        assert e.value.code == he.HE_EINVAL

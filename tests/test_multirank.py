@@ -133,3 +133,54 @@ def test_two_ranks_sum_weights_modulo_each_prime():
     for rank, got, bcast, level, scale in res:
         assert np.array_equal(got, want), rank
         assert np.array_equal(bcast, cts[0].data) and level == 3 and scale == cts[0].scale
+
+
+# ---------------------------------------------------------------- refresh failures (host side)
+
+
+def _check_in_rank(rank: int, port: int, scenario: str, out):
+    import datetime
+    import time
+    from paper_2006_10091_gb300 import sharding
+    store = dist.TCPStore("127.0.0.1", port, 2, rank == 0, timeout=datetime.timedelta(seconds=30))
+    level, scale = 4, 2.0 ** 40
+    try:
+        if rank == 1 and scenario == "drop":  # the worker's refresh never arrives
+            out.put((rank, "skipped", None))
+            time.sleep(3.0)  # keep the connection while rank 0 waits
+            return
+        if rank == 1 and scenario == "stale":  # weights from an older step: one level more
+            level = 5
+        if rank == 1 and scenario == "delay":
+            time.sleep(0.5)
+        sharding.refresh_check_in(store, 7, rank, 2, level, scale, timeout_s=1.5 if scenario == "drop" else 10.0)
+        out.put((rank, "ok", None))
+    except sharding.RefreshError as e:
+        out.put((rank, "error", e.code))
+    if rank == 0:
+        time.sleep(1.0)  # the store lives in rank 0: let rank 1 finish reading it
+
+
+@pytest.mark.parametrize("scenario", ["ok", "delay", "drop", "stale"])
+def test_refresh_check_in_detects_failed_ranks(scenario):
+    """Two CPU ranks check in before the key holder's aggregation: on time or
+    late but within the limit, both proceed; if rank 1's refresh never
+    arrives, rank 0 gets HE_ETIMEOUT after the limit instead of blocking in a
+    collective; if rank 1 brings weights at another level, both get HE_ESCALE."""
+    import paper_2006_10091_gb300 as he
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_check_in_rank, args=(r, port, scenario, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict((r, (s, c)) for r, s, c in (q.get(timeout=120) for _ in procs))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    if scenario in ("ok", "delay"):
+        assert res == {0: ("ok", None), 1: ("ok", None)}
+    elif scenario == "drop":
+        assert res[0] == ("error", he.HE_ETIMEOUT)
+    else:
+        assert res == {0: ("error", he.HE_ESCALE), 1: ("error", he.HE_ESCALE)}
