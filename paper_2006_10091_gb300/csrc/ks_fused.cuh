@@ -47,6 +47,32 @@ __device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level, uint32_
   return t < level ? t : L + t - level;
 }
 
+// The basis conversion of one tile into shared memory: for the T threads'
+// elements idx of the tile, sum over u < CNT of wv[u][idx] times the constant
+// (w[u * stride], its Shoup companion), reduced to [0, q); the CNT constants
+// sit in registers for the whole tile.  Returns the sums still in [0, q).
+template <int TILE, int T, int CNT>
+__device__ __forceinline__ void conv_sum_tile(uint64_t* sm, const uint64_t* wv, const uint64_t* w, const uint64_t* wsh,
+                                              uint32_t stride, uint64_t q) {
+  uint64_t cw[CNT], cs[CNT];
+#pragma unroll
+  for (int u = 0; u < CNT; ++u) {
+    cw[u] = w[(size_t)u * stride];
+    cs[u] = wsh[(size_t)u * stride];
+  }
+  const uint64_t q2 = q + q;
+#pragma unroll 2
+  for (uint32_t idx = threadIdx.x; idx < (uint32_t)TILE; idx += T) {
+    uint64_t y = 0;
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+      y += mul_shoup_lazy(wv[(size_t)u * TILE + idx], cw[u], cs[u], q);
+      y = y >= q2 ? y - q2 : y;
+    }
+    sm[idx + (idx >> 3)] = y >= q ? y - q : y;
+  }
+}
+
 // Column pass with the ModUp conversion in its load.  Grid: count * beta * nt * TILES.
 template <int LOG_N, int LOG_M, int LOG_K>
 __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col(KsFusedArgs a) {
@@ -159,22 +185,28 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
     // the previous target's rounds ended with a barrier, and its write-out
     // reads only the words each thread rewrites below
     stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)prime * N, tile);
+    // Shoup products by (Q_j/q_i) mod q_t, the digit's limb count a compile-time
+    // constant for the usual digit sizes
+    if (cnt == 2) conv_sum_tile<S::TILE, S::T, 2>(sm, wv, mat + prime, mat_sh + prime, a.np, pr.q);
+    else if (cnt == 3) conv_sum_tile<S::TILE, S::T, 3>(sm, wv, mat + prime, mat_sh + prime, a.np, pr.q);
+    else if (cnt == 4) conv_sum_tile<S::TILE, S::T, 4>(sm, wv, mat + prime, mat_sh + prime, a.np, pr.q);
+    else
 #pragma unroll 2
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t y;
-      if (cnt == 1) {
-        y = reduce64(wv[idx], pr);  // Q_j / q_lo = 1
-      } else {  // Shoup products by (Q_j/q_i) mod q_t, kept in [0, 2q)
-        y = 0;
-        for (uint32_t u = 0; u < cnt; ++u) {
-          y += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.np + prime],
-                              mat_sh[(size_t)u * a.np + prime], pr.q);
-          y = y >= q2 ? y - q2 : y;
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+        uint64_t y;
+        if (cnt == 1) {
+          y = reduce64(wv[idx], pr);  // Q_j / q_lo = 1
+        } else {  // kept in [0, 2q)
+          y = 0;
+          for (uint32_t u = 0; u < cnt; ++u) {
+            y += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.np + prime],
+                                mat_sh[(size_t)u * a.np + prime], pr.q);
+            y = y >= q2 ? y - q2 : y;
+          }
+          y = y >= pr.q ? y - pr.q : y;
         }
-        y = y >= pr.q ? y - pr.q : y;
+        sm[idx + (idx >> 3)] = y;
       }
-      sm[idx + (idx >> 3)] = y;
-    }
     __syncthreads();
     uint64_t* out = a.ext + (((size_t)i * a.beta + j) * a.nt + t) * N;
     if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
@@ -485,17 +517,31 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     const uint64_t q2 = pr.q + pr.q, hQ = hP[a.alpha + t];
     const uint64_t* vP = wlo + a.alpha + a.L + (size_t)t * 8;  // v P mod q_t, v < 8
     stage_twiddles<LOG_N, LOG_M, LOG_K, true>(stw, a.tw + (size_t)t * N, tile);
+    // Shoup products by (P/p_u) mod q_t (the dropped-prime count a
+    // compile-time constant for the usual counts), then - v P - h
+    if (a.alpha >= 2 && a.alpha <= 5) {
+      if (a.alpha == 2) conv_sum_tile<S::TILE, S::T, 2>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
+      else if (a.alpha == 3) conv_sum_tile<S::TILE, S::T, 3>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
+      else if (a.alpha == 4) conv_sum_tile<S::TILE, S::T, 4>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
+      else conv_sum_tile<S::TILE, S::T, 5>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
 #pragma unroll 2
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t acc = 0;  // Shoup products by (P/p_u) mod q_t, kept in [0, 2q)
-      for (uint32_t u = 0; u < a.alpha; ++u) {
-        acc += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t],
-                              pr.q);
-        acc = acc >= q2 ? acc - q2 : acc;
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+        const uint64_t acc = sub_mod(sm[idx + (idx >> 3)], vP[vv[idx]], pr.q);
+        sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
       }
-      acc = acc >= pr.q ? acc - pr.q : acc;
-      acc = sub_mod(acc, vP[vv[idx]], pr.q);
-      sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
+    } else {
+#pragma unroll 2
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
+        uint64_t acc = 0;  // kept in [0, 2q)
+        for (uint32_t u = 0; u < a.alpha; ++u) {
+          acc += mul_shoup_lazy(wv[(size_t)u * S::TILE + idx], mat[(size_t)u * a.L + t], mat_sh[(size_t)u * a.L + t],
+                                pr.q);
+          acc = acc >= q2 ? acc - q2 : acc;
+        }
+        acc = acc >= pr.q ? acc - pr.q : acc;
+        acc = sub_mod(acc, vP[vv[idx]], pr.q);
+        sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
+      }
     }
     __syncthreads();
     if (pr.q < (1ull << 58)) run_rounds<false, true, LOG_N, LOG_M, LOG_K, true>(sm, stw, pr.q);
