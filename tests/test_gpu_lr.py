@@ -85,6 +85,19 @@ def test_lr_step_refuses_negative_l2(lr_pair):
     assert e.value.code == he.HE_EINVAL
 
 
+def test_lr_step_refuses_empty_data(lr_pair):
+    pair, g = lr_pair
+    he = pair.he
+    W = pair.gpu_enc(workloads.int_poly(7, pair.n, 100), 7, 7, scale=2.0 ** 40)
+    out = pair.g.new_ct(7)
+    with pytest.raises(he.HeError) as e:
+        he.he_lr_gradient_step(pair.g, [], W, he.lr_config(table2()["binomial"], 0.1, g, 2.0 ** 40), out)
+    assert e.value.code == he.HE_EINVAL
+    with pytest.raises(he.HeError) as e:  # a worker without data in a batched call
+        he.he_lr_gradient_step_workers(pair.g, [([], W, out)], he.lr_config(table2()["binomial"], 0.1, g, 2.0 ** 40))
+    assert e.value.code == he.HE_EINVAL
+
+
 def test_lr_step_non_uniform_inputs(lr_pair):
     pair, g = lr_pair
     he = pair.he

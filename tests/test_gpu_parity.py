@@ -771,3 +771,27 @@ def test_library_owned_ciphertexts(small, he):
         with pytest.raises(he.HeError) as e:
             he.he_ct_alloc(small.g, cap)
         assert e.value.code == he.HE_EINVAL
+
+
+def test_empty_and_degenerate_inputs(small, he):
+    """Empty batches are no-ops; a rotation by 0 or by N/2 slots (the identity
+    automorphism) returns the input's residues; operations on one-limb
+    ciphertexts that need none of the consumed limbs work at level 1 and
+    equal the oracle; an empty sum is refused."""
+    he.he_mul_relin_rescale_batch(small.g, [], [], [])
+    he.he_rotate_batch(small.g, [], 1, [])
+    he.he_rotate_sum_batch(small.g, [], [1], [])
+    ga, oa = _ct_pair(small, 1300, 3)
+    for steps in (0, small.n // 2):
+        out = small.g.new_ct(3)
+        he.he_rotate(small.g, ga, steps, out)
+        assert np.array_equal(he.he_ct_export(small.g, out), oa.data)
+    g1, o1 = _ct_pair(small, 1301, 1)
+    out = small.g.new_ct(1)
+    he.he_rotate(small.g, g1, 1, out)  # key switching with a single limb
+    assert_same_residues(out, small.o.rotate(o1, 1), he, small.g)
+    he.he_add(small.g, g1, g1, out)
+    assert_same_residues(out, small.o.add(o1, o1), he, small.g)
+    with pytest.raises(he.HeError) as e:
+        he.he_sum(small.g, [], out)
+    assert e.value.code == he.HE_EINVAL
