@@ -594,11 +594,20 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8, 3) md_row_combine(
       const uint32_t idx = threadIdx.x + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       av[u] = __ldg(accq + e);
-      uint64_t d = add_plain ? __ldg(ad + e) : 0;
-      if (add_perm)
-        for (uint32_t g = 0; g < a.n_gal; ++g) d = add_mod(d, __ldg(ad + automorph_src(e, a.gal[g], LOG_N)), q);
-      dv[u] = d;
+      dv[u] = add_plain ? __ldg(ad + e) : 0;
     }
+    if (add_perm)  // one automorphism at a time: the thread's PER gathers are independent loads
+      for (uint32_t g = 0; g < a.n_gal; ++g) {
+        uint64_t gv[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const uint32_t idx = threadIdx.x + u * S::T;
+          const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+          gv[u] = __ldg(ad + automorph_src(e, a.gal[g], LOG_N));
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) dv[u] = add_mod(dv[u], gv[u], q);
+      }
     __syncthreads();
     if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
     else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q);
