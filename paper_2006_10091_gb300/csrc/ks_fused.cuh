@@ -163,16 +163,19 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) ks_modup_col_all(K
       __syncthreads();
       run_rounds<true, false, LOG_N, LOG_M, LOG_K, true>(sm, stw, pa.q);
     }
+    if (a.half) {  // the scaling by N^-1 and the product by (Q_j/q_i)^-1 as one constant
+      const uint64_t* tabn = mat_sh + (size_t)cnt * a.np;
+      const uint64_t w = tabn[2 * u], wsh = tabn[2 * u + 1];
 #pragma unroll 8
-    for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-      uint64_t xv;
-      if (a.half) {
-        xv = mul_shoup(sm[idx + (idx >> 3)], pa.n_inv, pa.n_inv_sh, pa.q);
-      } else {
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T)
+        wv[(size_t)u * S::TILE + idx] = mul_shoup(sm[idx + (idx >> 3)], w, wsh, pa.q);
+    } else {
+#pragma unroll 8
+      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
         const uint32_t e = S::gidx(tile, idx & (S::K - 1), idx >> LOG_K);
-        xv = __ldg(x + (size_t)(lo + u) * N + e);
+        const uint64_t xv = __ldg(x + (size_t)(lo + u) * N + e);
+        wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], pa.q);
       }
-      wv[(size_t)u * S::TILE + idx] = cnt == 1 ? xv : mul_shoup(xv, tab[2 * u], tab[2 * u + 1], pa.q);
     }
     // the next limb's staging overwrites stw and sm: wait for every thread
     __syncthreads();

@@ -204,7 +204,9 @@ int build_tables(he_ctx* c) {
 
   // ModUp constants per (level, digit): digit D_j = [j*alpha, min((j+1)*alpha, level)).
   // Table: [cnt] Shoup pairs (inv_i = (Q_j/q_i)^-1 mod q_i), then [cnt][np] values
-  // (Q_j/q_i) mod p for every prime index p, then their [cnt][np] Shoup companions.
+  // (Q_j/q_i) mod p for every prime index p, then their [cnt][np] Shoup companions,
+  // then [cnt] Shoup pairs of inv_i * N^-1 mod q_i (the conversion's first product
+  // folded with the scaling that ends an inverse transform).
   {
     std::vector<uint64_t> words;
     c->modup.assign(L + 1, {});
@@ -236,6 +238,12 @@ int build_tables(he_ctx* c) {
         }
         for (uint32_t a = 0; a < mc.cnt; ++a)
           for (int p = 0; p < np; ++p) words.push_back(h_shoup(words[mat0 + (size_t)a * np + p], c->q[p]));
+        for (uint32_t a = 0; a < mc.cnt; ++a) {
+          const uint64_t qi = c->q[mc.lo + a];
+          const uint64_t v = h_mulmod(words[mc.off + 2 * a], h_invmod((uint64_t)n % qi, qi), qi);
+          words.push_back(v);
+          words.push_back(h_shoup(v, qi));
+        }
         c->modup[lv].push_back(mc);
       }
     }
