@@ -255,6 +255,38 @@ struct KsRotArgs {
 // last ciphertext in the groups beyond the count and stores nothing for them.
 // Shared memory: the tile's twiddles and every digit's transformed tile of
 // each ciphertext ([CT][beta][TILE + TILE/8] words).
+// Key products of a closed stage on a prime of k <= 2*sb bits whose sums
+// fit in 64 bits (2*sb + 2 + bitlen(nrot*beta) <= 64): every residue (digit and key,
+// canonical, below 2^k) is split as x = xh 2^sb + xl, and x w is summed as three
+// 64-bit sums of 32 x 32 -> 64-bit products (Karatsuba):
+//   S_ll = sum xl wl,  S_hh = sum xh wh,  S_s = sum (xl + xh)(wl + wh),
+//   sum x w = S_ll + (S_s - S_ll - S_hh) 2^sb + S_hh 2^(2 sb),
+// formed as one 128-bit value and reduced once per residue.  The same exact
+// sum as the 128-bit multiply-accumulates, so the same residues.
+struct Split3 {
+  uint32_t l, h, s;
+};
+__device__ __forceinline__ Split3 split3(uint64_t x, uint32_t sb, uint32_t mask) {
+  const uint32_t l = (uint32_t)x & mask, h = (uint32_t)(x >> sb);
+  return Split3{l, h, l + h};
+}
+__device__ __forceinline__ void mac_split3(uint64_t& ll, uint64_t& hh, uint64_t& ss, const Split3& x,
+                                           const Split3& w) {
+  ll += (uint64_t)x.l * w.l;
+  hh += (uint64_t)x.h * w.h;
+  ss += (uint64_t)x.s * w.s;
+}
+__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
+                                                  const PrimeDev& pr) {
+  const uint64_t mid = ss - ll - hh;  // sum (xl wh + xh wl), exact
+  uint64_t lo = ll, hi = 0;
+  const uint64_t m_lo = mid << sb, m_hi = mid >> (64 - sb);      // 1 <= sb <= 31
+  const uint64_t h_lo = hh << (2 * sb), h_hi = hh >> (64 - 2 * sb);
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m_lo), "l"(m_hi));
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(h_lo), "l"(h_hi));
+  return reduce128_any(hi, lo, pr);
+}
+
 template <int LOG_N, int LOG_M, int LOG_K, int CT>
 __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_row_rot(KsRotArgs ra) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
@@ -309,6 +341,64 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
   // 2. the products of the permuted digits with each rotation's key, summed
   // as full 128-bit products and reduced once per residue
   const uint32_t row0 = (uint32_t)tile << LOG_K;
+  const uint32_t sb = (pr.k + 1) >> 1;
+  if (ra.closed && 2 * sb + 2 + (32 - __clz(ra.nrot * a.beta)) <= 64) {
+    // the split sums (mac_split3), one pair of neighbouring positions per
+    // pass, all CT ciphertexts with each key load
+    constexpr int PPT = PER / 2 / CT;
+    const uint32_t mask = (1u << sb) - 1;
+#pragma unroll 1
+    for (int v0 = 0; v0 < PPT; ++v0) {
+      const uint32_t idx = 2 * (threadIdx.x + v0 * CT * S::T);
+      const uint32_t eo = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
+      uint64_t ll[CT][2][2], hh[CT][2][2], ss[CT][2][2];  // [ciphertext][part][position]
+#pragma unroll
+      for (int c = 0; c < CT; ++c)
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) ll[c][p][u] = hh[c][p][u] = ss[c][p][u] = 0;
+      for (uint32_t r = 0; r < ra.nrot; ++r) {
+        uint32_t so[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t p = automorph_src(eo + u, ra.gal[r], LOG_N);
+          const uint32_t sl = (((p >> LOG_M) - row0) << LOG_M) | (p & (S::M - 1));
+          so[u] = sl + (sl >> 3);
+        }
+        const uint64_t* ev = ra.evk[r];
+#pragma unroll 2
+        for (uint32_t j = 0; j < a.beta; ++j) {
+          const uint64_t* kb = ev + (((size_t)j * 2 + 0) * a.np + prime) * N;
+          const uint64_t* ka = ev + (((size_t)j * 2 + 1) * a.np + prime) * N;
+          const ulonglong2 wb = __ldg(reinterpret_cast<const ulonglong2*>(kb + eo));
+          const ulonglong2 wa = __ldg(reinterpret_cast<const ulonglong2*>(ka + eo));
+          const Split3 kb0 = split3(wb.x, sb, mask), kb1 = split3(wb.y, sb, mask);
+          const Split3 ka0 = split3(wa.x, sb, mask), ka1 = split3(wa.y, sb, mask);
+#pragma unroll
+          for (int c = 0; c < CT; ++c) {
+            const uint64_t* sm = dig + ((size_t)c * a.beta + j) * TW;
+            const Split3 x0 = split3(sm[so[0]], sb, mask), x1 = split3(sm[so[1]], sb, mask);
+            mac_split3(ll[c][0][0], hh[c][0][0], ss[c][0][0], x0, kb0);
+            mac_split3(ll[c][0][1], hh[c][0][1], ss[c][0][1], x1, kb1);
+            mac_split3(ll[c][1][0], hh[c][1][0], ss[c][1][0], x0, ka0);
+            mac_split3(ll[c][1][1], hh[c][1][1], ss[c][1][1], x1, ka1);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CT; ++c) {
+        if (i0 + c >= ra.count) break;
+        uint64_t* o0 = a.acc + ((size_t)(i0 + c) * 2 * a.nt + t) * N;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+          *reinterpret_cast<ulonglong2*>(o0 + (size_t)p * a.nt * N + eo) =
+              make_ulonglong2(reduce_split3(ll[c][p][0], hh[c][p][0], ss[c][p][0], sb, pr),
+                              reduce_split3(ll[c][p][1], hh[c][p][1], ss[c][p][1], sb, pr));
+      }
+    }
+    return;
+  }
   if (ra.closed) {
     // each thread sums every rotation's products for its own positions, two
     // neighbouring positions at a time (16-byte key loads and stores), for
