@@ -144,6 +144,8 @@ ALU_PEAK = {"per_second": ALU_MODMUL_PEAK, "note": "fallback: 152 SMs x 2070 MHz
                                                   "per 64-bit Shoup product",
             # 64 x 64 -> 128-bit multiply-accumulates (he_probe_alu kind 3); fallback: the Shoup rate
             "mac_per_second": ALU_MODMUL_PEAK, "mac_note": "fallback: the Shoup-product rate",
+            # split key products, three 32 x 32 -> 64-bit multiply-adds each (kind 4); fallback: the Shoup rate
+            "mac3_per_second": ALU_MODMUL_PEAK, "mac3_note": "fallback: the Shoup-product rate",
             # radix-8 rounds of the lazy butterfly in registers (kind 2): the practical ceiling of a transform
             "butterfly_per_second": None}
 
@@ -159,6 +161,10 @@ def measure_alu_peak(he) -> None:
         ALU_PEAK["mac_per_second"] = m["per_second"]
         ALU_PEAK["mac_note"] = (f"measured: register-resident 64x64->128-bit multiply-accumulate chain "
                                 f"({m['per_clock_per_sm']:.2f} per clock per SM)")
+        m3 = he.he_probe_alu(4)
+        ALU_PEAK["mac3_per_second"] = m3["per_second"]
+        ALU_PEAK["mac3_note"] = (f"measured: register-resident split key-product chain, three 32x32->64-bit "
+                                 f"multiply-adds each ({m3['per_clock_per_sm']:.2f} per clock per SM)")
         ALU_PEAK["butterfly_per_second"] = he.he_probe_alu(2)["per_second"]
     except Exception:  # keep the fallbacks
         return
@@ -181,14 +187,17 @@ def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: boo
     each kind of work at its own measured register-resident rate: NTT
     butterflies at the radix-8 lazy butterfly chain (he_probe_alu kind 2),
     Shoup/Barrett products (conversions, scalings, reductions) at the Shoup
-    product chain (kind 1), and the unreduced 128-bit key products at the
-    multiply-accumulate chain (kind 3).  `frac_shoup_only` is the single-rate
-    figure (every unit of work at the Shoup rate)."""
+    product chain (kind 1), the unreduced 128-bit key products at the
+    multiply-accumulate chain (kind 3) and the split key products at their own
+    chain (kind 4).  `frac_shoup_only` is the single-rate figure (every unit
+    of work at the Shoup rate)."""
     t = p["ms"] * 1e-3
     work, mac, bfly, by = p["work"], p.get("mac", 0.0), p.get("bfly", 0.0), p["bytes"]
+    mac3 = p.get("mac3", 0.0)
     r_bfly = ALU_PEAK["butterfly_per_second"] or ALU_PEAK["per_second"]
-    other = max(work - mac - bfly, 0.0)
-    t_alu = bfly / r_bfly + other / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
+    other = max(work - mac - mac3 - bfly, 0.0)
+    t_alu = (bfly / r_bfly + other / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
+             + mac3 / ALU_PEAK["mac3_per_second"])
     t_hbm = by / (hbm_peak * 1e9)
     gbs = by / t / 1e9 if t > 0 else 0.0
     base = {"kernel": name, "per_launch_ms": p["ms"] / max(1, p["launches"]), "launches": p["launches"],
@@ -202,12 +211,15 @@ def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: boo
             base.update({"bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "G modmul/s",
                          "frac": t_alu / t if t > 0 else 0.0,
                          "frac_shoup_only": rate / ALU_PEAK["per_second"],
-                         "work_mix": {"butterflies": bfly, "shoup_products": other, "macs": mac},
+                         "work_mix": {"butterflies": bfly, "shoup_products": other, "macs": mac,
+                                      "split_macs": mac3},
                          "peak_note": (f"weighted integer roof: {bfly:.3g} butterflies at the measured radix-8 "
                                        f"lazy butterfly chain ({r_bfly / 1e9:.0f} G/s), {other:.3g} Shoup/Barrett "
                                        f"products at {ALU_PEAK['note']} ({ALU_PEAK['per_second'] / 1e9:.0f} G/s), "
                                        f"{mac:.3g} 128-bit key multiply-accumulates at {ALU_PEAK['mac_note']} "
-                                       f"({ALU_PEAK['mac_per_second'] / 1e9:.0f} G/s)")})
+                                       f"({ALU_PEAK['mac_per_second'] / 1e9:.0f} G/s), {mac3:.3g} split key "
+                                       f"products at {ALU_PEAK['mac3_note']} "
+                                       f"({ALU_PEAK['mac3_per_second'] / 1e9:.0f} G/s)")})
             if name in ("ntt", "intt"):
                 base["butterfly_chain_frac"] = rate / r_bfly
             return base
@@ -510,7 +522,7 @@ def large_rooflines(he, torch, stream, ctx, A, B, O, T):
 
     def summed(prof, names):
         keys = [k for k in names if k in prof]
-        return {f: sum(prof[k][f] for k in keys) for f in ("ms", "work", "mac", "bfly", "bytes", "launches")}
+        return {f: sum(prof[k][f] for k in keys) for f in ("ms", "work", "mac", "mac3", "bfly", "bytes", "launches")}
 
     for key, fn in (("keyswitch_rotation", lambda: he.he_rotate_batch(ctx, A, 1, O)),
                     ("mul_relin_rescale", lambda: he.he_mul_relin_rescale_batch(ctx, A, B, O))):
@@ -1190,7 +1202,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         import paper_2006_10091_gb300 as he
-        names = ("imad_32", "shoup_product_64", "lazy_butterfly_radix8", "mac_128")
+        names = ("imad_32", "shoup_product_64", "lazy_butterfly_radix8", "mac_128", "mac_split3")
         print(json.dumps({"micro": "alu", **{n: he.he_probe_alu(k) for k, n in enumerate(names)},
                           "fallback_roof": {"per_second": ALU_MODMUL_PEAK,
                                             "note": "152 SMs x 2070 MHz x 64 / 17.3 (Shoup product)"}}))

@@ -112,7 +112,9 @@ int he_get_tuning(he_ctx* ctx, const char* key, double* value);
  * throughput on the current device of kind 0 = 32-bit multiply-adds, 1 =
  * 64-bit Shoup modular products (the integer roof of the transforms), 2 =
  * radix-8 rounds of the lazy forward butterfly, 3 = 64 x 64 -> 128-bit
- * multiply-accumulates (the key switch's unreduced key products); per clock
+ * multiply-accumulates (the key switch's unreduced key products on wide
+ * primes), 4 = split key products of residues below 2^40 (three 32 x 32 ->
+ * 64-bit multiply-adds each, the key products on narrower primes); per clock
  * per SM (at the device's maximum clock) and per second.  Runs two short
  * kernels on the default stream and synchronises. */
 int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second);
@@ -513,12 +515,15 @@ int he_profile_read(he_ctx* ctx, const char* kernel_class, uint64_t* launches, d
                     double* work, double* bytes);
 int he_profile_names(he_ctx* ctx, char* buf, size_t cap);
 /* How a class's work (as counted by he_profile_read) splits by kind: NTT
- * butterflies, and 64 x 64 -> 128-bit multiply-accumulates summed without
- * reduction (the key products of the fused key switch); the rest is Shoup or
- * Barrett products (basis conversion, scaling, reductions).  Lets a roofline
- * weigh each kind at its own measured rate (he_probe_alu kinds 2, 3, 1).
- * Either output may be NULL. */
-int he_profile_read_kinds(he_ctx* ctx, const char* kernel_class, double* butterflies, double* macs);
+ * butterflies; 64 x 64 -> 128-bit multiply-accumulates summed without
+ * reduction (the key products of the fused key switch on wide primes); and
+ * split key products, each three 32 x 32 -> 64-bit multiply-adds into 64-bit
+ * sums (the key products on primes of up to about 50 bits); the rest is
+ * Shoup or Barrett products (basis conversion, scaling, reductions).  Lets a
+ * roofline weigh each kind at its own measured rate (he_probe_alu kinds 2,
+ * 3, 4, 1).  Any output may be NULL. */
+int he_profile_read_kinds(he_ctx* ctx, const char* kernel_class, double* butterflies, double* macs,
+                          double* split_macs);
 
 #ifdef __cplusplus
 }

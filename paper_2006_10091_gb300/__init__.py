@@ -129,7 +129,8 @@ def load():
         "he_profile_enable": [VP, ctypes.c_int],
         "he_profile_read": [VP, ctypes.c_char_p, VP, VP, VP, VP],
         "he_profile_names": [VP, ctypes.c_char_p, ctypes.c_size_t],
-        "he_profile_read_kinds": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "he_profile_read_kinds": [VP, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)],
         "he_set_tuning": [VP, ctypes.c_char_p, ctypes.c_double],
         "he_lr_train": [VP, VP, ctypes.c_size_t, ctypes.POINTER(he_lr_config), ctypes.c_uint32, ctypes.c_uint32,
                         ctypes.c_uint32, ctypes.c_uint32, CTP],
@@ -738,10 +739,11 @@ def he_profile_read(ctx, kernel_class: str) -> dict:
     ms, work, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(load().he_profile_read(ctx.ptr, kernel_class.encode(), ctypes.byref(n), ctypes.byref(ms),
                                   ctypes.byref(work), ctypes.byref(by)))
-    bfly, mac = ctypes.c_double(), ctypes.c_double()
-    _check(load().he_profile_read_kinds(ctx.ptr, kernel_class.encode(), ctypes.byref(bfly), ctypes.byref(mac)))
+    bfly, mac, mac3 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().he_profile_read_kinds(ctx.ptr, kernel_class.encode(), ctypes.byref(bfly), ctypes.byref(mac),
+                                        ctypes.byref(mac3)))
     return {"launches": n.value, "ms": ms.value, "work": work.value, "bytes": by.value, "mac": mac.value,
-            "bfly": bfly.value}
+            "mac3": mac3.value, "bfly": bfly.value}
 
 
 def he_profile_names(ctx) -> list:

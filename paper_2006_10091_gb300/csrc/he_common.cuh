@@ -134,6 +134,37 @@ __device__ __forceinline__ uint64_t from_signed(int64_t x, const PrimeDev& p) {
 }
 
 // (hi:lo) += a*b, the full 128-bit product (no reduction).
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): each
+// thread's copies are grouped by commit; wait_group n returns when at most n
+// of the thread's groups are still in flight (a barrier then makes every
+// thread's copies visible).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// at most n groups in flight (n >= 7: at most 7, which waits for more than asked)
+__device__ __forceinline__ void cp_async_wait_dyn(uint32_t n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
+
 __device__ __forceinline__ void mac128(uint64_t& lo, uint64_t& hi, uint64_t a, uint64_t b) {
   asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\tmadc.hi.u64 %1, %2, %3, %1;" : "+l"(lo), "+l"(hi) : "l"(a), "l"(b));
 }
@@ -145,6 +176,38 @@ __device__ __forceinline__ uint64_t reduce128_any(uint64_t hi, uint64_t lo, cons
   uint64_t r = mul_shoup_lazy(hi, p.r64, p.r64_sh, q) + reduce64(lo, p);
   r = r >= q + q ? r - q - q : r;
   return r >= q ? r - q : r;
+}
+
+// Sums of products of residues below 2^k, k <= 2 sb, whose sums fit in 64
+// bits (2 sb + 2 + bitlen(terms) <= 64; the fused key switch's key products):
+// every residue is split as x = xh 2^sb + xl, and x w is summed as three
+// 64-bit sums of 32 x 32 -> 64-bit products (Karatsuba):
+//   S_ll = sum xl wl,  S_hh = sum xh wh,  S_s = sum (xl + xh)(wl + wh),
+//   sum x w = S_ll + (S_s - S_ll - S_hh) 2^sb + S_hh 2^(2 sb),
+// formed as one 128-bit value and reduced once per residue.  The same exact
+// sum as the 128-bit multiply-accumulates, so the same residues.
+struct Split3 {
+  uint32_t l, h, s;
+};
+__device__ __forceinline__ Split3 split3(uint64_t x, uint32_t sb, uint32_t mask) {
+  const uint32_t l = (uint32_t)x & mask, h = (uint32_t)(x >> sb);
+  return Split3{l, h, l + h};
+}
+__device__ __forceinline__ void mac_split3(uint64_t& ll, uint64_t& hh, uint64_t& ss, const Split3& x,
+                                           const Split3& w) {
+  ll += (uint64_t)x.l * w.l;
+  hh += (uint64_t)x.h * w.h;
+  ss += (uint64_t)x.s * w.s;
+}
+__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
+                                                  const PrimeDev& pr) {
+  const uint64_t mid = ss - ll - hh;  // sum (xl wh + xh wl), exact
+  uint64_t lo = ll, hi = 0;
+  const uint64_t m_lo = mid << sb, m_hi = mid >> (64 - sb);      // 1 <= sb <= 31
+  const uint64_t h_lo = hh << (2 * sb), h_hi = hh >> (64 - 2 * sb);
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m_lo), "l"(m_hi));
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(h_lo), "l"(h_hi));
+  return reduce128_any(hi, lo, pr);
 }
 
 // 128-bit word (w3:w2:w1:w0) mod q, by Horner on 64-bit halves:

@@ -71,6 +71,7 @@ struct ProfClass {
   uint64_t launches = 0;
   double work = 0.0, bytes = 0.0;
   double mac = 0.0;   // the part of work that is unreduced 128-bit multiply-accumulates
+  double mac3 = 0.0;  // ... that is split products summed as three 64-bit sums (mac_split3)
   double bfly = 0.0;  // the part of work that is NTT butterflies
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
 };
@@ -155,7 +156,8 @@ namespace he {
 // (algorithmic DRAM bytes) to kernel class `name` when timing is enabled.
 class ProfScope {
  public:
-  ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac = 0.0, double bfly = 0.0);
+  ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac = 0.0, double bfly = 0.0,
+            double mac3 = 0.0);
   ~ProfScope();
 
  private:

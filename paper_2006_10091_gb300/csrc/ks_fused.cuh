@@ -43,7 +43,7 @@ struct KsFusedArgs {
   uint64_t off[HE_MAX_PRIMES];
 };
 
-__device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level, uint32_t L) {
+__host__ __device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level, uint32_t L) {
   return t < level ? t : L + t - level;
 }
 
@@ -255,38 +255,6 @@ struct KsRotArgs {
 // last ciphertext in the groups beyond the count and stores nothing for them.
 // Shared memory: the tile's twiddles and every digit's transformed tile of
 // each ciphertext ([CT][beta][TILE + TILE/8] words).
-// Key products of a closed stage on a prime of k <= 2*sb bits whose sums
-// fit in 64 bits (2*sb + 2 + bitlen(nrot*beta) <= 64): every residue (digit and key,
-// canonical, below 2^k) is split as x = xh 2^sb + xl, and x w is summed as three
-// 64-bit sums of 32 x 32 -> 64-bit products (Karatsuba):
-//   S_ll = sum xl wl,  S_hh = sum xh wh,  S_s = sum (xl + xh)(wl + wh),
-//   sum x w = S_ll + (S_s - S_ll - S_hh) 2^sb + S_hh 2^(2 sb),
-// formed as one 128-bit value and reduced once per residue.  The same exact
-// sum as the 128-bit multiply-accumulates, so the same residues.
-struct Split3 {
-  uint32_t l, h, s;
-};
-__device__ __forceinline__ Split3 split3(uint64_t x, uint32_t sb, uint32_t mask) {
-  const uint32_t l = (uint32_t)x & mask, h = (uint32_t)(x >> sb);
-  return Split3{l, h, l + h};
-}
-__device__ __forceinline__ void mac_split3(uint64_t& ll, uint64_t& hh, uint64_t& ss, const Split3& x,
-                                           const Split3& w) {
-  ll += (uint64_t)x.l * w.l;
-  hh += (uint64_t)x.h * w.h;
-  ss += (uint64_t)x.s * w.s;
-}
-__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
-                                                  const PrimeDev& pr) {
-  const uint64_t mid = ss - ll - hh;  // sum (xl wh + xh wl), exact
-  uint64_t lo = ll, hi = 0;
-  const uint64_t m_lo = mid << sb, m_hi = mid >> (64 - sb);      // 1 <= sb <= 31
-  const uint64_t h_lo = hh << (2 * sb), h_hi = hh >> (64 - 2 * sb);
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m_lo), "l"(m_hi));
-  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(h_lo), "l"(h_hi));
-  return reduce128_any(hi, lo, pr);
-}
-
 template <int LOG_N, int LOG_M, int LOG_K, int CT>
 __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_row_rot(KsRotArgs ra) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
@@ -310,8 +278,11 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
   const PrimeDev pr = a.primes[prime];
   const uint64_t q = pr.q;
   const bool lazy = q < (1ull << 58);
-  stage_twiddles<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile, threadIdx.x, CT * S::T);
-  // 1. every digit's tile in evaluation form, canonical residues
+  // 1. every digit's tile in evaluation form, canonical residues: the
+  // twiddles and all digit tiles are copied asynchronously up front (one
+  // group each), so that later tiles arrive while earlier ones transform
+  stage_twiddles_async<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile, threadIdx.x, CT * S::T);
+  cp_async_commit();
   for (uint32_t j = 0; j < a.beta; ++j) {
     uint64_t* sm = dig + ((size_t)grp * a.beta + j) * TW;
     const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
@@ -324,9 +295,15 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = ltid + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
-      sm[idx + (idx >> 3)] = __ldg(src + (in_gal ? automorph_src(e, in_gal, LOG_N) : e));
+      cp_async8(sm + idx + (idx >> 3), src + (in_gal ? automorph_src(e, in_gal, LOG_N) : e));
     }
+    cp_async_commit();
+  }
+  for (uint32_t j = 0; j < a.beta; ++j) {
+    uint64_t* sm = dig + ((size_t)grp * a.beta + j) * TW;
+    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
     if (own) continue;
+    cp_async_wait_dyn(a.beta - 1 - j);  // the twiddles and tiles 0 .. j have arrived
     __syncthreads();
     if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
     else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
@@ -337,14 +314,17 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
       sm[idx + (idx >> 3)] = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
     }
   }
+  cp_async_wait<0>();  // the own limb's tile
   __syncthreads();
   // 2. the products of the permuted digits with each rotation's key, summed
   // as full 128-bit products and reduced once per residue
   const uint32_t row0 = (uint32_t)tile << LOG_K;
+  // key products as split sums (mac_split3) when the prime and the number of
+  // summed terms allow it
   const uint32_t sb = (pr.k + 1) >> 1;
   if (ra.closed && 2 * sb + 2 + (32 - __clz(ra.nrot * a.beta)) <= 64) {
-    // the split sums (mac_split3), one pair of neighbouring positions per
-    // pass, all CT ciphertexts with each key load
+    // one pair of neighbouring positions per pass, all CT ciphertexts with
+    // each key load
     constexpr int PPT = PER / 2 / CT;
     const uint32_t mask = (1u << sb) - 1;
 #pragma unroll 1
@@ -861,19 +841,28 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
   for (uint32_t j = 0; j < a.beta; ++j) own += a.cnt[j];
   const double conv = (double)a.beta * a.nt - own;
   {
-    // work: the converted limbs' row-pass butterflies, one reduction per
-    // accumulator residue, and the key products (128-bit multiply-accumulates);
-    // bytes: the limbs read once, one accumulator written (the rotations'
-    // products are summed into it), each rotation's key read once per launch
-    const double macs = count * 2.0 * ra.nrot * a.beta * a.nt * n;
-    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs,
-                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs,
-                   count * conv * n / 2 * M2);
     KsRotArgs rc = ra;
     rc.count = count;
     rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits
     for (uint32_t r = 0; r < ra.nrot; ++r) rc.closed &= rot_closed<LOG_N, M2, K2 - 1>(ra.gal_inv[r]) ? 1 : 0;
     *closed_out = rc.closed;
+    // work: the converted limbs' row-pass butterflies, one reduction per
+    // accumulator residue, and the key products (split sums on the target
+    // limbs whose primes allow them in a closed stage, as the kernel decides;
+    // 128-bit multiply-accumulates on the others); bytes: the limbs read once,
+    // one accumulator written (the rotations' products are summed into it),
+    // each rotation's key read once per launch
+    const uint32_t terms_bits = 32 - __builtin_clz(ra.nrot * a.beta);
+    double split_limbs = 0;
+    for (uint32_t t = 0; t < a.nt && rc.closed; ++t) {
+      const uint32_t k = 64 - __builtin_clzll(c->q[ks_prime(t, a.level, a.L)]), sb = (k + 1) / 2;
+      if (2 * sb + 2 + terms_bits <= 64) split_limbs += 1;
+    }
+    const double per_limb = count * 2.0 * ra.nrot * a.beta * n;
+    const double macs = per_limb * (a.nt - split_limbs), mac3 = per_limb * split_limbs;
+    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs + mac3,
+                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs,
+                   count * conv * n / 2 * M2, mac3);
     if (!rc.closed)
       HE_CUDA(cudaMemsetAsync(ra.k.acc, 0, sizeof(uint64_t) * count * 2 * a.nt * (1u << LOG_N), c->stream));
     // ciphertexts per CTA (closed stages only): the knob, else 2 when that

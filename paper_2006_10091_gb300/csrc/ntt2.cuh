@@ -122,6 +122,26 @@ __device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2
   }
 }
 
+// The same copies as asynchronous 16-byte copies (cp_async16; the caller
+// commits and waits).
+template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
+__device__ __forceinline__ void stage_twiddles_async(ulonglong2* stw, const ulonglong2* tw, uint32_t tile,
+                                                     uint32_t tid, uint32_t nthreads) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
+  if (COL) {
+    for (uint32_t e = tid; e < (uint32_t)S::M; e += nthreads) cp_async16(stw + e, tw + e);
+  } else {
+    const uint32_t f0 = tile << LOG_K;
+#pragma unroll
+    for (int sig = 0; sig < LOG_M; ++sig) {
+      const uint32_t cnt = (uint32_t)S::K << sig;
+      const uint32_t off = (uint32_t)(S::K * ((1 << sig) - 1));
+      const ulonglong2* g = tw + (1u << (S::S0 + sig)) + (f0 << sig);
+      for (uint32_t e = tid; e < cnt; e += nthreads) cp_async16(stw + off + e, g + e);
+    }
+  }
+}
+
 template <int LOG_N, int LOG_M, int LOG_K, bool COL, int LOG_V = 3>
 __device__ __forceinline__ void stage_twiddles(ulonglong2* stw, const ulonglong2* tw, uint32_t tile) {
   stage_twiddles<LOG_N, LOG_M, LOG_K, COL, LOG_V>(stw, tw, tile, threadIdx.x,

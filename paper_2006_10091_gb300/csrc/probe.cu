@@ -1,7 +1,8 @@
 // probe.cu -- register-resident integer throughput probes behind the integer
 // roof the benchmark reports: chains of 32-bit multiply-adds, chains of 64-bit
 // Shoup products (w known: a*w - umulhi(a, w')*q), radix-8 rounds of the
-// lazy forward butterfly, and 64 x 64 -> 128-bit multiply-accumulates.  No memory traffic inside the timed loops; every
+// lazy forward butterfly, 64 x 64 -> 128-bit multiply-accumulates, and the
+// split (Karatsuba) key products of residues below 2^40.  No memory traffic inside the timed loops; every
 // thread writes one word at the end (the output buffer holds exactly one word
 // per thread).
 #include <cuda_runtime.h>
@@ -88,12 +89,35 @@ __global__ void probe_mac(uint64_t* out, int iters, uint64_t q) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = (lo[0] ^ lo[1] ^ lo[2] ^ lo[3]) + (hi[0] ^ hi[1] ^ hi[2] ^ hi[3]) % q;
 }
 
+// The split key products of the fused key switch on primes below 2^40
+// (mac_split3: three 32 x 32 -> 64-bit multiply-adds into 64-bit sums per
+// product, no carries), laid out like probe_mac: four second operands split
+// once, eight first operands perturbed and split again after every iteration.
+__global__ void probe_mac3(uint64_t* out, int iters, uint64_t q) {
+  constexpr uint32_t sb = 20, mask = (1u << sb) - 1;
+  uint64_t x[8], ll[4] = {0, 0, 0, 0}, hh[4] = {0, 0, 0, 0}, ss[4] = {0, 0, 0, 0};
+  Split3 ys[4];
+  for (int k = 0; k < 8; ++k) x[k] = (0x9E3779B97F4A7C15ull * (threadIdx.x + 8u * k + 1)) % q;
+  for (int k = 0; k < 4; ++k) ys[k] = split3((0xC2B2AE3D27D4EB4Full * (blockIdx.x + 8u * k + 3)) % q, sb, mask);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const Split3 xs = split3(x[u], sb, mask);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mac_split3(ll[k], hh[k], ss[k], xs, ys[k]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (x[u] + (ll[u & 3] & 0xFF)) & ((1ull << 40) - 1);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = (ll[0] ^ hh[1] ^ ss[2] ^ ll[3]) + (hh[0] ^ ss[1] ^ ll[2] ^ ss[3]) % q;
+}
+
 }  // namespace he
 
 using namespace he;
 
 extern "C" int he_probe_alu(int kind, double* per_clock_per_sm, double* per_second) {
-  if (kind < 0 || kind > 3 || !per_clock_per_sm || !per_second) return fail(HE_EINVAL, "he_probe_alu: bad argument");
+  if (kind < 0 || kind > 4 || !per_clock_per_sm || !per_second) return fail(HE_EINVAL, "he_probe_alu: bad argument");
   int dev = 0, sms = 0, khz = 0;
   HE_CUDA(cudaGetDevice(&dev));
   HE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -129,8 +153,11 @@ extern "C" int he_probe_alu(int kind, double* per_clock_per_sm, double* per_seco
     } else if (kind == 2) {
       probe_bfly<<<blocks, threads>>>((uint64_t*)out, 2000, q, tw);
       ops = (double)blocks * threads * 2000 * 12;
-    } else {
+    } else if (kind == 3) {
       probe_mac<<<blocks, threads>>>((uint64_t*)out, 1024, q);
+      ops = (double)blocks * threads * 1024 * 8 * 4;
+    } else {
+      probe_mac3<<<blocks, threads>>>((uint64_t*)out, 1024, q);
       ops = (double)blocks * threads * 1024 * 8 * 4;
     }
     cudaEventRecord(e1);

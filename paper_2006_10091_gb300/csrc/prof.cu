@@ -13,7 +13,8 @@ static thread_local bool tl_prof_suppressed = false;
 ProfSuppress::ProfSuppress() : prev_(tl_prof_suppressed) { tl_prof_suppressed = true; }
 ProfSuppress::~ProfSuppress() { tl_prof_suppressed = prev_; }
 
-ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac, double bfly) : c_(c) {
+ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, double mac, double bfly, double mac3)
+    : c_(c) {
   if (!c->prof_on || tl_prof_suppressed) {
     c_ = nullptr;
     return;
@@ -22,6 +23,7 @@ ProfScope::ProfScope(he_ctx* c, const char* name, double work, double bytes, dou
   k.work += work;
   k.bytes += bytes;
   k.mac += mac;
+  k.mac3 += mac3;
   k.bfly += bfly;
   k.launches += 1;
   cudaEvent_t a, b;
@@ -94,10 +96,12 @@ extern "C" int he_profile_names(he_ctx* c, char* buf, size_t cap) {
   return HE_OK;
 }
 
-extern "C" int he_profile_read_kinds(he_ctx* c, const char* name, double* butterflies, double* macs) {
+extern "C" int he_profile_read_kinds(he_ctx* c, const char* name, double* butterflies, double* macs,
+                                     double* split_macs) {
   if (!c || !name) return fail(HE_EINVAL, "null argument");
   auto it = c->prof.find(name);
   if (butterflies) *butterflies = it == c->prof.end() ? 0.0 : it->second.bfly;
   if (macs) *macs = it == c->prof.end() ? 0.0 : it->second.mac;
+  if (split_macs) *split_macs = it == c->prof.end() ? 0.0 : it->second.mac3;
   return HE_OK;
 }

@@ -745,7 +745,7 @@ def test_rotate_sum_many_digits_unfused(he):
 def test_alu_probes_run(he):
     """The throughput probes behind the integer roof return positive rates in
     the expected order (a Shoup product costs several multiply-adds)."""
-    r = [he.he_probe_alu(k) for k in range(3)]
+    r = [he.he_probe_alu(k) for k in range(5)]
     assert all(x["per_second"] > 0 and x["per_clock_per_sm"] > 0 for x in r)
     assert r[0]["per_clock_per_sm"] > 4 * r[1]["per_clock_per_sm"]
     with pytest.raises(he.HeError):
