@@ -199,14 +199,21 @@ __device__ __forceinline__ void mac_split3(uint64_t& ll, uint64_t& hh, uint64_t&
   hh += (uint64_t)x.h * w.h;
   ss += (uint64_t)x.s * w.s;
 }
-__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
-                                                  const PrimeDev& pr) {
+// The sum as a 128-bit value (hi:lo).
+__device__ __forceinline__ void split3_total(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb, uint64_t& lo,
+                                             uint64_t& hi) {
   const uint64_t mid = ss - ll - hh;  // sum (xl wh + xh wl), exact
-  uint64_t lo = ll, hi = 0;
-  const uint64_t m_lo = mid << sb, m_hi = mid >> (64 - sb);      // 1 <= sb <= 31
+  lo = ll;
+  hi = 0;
+  const uint64_t m_lo = mid << sb, m_hi = mid >> (64 - sb);  // 1 <= sb <= 31
   const uint64_t h_lo = hh << (2 * sb), h_hi = hh >> (64 - 2 * sb);
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m_lo), "l"(m_hi));
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(h_lo), "l"(h_hi));
+}
+__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
+                                                  const PrimeDev& pr) {
+  uint64_t lo, hi;
+  split3_total(ll, hh, ss, sb, lo, hi);
   return reduce128_any(hi, lo, pr);
 }
 

@@ -69,14 +69,17 @@ bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot) {
 // of rs.n residues (the rotations moved rows between CTAs).
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
            const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced,
-           uint64_t in_gal) {
+           uint64_t in_gal, const uint64_t* c0, uint64_t c0_stride, bool* c0_added) {
   *handled = false;
   *unreduced = false;
+  if (c0_added) *c0_added = false;
   if (!ks_rot_fits(c, level, rs.n)) return HE_OK;
   KsRotArgs ra;
   ra.k = ks_args(c, d, d_stride, d2c, ext, acc, nullptr, level, in_gal, half);
   ra.nrot = rs.n;
   ra.count = count;
+  ra.c0 = c0;
+  ra.c0_stride = c0_stride;
   // the summed path adds nrot * beta products below q^2 in 128 bits (the
   // other path beta of them)
   uint32_t bits = 0;
@@ -97,7 +100,8 @@ int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c,
     case 15: rc = ks_rot_n15(c, ra, count, handled, &closed); break;
     default: rc = ks_rot_n16(c, ra, count, handled, &closed); break;
   }
-  *unreduced = *handled && !closed;
+  *unreduced = *handled && !(closed & 1);
+  if (c0_added) *c0_added = *handled && (closed & 2);
   return rc;
 }
 

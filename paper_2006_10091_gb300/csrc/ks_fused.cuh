@@ -242,6 +242,13 @@ struct KsRotArgs {
   int closed;              // every rotation maps each tile's rows onto themselves
   uint64_t gal[HE_MAX_ROT], gal_inv[HE_MAX_ROT];
   const uint64_t* evk[HE_MAX_ROT];
+  // part 0 of the input (evaluation form, count x [level][N] at c0_stride):
+  // when set, part 0 of the accumulator's limbs q_t also receives
+  // (P mod q_t) * sum_r kappa_r(c0), which the ModDown turns into
+  // sum_r kappa_r(c0) exactly (nullptr: not added; closed stages whose
+  // target limbs q_t all take the split sums only)
+  const uint64_t* c0;
+  uint64_t c0_stride;
 };
 
 // Grid: nt * ceil(count / CT) * TILES, target limb slowest and row tile
@@ -278,9 +285,13 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
   const PrimeDev pr = a.primes[prime];
   const uint64_t q = pr.q;
   const bool lazy = q < (1ull << 58);
+  // the input's part 0, added through each rotation on the limbs q_t
+  const bool add_c0 = ra.c0 && t < a.level;
+  uint64_t* c0s = dig + (size_t)CT * a.beta * TW;  // its tiles, [CT][TW] after every digit tile
   // 1. every digit's tile in evaluation form, canonical residues: the
   // twiddles and all digit tiles are copied asynchronously up front (one
-  // group each), so that later tiles arrive while earlier ones transform
+  // group each, part 0's tile with the last), so that later tiles arrive
+  // while earlier ones transform
   stage_twiddles_async<LOG_N, LOG_M, LOG_K, false>(stw, a.tw + (size_t)prime * N, tile, threadIdx.x, CT * S::T);
   cp_async_commit();
   for (uint32_t j = 0; j < a.beta; ++j) {
@@ -296,6 +307,14 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
       const uint32_t idx = ltid + u * S::T;
       const uint32_t e = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       cp_async8(sm + idx + (idx >> 3), src + (in_gal ? automorph_src(e, in_gal, LOG_N) : e));
+    }
+    if (add_c0 && j + 1 == a.beta) {
+      const uint64_t* s0 = ra.c0 + (size_t)i * ra.c0_stride + (size_t)t * N;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const uint32_t idx = ltid + u * S::T;
+        cp_async8(c0s + (size_t)grp * TW + idx + (idx >> 3), s0 + S::gidx(tile, idx >> LOG_M, idx & (S::M - 1)));
+      }
     }
     cp_async_commit();
   }
@@ -327,17 +346,23 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
     // each key load
     constexpr int PPT = PER / 2 / CT;
     const uint32_t mask = (1u << sb) - 1;
+    uint64_t pm = 1;  // P mod q_t
+    if (add_c0)
+      for (uint32_t u = 0; u < a.alpha; ++u) pm = mul_mod(pm, reduce64(a.primes[a.L + u].q, pr), pr);
 #pragma unroll 1
     for (int v0 = 0; v0 < PPT; ++v0) {
       const uint32_t idx = 2 * (threadIdx.x + v0 * CT * S::T);
       const uint32_t eo = S::gidx(tile, idx >> LOG_M, idx & (S::M - 1));
       uint64_t ll[CT][2][2], hh[CT][2][2], ss[CT][2][2];  // [ciphertext][part][position]
+      uint64_t s0[CT][2];                                  // sum_r kappa_r(c0) (below nrot q)
 #pragma unroll
-      for (int c = 0; c < CT; ++c)
+      for (int c = 0; c < CT; ++c) {
+        s0[c][0] = s0[c][1] = 0;
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
           for (int u = 0; u < 2; ++u) ll[c][p][u] = hh[c][p][u] = ss[c][p][u] = 0;
+      }
       for (uint32_t r = 0; r < ra.nrot; ++r) {
         uint32_t so[2];
 #pragma unroll
@@ -346,6 +371,12 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
           const uint32_t sl = (((p >> LOG_M) - row0) << LOG_M) | (p & (S::M - 1));
           so[u] = sl + (sl >> 3);
         }
+        if (add_c0)
+#pragma unroll
+          for (int c = 0; c < CT; ++c) {
+            s0[c][0] += c0s[(size_t)c * TW + so[0]];
+            s0[c][1] += c0s[(size_t)c * TW + so[1]];
+          }
         const uint64_t* ev = ra.evk[r];
 #pragma unroll 2
         for (uint32_t j = 0; j < a.beta; ++j) {
@@ -371,10 +402,17 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
         if (i0 + c >= ra.count) break;
         uint64_t* o0 = a.acc + ((size_t)(i0 + c) * 2 * a.nt + t) * N;
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
-          *reinterpret_cast<ulonglong2*>(o0 + (size_t)p * a.nt * N + eo) =
-              make_ulonglong2(reduce_split3(ll[c][p][0], hh[c][p][0], ss[c][p][0], sb, pr),
-                              reduce_split3(ll[c][p][1], hh[c][p][1], ss[c][p][1], sb, pr));
+        for (int p = 0; p < 2; ++p) {
+          uint64_t r2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            uint64_t lo, hi;
+            split3_total(ll[c][p][u], hh[c][p][u], ss[c][p][u], sb, lo, hi);
+            if (p == 0 && add_c0) mac128(lo, hi, s0[c][u], pm);
+            r2[u] = reduce128_any(hi, lo, pr);
+          }
+          *reinterpret_cast<ulonglong2*>(o0 + (size_t)p * a.nt * N + eo) = make_ulonglong2(r2[0], r2[1]);
+        }
       }
     }
     return;
@@ -793,11 +831,12 @@ int ks_modup_launch(he_ctx* c, const KsFusedArgs& a, uint32_t count) {
 }
 
 // Dynamic shared memory of ks_row_rot (row tiles of half the row pass's
-// tile: M2 x 2^(K2-1)) for beta digits of ct ciphertexts.
+// tile: M2 x 2^(K2-1)) for beta digits of ct ciphertexts (and their part 0's
+// tiles when c0).
 template <int LOG_N, int M2, int K2>
-size_t ks_rot_smem(uint32_t beta, uint32_t ct = 1) {
+size_t ks_rot_smem(uint32_t beta, uint32_t ct = 1, bool c0 = false) {
   using SR = Shape<LOG_N, M2, K2 - 1, false>;
-  return sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8) * beta * ct;
+  return sizeof(ulonglong2) * SR::NTW + sizeof(uint64_t) * (SR::TILE + SR::TILE / 8) * (beta + (c0 ? 1 : 0)) * ct;
 }
 
 
@@ -845,7 +884,6 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     rc.count = count;
     rc.closed = ra.closed;  // 0 when the summed products could exceed 128 bits
     for (uint32_t r = 0; r < ra.nrot; ++r) rc.closed &= rot_closed<LOG_N, M2, K2 - 1>(ra.gal_inv[r]) ? 1 : 0;
-    *closed_out = rc.closed;
     // work: the converted limbs' row-pass butterflies, one reduction per
     // accumulator residue, and the key products (split sums on the target
     // limbs whose primes allow them in a closed stage, as the kernel decides;
@@ -853,16 +891,28 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     // one accumulator written (the rotations' products are summed into it),
     // each rotation's key read once per launch
     const uint32_t terms_bits = 32 - __builtin_clz(ra.nrot * a.beta);
-    double split_limbs = 0;
+    double split_limbs = 0, split_q = 0;
     for (uint32_t t = 0; t < a.nt && rc.closed; ++t) {
       const uint32_t k = 64 - __builtin_clzll(c->q[ks_prime(t, a.level, a.L)]), sb = (k + 1) / 2;
-      if (2 * sb + 2 + terms_bits <= 64) split_limbs += 1;
+      if (2 * sb + 2 + terms_bits <= 64) {
+        split_limbs += 1;
+        split_q += t < a.level ? 1 : 0;
+      }
     }
+    // part 0 through the rotations: in closed stages whose limbs q_t all take
+    // the split sums, when its tile fits beside the digits'
+    if (!rc.closed || split_q < a.level || ks_rot_smem<LOG_N, M2, K2>(a.beta, 1, true) > kRotSmemMax)
+      rc.c0 = nullptr;
+    const bool c0 = rc.c0 != nullptr;
+    *closed_out = rc.closed | (c0 ? 2 : 0);
     const double per_limb = count * 2.0 * ra.nrot * a.beta * n;
     const double macs = per_limb * (a.nt - split_limbs), mac3 = per_limb * split_limbs;
-    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs + mac3,
-                   count * n * 8 * (conv + own + 2.0 * a.nt) + 8.0 * n * ra.nrot * a.beta * 2.0 * a.nt, macs,
-                   count * conv * n / 2 * M2, mac3);
+    // (with part 0: nrot additions and one 128-bit product per residue of its limbs, and those limbs read)
+    const double c0_work = c0 ? count * (double)a.level * n : 0.0;
+    ProfScope prof(c, "ks_ntt_rot_products", count * (conv * n / 2 * M2 + 2.0 * a.nt * n) + macs + mac3 + c0_work,
+                   count * n * 8 * (conv + own + 2.0 * a.nt + (c0 ? a.level : 0)) +
+                       8.0 * n * ra.nrot * a.beta * 2.0 * a.nt,
+                   macs + c0_work, count * conv * n / 2 * M2, mac3);
     if (!rc.closed)
       HE_CUDA(cudaMemsetAsync(ra.k.acc, 0, sizeof(uint64_t) * count * 2 * a.nt * (1u << LOG_N), c->stream));
     // ciphertexts per CTA (closed stages only): the knob, else 2 when that
@@ -873,18 +923,18 @@ int ks_rot_run(he_ctx* c, const KsRotArgs& ra, uint32_t count, bool* handled, in
     uint32_t ct = 1;
     if (rc.closed) {
       auto warps = [&](uint32_t k) {  // resident warps per SM with k ciphertexts per CTA
-        const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, k) + 1024;  // + the runtime's reserve per CTA
+        const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, k, c0) + 1024;  // + the runtime's reserve per CTA
         const size_t by_smem = c->smem_per_sm / sm, by_regs = 4 / k;
         return std::min(by_smem, by_regs) * k * (size_t)SR::T / 32;
       };
       const uint32_t want = c->ks_ct ? (uint32_t)c->ks_ct : 2u;
       for (uint32_t cand : {4u, 2u})
-        if (ct == 1 && cand <= want && cand <= count && ks_rot_smem<LOG_N, M2, K2>(a.beta, cand) <= kRotSmemMax &&
+        if (ct == 1 && cand <= want && cand <= count && ks_rot_smem<LOG_N, M2, K2>(a.beta, cand, c0) <= kRotSmemMax &&
             (c->ks_ct || warps(cand) >= warps(1)))
           ct = cand;
     }
     const size_t blocks = (size_t)a.nt * ((count + ct - 1) / ct) * SR::TILES;
-    const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, ct);
+    const size_t sm = ks_rot_smem<LOG_N, M2, K2>(a.beta, ct, c0);
     if (ct == 4) ks_row_rot<LOG_N, M2, K2 - 1, 4><<<(unsigned)blocks, 4 * SR::T, sm, c->stream>>>(rc);
     else if (ct == 2) ks_row_rot<LOG_N, M2, K2 - 1, 2><<<(unsigned)blocks, 2 * SR::T, sm, c->stream>>>(rc);
     else ks_row_rot<LOG_N, M2, K2 - 1, 1><<<(unsigned)blocks, SR::T, sm, c->stream>>>(rc);

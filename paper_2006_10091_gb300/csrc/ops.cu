@@ -27,7 +27,7 @@ int rs_fused(he_ctx* c, CtBatch in, const uint64_t* last, uint64_t* conv, CtBatc
 bool ks_rot_fits(const he_ctx* c, uint32_t level, uint32_t nrot);
 int ks_rot(he_ctx* c, const uint64_t* d, uint64_t d_stride, const uint64_t* d2c, uint64_t* ext, uint64_t* acc,
            const RotSet& rs, uint32_t level, uint32_t count, bool half, bool* handled, bool* unreduced,
-           uint64_t in_gal = 0);
+           uint64_t in_gal = 0, const uint64_t* c0 = nullptr, uint64_t c0_stride = 0, bool* c0_added = nullptr);
 int md_fused_gals(he_ctx* c, const uint64_t* acc, uint64_t acc_stride, uint64_t* conv, CtBatch add, int add_mode,
                   const uint64_t* gals, uint32_t n_gal, CtBatch out, uint32_t level, uint32_t count, bool half,
                   bool* handled);
@@ -360,8 +360,12 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     const PolyBatch b = pb(d, d2c, A.stride, (size_t)level * n, count, level, 0, level);
     HE_TRY(half ? ntt2_inverse_rows(c, b) : ntt_inverse(c, b));
   }
-  bool fused = false, unreduced = false;
-  if (fits) HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rs, level, count, half, &fused, &unreduced));
+  // the fused kernel also adds P sum_r kappa_r(A0) to the accumulator where it
+  // can (c0_added): the ModDown then adds A0 and A1 as they are
+  bool fused = false, unreduced = false, c0_added = false;
+  if (fits)
+    HE_TRY(ks_rot(c, d, A.stride, d2c, ext, acc, rs, level, count, half, &fused, &unreduced, 0, A.base, A.stride,
+                  &c0_added));
   if (!fused) {
     if (half) return fail(HE_ECUDA, "rotate-and-sum: fused kernels declined a half-transformed input");
     HE_TRY(modup_unfused(c, d2c, ext, level, count));
@@ -388,8 +392,10 @@ int rotsum_batch(he_ctx* c, CtBatch A, uint32_t level, uint32_t count, const uin
     HE_TRY(mh ? ntt2_inverse_rows(c, bd) : ntt_inverse(c, bd));
   }
   bool md_done = false;
-  HE_TRY(md_fused_gals(c, acc, acc_stride, conv, A, 3, gals, nrot, out, level, count, mh, &md_done));
+  HE_TRY(md_fused_gals(c, acc, acc_stride, conv, A, c0_added ? 2 : 3, gals, c0_added ? 0 : nrot, out, level, count,
+                       mh, &md_done));
   if (md_done) return HE_OK;
+  if (c0_added) return moddown_unfused(c, acc, conv, A, 2, out, level, count);
   uint64_t* sa = ar.take<uint64_t>((size_t)count * 2 * level * n);
   if (!sa) return fail(HE_ENOMEM, "rotate-and-sum scratch too small");
   const CtBatch S{sa, (uint64_t)2 * level * n, level, 0};
