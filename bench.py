@@ -181,6 +181,19 @@ ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_rot_products", "moddown_nt
 KS_ROT_TRAFFIC_PER_ALG_BYTE = 555.8 / 577.8
 
 
+def roof_time(p: dict, hbm_peak: float, name: str | None = None) -> float:
+    """Seconds the class's work takes at its roof: max(weighted integer-pipe
+    time, HBM time) for the integer classes (the transform and key-switching
+    kernels and the tensor product's products), the HBM time for the rest."""
+    work, mac, bfly, by = p["work"], p.get("mac", 0.0), p.get("bfly", 0.0), p["bytes"]
+    mac3 = p.get("mac3", 0.0)
+    r_bfly = ALU_PEAK["butterfly_per_second"] or ALU_PEAK["per_second"]
+    other = max(work - mac - mac3 - bfly, 0.0)
+    t_alu = (bfly / r_bfly + other / ALU_PEAK["per_second"] + mac / ALU_PEAK["mac_per_second"]
+             + mac3 / ALU_PEAK["mac3_per_second"])
+    return max(t_alu, by / (hbm_peak * 1e9))
+
+
 def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: bool | None = None) -> dict:
     """Roofline of one kernel class (or of several summed): the launch time
     against max(integer-pipe time, HBM time).  The integer-pipe time weighs
@@ -527,8 +540,19 @@ def large_rooflines(he, torch, stream, ctx, A, B, O, T):
     for key, fn in (("keyswitch_rotation", lambda: he.he_rotate_batch(ctx, A, 1, O)),
                     ("mul_relin_rescale", lambda: he.he_mul_relin_rescale_batch(ctx, A, B, O))):
         prof = profiled(fn)
+        keys = [k for k in ks_classes if k in prof]
         out[key] = class_roof(summed(prof, ks_classes), hbm_peak, peak_kind, key, integer=True)
-        out[key]["classes"] = [k for k in ks_classes if k in prof]
+        out[key]["classes"] = keys
+        # the operation's roof as the sum over its kernels of each one's own
+        # roof time (integer pipe, weighted, or HBM, whichever is longer: the
+        # tensor product is bound by HBM); `frac` above counts all their work
+        # as integer work, which undercounts an HBM-bound kernel's roof
+        t_roof = sum(roof_time(prof[k], hbm_peak) for k in keys)
+        t_all = sum(prof[k]["ms"] for k in keys) * 1e-3
+        out[key]["frac_all_integer"] = out[key]["frac"]
+        out[key]["frac"] = t_roof / t_all if t_all > 0 else 0.0
+        out[key]["frac_note"] = ("sum over the kernel classes of max(weighted integer-pipe time, HBM time) "
+                                 "over their measured time; frac_all_integer: all work as integer work")
         if key == "keyswitch_rotation":
             out["ks_ntt_rot_products"] = class_roof(prof["ks_ntt_rot_products"], hbm_peak, peak_kind,
                                                     "ks_ntt_rot_products")
