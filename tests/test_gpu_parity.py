@@ -685,7 +685,7 @@ def test_rotate_sum_batch_and_errors(hoist, he):
 
 
 @pytest.fixture(scope="module")
-def wide():
+def wide58():
     # N = 2^12, four 58-bit limbs, one 61-bit special prime
     return Pair(12, 4, 58, 1, 61, 2.0 ** 40, seed=31, rots=[2, 4, 6, 8, 10, 12])
 
@@ -699,7 +699,7 @@ def split_sums(bits: int, nrot: int, beta: int) -> bool:
 
 @pytest.mark.parametrize("level,steps,limb_split", [(4, [2, 4, 6, 8, 10, 12], False), (3, [2, 4, 6, 8], True),
                                                     (2, [2, 4], True)])
-def test_rotate_sum_wide_primes_bit_exact(wide, he, level, steps, limb_split):
+def test_rotate_sum_wide_primes_bit_exact(wide58, he, level, steps, limb_split):
     """Closed hoisted stages on 58-bit limbs and a 61-bit special prime, on
     uniform residues and on residues all q - 1: with 24 key products per
     residue the limbs' sums are 128-bit multiply-accumulates and part 0 goes
@@ -709,21 +709,21 @@ def test_rotate_sum_wide_primes_bit_exact(wide, he, level, steps, limb_split):
     sums; with 4, both.  Every tile shape, equal to the oracle."""
     beta = level  # one special prime: digits of one limb
     assert split_sums(58, len(steps), beta) == limb_split and not split_sums(61, len(steps), beta)
-    assert all(q.bit_length() == 58 for q in wide.o.primes[:4]) and wide.o.primes[4].bit_length() == 61
+    assert all(q.bit_length() == 58 for q in wide58.o.primes[:4]) and wide58.o.primes[4].bit_length() == 61
     for fill in (False, True):
-        data = workloads.residues(3100 + level, wide.o.primes[:level], wide.n, parts=2)
+        data = workloads.residues(3100 + level, wide58.o.primes[:level], wide58.n, parts=2)
         if fill:
             for k in range(level):
-                data[:, k, :] = wide.o.primes[k] - 1
-        oa = oracle.Ciphertext(data, level, wide.o.scale)
-        want = wide.o.rotate_sum(oa, steps)
-        ga = wide.gpu_ct(oa)
+                data[:, k, :] = wide58.o.primes[k] - 1
+        oa = oracle.Ciphertext(data, level, wide58.o.scale)
+        want = wide58.o.rotate_sum(oa, steps)
+        ga = wide58.gpu_ct(oa)
         for shape in (0, 1, 2):
-            he.he_set_tuning(wide.g, "ntt_shape", shape)
-            out = wide.g.new_ct(level)
-            he.he_rotate_sum(wide.g, ga, steps, out)
-            assert_same_residues(out, want, he, wide.g)
-    he.he_set_tuning(wide.g, "ntt_shape", 0)
+            he.he_set_tuning(wide58.g, "ntt_shape", shape)
+            out = wide58.g.new_ct(level)
+            he.he_rotate_sum(wide58.g, ga, steps, out)
+            assert_same_residues(out, want, he, wide58.g)
+    he.he_set_tuning(wide58.g, "ntt_shape", 0)
 
 
 @pytest.mark.parametrize("ks_ct", [1, 2, 4])
