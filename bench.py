@@ -233,8 +233,8 @@ def class_roof(p: dict, hbm_peak: float, peak_kind: str, name: str, integer: boo
                                        f"({ALU_PEAK['mac_per_second'] / 1e9:.0f} G/s), {mac3:.3g} split key "
                                        f"products at {ALU_PEAK['mac3_note']} "
                                        f"({ALU_PEAK['mac3_per_second'] / 1e9:.0f} G/s)")})
-            if name in ("ntt", "intt"):
-                base["butterfly_chain_frac"] = rate / r_bfly
+            if name in ("ntt", "intt"):  # butterflies alone against their chain
+                base["butterfly_chain_frac"] = (bfly / t) / r_bfly if t > 0 else 0.0
             return base
     base.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                  "peak_note": f"{peak_kind} HBM copy bandwidth"})

@@ -226,7 +226,9 @@ static int launch_pass(he_ctx* c, const PolyBatch& b, bool inv, bool col, int lo
     }
   }
   const double nn = (double)(1u << c->log_n);
-  ProfScope prof(c, inv ? "intt" : "ntt", transforms * nn / 2 * log_m, transforms * nn * 16, 0.0,
+  // work: the butterflies, and the inverse's scaling by N^-1 in its last pass
+  const double scale = inv && last ? transforms * nn : 0.0;
+  ProfScope prof(c, inv ? "intt" : "ntt", transforms * nn / 2 * log_m + scale, transforms * nn * 16, 0.0,
                  transforms * nn / 2 * log_m);
   if (inv) {
     if (col) ntt_pass_kernel<true, true><<<(unsigned)blocks, threads, smem, c->stream>>>(a);

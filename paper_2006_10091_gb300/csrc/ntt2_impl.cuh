@@ -141,7 +141,9 @@ int launch2(he_ctx* c, const PolyBatch& b, const uint64_t* src, uint64_t* dst, u
     }
   }
   const double nn = (double)(1u << LOG_N);
-  ProfScope prof(c, INV ? "intt" : "ntt", transforms * nn / 2 * LOG_M, transforms * nn * 16, 0.0,
+  // work: the butterflies, and the inverse's scaling by N^-1 in its last pass
+  const double scale = INV && last ? transforms * nn : 0.0;
+  ProfScope prof(c, INV ? "intt" : "ntt", transforms * nn / 2 * LOG_M + scale, transforms * nn * 16, 0.0,
                  transforms * nn / 2 * LOG_M);
   ntt2_kernel<INV, LOG_N, LOG_M, LOG_K, COL, LOG_V><<<(unsigned)blocks, S::T, smem, c->stream>>>(a);
   HE_CUDA(cudaGetLastError());
