@@ -11,7 +11,9 @@
 //    every digit's tile (or, on the digit's own limb, reads the input as it
 //    is), keeps the tiles in shared memory and adds their products with the
 //    key polynomials of each rotation (a plain key switch is one rotation by
-//    the identity); the transformed digits are never written.
+//    the identity); the transformed digits are never written.  The products
+//    are summed as split sums of 32 x 32 -> 64-bit products on primes that
+//    allow it (mac_split3) and as 128-bit multiply-accumulates otherwise.
 #pragma once
 #include <algorithm>
 #include <atomic>
@@ -257,11 +259,12 @@ struct KsRotArgs {
 // A CTA holds CT ciphertexts of one limb and tile: group g of T threads runs
 // the row passes of ciphertext i0 + g, and in a closed stage every thread
 // then sums the products for its positions of all CT ciphertexts, so each
-// key word it loads serves CT ciphertexts (8/CT bytes of key per 128-bit
-// multiply-accumulate).  CT > 1 only for closed stages; a tail CTA repeats its
-// last ciphertext in the groups beyond the count and stores nothing for them.
-// Shared memory: the tile's twiddles and every digit's transformed tile of
-// each ciphertext ([CT][beta][TILE + TILE/8] words).
+// key word it loads serves CT ciphertexts (8/CT bytes of key per key
+// product).  CT > 1 only for closed stages; a tail CTA repeats its last
+// ciphertext in the groups beyond the count and stores nothing for them.
+// Shared memory: the tile's twiddles, every digit's transformed tile of each
+// ciphertext ([CT][beta][TILE + TILE/8] words) and, with ra.c0, each
+// ciphertext's part-0 tile ([CT][TILE + TILE/8]).
 template <int LOG_N, int LOG_M, int LOG_K, int CT>
 __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_row_rot(KsRotArgs ra) {
   using S = Shape<LOG_N, LOG_M, LOG_K, false>;
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
   cp_async_wait<0>();  // the own limb's tile
   __syncthreads();
   // 2. the products of the permuted digits with each rotation's key, summed
-  // as full 128-bit products and reduced once per residue
+  // exactly (split sums or 128-bit sums) and reduced once per residue
   const uint32_t row0 = (uint32_t)tile << LOG_K;
   // key products as split sums (mac_split3) when the prime and the number of
   // summed terms allow it
