@@ -321,20 +321,40 @@ __global__ void __launch_bounds__(CT * ((1 << (LOG_M + LOG_K)) / 8), 4 / CT) ks_
     }
     cp_async_commit();
   }
-  for (uint32_t j = 0; j < a.beta; ++j) {
-    uint64_t* sm = dig + ((size_t)grp * a.beta + j) * TW;
-    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
-    if (own) continue;
-    cp_async_wait_dyn(a.beta - 1 - j);  // the twiddles and tiles 0 .. j have arrived
-    __syncthreads();
-    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
-    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
+  // the converted digits' row passes, two tiles at a time (one barrier per
+  // round for both, each twiddle loaded once for both)
+  auto finish_tile = [&](uint64_t* sm) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const uint32_t idx = ltid + u * S::T;
       const uint64_t v = sm[idx + (idx >> 3)];
       sm[idx + (idx >> 3)] = lazy ? fwd_final<true>(v, pr) : fwd_final<false>(v, pr);
     }
+  };
+  int pend = -1;  // a converted digit waiting for a partner
+  for (uint32_t j = 0; j < a.beta; ++j) {
+    const bool own = t >= a.lo[j] && t < a.lo[j] + a.cnt[j];
+    if (own) continue;
+    if (pend < 0) {
+      pend = (int)j;
+      continue;
+    }
+    cp_async_wait_dyn(a.beta - 1 - j);  // the twiddles and tiles 0 .. j have arrived
+    __syncthreads();
+    uint64_t* sms[2] = {dig + ((size_t)grp * a.beta + (uint32_t)pend) * TW, dig + ((size_t)grp * a.beta + j) * TW};
+    if (lazy) run_rounds_n<false, true, LOG_N, LOG_M, LOG_K, false, 2>(sms, stw, q, ltid);
+    else run_rounds_n<false, false, LOG_N, LOG_M, LOG_K, false, 2>(sms, stw, q, ltid);
+    finish_tile(sms[0]);
+    finish_tile(sms[1]);
+    pend = -1;
+  }
+  if (pend >= 0) {
+    uint64_t* sm = dig + ((size_t)grp * a.beta + (uint32_t)pend) * TW;
+    cp_async_wait_dyn(a.beta - 1 - (uint32_t)pend);
+    __syncthreads();
+    if (lazy) run_rounds<false, true, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
+    else run_rounds<false, false, LOG_N, LOG_M, LOG_K, false>(sm, stw, q, ltid);
+    finish_tile(sm);
   }
   cp_async_wait<0>();  // the own limb's tile
   __syncthreads();

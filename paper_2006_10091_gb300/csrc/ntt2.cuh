@@ -100,6 +100,93 @@ __device__ __forceinline__ void round2(uint64_t* sm, const ulonglong2* stw, int 
   }
 }
 
+// The same round on NT tiles of the same prime and positions at once (each
+// twiddle loaded once for all of them; NT independent groups in registers).
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int R, int NT, int LOG_V = 3>
+__device__ __forceinline__ void round2_n(uint64_t* const* sms, const ulonglong2* stw, int sig0, uint64_t q,
+                                         uint32_t tid) {
+  using S = Shape<LOG_N, LOG_M, LOG_K, COL, LOG_V>;
+  constexpr int G = 1 << R, GPT = (1 << LOG_V) >> R;
+  const uint64_t q2 = q + q;
+  const int lo_bits = LOG_M - sig0 - R;
+  const uint32_t lo_mask = (1u << lo_bits) - 1;
+  const uint32_t s = COL ? (1u << (lo_bits + LOG_K)) : (1u << lo_bits);
+#pragma unroll
+  for (int u = 0; u < GPT; ++u) {
+    const uint32_t g = tid + u * S::T;
+    uint32_t k, xhi, xlo;
+    if (COL) {
+      k = g & (S::K - 1);
+      const uint32_t r = g >> LOG_K;
+      xlo = r & lo_mask;
+      xhi = r >> lo_bits;
+    } else {
+      xlo = g & lo_mask;
+      const uint32_t r = g >> lo_bits;
+      xhi = r & ((1u << sig0) - 1);
+      k = r >> sig0;
+    }
+    const uint32_t s0 = S::sidx(k, (xhi << (LOG_M - sig0)) | xlo);
+    uint64_t v[NT][G];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int j = 0; j < G; ++j) v[t][j] = sms[t][s0 + j * s + ((j * s) >> 3)];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int st = INV ? R - 1 - i : i;
+      const int sg = sig0 + st, half = G >> (st + 1);
+      const uint32_t tb = COL ? ((1u << sg) | (xhi << st))
+                              : (uint32_t)(S::K * ((1 << sg) - 1)) + (k << sg) + (xhi << st);
+#pragma unroll
+      for (int b = 0; b < (1 << st); ++b) {
+        const ulonglong2 w = stw[tb + b];
+#pragma unroll
+        for (int jj = 0; jj < half; ++jj) {
+          const int j = (b << (R - st)) + jj;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (!INV) {
+              uint64_t X = v[t][j];
+              if (!LAZY) X = X >= q2 ? X - q2 : X;
+              const uint64_t tt = mul_shoup_lazy(v[t][j + half], w.x, w.y, q);
+              v[t][j] = X + tt;
+              v[t][j + half] = X + q2 - tt;
+            } else {
+              const uint64_t X = v[t][j], Y = v[t][j + half];
+              uint64_t sum = X + Y;
+              sum = sum >= q2 ? sum - q2 : sum;
+              v[t][j + half] = mul_shoup_lazy(X + q2 - Y, w.x, w.y, q);
+              v[t][j] = sum;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int j = 0; j < G; ++j) sms[t][s0 + j * s + ((j * s) >> 3)] = v[t][j];
+  }
+}
+
+// All rounds of one pass on NT tiles at once (ends with a barrier).
+template <bool INV, bool LAZY, int LOG_N, int LOG_M, int LOG_K, bool COL, int NT, int LOG_V = 3>
+__device__ __forceinline__ void run_rounds_n(uint64_t* const* sms, const ulonglong2* stw, uint64_t q, uint32_t tid) {
+  constexpr int NR = (LOG_M + LOG_V - 1) / LOG_V;
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) {
+    const int r = INV ? NR - 1 - rr : rr;
+    const int sig0 = LOG_V * r;
+    const int R = LOG_M - sig0 < LOG_V ? LOG_M - sig0 : LOG_V;
+    if (R == 4) round2_n<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, (LOG_V >= 4 ? 4 : 1), NT, LOG_V>(sms, stw, sig0, q, tid);
+    else if (R == 3) round2_n<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 3, NT, LOG_V>(sms, stw, sig0, q, tid);
+    else if (R == 2) round2_n<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 2, NT, LOG_V>(sms, stw, sig0, q, tid);
+    else round2_n<INV, LAZY, LOG_N, LOG_M, LOG_K, COL, 1, NT, LOG_V>(sms, stw, sig0, q, tid);
+    __syncthreads();
+  }
+}
+
 // Stage the twiddle pairs of one pass into shared memory: a column pass
 // needs tw[0 .. M), a row pass for rows f0 .. f0+K-1 needs, per local stage
 // sigma, the K*2^sigma entries from 2^(S0+sigma) + f0*2^sigma on.
