@@ -173,12 +173,12 @@ def measure_alu_peak(he) -> None:
 ALU_CLASSES = ("ntt", "intt", "ks_modup_ntt", "ks_ntt_rot_products", "moddown_ntt", "moddown_ntt_combine",
                "moddown_rescale_ntt", "moddown_rescale_ntt_combine", "rescale_ntt", "rescale_ntt_final")
 # DRAM bytes per algorithmic byte of the hoisted stage's row kernel, from an
-# ncu capture of one 7-rotation stage over 64 ciphertexts at level 7: 555.8 MB
+# ncu capture of one 7-rotation stage over 64 ciphertexts at level 7: 555.7 MB
 # of DRAM traffic against 577.8 MB of algorithmic bytes (511.7 MB of
 # ciphertext limbs read -- digits and part 0 -- and accumulators written,
 # 66.1 MB of the seven keys read once); its traffic grows with the
 # ciphertexts, so the roofline scales the launch's algorithmic bytes by it.
-KS_ROT_TRAFFIC_PER_ALG_BYTE = 555.8 / 577.8
+KS_ROT_TRAFFIC_PER_ALG_BYTE = 555.7 / 577.8
 
 
 def roof_time(p: dict, hbm_peak: float, name: str | None = None) -> float:
