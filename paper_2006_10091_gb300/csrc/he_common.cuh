@@ -210,12 +210,6 @@ __device__ __forceinline__ void split3_total(uint64_t ll, uint64_t hh, uint64_t 
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m_lo), "l"(m_hi));
   asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(h_lo), "l"(h_hi));
 }
-__device__ __forceinline__ uint64_t reduce_split3(uint64_t ll, uint64_t hh, uint64_t ss, uint32_t sb,
-                                                  const PrimeDev& pr) {
-  uint64_t lo, hi;
-  split3_total(ll, hh, ss, sb, lo, hi);
-  return reduce128_any(hi, lo, pr);
-}
 
 // 128-bit word (w3:w2:w1:w0) mod q, by Horner on 64-bit halves:
 // x = hi*2^64 + lo; hi*2^64 mod q = (hi mod q) * (2^64 mod q).
