@@ -3,11 +3,26 @@
 //
 // Every kernel walks (ciphertext, limb, coefficient) with the coefficient
 // index fastest, so a warp stays on one limb (one prime) and reads 2 x 64-bit
-// words per thread through 128-bit accesses.
+// words per thread through 128-bit accesses.  The flat index splits into
+// (row, coefficient) by a shift (N is a power of two) and the row into
+// (ciphertext, part, limb) by divisions that run in 32 bits whenever the row
+// index fits, as it does for any batch of fewer than 2^31 limbs (rmod).
 #include "he_internal.h"
 #include "he_kernels.h"
 
 namespace he {
+
+// r mod d, and r <- r / d.
+__device__ __forceinline__ uint32_t rmod(size_t& r, uint32_t d) {
+  if (r <= 0xffffffffull) {
+    const uint32_t r32 = (uint32_t)r, m = r32 % d;
+    r = r32 / d;
+    return m;
+  }
+  const uint32_t m = (uint32_t)(r % d);
+  r /= d;
+  return m;
+}
 
 // ---- tensor product: (a0 b0, a0 b1 + a1 b0, a1 b1) ---------------------------
 __global__ void k_tensor(CtBatch A, CtBatch B, CtBatch D, uint64_t* d2, uint64_t d2_stride,
@@ -15,9 +30,10 @@ __global__ void k_tensor(CtBatch A, CtBatch B, CtBatch D, uint64_t* d2, uint64_t
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    const size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level), i = (uint32_t)(r / level);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    const size_t r = g >> (log_n - 1);
+    size_t rq = r;
+    const uint32_t t = rmod(rq, level), i = (uint32_t)rq;
     const PrimeDev pr = primes[t];
     const ulonglong2 a0 = *(const ulonglong2*)(cpoly(A, i, 0, t, n) + k);
     const ulonglong2 a1 = *(const ulonglong2*)(cpoly(A, i, 1, t, n) + k);
@@ -47,9 +63,10 @@ __global__ void k_modup(const uint64_t* xc, uint64_t xc_stride, uint64_t* ext, u
   const uint32_t nt = m.level + m.alpha;
   const size_t total = (size_t)count * m.beta * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % n);
-    const size_t r = g / n;
-    const uint32_t j = (uint32_t)(r % m.beta), i = (uint32_t)(r / m.beta);
+    const uint32_t k = (uint32_t)(g & (n - 1));
+    const size_t r = g >> log_n;
+    size_t rq = r;
+    const uint32_t j = rmod(rq, m.beta), i = (uint32_t)rq;
     const uint32_t lo = m.lo[j], cnt = m.cnt[j];
     const uint64_t* tab = consts + m.off[j];
     uint64_t u[HE_MAX_DIGIT];
@@ -84,9 +101,10 @@ __global__ void k_inner_product(const uint64_t* ext, uint64_t ext_stride, const 
   const uint32_t nt = level + alpha;
   const size_t total = (size_t)count * nt * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    const size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % nt), i = (uint32_t)(r / nt);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    const size_t r = g >> (log_n - 1);
+    size_t rq = r;
+    const uint32_t t = rmod(rq, nt), i = (uint32_t)rq;
     const uint32_t p = t < level ? t : L + t - level;
     const PrimeDev pr = primes[p];
     uint64_t s0x = 0, s0y = 0, s1x = 0, s1y = 0;
@@ -124,9 +142,10 @@ __global__ void k_inner_product_rot(const uint64_t* ext, uint64_t ext_stride, co
   const uint32_t nt = level + alpha;
   const size_t total = (size_t)count * nt * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t e = (uint32_t)(g % n);
-    const size_t r2 = g / n;
-    const uint32_t t = (uint32_t)(r2 % nt), i = (uint32_t)(r2 / nt);
+    const uint32_t e = (uint32_t)(g & (n - 1));
+    const size_t r2 = g >> log_n;
+    size_t r2q = r2;
+    const uint32_t t = rmod(r2q, nt), i = (uint32_t)r2q;
     const uint32_t p = t < level ? t : L + t - level;
     const PrimeDev pr = primes[p];
     uint64_t s0 = 0, s1 = 0;
@@ -155,11 +174,11 @@ __global__ void k_reduce_acc(uint64_t* acc, uint64_t acc_stride, uint32_t nt, ui
   const uint32_t n = 1u << log_n;
   const size_t total = (size_t)count * 2 * nt * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t e = (uint32_t)(g % n);
-    size_t r = g / n;
-    const uint32_t t = (uint32_t)(r % nt);
-    r /= nt;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t e = (uint32_t)(g & (n - 1));
+    size_t r = g >> log_n;
+    const uint32_t t = rmod(r, nt);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     uint64_t* a = acc + (size_t)i * acc_stride + ((size_t)p * nt + t) * n + e;
     *a = reduce64(*a, primes[t < level ? t : L + t - level]);
   }
@@ -171,11 +190,11 @@ __global__ void k_add_automorphs(CtBatch A, CtBatch O, RotSet rs, uint32_t level
   const uint32_t n = 1u << log_n;
   const size_t total = (size_t)count * 2 * level * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t e = (uint32_t)(g % n);
-    size_t r = g / n;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t e = (uint32_t)(g & (n - 1));
+    size_t r = g >> log_n;
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q;
     const uint64_t* a = cpoly(A, i, p, t, n);
     uint64_t v = a[e];
@@ -198,9 +217,10 @@ __global__ void k_moddown_conv(const uint64_t* acc, uint64_t acc_stride, uint32_
   const size_t total = (size_t)count * 2 * n;
   const uint64_t* mat = md + 2 * alpha;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % n);
-    const size_t r = g / n;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (n - 1));
+    const size_t r = g >> log_n;
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     uint64_t u[HE_MAX_DIGIT];
     const uint64_t* hP = md + 2 * alpha + (size_t)alpha * L + 2 * L;
     const uint64_t* hQ = hP + alpha;
@@ -241,11 +261,11 @@ __global__ void k_ks_combine(const uint64_t* acc, uint64_t acc_stride, uint32_t 
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q;
     const uint64_t w = pinv[2 * t], wsh = pinv[2 * t + 1];
     const ulonglong2 a = *(const ulonglong2*)(acc + (size_t)i * acc_stride + ((size_t)p * nt + t) * n + k);
@@ -274,9 +294,10 @@ __global__ void k_add_pd(uint64_t* acc, uint64_t acc_stride, uint32_t nt, CtBatc
   const size_t total = (size_t)count * 2 * n;
   const uint64_t q = primes[l].q;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % n);
-    const size_t r = g / n;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (n - 1));
+    const size_t r = g >> log_n;
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     uint64_t* a = acc + (size_t)i * acc_stride + ((size_t)p * nt + l) * n + k;
     *a = add_mod(*a, mul_shoup(cpoly(d, i, p, l, n)[k], Pl, Pl_sh, q), q);
   }
@@ -293,8 +314,8 @@ __global__ void k_rescale_corr(const uint64_t* last, uint64_t* corr, uint32_t le
   const size_t total = (size_t)count * 2 * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const uint64_t x = last[g];
-    const size_t ip = g / n;
-    const uint32_t k = (uint32_t)(g % n);
+    const size_t ip = g >> log_n;
+    const uint32_t k = (uint32_t)(g & (n - 1));
     const bool neg = x > h;
     const uint64_t mag = neg ? ql - x : x;
     uint64_t* out = corr + ip * (size_t)lt * n + k;
@@ -313,11 +334,11 @@ __global__ void k_rescale_final(CtBatch in, const uint64_t* corr, CtBatch out, u
   const uint32_t lt = level - 1;
   const size_t total = (size_t)count * 2 * lt * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % lt);
-    r /= lt;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, lt);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q, w = rs[2 * t], wsh = rs[2 * t + 1];
     const ulonglong2 a = *(const ulonglong2*)(cpoly(in, i, p, t, n) + k);
     const ulonglong2 c = *(const ulonglong2*)(corr + (((size_t)i * 2 + p) * lt + t) * n + k);
@@ -335,11 +356,11 @@ __global__ void k_automorph(CtBatch in, CtBatch out, uint32_t nparts, uint32_t l
   const uint32_t n = 1u << log_n;
   const size_t total = (size_t)count * nparts * level * n;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t j = (uint32_t)(g % n);
-    size_t r = g / n;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % nparts), i = (uint32_t)(r / nparts);
+    const uint32_t j = (uint32_t)(g & (n - 1));
+    size_t r = g >> log_n;
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, nparts), i = (uint32_t)rq;
     cpoly(out, i, p, t, n)[j] = cpoly(in, i, p, t, n)[automorph_src(j, gal, log_n)];
   }
 }
@@ -351,11 +372,11 @@ __global__ void k_addsub(CtBatch A, CtBatch B, CtBatch O, int op, uint32_t level
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q;
     const ulonglong2 a = *(const ulonglong2*)(cpoly(A, i, p, t, n) + k);
     const ulonglong2 b = *(const ulonglong2*)(cpoly(B, i, p, t, n) + k);
@@ -372,11 +393,11 @@ __global__ void k_mul_const(CtBatch A, CtBatch O, LimbConsts kc, uint32_t level,
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q;
     const ulonglong2 a = *(const ulonglong2*)(cpoly(A, i, p, t, n) + k);
     ulonglong2 o;
@@ -392,11 +413,11 @@ __global__ void k_add_const(CtBatch A, CtBatch O, LimbConsts kc, uint32_t level,
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const uint64_t q = primes[t].q;
     ulonglong2 a = *(const ulonglong2*)(cpoly(A, i, p, t, n) + k);
     if (p == 0) { a.x = add_mod(a.x, kc.w[t], q); a.y = add_mod(a.y, kc.w[t], q); }
@@ -410,11 +431,11 @@ __global__ void k_mul_plain(CtBatch A, const uint64_t* pt, CtBatch O, uint32_t l
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     const PrimeDev pr = primes[t];
     const ulonglong2 a = *(const ulonglong2*)(cpoly(A, i, p, t, n) + k);
     const ulonglong2 b = *(const ulonglong2*)(pt + (size_t)t * n + k);
@@ -430,11 +451,11 @@ __global__ void k_copy_limbs(CtBatch A, CtBatch O, uint32_t level, uint32_t coun
   const uint32_t n = 1u << log_n, half = n >> 1;
   const size_t total = (size_t)count * 2 * level * half;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % half) * 2;
-    size_t r = g / half;
-    const uint32_t t = (uint32_t)(r % level);
-    r /= level;
-    const uint32_t p = (uint32_t)(r % 2), i = (uint32_t)(r / 2);
+    const uint32_t k = (uint32_t)(g & (half - 1)) * 2;
+    size_t r = g >> (log_n - 1);
+    const uint32_t t = rmod(r, level);
+    size_t rq = r;
+    const uint32_t p = rmod(rq, 2), i = (uint32_t)rq;
     *(ulonglong2*)(cpoly(O, i, p, t, n) + k) = *(const ulonglong2*)(cpoly(A, i, p, t, n) + k);
   }
 }

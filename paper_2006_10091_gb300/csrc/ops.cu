@@ -491,36 +491,58 @@ int accumulate_batch(he_ctx* c, CtBatch in, uint32_t count, CtBatch acc, uint32_
 
 // acc += sum over i < count of tensor(A_i, B_i): the three parts
 // (a0 b0, a0 b1 + a1 b0, a1 b1) of each product summed into the three-part
-// accumulator acc [3][level][N] (limbs below level of A and B).
-__global__ void k_tensor_acc(CtBatch A, CtBatch B, uint32_t count, uint64_t* acc, uint32_t level, int log_n,
-                             const PrimeDev* primes) {
+// accumulator acc [3][level][N] (limbs below level of A and B).  A CTA of
+// kTaSlices warps takes 32 consecutive coefficients (one per lane, coalesced
+// loads); warp w sums the products of ciphertexts w, w + kTaSlices, ..., and
+// the slices' sums are added in shared memory (modular sums are exact, so
+// the order does not change a residue).
+constexpr int kTaSlices = 8;
+
+__global__ void __launch_bounds__(32 * kTaSlices) k_tensor_acc(CtBatch A, CtBatch B, uint32_t count, uint64_t* acc,
+                                                             uint32_t level, int log_n, const PrimeDev* primes) {
+  __shared__ uint64_t part[3][kTaSlices][32];
   const uint32_t n = 1u << log_n;
+  const uint32_t lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
   const size_t total = (size_t)level * n;
-  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t k = (uint32_t)(g % n), t = (uint32_t)(g / n);
-    const PrimeDev pr = primes[t];
-    uint64_t* a0p = acc + (size_t)t * n + k;
-    uint64_t* a1p = a0p + (size_t)level * n;
-    uint64_t* a2p = a1p + (size_t)level * n;
-    uint64_t s0 = *a0p, s1 = *a1p, s2 = *a2p;
-    for (uint32_t i = 0; i < count; ++i) {
-      const uint64_t x0 = cpoly(A, i, 0, t, n)[k], x1 = cpoly(A, i, 1, t, n)[k];
-      const uint64_t y0 = cpoly(B, i, 0, t, n)[k], y1 = cpoly(B, i, 1, t, n)[k];
-      s0 = add_mod(s0, mul_mod(x0, y0, pr), pr.q);
-      s1 = add_mod(s1, add_mod(mul_mod(x0, y1, pr), mul_mod(x1, y0, pr), pr.q), pr.q);
-      s2 = add_mod(s2, mul_mod(x1, y1, pr), pr.q);
+  for (size_t base = (size_t)blockIdx.x * 32; base < total; base += (size_t)gridDim.x * 32) {
+    const size_t g = base + lane;
+    const bool in = g < total;
+    uint64_t s0 = 0, s1 = 0, s2 = 0;
+    uint32_t k = 0, t = 0;
+    PrimeDev pr{};
+    if (in) {
+      k = (uint32_t)(g & (n - 1));
+      t = (uint32_t)(g >> log_n);
+      pr = primes[t];
+      for (uint32_t i = slice; i < count; i += kTaSlices) {
+        const uint64_t x0 = __ldg(cpoly(A, i, 0, t, n) + k), x1 = __ldg(cpoly(A, i, 1, t, n) + k);
+        const uint64_t y0 = __ldg(cpoly(B, i, 0, t, n) + k), y1 = __ldg(cpoly(B, i, 1, t, n) + k);
+        s0 = add_mod(s0, mul_mod(x0, y0, pr), pr.q);
+        s1 = add_mod(s1, add_mod(mul_mod(x0, y1, pr), mul_mod(x1, y0, pr), pr.q), pr.q);
+        s2 = add_mod(s2, mul_mod(x1, y1, pr), pr.q);
+      }
     }
-    *a0p = s0;
-    *a1p = s1;
-    *a2p = s2;
+    part[0][slice][lane] = s0;
+    part[1][slice][lane] = s1;
+    part[2][slice][lane] = s2;
+    __syncthreads();
+    if (in && slice < 3) {  // warps 0, 1, 2 finish parts 0, 1, 2
+      uint64_t* ap = acc + (size_t)slice * level * n + (size_t)t * n + k;
+      uint64_t s = *ap;
+#pragma unroll
+      for (int w = 0; w < kTaSlices; ++w) s = add_mod(s, part[slice][w][lane], pr.q);
+      *ap = s;
+    }
+    __syncthreads();
   }
 }
 
 int tensor_acc_batch(he_ctx* c, CtBatch A, CtBatch B, uint32_t count, uint64_t* acc, uint32_t level) {
   {
     ProfScope prof(c, "tensor", 4.0 * count * level * c->n, (double)(4 * count + 6) * level * c->n * 8);
-    k_tensor_acc<<<grid_for((size_t)level * c->n), 256, 0, c->stream>>>(A, B, count, acc, level, c->log_n,
-                                                                       c->d_primes);
+    const size_t groups = ((size_t)level * c->n + 31) / 32;  // CTAs of 32 coefficients
+    k_tensor_acc<<<(unsigned)std::min<size_t>(groups, 152 * 32), 32 * kTaSlices, 0, c->stream>>>(
+        A, B, count, acc, level, c->log_n, c->d_primes);
   }
   HE_CUDA(cudaGetLastError());
   return HE_OK;
