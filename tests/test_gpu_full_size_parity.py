@@ -55,6 +55,11 @@ LARGE = {
     # name: (log_n, L, limb bits, alpha, special bits, scale, rotate-and-sum steps)
     "n16_l24": (16, 24, 50, 4, 60, 2.0 ** 50, list(range(1, 16))),
     "n15_l20": (15, 20, 50, 4, 60, 2.0 ** 50, list(range(1, 8))),
+    # the serving mix's other rings: rotations that move rows between tiles
+    # at N = 2^13, a closed stage (every row tile onto itself: split sums,
+    # part 0 in the product kernel) at N = 2^14 with five four-limb digits
+    "n13_l20": (13, 20, 50, 4, 60, 2.0 ** 50, list(range(1, 8))),
+    "n14_l20_closed": (14, 20, 50, 4, 60, 2.0 ** 50, [8, 16, 24, 32, 40, 48, 56]),
 }
 
 
