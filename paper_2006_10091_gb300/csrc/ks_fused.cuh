@@ -52,10 +52,13 @@ __host__ __device__ __forceinline__ uint32_t ks_prime(uint32_t t, uint32_t level
 // The basis conversion of one tile into shared memory: for the T threads'
 // elements idx of the tile, sum over u < CNT of wv[u][idx] times the constant
 // (w[u * stride], its Shoup companion), reduced to [0, q); the CNT constants
-// sit in registers for the whole tile.  Returns the sums still in [0, q).
+// sit in registers for the whole tile.  With vv (ModDown's exact lift), the
+// element's multiple of P and h are then subtracted in the same pass:
+// - vP[vv[idx]] - h mod q.
 template <int TILE, int T, int CNT>
 __device__ __forceinline__ void conv_sum_tile(uint64_t* sm, const uint64_t* wv, const uint64_t* w, const uint64_t* wsh,
-                                              uint32_t stride, uint64_t q) {
+                                              uint32_t stride, uint64_t q, const uint32_t* vv = nullptr,
+                                              const uint64_t* vP = nullptr, uint64_t h = 0) {
   uint64_t cw[CNT], cs[CNT];
 #pragma unroll
   for (int u = 0; u < CNT; ++u) {
@@ -71,7 +74,9 @@ __device__ __forceinline__ void conv_sum_tile(uint64_t* sm, const uint64_t* wv, 
       y += mul_shoup_lazy(wv[(size_t)u * TILE + idx], cw[u], cs[u], q);
       y = y >= q2 ? y - q2 : y;
     }
-    sm[idx + (idx >> 3)] = y >= q ? y - q : y;
+    y = y >= q ? y - q : y;
+    if (vv) y = sub_mod(sub_mod(y, vP[vv[idx]], q), h, q);
+    sm[idx + (idx >> 3)] = y;
   }
 }
 
@@ -654,15 +659,10 @@ __global__ void __launch_bounds__((1 << (LOG_M + LOG_K)) / 8) md_conv_col(MdArgs
     // Shoup products by (P/p_u) mod q_t (the dropped-prime count a
     // compile-time constant for the usual counts), then - v P - h
     if (a.alpha >= 2 && a.alpha <= 5) {
-      if (a.alpha == 2) conv_sum_tile<S::TILE, S::T, 2>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
-      else if (a.alpha == 3) conv_sum_tile<S::TILE, S::T, 3>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
-      else if (a.alpha == 4) conv_sum_tile<S::TILE, S::T, 4>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
-      else conv_sum_tile<S::TILE, S::T, 5>(sm, wv, mat + t, mat_sh + t, a.L, pr.q);
-#pragma unroll 2
-      for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
-        const uint64_t acc = sub_mod(sm[idx + (idx >> 3)], vP[vv[idx]], pr.q);
-        sm[idx + (idx >> 3)] = sub_mod(acc, hQ, pr.q);
-      }
+      if (a.alpha == 2) conv_sum_tile<S::TILE, S::T, 2>(sm, wv, mat + t, mat_sh + t, a.L, pr.q, vv, vP, hQ);
+      else if (a.alpha == 3) conv_sum_tile<S::TILE, S::T, 3>(sm, wv, mat + t, mat_sh + t, a.L, pr.q, vv, vP, hQ);
+      else if (a.alpha == 4) conv_sum_tile<S::TILE, S::T, 4>(sm, wv, mat + t, mat_sh + t, a.L, pr.q, vv, vP, hQ);
+      else conv_sum_tile<S::TILE, S::T, 5>(sm, wv, mat + t, mat_sh + t, a.L, pr.q, vv, vP, hQ);
     } else {
 #pragma unroll 2
       for (uint32_t idx = threadIdx.x; idx < (uint32_t)S::TILE; idx += S::T) {
