@@ -387,6 +387,17 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     got_e2e = host_out.numpy().view(np.uint64)
+    # this box's pinned host-to-device bandwidth (one copy of the step's
+    # inputs, alone): the e2e figure depends on it, and it varies by box
+    dev_in = torch.empty(host_in.shape, dtype=host_in.dtype, device=dev)
+    dev_in.copy_(host_in, non_blocking=True)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    dev_in.copy_(host_in, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = host_in.numel() * 8 / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    del dev_in
     he.he_lr_gradient_step(ctx, Z, W, cfg, out)
     e2e_same = bool(np.array_equal(got_e2e, he.he_ct_export(ctx, out)))
     h2d = (nZ + 1) * 2 * L * ctx.n * 8
@@ -414,6 +425,7 @@ def run_ours(args, rank: int, world: int):
         "accuracy": {"max_rel_err_vs_fp64": rel_err, "gate": 2.0 ** -20, "ok": rel_err < 2.0 ** -20},
         "e2e": {"value": weak_scaling_value(1.0, world, e2e_s), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "he_lr_gradient_step_host (pinned host buffers)",
+                "h2d_gbs_measured": h2d_gbs,
                 "same_residues_as_device_step": e2e_same},
         "gpu_launches": int(sum(v["launches"] for v in prof.values()) // prof_steps),
         "autotune": tuned,
